@@ -1,0 +1,146 @@
+/*
+ * psht.h -- C ABI of the GB300 (sm_103a) partial-sky spin-s spherical harmonic transforms.
+ *
+ * The library computes the two operations that open Carron & Reinecke, "Fast partial-sky
+ * spherical harmonic transforms" (Sec. I):
+ *
+ *   synthesis general       f_p = - sum_{l<=lmax} sum_{|m|<=l} (g_lm + i c_lm) sY_lm(theta_p, phi_p)
+ *   adjoint synthesis general
+ *       g~_lm = -1/2    sum_p [ f_p sY*_lm(theta_p, phi_p) + (-1)^s f*_p _{-s}Y*_lm(theta_p, phi_p) ]
+ *       c~_lm = -1/(2i) sum_p [ f_p sY*_lm(theta_p, phi_p) - (-1)^s f*_p _{-s}Y*_lm(theta_p, phi_p) ]
+ *
+ * with sY_lm(theta, phi) = sqrt((2l+1)/4pi) d^l_{m,-s}(theta) e^{i m phi} (appendix, eq. Ylm), by the
+ * partial-sky Fourier-sphere route (Sec. II, steps 1-4): a Wigner-d recursion onto the few apodised
+ * rings that cover the patch, FFTs onto an oversampled reduced Fourier grid, and ES-kernel
+ * interpolation (gather) or spreading (scatter-add) at the points.
+ *
+ * Conventions shared by every entry point
+ *   a_lm    packed m-major, idx(l, m) = m(2 lmax + 1 - m)/2 + l for 0 <= m <= l <= lmax,
+ *           (lmax+1)(lmax+2)/2 complex values, interleaved (re, im); complex128 in the FP64 form,
+ *           complex64 in the FP32 form.  The negative orders follow the reality rule
+ *           a_{l,-m} = (-1)^m a*_lm for g and c separately (Sec. I).  On input Im(a_l0) and l < s
+ *           are ignored; on output they are written as 0.
+ *   f       npts complex values, interleaved, complex128 (FP64 form) or complex64 (FP32 form).
+ *   points  theta, phi: npts float64 values in every form; theta in [0, pi], phi any finite value.
+ *   streams every device-side call enqueues all its work on `stream` (a cudaStream_t passed as
+ *           void*, NULL = legacy default stream) and returns without synchronising, except where
+ *           stated.  Pointers marked DEVICE must be device (or managed) memory owned by the caller;
+ *           the library never frees caller memory.
+ *   errors  0 on success, a negative PSHT_E* code on failure; psht_last_error() then returns a
+ *           message for the calling thread.  Failed calls leave caller buffers unspecified but
+ *           never write outside them.  Arguments are validated on the host before any launch.
+ */
+#ifndef PSHT_H
+#define PSHT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PSHT_OK 0
+#define PSHT_EINVAL (-22)   /* bad argument (sizes, spin, eps, NaN or out-of-range theta, ...) */
+#define PSHT_ENOMEM (-12)   /* device allocation failed or above the plan's memory budget      */
+#define PSHT_ECUDA (-5)     /* a CUDA runtime call failed                                       */
+#define PSHT_ENOTSUP (-95)  /* configuration outside what this build supports (message says why) */
+
+/* precision / option flags for psht_plan_create */
+#define PSHT_AUTO 0u        /* FP32 form for eps >= 1e-5, FP64 form below                       */
+#define PSHT_FP64 1u        /* FP64 everywhere                                                   */
+#define PSHT_FP32 2u        /* FP32 recursion (FP64 seeds and rescaling), FP32 FFT and kernels   */
+
+typedef struct psht_plan psht_plan; /* opaque; owned by the library, freed by psht_plan_destroy */
+
+/* Plan parameters, filled by psht_plan_info.  Names follow the paper (Sec. II). */
+typedef struct psht_info {
+  int spin, lmax, precision;     /* precision: 64 or 32                                        */
+  int pole;                      /* +1: north pole used, -1: south pole (Sec. II step 1)       */
+  int full_sky;                  /* 1 when theta_max >= pi or Lmax >= lmax (no apodisation)    */
+  double eps, theta_star, eps_apo, theta_max, alpha, dTheta;
+  int Lmax, L, nring;            /* rings Theta_j = j pi/L, j < nring                         */
+  int M;                         /* phi band limit after polar optimisation                    */
+  int W;                         /* ES kernel width (cells)                                    */
+  double beta_es;                /* ES kernel shape                                            */
+  int nTheta, nphi;              /* oversampled grid; nTheta = 4L                              */
+  int r_lo, nrows;               /* grid rows kept: r_lo .. r_lo + nrows - 1                   */
+  int64_t npts;
+  int64_t ring_mode_pairs;       /* (ring, m) pairs the recursion computes                    */
+  int64_t recursion_triples;     /* (ring, m, l) steps of the recursion                       */
+  size_t device_bytes;           /* device memory held by the plan                             */
+} psht_info;
+
+/*
+ * Create a plan for synthesis/adjoint at fixed points (Sec. II steps 1-4, parameter choice of
+ * Sec. II.C-D).  theta, phi: DEVICE float64[npts], read during this call only.  Synchronises
+ * `stream` once (theta* reduction and point binning).  Returns PSHT_EINVAL for spin < 0,
+ * lmax < spin, eps outside [1e-14, 1e-1], npts < 0, NaN/out-of-range theta or non-finite phi;
+ * PSHT_ENOMEM if the plan does not fit in device memory.  *out receives the plan.
+ */
+int psht_plan_create(int spin, int lmax, const double* theta, const double* phi, int64_t npts, double eps,
+                     uint32_t flags, void* stream, psht_plan** out);
+
+/* Copy the plan's parameters into *info (host memory).  Never fails for a valid plan. */
+int psht_plan_info(const psht_plan* plan, psht_info* info);
+
+/*
+ * Synthesis general (Sec. I eq. syn) at the plan's points.  g, c: DEVICE packed a_lm (c may be
+ * NULL: c = 0); f: DEVICE output, npts complex values in the caller's point order.
+ * Overwrites f entirely.  Concurrent calls on one plan must use the same stream (the plan's
+ * work buffers are reused).
+ */
+int psht_plan_synthesis(psht_plan* plan, const void* g, const void* c, void* f, void* stream);
+
+/*
+ * Adjoint synthesis general (Sec. I) at the plan's points: the exact transpose of
+ * psht_plan_synthesis for <f, f'> = Re sum_p conj(f_p) f'_p and <a, a'> = sum_l sum_{|m|<=l}
+ * Re(conj(a_lm) a'_lm) summed over g and c.  f: DEVICE input; g: DEVICE output (required);
+ * c: DEVICE output or NULL (then c~ is not written).  Overwrites g and c entirely.
+ */
+int psht_plan_adjoint(psht_plan* plan, const void* f, void* g, void* c, void* stream);
+
+/*
+ * Host-buffer forms of the two calls above: g, c, f are HOST pointers (pinned memory gives the
+ * fastest copies).  Copies inputs to the device, runs the transform on `stream` and copies the
+ * result back; returns after `stream` has synchronised, so the host buffers hold the result.
+ */
+int psht_plan_synthesis_host(psht_plan* plan, const void* g, const void* c, void* f, void* stream);
+int psht_plan_adjoint_host(psht_plan* plan, const void* f, void* g, void* c, void* stream);
+
+/* Release the plan and all device memory it holds.  Synchronises the device. NULL is a no-op. */
+int psht_plan_destroy(psht_plan* plan);
+
+/*
+ * Diagnostic stage access, used by the stage-parity tests.
+ *   psht_plan_rings: the planner's ring table, HOST outputs theta_j[nring], w_j[nring],
+ *     Mj[nring] (int32), any of them may be NULL.
+ *   psht_plan_ring_coeffs: ring Fourier coefficients F_j[m] = -sum_l (g+ic)_lm N_l d^l_{m,-s}(theta_j)
+ *     (Sec. II step 4 applied to the rings), DEVICE output F[nring][2M+1] (m + M fastest),
+ *     complex in the plan's precision; zero where |m| > M_j.
+ */
+int psht_plan_rings(const psht_plan* plan, double* theta_j, double* w_j, int32_t* Mj);
+int psht_plan_ring_coeffs(psht_plan* plan, const void* g, const void* c, void* F, void* stream);
+
+/*
+ * One-shot forms with the paper's argument list (g, c, spin, lmax, theta, phi, eps): plan,
+ * execute and destroy.  All pointers DEVICE.  Precision PSHT_AUTO.  Synchronise `stream`.
+ */
+int psht_synthesis(const void* g, const void* c, int spin, int lmax, const double* theta, const double* phi,
+                   int64_t npts, double eps, void* f, void* stream);
+int psht_adjoint_synthesis(const void* f, int spin, int lmax, const double* theta, const double* phi,
+                           int64_t npts, double eps, void* g, void* c, void* stream);
+
+/* Device bytes a plan for these arguments would hold (theta_star = max distance to the pole). */
+size_t psht_estimate_bytes(int spin, int lmax, double theta_star, int64_t npts, double eps, uint32_t flags);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* psht_last_error(void);
+
+/* Library version string. */
+const char* psht_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSHT_H */

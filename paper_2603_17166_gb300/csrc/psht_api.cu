@@ -1,0 +1,634 @@
+// Planner (host) and the C-ABI entry points of include/psht.h.
+//
+// The planner follows Sec. II of Carron & Reinecke (steps 1-4) and the parameter choice of
+// Sec. II.C-D, plus the numerical choices the paper leaves open (ring count rounding, polar
+// optimisation cutoff, NUFFT grid), which the FP64 CPU oracle states identically.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "psht_internal.h"
+
+namespace psht {
+
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+
+namespace {
+
+// ---------------------------------------------------------------------------------------------
+// small numerical helpers
+int fft_friendly(int n) {
+  n = std::max(n, 1);
+  for (;; ++n) {
+    int k = n;
+    for (int p : {2, 3, 5, 7})
+      while (k % p == 0) k /= p;
+    if (k == 1) return n;
+  }
+}
+
+FftDev radix_schedule(int n) {
+  FftDev f{};
+  f.n = n;
+  int k = n, st = 0;
+  auto push = [&](int r) { f.rad[st++] = r; k /= r; };
+  while (k % 8 == 0) push(8);
+  while (k % 4 == 0) push(4);
+  while (k % 2 == 0) push(2);
+  for (int p : {3, 5, 7})
+    while (k % p == 0) push(p);
+  PSHT_REQUIRE(k == 1 && st <= 32, PSHT_ENOTSUP, "FFT length has a prime factor above 7");
+  f.nst = st;
+  return f;
+}
+
+// DIF output position of frequency k: sum_i q_i s_i, q_i = (k / (R_1..R_{i-1})) mod R_i, s_i = N/(R_1..R_i)
+std::vector<int> fft_perm(const FftDev& f) {
+  std::vector<int> pos(f.n);
+  for (int k0 = 0; k0 < f.n; ++k0) {
+    int k = k0, p = 0, s = f.n;
+    for (int i = 0; i < f.nst; ++i) {
+      s /= f.rad[i];
+      p += (k % f.rad[i]) * s;
+      k /= f.rad[i];
+    }
+    pos[k0] = p;
+  }
+  return pos;
+}
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_n
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double z = cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+    }
+    x[i] = -z;
+    x[n - 1 - i] = z;
+    w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+struct Quad {
+  std::vector<double> x, w;
+  Quad() { gauss_legendre(256, x, w); }
+  template <class F>
+  double integrate(F f, double a, double b) const {
+    const double xm = 0.5 * (a + b), xr = 0.5 * (b - a);
+    double s = 0;
+    for (size_t i = 0; i < x.size(); ++i) s += w[i] * f(xm + xr * x[i]);
+    return xr * s;
+  }
+};
+
+// window w(Theta) = B(pi - dTheta/2 - |Theta|), B the CDF of the unit-area ES bell of support dTheta
+// (Sec. II.D); u = (dTheta/2) sin(tau) makes the integrand smooth.
+double window_value(double Theta, double dTheta, double cexp, const Quad& q) {
+  const double x = M_PI - 0.5 * dTheta - fabs(Theta);
+  const double z = 2.0 * x / dTheta;
+  if (z <= -1.0) return 0.0;
+  if (z >= 1.0) return 1.0;
+  auto dens = [&](double tau) { return exp(cexp * (cos(tau) - 1.0)) * cos(tau); };
+  return q.integrate(dens, -0.5 * M_PI, asin(z)) / q.integrate(dens, -0.5 * M_PI, 0.5 * M_PI);
+}
+
+// continuous FT of psi(x/a), a = W pi/nfine, at integer frequency k
+double es_ft(double k, int W, double beta, int nfine, const Quad& q) {
+  const double a = W * M_PI / nfine;
+  auto f = [&](double tau) { return exp(beta * (cos(tau) - 1.0)) * cos(k * a * sin(tau)) * cos(tau); };
+  return a * q.integrate(f, -0.5 * M_PI, 0.5 * M_PI);
+}
+
+int es_width(double eps) { return std::min(16, (int)ceil(-log10(eps) - 1e-9) + 1); }
+
+// polar-optimisation cutoff (Sec. II.A): turning point x = (lmax + 1/2) sin(beta) plus the
+// Airy-type tail kept down to 1e-3 eps
+int mcut(int lmax, int s, double eps, double beta) {
+  const double z = pow(1.5 * log(1.0 / (1e-3 * eps)), 2.0 / 3.0);
+  const double x = (lmax + 0.5) * fabs(sin(beta));
+  const double v = ceil(x + s + 1.25 * z * pow(x / 2.0, 1.0 / 3.0) + 8.0);
+  return (int)std::min<double>(lmax, v);
+}
+
+template <typename T>
+void* upload(Plan& p, const std::vector<T>& h, cudaStream_t st) {
+  void* d = nullptr;
+  const size_t b = std::max<size_t>(1, h.size()) * sizeof(T);
+  PSHT_CUDA_TRY(cudaMalloc(&d, b));
+  p.allocs.push_back(d);
+  p.bytes += b;
+  if (!h.empty()) PSHT_CUDA_TRY(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+  return d;
+}
+
+void* dalloc(Plan& p, size_t b) {
+  void* d = nullptr;
+  b = std::max<size_t>(b, 16);
+  cudaError_t e = cudaMalloc(&d, b);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    char msg[160];
+    snprintf(msg, sizeof(msg), "device allocation of %zu bytes failed (plan holds %zu)", b, p.bytes);
+    throw Error{PSHT_ENOMEM, msg};
+  }
+  p.allocs.push_back(d);
+  p.bytes += b;
+  return d;
+}
+
+template <typename T>
+std::vector<T> cast_vec(const std::vector<double>& v) {
+  return std::vector<T>(v.begin(), v.end());
+}
+
+// ---------------------------------------------------------------------------------------------
+// P1-P2 and the grid: everything that depends on (spin, lmax, eps, precision, theta*, pole)
+void layout(Plan& p, double theta_star) {
+  const double lneps = fabs(log(p.eps));
+  p.theta_star = std::max(theta_star, 1e-9);
+  bool full = p.lmax < 1;
+  if (!full) {
+    p.eps_apo = sqrt(2.0 * lneps / (p.theta_star * p.lmax));
+    p.theta_max = p.theta_star * (1.0 + p.eps_apo);
+    p.Lmax = (int)ceil(p.lmax * p.theta_star / M_PI * (1.0 + p.eps_apo) * (1.0 + p.eps_apo));
+    if (p.theta_max >= M_PI || p.Lmax >= p.lmax) full = true;
+  }
+  p.full = full ? 1 : 0;
+  if (full) {
+    p.eps_apo = 0.0;
+    p.theta_max = M_PI;
+    p.Lmax = p.lmax;
+    p.dTheta = 0.0;
+  } else {
+    p.dTheta = M_PI * p.eps_apo / (1.0 + p.eps_apo);
+  }
+  p.alpha = lneps / M_PI;
+  p.L = fft_friendly(p.Lmax + 1);
+  p.nring = full ? p.L + 1 : p.L;
+  p.theta_j.resize(p.nring);
+  p.beta_j.resize(p.nring);
+  p.w_j.resize(p.nring);
+  p.Mj.resize(p.nring);
+  static const Quad quad;
+  for (int j = 0; j < p.nring; ++j) {
+    const double Th = j * (M_PI / p.L);
+    p.beta_j[j] = Th * (p.theta_max / M_PI);
+    p.theta_j[j] = p.pole > 0 ? p.beta_j[j] : M_PI - p.beta_j[j];
+    p.w_j[j] = full ? 1.0 : window_value(Th, p.dTheta, lneps, quad);
+    p.Mj[j] = mcut(p.lmax, p.spin, p.eps, p.beta_j[j]);
+  }
+  p.M = *std::max_element(p.Mj.begin(), p.Mj.end());
+  p.W = es_width(p.eps);
+  p.beta_es = 2.30 * p.W;
+  p.nTheta = 4 * p.L;
+  p.nphi = 2 * fft_friendly(2 * p.M + 1);
+  const double t_max = p.theta_star * p.nTheta / (2.0 * p.theta_max);
+  p.r_lo = (int)ceil(-0.5 * p.W);
+  const int r_hi = (int)ceil(t_max - 0.5 * p.W) + p.W;
+  p.nrows = r_hi - p.r_lo + 1;
+  p.ncols = 2 * p.M + 1;
+  p.Lpad = (p.nring + 31) / 32 * 32;
+  p.padq = 8;
+  p.gstride = (p.nphi + 2 * p.padq + 7) / 8 * 8;
+  p.TR = 16;
+  p.TQ = 32;
+  p.ntr = (p.nrows - 1) / p.TR + 1;
+  p.ntq = (p.nphi + p.padq) / p.TQ + 1;
+  p.nalm = (int64_t)(p.lmax + 1) * (p.lmax + 2) / 2;
+  // launch shapes of the recursion
+  p.syn_rpt = (p.prec == 64) ? 1 : 4;
+  p.syn_threads = 128;
+  int rpt = (p.prec == 64) ? 1 : 2;
+  while (rpt * 512 < p.nring && rpt < 8) rpt *= 2;
+  p.adj_rpt = rpt;
+  p.adj_threads = std::min(512, ((p.nring + rpt - 1) / rpt + 31) / 32 * 32);
+  PSHT_REQUIRE(p.nring <= 8 * 512, PSHT_ENOTSUP, "more than 4096 rings (lmax theta* too large for this build)");
+  const int maxlen = max_fft_len(p.prec);
+  PSHT_REQUIRE(p.nTheta <= maxlen, PSHT_ENOTSUP,
+               "Theta FFT length " + std::to_string(p.nTheta) + " above the shared-memory limit " + std::to_string(maxlen));
+  PSHT_REQUIRE(p.nphi <= maxlen, PSHT_ENOTSUP,
+               "phi FFT length " + std::to_string(p.nphi) + " above the shared-memory limit " + std::to_string(maxlen));
+}
+
+size_t planned_bytes(const Plan& p) {
+  const size_t cb = p.prec == 64 ? 16 : 8, rb = p.prec == 64 ? 8 : 4;
+  size_t b = 0;
+  b += 3 * (size_t)p.nalm * rb;                                // recursion table
+  b += (size_t)p.ncols * p.Lpad * cb;                          // ring coefficients
+  b += (size_t)p.nrows * p.ncols * cb;                         // Theta-stage rows
+  b += (size_t)p.nrows * p.gstride * cb;                       // grid
+  b += (size_t)p.npts * 8;                                     // index + cell
+  b += p.prec == 64 ? (size_t)p.npts * 2 * p.W * 8 : (size_t)p.npts * 8;  // weights / fractions
+  b += (size_t)(p.nTheta + 2 * p.L + p.nphi) * (cb + 4);       // twiddles + permutations
+  return b;
+}
+
+void destroy(Plan* p) {
+  if (!p) return;
+  cudaDeviceSynchronize();
+  for (void* a : p->allocs) cudaFree(a);
+  delete p;
+}
+
+Plan* create(int spin, int lmax, const double* theta, const double* phi, int64_t npts, double eps, uint32_t flags,
+             cudaStream_t st) {
+  PSHT_REQUIRE(spin >= 0, PSHT_EINVAL, "spin must be >= 0");
+  PSHT_REQUIRE(lmax >= spin, PSHT_EINVAL, "lmax must be >= spin");
+  PSHT_REQUIRE(lmax <= 65535, PSHT_EINVAL, "lmax above 65535");
+  PSHT_REQUIRE(eps >= 1e-14 && eps <= 1e-1, PSHT_EINVAL, "eps must lie in [1e-14, 1e-1]");
+  PSHT_REQUIRE(npts >= 0 && npts < ((int64_t)1 << 31), PSHT_EINVAL, "npts must lie in [0, 2^31)");
+  PSHT_REQUIRE(npts == 0 || (theta && phi), PSHT_EINVAL, "theta and phi must be device pointers");
+  const uint32_t pf = flags & 3u;
+  PSHT_REQUIRE(pf != 3u, PSHT_EINVAL, "PSHT_FP32 and PSHT_FP64 are exclusive");
+  int prec = (pf == PSHT_FP64) ? 64 : (pf == PSHT_FP32) ? 32 : (eps >= 1e-5 ? 32 : 64);
+  PSHT_REQUIRE(!(prec == 32 && eps < 1e-7), PSHT_EINVAL, "the FP32 form needs eps >= 1e-7");
+
+  Plan* p = new Plan();
+  try {
+    p->spin = spin;
+    p->lmax = lmax;
+    p->eps = eps;
+    p->prec = prec;
+    p->npts = npts;
+    // step 1: nearer pole and theta* (one device reduction, validates the points)
+    double red[3];
+    reduce_points(theta, phi, npts, red, st);
+    PSHT_REQUIRE(red[2] == 0.0, PSHT_EINVAL, "theta outside [0, pi], NaN, or non-finite phi in the points");
+    p->pole = (red[0] <= red[1]) ? 1 : -1;
+    layout(*p, p->pole > 0 ? red[0] : red[1]);
+
+    // ring table
+    std::vector<RingDev> rings(p->nring);
+    for (int j = 0; j < p->nring; ++j) {
+      const double b = p->beta_j[j];
+      RingDev r;
+      // cos and half angles from beta (accurate near either pole)
+      r.x = p->pole > 0 ? cos(b) : -cos(b);
+      const double ch = p->pole > 0 ? cos(0.5 * b) : sin(0.5 * b);
+      const double sh = p->pole > 0 ? sin(0.5 * b) : cos(0.5 * b);
+      r.l2c = ch > 0 ? log2(ch) : -INFINITY;
+      r.l2s = sh > 0 ? log2(sh) : -INFINITY;
+      r.xhi = (float)r.x;
+      r.xlo = (float)(r.x - (double)r.xhi);
+      rings[j] = r;
+    }
+    p->d_ring = (RingDev*)upload(*p, rings, st);
+    // per-m seeds
+    std::vector<MSeed> ms(lmax + 1);
+    for (int m = 0; m <= lmax; ++m) {
+      MSeed d;
+      d.l0 = std::max(m, spin);
+      if (m >= spin) {
+        d.p1 = m - spin;
+        d.q1 = m + spin;
+        d.sign1 = d.sign2 = ((m + spin) & 1) ? -1 : 1;
+      } else {
+        d.p1 = spin - m;
+        d.q1 = spin + m;
+        d.sign1 = ((spin + m) & 1) ? -1 : 1;
+        d.sign2 = 1;
+      }
+      const long double l0 = d.l0;
+      const long double lb = 0.5L * (lgammal(2 * l0 + 1) - lgammal((long double)d.p1 + 1) - lgammal((long double)d.q1 + 1)) /
+                             logl(2.0L);
+      const long double ln = 0.5L * log2l((2 * l0 + 1) / (4.0L * 3.14159265358979323846264338327950288L));
+      d.lbin = (double)(lb + ln);
+      ms[m] = d;
+    }
+    p->d_mseed = (MSeed*)upload(*p, ms, st);
+    // active ring ranges and synthesis work items
+    std::vector<int2> mr(lmax + 1, make_int2(0, 0));
+    std::vector<RecItem> items;
+    const int cap = p->syn_rpt * p->syn_threads;
+    for (int m = 0; m <= p->M; ++m) {
+      int lo = -1, hi = -1;
+      for (int j = 0; j < p->nring; ++j)
+        if (p->Mj[j] >= m) {
+          if (lo < 0) lo = j;
+          hi = j + 1;
+        }
+      if (lo < 0) continue;
+      mr[m] = make_int2(lo, hi);
+      const int n = hi - lo, nchunk = (n + cap - 1) / cap;
+      for (int c = 0; c < nchunk; ++c) {
+        const int a = lo + (int)((int64_t)n * c / nchunk), b = lo + (int)((int64_t)n * (c + 1) / nchunk);
+        items.push_back(RecItem{m, a, b - a, 0});
+      }
+      p->pairs += n;
+      p->triples += (int64_t)n * (lmax - std::max(m, spin) + 1);
+    }
+    p->d_mrange = (int2*)upload(*p, mr, st);
+    p->nitems = (int)items.size();
+    p->d_items = (RecItem*)upload(*p, items, st);
+    // deconvolution tables, ring weights, FFT twiddles and digit-reversal tables
+    static const Quad quad;
+    std::vector<double> sT(2 * p->L - 1), sP(2 * p->M + 1);
+    const double hT = 2.0 * M_PI / p->nTheta, hP = 2.0 * M_PI / p->nphi;
+    for (int i = 0; i < 2 * p->L - 1; ++i)
+      sT[i] = hT / (2.0 * p->L * es_ft(i - (p->L - 1), p->W, p->beta_es, p->nTheta, quad));
+    for (int i = 0; i < 2 * p->M + 1; ++i) sP[i] = hP / es_ft(i - p->M, p->W, p->beta_es, p->nphi, quad);
+    p->f2L = radix_schedule(2 * p->L);
+    p->f4L = radix_schedule(4 * p->L);
+    p->fP = radix_schedule(p->nphi);
+    p->d_perm2L = (int*)upload(*p, fft_perm(p->f2L), st);
+    p->d_perm4L = (int*)upload(*p, fft_perm(p->f4L), st);
+    p->d_permP = (int*)upload(*p, fft_perm(p->fP), st);
+    auto twid = [](int n) {
+      std::vector<double> t(2 * (size_t)n);
+      for (int k = 0; k < n; ++k) {
+        const double a = 2.0 * M_PI * k / n;
+        t[2 * k] = cos(a);
+        t[2 * k + 1] = -sin(a);
+      }
+      return t;
+    };
+    if (prec == 64) {
+      p->d_sT = upload(*p, sT, st);
+      p->d_sP = upload(*p, sP, st);
+      p->d_w = upload(*p, p->w_j, st);
+      p->d_tw2L = upload(*p, twid(2 * p->L), st);
+      p->d_tw4L = upload(*p, twid(4 * p->L), st);
+      p->d_twP = upload(*p, twid(p->nphi), st);
+    } else {
+      p->d_sT = upload(*p, cast_vec<float>(sT), st);
+      p->d_sP = upload(*p, cast_vec<float>(sP), st);
+      p->d_w = upload(*p, cast_vec<float>(p->w_j), st);
+      p->d_tw2L = upload(*p, cast_vec<float>(twid(2 * p->L)), st);
+      p->d_tw4L = upload(*p, cast_vec<float>(twid(4 * p->L)), st);
+      p->d_twP = upload(*p, cast_vec<float>(twid(p->nphi)), st);
+    }
+    // work buffers
+    const size_t cb = prec == 64 ? 16 : 8, rb = prec == 64 ? 8 : 4;
+    p->d_rtab = dalloc(*p, 3 * (size_t)p->nalm * rb);
+    p->d_F = dalloc(*p, (size_t)p->ncols * p->Lpad * cb);
+    p->d_X = dalloc(*p, (size_t)p->nrows * p->ncols * cb);
+    p->d_G = dalloc(*p, (size_t)p->nrows * p->gstride * cb);
+    build_rec_table(*p, st);
+    // step 3 for the points: Theta_p, tiles, sorted layout (and FP64 kernel weights)
+    p->d_pidx = (int32_t*)dalloc(*p, (size_t)std::max<int64_t>(npts, 1) * 4);
+    p->d_pcell = (int32_t*)dalloc(*p, (size_t)std::max<int64_t>(npts, 1) * 4);
+    if (prec == 64) p->d_pw = dalloc(*p, (size_t)std::max<int64_t>(npts, 1) * 2 * p->W * 8);
+    else p->d_pfrac = (float*)dalloc(*p, (size_t)std::max<int64_t>(npts, 1) * 2 * 4);
+    bin_points(*p, theta, phi, st);
+    PSHT_CUDA_TRY(cudaStreamSynchronize(st));
+    return p;
+  } catch (...) {
+    destroy(p);
+    throw;
+  }
+}
+
+int fail(const Error& e) {
+  set_error(e.msg);
+  return e.code;
+}
+
+template <class F>
+int guarded(F&& f) {
+  try {
+    g_err.clear();
+    f();
+    return PSHT_OK;
+  } catch (const Error& e) {
+    return fail(e);
+  } catch (const std::bad_alloc&) {
+    return fail(Error{PSHT_ENOMEM, "host allocation failed"});
+  } catch (...) {
+    return fail(Error{PSHT_ECUDA, "unexpected failure"});
+  }
+}
+
+void run_synthesis(Plan& p, const void* g, const void* c, void* f, cudaStream_t st) {
+  launch_rec_synthesis(p, g, c, st);
+  launch_theta_synthesis(p, st);
+  launch_phi_synthesis(p, st);
+  launch_gather(p, f, st);
+}
+
+void run_adjoint(Plan& p, const void* f, void* g, void* c, cudaStream_t st) {
+  const size_t cb = p.prec == 64 ? 16 : 8;
+  PSHT_CUDA_TRY(cudaMemsetAsync(p.d_G, 0, (size_t)p.nrows * p.gstride * cb, st));
+  launch_scatter(p, f, st);
+  launch_phi_adjoint(p, st);
+  launch_theta_adjoint(p, st);
+  launch_rec_adjoint(p, g, c, st);
+}
+
+void ensure_io(Plan& p) {
+  const size_t cb = p.prec == 64 ? 16 : 8;
+  if (!p.d_io_a) p.d_io_a = dalloc(p, 2 * (size_t)p.nalm * cb);
+  if (!p.d_io_f) p.d_io_f = dalloc(p, (size_t)std::max<int64_t>(p.npts, 1) * cb);
+}
+
+}  // namespace
+}  // namespace psht
+
+using namespace psht;
+
+extern "C" {
+
+struct psht_plan {
+  Plan* p;
+};
+
+int psht_plan_create(int spin, int lmax, const double* theta, const double* phi, int64_t npts, double eps,
+                     uint32_t flags, void* stream, psht_plan** out) {
+  return guarded([&] {
+    PSHT_REQUIRE(out != nullptr, PSHT_EINVAL, "out must not be NULL");
+    *out = nullptr;
+    Plan* p = create(spin, lmax, theta, phi, npts, eps, flags, (cudaStream_t)stream);
+    *out = new psht_plan{p};
+  });
+}
+
+int psht_plan_info(const psht_plan* plan, psht_info* info) {
+  return guarded([&] {
+    PSHT_REQUIRE(plan && info, PSHT_EINVAL, "plan and info must not be NULL");
+    const Plan& p = *plan->p;
+    psht_info i;
+    memset(&i, 0, sizeof(i));
+    i.spin = p.spin;
+    i.lmax = p.lmax;
+    i.precision = p.prec;
+    i.pole = p.pole;
+    i.full_sky = p.full;
+    i.eps = p.eps;
+    i.theta_star = p.theta_star;
+    i.eps_apo = p.eps_apo;
+    i.theta_max = p.theta_max;
+    i.alpha = p.alpha;
+    i.dTheta = p.dTheta;
+    i.Lmax = p.Lmax;
+    i.L = p.L;
+    i.nring = p.nring;
+    i.M = p.M;
+    i.W = p.W;
+    i.beta_es = p.beta_es;
+    i.nTheta = p.nTheta;
+    i.nphi = p.nphi;
+    i.r_lo = p.r_lo;
+    i.nrows = p.nrows;
+    i.npts = p.npts;
+    i.ring_mode_pairs = p.pairs;
+    i.recursion_triples = p.triples;
+    i.device_bytes = p.bytes;
+    *info = i;
+  });
+}
+
+int psht_plan_synthesis(psht_plan* plan, const void* g, const void* c, void* f, void* stream) {
+  return guarded([&] {
+    PSHT_REQUIRE(plan && g, PSHT_EINVAL, "plan and g must not be NULL");
+    PSHT_REQUIRE(f || plan->p->npts == 0, PSHT_EINVAL, "f must not be NULL");
+    run_synthesis(*plan->p, g, c, f, (cudaStream_t)stream);
+  });
+}
+
+int psht_plan_adjoint(psht_plan* plan, const void* f, void* g, void* c, void* stream) {
+  return guarded([&] {
+    PSHT_REQUIRE(plan && g, PSHT_EINVAL, "plan and g must not be NULL");
+    PSHT_REQUIRE(f || plan->p->npts == 0, PSHT_EINVAL, "f must not be NULL");
+    run_adjoint(*plan->p, f, g, c, (cudaStream_t)stream);
+  });
+}
+
+int psht_plan_synthesis_host(psht_plan* plan, const void* g, const void* c, void* f, void* stream) {
+  return guarded([&] {
+    PSHT_REQUIRE(plan && g && f, PSHT_EINVAL, "plan, g and f must not be NULL");
+    Plan& p = *plan->p;
+    cudaStream_t st = (cudaStream_t)stream;
+    ensure_io(p);
+    const size_t cb = p.prec == 64 ? 16 : 8, na = (size_t)p.nalm * cb;
+    char* da = (char*)p.d_io_a;
+    PSHT_CUDA_TRY(cudaMemcpyAsync(da, g, na, cudaMemcpyHostToDevice, st));
+    if (c) PSHT_CUDA_TRY(cudaMemcpyAsync(da + na, c, na, cudaMemcpyHostToDevice, st));
+    run_synthesis(p, da, c ? da + na : nullptr, p.d_io_f, st);
+    PSHT_CUDA_TRY(cudaMemcpyAsync(f, p.d_io_f, (size_t)p.npts * cb, cudaMemcpyDeviceToHost, st));
+    PSHT_CUDA_TRY(cudaStreamSynchronize(st));
+  });
+}
+
+int psht_plan_adjoint_host(psht_plan* plan, const void* f, void* g, void* c, void* stream) {
+  return guarded([&] {
+    PSHT_REQUIRE(plan && g && f, PSHT_EINVAL, "plan, f and g must not be NULL");
+    Plan& p = *plan->p;
+    cudaStream_t st = (cudaStream_t)stream;
+    ensure_io(p);
+    const size_t cb = p.prec == 64 ? 16 : 8, na = (size_t)p.nalm * cb;
+    char* da = (char*)p.d_io_a;
+    PSHT_CUDA_TRY(cudaMemcpyAsync(p.d_io_f, f, (size_t)p.npts * cb, cudaMemcpyHostToDevice, st));
+    run_adjoint(p, p.d_io_f, da, c ? da + na : nullptr, st);
+    PSHT_CUDA_TRY(cudaMemcpyAsync(g, da, na, cudaMemcpyDeviceToHost, st));
+    if (c) PSHT_CUDA_TRY(cudaMemcpyAsync(c, da + na, na, cudaMemcpyDeviceToHost, st));
+    PSHT_CUDA_TRY(cudaStreamSynchronize(st));
+  });
+}
+
+int psht_plan_destroy(psht_plan* plan) {
+  if (!plan) return PSHT_OK;
+  destroy(plan->p);
+  delete plan;
+  return PSHT_OK;
+}
+
+int psht_plan_rings(const psht_plan* plan, double* theta_j, double* w_j, int32_t* Mj) {
+  return guarded([&] {
+    PSHT_REQUIRE(plan, PSHT_EINVAL, "plan must not be NULL");
+    const Plan& p = *plan->p;
+    for (int j = 0; j < p.nring; ++j) {
+      if (theta_j) theta_j[j] = p.theta_j[j];
+      if (w_j) w_j[j] = p.w_j[j];
+      if (Mj) Mj[j] = p.Mj[j];
+    }
+  });
+}
+
+int psht_plan_ring_coeffs(psht_plan* plan, const void* g, const void* c, void* F, void* stream) {
+  return guarded([&] {
+    PSHT_REQUIRE(plan && g && F, PSHT_EINVAL, "plan, g and F must not be NULL");
+    launch_rec_synthesis(*plan->p, g, c, (cudaStream_t)stream);
+    launch_ring_coeffs_export(*plan->p, F, (cudaStream_t)stream);
+  });
+}
+
+int psht_synthesis(const void* g, const void* c, int spin, int lmax, const double* theta, const double* phi,
+                   int64_t npts, double eps, void* f, void* stream) {
+  return guarded([&] {
+    Plan* p = create(spin, lmax, theta, phi, npts, eps, PSHT_AUTO, (cudaStream_t)stream);
+    try {
+      PSHT_REQUIRE(g && (f || npts == 0), PSHT_EINVAL, "g and f must not be NULL");
+      run_synthesis(*p, g, c, f, (cudaStream_t)stream);
+      PSHT_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    } catch (...) {
+      destroy(p);
+      throw;
+    }
+    destroy(p);
+  });
+}
+
+int psht_adjoint_synthesis(const void* f, int spin, int lmax, const double* theta, const double* phi, int64_t npts,
+                           double eps, void* g, void* c, void* stream) {
+  return guarded([&] {
+    Plan* p = create(spin, lmax, theta, phi, npts, eps, PSHT_AUTO, (cudaStream_t)stream);
+    try {
+      PSHT_REQUIRE(g && (f || npts == 0), PSHT_EINVAL, "f and g must not be NULL");
+      run_adjoint(*p, f, g, c, (cudaStream_t)stream);
+      PSHT_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    } catch (...) {
+      destroy(p);
+      throw;
+    }
+    destroy(p);
+  });
+}
+
+size_t psht_estimate_bytes(int spin, int lmax, double theta_star, int64_t npts, double eps, uint32_t flags) {
+  try {
+    Plan p;
+    p.spin = spin;
+    p.lmax = lmax;
+    p.eps = eps;
+    const uint32_t pf = flags & 3u;
+    p.prec = (pf == PSHT_FP64) ? 64 : (pf == PSHT_FP32) ? 32 : (eps >= 1e-5 ? 32 : 64);
+    p.npts = npts;
+    p.pole = 1;
+    layout(p, theta_star);
+    return planned_bytes(p);
+  } catch (...) {
+    return 0;
+  }
+}
+
+const char* psht_last_error(void) { return g_err.c_str(); }
+
+const char* psht_version(void) { return "psht 0.1 (sm_103a)"; }
+
+}  // extern "C"

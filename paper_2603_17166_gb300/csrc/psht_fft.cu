@@ -1,0 +1,316 @@
+// FFT stages between the ring coefficients and the oversampled grid.
+//
+// Theta stage (per phi-order column m, Sec. I.A-B and Sec. II steps 3-4):
+//   h_k = w_k F_k[m] (k <= L),  h_k = (-1)^(s+m) w_{2L-k} F_{2L-k}[m] (L < k < 2L)     (pole-crossing rule)
+//   H[n] = sum_k h_k e^{-i pi n k/L},  b[n] = H[n] sT(n) sP(m) for |n| <= L-1  (ES deconvolution)
+//   C[r] = sum_n b[n] e^{+2 pi i n r/nTheta} for the kept rows r in [r_lo, r_lo + nrows)
+// Phi stage (per kept row):  G[r, q] = sum_{|m|<=M} C[r, m] e^{+2 pi i m q/nphi}, stored with a
+// wrapped halo of padq columns on both sides.
+// The adjoint kernels apply the exact transposes in reverse order.
+// Every transform runs in place in shared memory (psht_common.cuh), one CTA per column or row.
+#include <cuda_runtime.h>
+
+#include "psht_common.cuh"
+
+namespace psht {
+
+namespace {
+
+constexpr int kFftThreads = 512;
+constexpr int kMaxLenF64 = 14336;  // complex128 elements in 224 KiB of shared memory
+constexpr int kMaxLenF32 = 28672;  // complex64
+// |n| <= L-1 values held per thread while the buffer is re-laid out (2L <= max length / 2)
+template <typename T>
+struct QPer {
+  static constexpr int v = ((sizeof(T) == 8 ? kMaxLenF64 : kMaxLenF32) / 2 + kFftThreads - 1) / kFftThreads;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kFftThreads) k_theta_syn(const typename Cx<T>::V* __restrict__ F, int Lpad,
+                                                           const T* __restrict__ w, int nring,
+                                                           const int2* __restrict__ mrange, int s, int L,
+                                                           const T* __restrict__ sT, const T* __restrict__ sP, int M,
+                                                           FftDev f2L, const typename Cx<T>::V* __restrict__ tw2L,
+                                                           const int* __restrict__ perm2L, FftDev f4L,
+                                                           const typename Cx<T>::V* __restrict__ tw4L,
+                                                           const int* __restrict__ perm4L, int r_lo, int nrows,
+                                                           typename Cx<T>::V* __restrict__ X, int ncols) {
+  using V = typename Cx<T>::V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* buf = reinterpret_cast<V*>(smraw);
+  const int mi = blockIdx.x;
+  const int m = col_m(mi), am = m < 0 ? -m : m;
+  const T sigma = ((s + am) & 1) ? (T)-1 : (T)1;
+  const int2 rr = mrange[am];
+  const int N2 = 2 * L, N4 = 4 * L;
+  const V* Fc = F + (int64_t)mi * Lpad;
+  for (int k = threadIdx.x; k < N2; k += blockDim.x) {
+    int j = k;
+    T sg = (T)1;
+    if (k > L) {
+      j = N2 - k;
+      sg = sigma;
+    }
+    V v = mk((T)0, (T)0);
+    if (j < nring && j >= rr.x && j < rr.y) v = cscale(Fc[j], sg * w[j]);
+    buf[k] = v;
+  }
+  __syncthreads();
+  fft_dif<false>(buf, f2L, tw2L);
+  // collect b[n] = H[n] sT(n) sP(m), |n| <= L-1, then lay them out for the inverse DIT of length 4L
+  constexpr int kQ = QPer<T>::v;
+  V hv[kQ];
+  const T sp = sP[m + M];
+#pragma unroll
+  for (int q = 0; q < kQ; ++q) {
+    const int i = threadIdx.x + q * blockDim.x;
+    if (i < N2 - 1) {
+      const int n = i - (L - 1);
+      hv[q] = cscale(buf[perm2L[n < 0 ? n + N2 : n]], sT[i] * sp);
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < N4; k += blockDim.x) buf[k] = mk((T)0, (T)0);
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < kQ; ++q) {
+    const int i = threadIdx.x + q * blockDim.x;
+    if (i < N2 - 1) {
+      const int n = i - (L - 1);
+      buf[perm4L[n < 0 ? n + N4 : n]] = hv[q];
+    }
+  }
+  __syncthreads();
+  fft_dit<true>(buf, f4L, tw4L);
+  for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
+    int r = (r_lo + i) % N4;
+    if (r < 0) r += N4;
+    X[(int64_t)i * ncols + mi] = buf[r];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFftThreads) k_phi_syn(const typename Cx<T>::V* __restrict__ X, int ncols,
+                                                         FftDev fP, const typename Cx<T>::V* __restrict__ twP,
+                                                         const int* __restrict__ permP, int padq, int gstride,
+                                                         typename Cx<T>::V* __restrict__ G) {
+  using V = typename Cx<T>::V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* buf = reinterpret_cast<V*>(smraw);
+  const int row = blockIdx.x;
+  const int nphi = fP.n;
+  for (int k = threadIdx.x; k < nphi; k += blockDim.x) buf[k] = mk((T)0, (T)0);
+  __syncthreads();
+  const V* Xr = X + (int64_t)row * ncols;
+  for (int mi = threadIdx.x; mi < ncols; mi += blockDim.x) {
+    const int m = col_m(mi);
+    buf[permP[m < 0 ? m + nphi : m]] = Xr[mi];
+  }
+  __syncthreads();
+  fft_dit<true>(buf, fP, twP);
+  V* Gr = G + (int64_t)row * gstride;
+  const int nq = nphi + 2 * padq;
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+    int src = (q - padq) % nphi;  // the halo may wrap more than once when nphi < padq
+    if (src < 0) src += nphi;
+    Gr[q] = buf[src];
+  }
+  for (int q = nq + threadIdx.x; q < gstride; q += blockDim.x) Gr[q] = mk((T)0, (T)0);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFftThreads) k_phi_adj(const typename Cx<T>::V* __restrict__ G, int gstride,
+                                                         int padq, FftDev fP, const typename Cx<T>::V* __restrict__ twP,
+                                                         const int* __restrict__ permP,
+                                                         typename Cx<T>::V* __restrict__ X, int ncols) {
+  using V = typename Cx<T>::V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* buf = reinterpret_cast<V*>(smraw);
+  const int row = blockIdx.x;
+  const int nphi = fP.n;
+  const V* Gr = G + (int64_t)row * gstride;
+  // fold every stored column qs (true column qs - padq) onto q = (qs - padq) mod nphi
+  const int nq = nphi + 2 * padq;
+  for (int q = threadIdx.x; q < nphi; q += blockDim.x) {
+    V v = mk((T)0, (T)0);
+    for (int qs = (q + padq) % nphi; qs < nq; qs += nphi) v = cadd(v, Gr[qs]);
+    buf[q] = v;
+  }
+  __syncthreads();
+  fft_dif<false>(buf, fP, twP);
+  V* Xr = X + (int64_t)row * ncols;
+  for (int mi = threadIdx.x; mi < ncols; mi += blockDim.x) {
+    const int m = col_m(mi);
+    Xr[mi] = buf[permP[m < 0 ? m + nphi : m]];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFftThreads) k_theta_adj(const typename Cx<T>::V* __restrict__ X, int ncols,
+                                                           int r_lo, int nrows, const T* __restrict__ w, int nring,
+                                                           int s, int L, const T* __restrict__ sT,
+                                                           const T* __restrict__ sP, int M, FftDev f2L,
+                                                           const typename Cx<T>::V* __restrict__ tw2L,
+                                                           const int* __restrict__ perm2L, FftDev f4L,
+                                                           const typename Cx<T>::V* __restrict__ tw4L,
+                                                           const int* __restrict__ perm4L,
+                                                           typename Cx<T>::V* __restrict__ Ft, int Lpad) {
+  using V = typename Cx<T>::V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* buf = reinterpret_cast<V*>(smraw);
+  const int mi = blockIdx.x;
+  const int m = col_m(mi), am = m < 0 ? -m : m;
+  const T sigma = ((s + am) & 1) ? (T)-1 : (T)1;
+  const int N2 = 2 * L, N4 = 4 * L;
+  // transpose of the row read-out: row r lands on r mod 4L, summing rows that coincide
+  for (int k = threadIdx.x; k < N4; k += blockDim.x) {
+    int i0 = (k - r_lo) % N4;  // first row index i >= 0 with r_lo + i = k (mod 4L)
+    if (i0 < 0) i0 += N4;
+    V v = mk((T)0, (T)0);
+    for (int i = i0; i < nrows; i += N4) v = cadd(v, X[(int64_t)i * ncols + mi]);
+    buf[k] = v;
+  }
+  __syncthreads();
+  fft_dif<false>(buf, f4L, tw4L);
+  constexpr int kQ = QPer<T>::v;
+  V hv[kQ];
+  const T sp = sP[m + M];
+#pragma unroll
+  for (int q = 0; q < kQ; ++q) {
+    const int i = threadIdx.x + q * blockDim.x;
+    if (i < N2 - 1) {
+      const int n = i - (L - 1);
+      hv[q] = cscale(buf[perm4L[n < 0 ? n + N4 : n]], sT[i] * sp);
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < N2; k += blockDim.x) buf[k] = mk((T)0, (T)0);
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < kQ; ++q) {
+    const int i = threadIdx.x + q * blockDim.x;
+    if (i < N2 - 1) {
+      const int n = i - (L - 1);
+      buf[perm2L[n < 0 ? n + N2 : n]] = hv[q];
+    }
+  }
+  __syncthreads();
+  fft_dit<true>(buf, f2L, tw2L);
+  V* Fc = Ft + (int64_t)mi * Lpad;
+  for (int j = threadIdx.x; j < nring; j += blockDim.x) {
+    V v = buf[j];
+    if (j >= 1 && j <= L - 1) v = cadd(v, cscale(buf[N2 - j], sigma));
+    Fc[j] = cscale(v, w[j]);
+  }
+}
+
+// F[mi][j] (column layout, active rings only) -> out[j][m + M], zero outside the active range
+template <typename T>
+__global__ void k_export_rings(const typename Cx<T>::V* __restrict__ F, int Lpad, const int2* __restrict__ mrange,
+                               int nring, int M, typename Cx<T>::V* __restrict__ out) {
+  using V = typename Cx<T>::V;
+  const int ncols = 2 * M + 1;
+  const int64_t tot = (int64_t)nring * ncols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e / ncols);
+    const int m = (int)(e % ncols) - M;
+    const int am = m < 0 ? -m : m;
+    const int2 rr = mrange[am];
+    V v = mk((T)0, (T)0);
+    if (j >= rr.x && j < rr.y) v = F[(int64_t)col_of(m) * Lpad + j];
+    out[e] = v;
+  }
+}
+
+template <typename T>
+void set_smem(const void* fn, size_t bytes) {
+  PSHT_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
+}  // namespace
+
+int max_fft_len(int prec) { return prec == 64 ? kMaxLenF64 : kMaxLenF32; }
+
+void launch_theta_synthesis(Plan& p, cudaStream_t st) {
+  const size_t smem = (size_t)4 * p.L * (p.prec == 64 ? 16 : 8);
+  if (p.prec == 64) {
+    using V = double2;
+    set_smem<double>((const void*)k_theta_syn<double>, smem);
+    k_theta_syn<double><<<p.ncols, kFftThreads, smem, st>>>(
+        (const V*)p.d_F, p.Lpad, (const double*)p.d_w, p.nring, p.d_mrange, p.spin, p.L, (const double*)p.d_sT,
+        (const double*)p.d_sP, p.M, p.f2L, (const V*)p.d_tw2L, p.d_perm2L, p.f4L, (const V*)p.d_tw4L, p.d_perm4L,
+        p.r_lo, p.nrows, (V*)p.d_X, p.ncols);
+  } else {
+    using V = float2;
+    set_smem<float>((const void*)k_theta_syn<float>, smem);
+    k_theta_syn<float><<<p.ncols, kFftThreads, smem, st>>>(
+        (const V*)p.d_F, p.Lpad, (const float*)p.d_w, p.nring, p.d_mrange, p.spin, p.L, (const float*)p.d_sT,
+        (const float*)p.d_sP, p.M, p.f2L, (const V*)p.d_tw2L, p.d_perm2L, p.f4L, (const V*)p.d_tw4L, p.d_perm4L,
+        p.r_lo, p.nrows, (V*)p.d_X, p.ncols);
+  }
+  PSHT_CUDA_TRY(cudaGetLastError());
+}
+
+void launch_phi_synthesis(Plan& p, cudaStream_t st) {
+  const size_t smem = (size_t)p.nphi * (p.prec == 64 ? 16 : 8);
+  if (p.prec == 64) {
+    set_smem<double>((const void*)k_phi_syn<double>, smem);
+    k_phi_syn<double><<<p.nrows, kFftThreads, smem, st>>>((const double2*)p.d_X, p.ncols, p.fP,
+                                                         (const double2*)p.d_twP, p.d_permP, p.padq, p.gstride,
+                                                         (double2*)p.d_G);
+  } else {
+    set_smem<float>((const void*)k_phi_syn<float>, smem);
+    k_phi_syn<float><<<p.nrows, kFftThreads, smem, st>>>((const float2*)p.d_X, p.ncols, p.fP,
+                                                        (const float2*)p.d_twP, p.d_permP, p.padq, p.gstride,
+                                                        (float2*)p.d_G);
+  }
+  PSHT_CUDA_TRY(cudaGetLastError());
+}
+
+void launch_phi_adjoint(Plan& p, cudaStream_t st) {
+  const size_t smem = (size_t)p.nphi * (p.prec == 64 ? 16 : 8);
+  if (p.prec == 64) {
+    set_smem<double>((const void*)k_phi_adj<double>, smem);
+    k_phi_adj<double><<<p.nrows, kFftThreads, smem, st>>>((const double2*)p.d_G, p.gstride, p.padq, p.fP,
+                                                         (const double2*)p.d_twP, p.d_permP, (double2*)p.d_X,
+                                                         p.ncols);
+  } else {
+    set_smem<float>((const void*)k_phi_adj<float>, smem);
+    k_phi_adj<float><<<p.nrows, kFftThreads, smem, st>>>((const float2*)p.d_G, p.gstride, p.padq, p.fP,
+                                                        (const float2*)p.d_twP, p.d_permP, (float2*)p.d_X, p.ncols);
+  }
+  PSHT_CUDA_TRY(cudaGetLastError());
+}
+
+void launch_theta_adjoint(Plan& p, cudaStream_t st) {
+  const size_t smem = (size_t)4 * p.L * (p.prec == 64 ? 16 : 8);
+  if (p.prec == 64) {
+    using V = double2;
+    set_smem<double>((const void*)k_theta_adj<double>, smem);
+    k_theta_adj<double><<<p.ncols, kFftThreads, smem, st>>>(
+        (const V*)p.d_X, p.ncols, p.r_lo, p.nrows, (const double*)p.d_w, p.nring, p.spin, p.L,
+        (const double*)p.d_sT, (const double*)p.d_sP, p.M, p.f2L, (const V*)p.d_tw2L, p.d_perm2L, p.f4L,
+        (const V*)p.d_tw4L, p.d_perm4L, (V*)p.d_F, p.Lpad);
+  } else {
+    using V = float2;
+    set_smem<float>((const void*)k_theta_adj<float>, smem);
+    k_theta_adj<float><<<p.ncols, kFftThreads, smem, st>>>(
+        (const V*)p.d_X, p.ncols, p.r_lo, p.nrows, (const float*)p.d_w, p.nring, p.spin, p.L, (const float*)p.d_sT,
+        (const float*)p.d_sP, p.M, p.f2L, (const V*)p.d_tw2L, p.d_perm2L, p.f4L, (const V*)p.d_tw4L, p.d_perm4L,
+        (V*)p.d_F, p.Lpad);
+  }
+  PSHT_CUDA_TRY(cudaGetLastError());
+}
+
+void launch_ring_coeffs_export(Plan& p, void* out, cudaStream_t st) {
+  const int nth = 256, nbl = 152 * 8;
+  if (p.prec == 64)
+    k_export_rings<double><<<nbl, nth, 0, st>>>((const double2*)p.d_F, p.Lpad, p.d_mrange, p.nring, p.M,
+                                                (double2*)out);
+  else
+    k_export_rings<float><<<nbl, nth, 0, st>>>((const float2*)p.d_F, p.Lpad, p.d_mrange, p.nring, p.M,
+                                               (float2*)out);
+  PSHT_CUDA_TRY(cudaGetLastError());
+}
+
+}  // namespace psht

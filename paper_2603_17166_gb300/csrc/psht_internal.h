@@ -1,0 +1,146 @@
+// Internal declarations of the psht library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/psht.h"
+
+namespace psht {
+
+// ---------------------------------------------------------------------------------------------
+// error handling
+void set_error(const std::string& msg);
+struct Error {
+  int code;
+  std::string msg;
+};
+#define PSHT_CUDA_TRY(call)                                                                  \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      throw ::psht::Error{PSHT_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};   \
+  } while (0)
+#define PSHT_REQUIRE(cond, code, msg)                  \
+  do {                                                 \
+    if (!(cond)) throw ::psht::Error{(code), (msg)};   \
+  } while (0)
+
+// ---------------------------------------------------------------------------------------------
+// constants of the scaled recursion.  A value is held as y * 2^(-SCALE_F * k) with k >= 0;
+// while k > 0 the true value is below 2^(SCALE_R - SCALE_F) and its contribution is dropped.
+template <typename T>
+struct ScaleConst;
+template <>
+struct ScaleConst<double> {
+  static constexpr int F = 500;      // exponent step of one rescale
+  static constexpr int R_EXP = 400;  // rescale when |y| >= 2^400
+};
+template <>
+struct ScaleConst<float> {
+  static constexpr int F = 80;
+  static constexpr int R_EXP = 50;   // threshold of the dropped region: 2^(50-80) = 2^-30
+};
+
+// ---------------------------------------------------------------------------------------------
+// device-side tables
+struct RingDev {
+  double x;         // cos(theta_j)
+  double l2c, l2s;  // log2 cos(theta_j/2), log2 sin(theta_j/2)  (-inf allowed)
+  float xhi, xlo;   // x split into two floats (FP32 form)
+};
+
+struct MSeed {      // per order m, for the two recursions m' = -s (e1) and m' = +s (e2)
+  double lbin;      // log2( N_{l0} sqrt(C(2 l0, p1)) )
+  int l0;           // max(m, s)
+  int p1, q1;       // e1 seed ~ cos^p1 sin^q1 of the half angle (e2 uses cos^q1 sin^p1)
+  int sign1, sign2; // signs of the two seeds
+};
+
+struct RecItem {    // one CTA of the synthesis recursion: order m, rings [j0, j0 + nj)
+  int m, j0, nj, pad;
+};
+
+struct TileItem {   // one CTA of the gather/scatter: a tile and a slice of its sorted points
+  int tr, tq;       // tile row/column index
+  int p0, np;       // first sorted point, count
+};
+
+struct FftDev {     // radix schedule of one FFT length (at most 32 stages)
+  int n, nst;
+  int rad[32];
+};
+
+// ---------------------------------------------------------------------------------------------
+struct Plan {
+  // parameters (names as in the paper)
+  int spin = 0, lmax = 0, prec = 64;
+  double eps = 0;
+  int pole = 1, full = 0;
+  double theta_star = 0, eps_apo = 0, theta_max = 0, dTheta = 0, alpha = 0;
+  int Lmax = 0, L = 0, nring = 0, M = 0, W = 0;
+  double beta_es = 0;
+  int nTheta = 0, nphi = 0, r_lo = 0, nrows = 0;
+  int64_t npts = 0, nalm = 0;
+  std::vector<double> theta_j, beta_j, w_j;
+  std::vector<int> Mj;
+  // layouts
+  int ncols = 0;    // 2M+1 columns of the ring / row arrays, column mi(m) = 2m (m>=0), 2|m|-1 (m<0)
+  int Lpad = 0;     // leading dimension of F (ring index fastest)
+  int padq = 0;     // grid columns stored at q + padq, q in [-padq, nphi + padq)
+  int gstride = 0;  // grid row stride (complex elements)
+  int TR = 0, TQ = 0, ntr = 0, ntq = 0;
+  // recursion launch shapes
+  int syn_rpt = 1, syn_threads = 128, adj_rpt = 1, adj_threads = 128;
+  int64_t pairs = 0, triples = 0;
+  // device memory
+  RingDev* d_ring = nullptr;
+  MSeed* d_mseed = nullptr;
+  int2* d_mrange = nullptr;     // active ring range [j_lo, j_hi) per m
+  void* d_rtab = nullptr;       // (A', B', kappa) per packed (l, m), precision T, 3 arrays
+  RecItem* d_items = nullptr;
+  int nitems = 0;
+  void* d_F = nullptr;          // complex T [ncols][Lpad]
+  void* d_X = nullptr;          // complex T [nrows][ncols]
+  void* d_G = nullptr;          // complex T [nrows][gstride]
+  void* d_sT = nullptr;         // T [2L-1], deconvolution in Theta incl. 1/(2L), n = -(L-1)..L-1
+  void* d_sP = nullptr;         // T [2M+1], deconvolution in phi, m = -M..M
+  void* d_w = nullptr;          // T [nring]
+  void* d_tw2L = nullptr;       // complex T twiddles e^{-2 pi i t/N}
+  void* d_tw4L = nullptr;
+  void* d_twP = nullptr;
+  FftDev f2L{}, f4L{}, fP{};
+  int* d_perm2L = nullptr;      // digit-reversed positions of each FFT length
+  int* d_perm4L = nullptr;
+  int* d_permP = nullptr;
+  // points (sorted by tile)
+  TileItem* d_titems = nullptr;
+  int ntitems = 0;
+  int32_t* d_pidx = nullptr;    // original index of sorted point
+  int32_t* d_pcell = nullptr;   // (r0 - tile row origin) | (q0 + padq - tile col origin) << 16
+  void* d_pw = nullptr;         // FP64 form: weights [2W][npts] (psi_r[i], then psi_q[k])
+  float* d_pfrac = nullptr;     // FP32 form: [2][npts] t - r0, u - q0
+  void* d_io_a = nullptr;       // device staging for the host-buffer entry points (lazy)
+  void* d_io_f = nullptr;
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+};
+
+// kernels / launchers ---------------------------------------------------------------------------
+void build_rec_table(Plan& p, cudaStream_t st);
+void launch_rec_synthesis(Plan& p, const void* g, const void* c, cudaStream_t st);
+void launch_rec_adjoint(Plan& p, void* g, void* c, cudaStream_t st);
+void launch_theta_synthesis(Plan& p, cudaStream_t st);
+void launch_phi_synthesis(Plan& p, cudaStream_t st);
+void launch_phi_adjoint(Plan& p, cudaStream_t st);
+void launch_theta_adjoint(Plan& p, cudaStream_t st);
+void launch_gather(Plan& p, void* f, cudaStream_t st);
+void launch_scatter(Plan& p, const void* f, cudaStream_t st);
+void launch_ring_coeffs_export(Plan& p, void* F, cudaStream_t st);
+void reduce_points(const double* theta, const double* phi, int64_t npts, double out[3], cudaStream_t st);
+void bin_points(Plan& p, const double* theta, const double* phi, cudaStream_t st);
+int max_fft_len(int prec);
+
+}  // namespace psht

@@ -1,0 +1,382 @@
+// Point side of the transform: theta* reduction, binning of the points into grid tiles, and the
+// ES-kernel interpolation (gather, synthesis) and spreading (scatter-add, adjoint).
+//
+// A point at colatitude theta is mapped to Theta = pi beta/theta_max, beta = theta or pi - theta
+// (Sec. II step 3), then to fine-grid coordinates t = Theta nTheta/2pi, u = (phi mod 2pi) nphi/2pi.
+// Its window is rows r0 .. r0+W-1 and columns q0 .. q0+W-1 with r0 = ceil(t - W/2), q0 = ceil(u - W/2),
+// and weights psi(2(t - r0 - i)/W) psi(2(u - q0 - k)/W), psi(z) = exp(beta_es (sqrt(1 - z^2) - 1))
+// (the ES kernel of Barnett, Magland & af Klinteberg 2019, the NUFFT the paper defers to, Sec. I.B).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "psht_common.cuh"
+
+namespace psht {
+
+namespace {
+
+constexpr int kBinThreads = 256;
+constexpr int kInterpThreads = 256;
+
+__device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
+
+// out[0] = max theta, out[1] = max (pi - theta), out[2] = count of invalid points (as bits/int)
+__global__ void k_reduce(const double* __restrict__ theta, const double* __restrict__ phi, int64_t n,
+                         unsigned long long* __restrict__ out) {
+  double mN = 0.0, mS = 0.0;
+  unsigned long long bad = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double t = theta[i], f = phi[i];
+    if (!(t >= 0.0 && t <= M_PI) || !isfinite(f)) {
+      ++bad;
+      continue;
+    }
+    mN = fmax(mN, t);
+    mS = fmax(mS, M_PI - t);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mN = fmax(mN, __shfl_xor_sync(0xffffffffu, mN, o));
+    mS = fmax(mS, __shfl_xor_sync(0xffffffffu, mS, o));
+    bad += __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    // non-negative doubles order like their bit patterns
+    atomicMax(&out[0], dbits(mN));
+    atomicMax(&out[1], dbits(mS));
+    if (bad) atomicAdd(&out[2], bad);
+  }
+}
+
+struct BinGeom {
+  int pole;
+  double theta_max, nTheta, nphi;
+  int W, r_lo, padq, TR, TQ, ntr, ntq;
+};
+
+__device__ __forceinline__ void point_tu(const BinGeom& g, double th, double ph, double& t, double& u) {
+  const double beta = g.pole > 0 ? th : M_PI - th;
+  const double Th = beta * (M_PI / g.theta_max);
+  t = Th * (g.nTheta / (2.0 * M_PI));
+  const double pr = ph - 2.0 * M_PI * floor(ph / (2.0 * M_PI));
+  u = pr * (g.nphi / (2.0 * M_PI));
+  if (u >= g.nphi) u -= g.nphi;
+  if (u < 0.0) u = 0.0;
+}
+
+__global__ void k_bin_count(const double* __restrict__ theta, const double* __restrict__ phi, int64_t n, BinGeom g,
+                            int* __restrict__ tile_of, int* __restrict__ counts) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double t, u;
+    point_tu(g, theta[i], phi[i], t, u);
+    const int r0 = (int)ceil(t - 0.5 * g.W), q0 = (int)ceil(u - 0.5 * g.W);
+    const int dr = r0 - g.r_lo, dq = q0 + g.padq;
+    if (dr < 0 || dq < 0 || dr / g.TR >= g.ntr || dq / g.TQ >= g.ntq) {  // outside the planned rows: reported
+      tile_of[i] = -1;
+      continue;
+    }
+    const int tile = (dr / g.TR) * g.ntq + dq / g.TQ;
+    tile_of[i] = tile;
+    atomicAdd(&counts[tile], 1);
+  }
+}
+
+__device__ __forceinline__ double es_psi(double z, double beta) {
+  if (z < -1.0 || z > 1.0) return 0.0;
+  return exp(beta * (sqrt(1.0 - z * z) - 1.0));
+}
+
+__global__ void k_bin_scatter(const double* __restrict__ theta, const double* __restrict__ phi, int64_t n, BinGeom g,
+                              const int* __restrict__ tile_of, const int* __restrict__ offsets,
+                              int* __restrict__ cursor, int32_t* __restrict__ pidx, int32_t* __restrict__ pcell,
+                              double* __restrict__ pw, float* __restrict__ pfrac, double beta_es) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double t, u;
+    point_tu(g, theta[i], phi[i], t, u);
+    const int r0 = (int)ceil(t - 0.5 * g.W), q0 = (int)ceil(u - 0.5 * g.W);
+    const int tile = tile_of[i];
+    if (tile < 0) continue;
+    const int tr = tile / g.ntq, tq = tile - tr * g.ntq;
+    const int pos = offsets[tile] + atomicAdd(&cursor[tile], 1);
+    pidx[pos] = (int32_t)i;
+    const int lr = r0 - g.r_lo - tr * g.TR, lq = q0 + g.padq - tq * g.TQ;
+    pcell[pos] = (int32_t)(lr | (lq << 16));
+    if (pw) {
+      for (int a = 0; a < g.W; ++a) {
+        pw[(int64_t)a * n + pos] = es_psi(2.0 * (t - (double)(r0 + a)) / g.W, beta_es);
+        pw[(int64_t)(g.W + a) * n + pos] = es_psi(2.0 * (u - (double)(q0 + a)) / g.W, beta_es);
+      }
+    }
+    if (pfrac) {
+      pfrac[pos] = (float)(t - (double)r0);
+      pfrac[n + pos] = (float)(u - (double)q0);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+template <typename T, int W>
+struct Weights;
+template <int W>
+struct Weights<double, W> {
+  __device__ __forceinline__ static void get(const double* pw, const float*, int64_t n, int64_t pt, double, double* wr,
+                                             double* wq) {
+#pragma unroll
+    for (int a = 0; a < W; ++a) {
+      wr[a] = pw[(int64_t)a * n + pt];
+      wq[a] = pw[(int64_t)(W + a) * n + pt];
+    }
+  }
+};
+template <int W>
+struct Weights<float, W> {
+  __device__ __forceinline__ static void get(const double*, const float* pf, int64_t n, int64_t pt, float beta,
+                                             float* wr, float* wq) {
+    const float ft = pf[pt], fu = pf[n + pt];
+    const float sc = 2.0f / W;
+#pragma unroll
+    for (int a = 0; a < W; ++a) {
+      const float zr = (ft - (float)a) * sc, zq = (fu - (float)a) * sc;
+      wr[a] = __expf(beta * (sqrtf(fmaxf(0.0f, 1.0f - zr * zr)) - 1.0f));
+      wq[a] = __expf(beta * (sqrtf(fmaxf(0.0f, 1.0f - zq * zq)) - 1.0f));
+    }
+  }
+};
+
+template <typename T, int W>
+__global__ void __launch_bounds__(kInterpThreads) k_gather(const TileItem* __restrict__ items,
+                                                           const int32_t* __restrict__ pidx,
+                                                           const int32_t* __restrict__ pcell,
+                                                           const double* __restrict__ pw,
+                                                           const float* __restrict__ pf, int64_t npts,
+                                                           const typename Cx<T>::V* __restrict__ G, int nrows,
+                                                           int gstride, int TR, int TQ, T beta,
+                                                           typename Cx<T>::V* __restrict__ f) {
+  using V = typename Cx<T>::V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* tile = reinterpret_cast<V*>(smraw);
+  const TileItem it = items[blockIdx.x];
+  const int pitch = TQ + W - 1, rows = TR + W - 1;
+  const int row0 = it.tr * TR, col0 = it.tq * TQ;
+  for (int e = threadIdx.x; e < rows * pitch; e += blockDim.x) {
+    const int rr = e / pitch, cc = e - rr * pitch;
+    const int gr = row0 + rr, gc = col0 + cc;
+    tile[e] = (gr < nrows && gc < gstride) ? G[(int64_t)gr * gstride + gc] : mk((T)0, (T)0);
+  }
+  __syncthreads();
+  for (int pt = it.p0 + threadIdx.x; pt < it.p0 + it.np; pt += blockDim.x) {
+    const int cell = pcell[pt];
+    const int lr = cell & 0xffff, lq = cell >> 16;
+    T wr[W], wq[W];
+    Weights<T, W>::get(pw, pf, npts, pt, beta, wr, wq);
+    T accr = 0, acci = 0;
+#pragma unroll
+    for (int a = 0; a < W; ++a) {
+      const V* tp = tile + (lr + a) * pitch + lq;
+      T rr = 0, ri = 0;
+#pragma unroll
+      for (int b = 0; b < W; ++b) {
+        const V gv = tp[b];
+        rr = fma(wq[b], gv.x, rr);
+        ri = fma(wq[b], gv.y, ri);
+      }
+      accr = fma(wr[a], rr, accr);
+      acci = fma(wr[a], ri, acci);
+    }
+    f[pidx[pt]] = mk(accr, acci);
+  }
+}
+
+template <typename T, int W>
+__global__ void __launch_bounds__(kInterpThreads) k_scatter(const TileItem* __restrict__ items,
+                                                            const int32_t* __restrict__ pidx,
+                                                            const int32_t* __restrict__ pcell,
+                                                            const double* __restrict__ pw,
+                                                            const float* __restrict__ pf, int64_t npts,
+                                                            const typename Cx<T>::V* __restrict__ f,
+                                                            typename Cx<T>::V* __restrict__ G, int nrows, int gstride,
+                                                            int TR, int TQ, T beta) {
+  using V = typename Cx<T>::V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* tile = reinterpret_cast<T*>(smraw);  // interleaved re, im
+  const TileItem it = items[blockIdx.x];
+  const int pitch = TQ + W - 1, rows = TR + W - 1;
+  const int row0 = it.tr * TR, col0 = it.tq * TQ;
+  for (int e = threadIdx.x; e < 2 * rows * pitch; e += blockDim.x) tile[e] = (T)0;
+  __syncthreads();
+  for (int pt = it.p0 + threadIdx.x; pt < it.p0 + it.np; pt += blockDim.x) {
+    const int cell = pcell[pt];
+    const int lr = cell & 0xffff, lq = cell >> 16;
+    T wr[W], wq[W];
+    Weights<T, W>::get(pw, pf, npts, pt, beta, wr, wq);
+    const V fv = f[pidx[pt]];
+#pragma unroll
+    for (int a = 0; a < W; ++a) {
+      const T vr = wr[a] * fv.x, vi = wr[a] * fv.y;
+      T* tp = tile + 2 * ((lr + a) * pitch + lq);
+#pragma unroll
+      for (int b = 0; b < W; ++b) {
+        atomicAdd(tp + 2 * b, wq[b] * vr);
+        atomicAdd(tp + 2 * b + 1, wq[b] * vi);
+      }
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < rows * pitch; e += blockDim.x) {
+    const T vr = tile[2 * e], vi = tile[2 * e + 1];
+    if (vr == (T)0 && vi == (T)0) continue;
+    const int rr = e / pitch, cc = e - rr * pitch;
+    const int gr = row0 + rr, gc = col0 + cc;
+    if (gr < nrows && gc < gstride) {
+      T* gp = reinterpret_cast<T*>(G + (int64_t)gr * gstride + gc);
+      atomicAdd(gp, vr);
+      atomicAdd(gp + 1, vi);
+    }
+  }
+}
+
+template <typename T, int W>
+void run_gather(Plan& p, void* f, cudaStream_t st) {
+  using V = typename Cx<T>::V;
+  const size_t smem = (size_t)(p.TR + W - 1) * (p.TQ + W - 1) * sizeof(V);
+  PSHT_CUDA_TRY(cudaFuncSetAttribute((const void*)k_gather<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+  k_gather<T, W><<<p.ntitems, kInterpThreads, smem, st>>>(p.d_titems, p.d_pidx, p.d_pcell, (const double*)p.d_pw,
+                                                          p.d_pfrac, p.npts, (const V*)p.d_G, p.nrows, p.gstride,
+                                                          p.TR, p.TQ, (T)p.beta_es, (V*)f);
+}
+template <typename T, int W>
+void run_scatter(Plan& p, const void* f, cudaStream_t st) {
+  using V = typename Cx<T>::V;
+  const size_t smem = (size_t)(p.TR + W - 1) * (p.TQ + W - 1) * sizeof(V);
+  PSHT_CUDA_TRY(cudaFuncSetAttribute((const void*)k_scatter<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+  k_scatter<T, W><<<p.ntitems, kInterpThreads, smem, st>>>(p.d_titems, p.d_pidx, p.d_pcell, (const double*)p.d_pw,
+                                                           p.d_pfrac, p.npts, (const V*)f, (V*)p.d_G, p.nrows,
+                                                           p.gstride, p.TR, p.TQ, (T)p.beta_es);
+}
+
+template <typename T, bool GATHER>
+void dispatch_w(Plan& p, void* f, cudaStream_t st) {
+#define PSHT_W_CASE(w)                         \
+  case w:                                      \
+    if (GATHER) run_gather<T, w>(p, f, st);    \
+    else run_scatter<T, w>(p, f, st);          \
+    break;
+  if (sizeof(T) == 8) {
+    switch (p.W) {
+      PSHT_W_CASE(2) PSHT_W_CASE(3) PSHT_W_CASE(4) PSHT_W_CASE(5) PSHT_W_CASE(6) PSHT_W_CASE(7) PSHT_W_CASE(8)
+      PSHT_W_CASE(9) PSHT_W_CASE(10) PSHT_W_CASE(11) PSHT_W_CASE(12) PSHT_W_CASE(13) PSHT_W_CASE(14)
+      PSHT_W_CASE(15) PSHT_W_CASE(16)
+      default: throw Error{PSHT_ENOTSUP, "kernel width outside 2..16"};
+    }
+  } else {
+    switch (p.W) {
+      PSHT_W_CASE(2) PSHT_W_CASE(3) PSHT_W_CASE(4) PSHT_W_CASE(5) PSHT_W_CASE(6) PSHT_W_CASE(7) PSHT_W_CASE(8)
+      default: throw Error{PSHT_ENOTSUP, "FP32 form supports kernel widths 2..8 (eps >= 1e-7)"};
+    }
+  }
+#undef PSHT_W_CASE
+}
+
+}  // namespace
+
+void reduce_points(const double* theta, const double* phi, int64_t npts, double out[3], cudaStream_t st) {
+  unsigned long long* d = nullptr;
+  PSHT_CUDA_TRY(cudaMallocAsync((void**)&d, 3 * sizeof(unsigned long long), st));
+  PSHT_CUDA_TRY(cudaMemsetAsync(d, 0, 3 * sizeof(unsigned long long), st));
+  if (npts > 0) {
+    const int nbl = (int)std::min<int64_t>((npts + kBinThreads - 1) / kBinThreads, 152 * 16);
+    k_reduce<<<nbl, kBinThreads, 0, st>>>(theta, phi, npts, d);
+    PSHT_CUDA_TRY(cudaGetLastError());
+  }
+  unsigned long long h[3];
+  PSHT_CUDA_TRY(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st));
+  PSHT_CUDA_TRY(cudaStreamSynchronize(st));
+  PSHT_CUDA_TRY(cudaFreeAsync(d, st));
+  memcpy(&out[0], &h[0], sizeof(double));
+  memcpy(&out[1], &h[1], sizeof(double));
+  out[2] = (double)h[2];
+}
+
+void bin_points(Plan& p, const double* theta, const double* phi, cudaStream_t st) {
+  const int64_t n = p.npts;
+  BinGeom g;
+  g.pole = p.pole;
+  g.theta_max = p.theta_max;
+  g.nTheta = p.nTheta;
+  g.nphi = p.nphi;
+  g.W = p.W;
+  g.r_lo = p.r_lo;
+  g.padq = p.padq;
+  g.TR = p.TR;
+  g.TQ = p.TQ;
+  g.ntr = p.ntr;
+  g.ntq = p.ntq;
+  const int ntiles = p.ntr * p.ntq;
+  int *d_tile = nullptr, *d_cnt = nullptr, *d_off = nullptr;
+  PSHT_CUDA_TRY(cudaMallocAsync((void**)&d_tile, sizeof(int) * std::max<int64_t>(n, 1), st));
+  PSHT_CUDA_TRY(cudaMallocAsync((void**)&d_cnt, sizeof(int) * ntiles, st));
+  PSHT_CUDA_TRY(cudaMallocAsync((void**)&d_off, sizeof(int) * ntiles, st));
+  PSHT_CUDA_TRY(cudaMemsetAsync(d_cnt, 0, sizeof(int) * ntiles, st));
+  const int nbl = (int)std::max<int64_t>(1, std::min<int64_t>((n + kBinThreads - 1) / kBinThreads, 152 * 32));
+  if (n > 0) k_bin_count<<<nbl, kBinThreads, 0, st>>>(theta, phi, n, g, d_tile, d_cnt);
+  PSHT_CUDA_TRY(cudaGetLastError());
+  std::vector<int> cnt(ntiles), off(ntiles);
+  PSHT_CUDA_TRY(cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int) * ntiles, cudaMemcpyDeviceToHost, st));
+  PSHT_CUDA_TRY(cudaStreamSynchronize(st));
+  // tile work items, dense tiles split so that no CTA holds more than kMaxPts points
+  const int kMaxPts = 2048;
+  std::vector<TileItem> items;
+  int64_t acc = 0;
+  for (int t = 0; t < ntiles; ++t) {
+    off[t] = (int)acc;
+    const int c = cnt[t];
+    for (int b = 0; b < c; b += kMaxPts) {
+      TileItem it;
+      it.tr = t / p.ntq;
+      it.tq = t % p.ntq;
+      it.p0 = (int)(acc + b);
+      it.np = std::min(kMaxPts, c - b);
+      items.push_back(it);
+    }
+    acc += c;
+  }
+  PSHT_REQUIRE(acc == n, PSHT_EINVAL, "a point falls outside the planned grid rows (theta* inconsistent)");
+  p.ntitems = (int)items.size();
+  if (p.ntitems > 0) {
+    PSHT_CUDA_TRY(cudaMalloc((void**)&p.d_titems, sizeof(TileItem) * items.size()));
+    p.allocs.push_back(p.d_titems);
+    p.bytes += sizeof(TileItem) * items.size();
+    PSHT_CUDA_TRY(cudaMemcpyAsync(p.d_titems, items.data(), sizeof(TileItem) * items.size(), cudaMemcpyHostToDevice, st));
+  }
+  PSHT_CUDA_TRY(cudaMemcpyAsync(d_off, off.data(), sizeof(int) * ntiles, cudaMemcpyHostToDevice, st));
+  PSHT_CUDA_TRY(cudaMemsetAsync(d_cnt, 0, sizeof(int) * ntiles, st));
+  if (n > 0)
+    k_bin_scatter<<<nbl, kBinThreads, 0, st>>>(theta, phi, n, g, d_tile, d_off, d_cnt, p.d_pidx, p.d_pcell,
+                                               (double*)p.d_pw, p.d_pfrac, p.beta_es);
+  PSHT_CUDA_TRY(cudaGetLastError());
+  PSHT_CUDA_TRY(cudaFreeAsync(d_tile, st));
+  PSHT_CUDA_TRY(cudaFreeAsync(d_cnt, st));
+  PSHT_CUDA_TRY(cudaFreeAsync(d_off, st));
+  PSHT_CUDA_TRY(cudaStreamSynchronize(st));
+}
+
+void launch_gather(Plan& p, void* f, cudaStream_t st) {
+  if (p.ntitems == 0) return;
+  if (p.prec == 64) dispatch_w<double, true>(p, f, st);
+  else dispatch_w<float, true>(p, f, st);
+  PSHT_CUDA_TRY(cudaGetLastError());
+}
+
+void launch_scatter(Plan& p, const void* f, cudaStream_t st) {
+  if (p.ntitems == 0) return;
+  if (p.prec == 64) dispatch_w<double, false>(p, const_cast<void*>(f), st);
+  else dispatch_w<float, false>(p, const_cast<void*>(f), st);
+  PSHT_CUDA_TRY(cudaGetLastError());
+}
+
+}  // namespace psht

@@ -1,0 +1,219 @@
+"""Thin ctypes binding of the psht C ABI (include/psht.h).
+
+Only argument marshalling happens here: every step of the transform runs in the CUDA library.
+PyTorch provides device memory and streams.  Names follow the C entry points.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+PSHT_AUTO, PSHT_FP64, PSHT_FP32 = 0, 1, 2
+_PREC = {"auto": PSHT_AUTO, "fp64": PSHT_FP64, "fp32": PSHT_FP32, 64: PSHT_FP64, 32: PSHT_FP32}
+
+
+class PshtError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"psht error {code}: {msg}")
+        self.code = code
+
+
+class PshtInfo(ctypes.Structure):
+    _fields_ = [
+        ("spin", ctypes.c_int), ("lmax", ctypes.c_int), ("precision", ctypes.c_int),
+        ("pole", ctypes.c_int), ("full_sky", ctypes.c_int),
+        ("eps", ctypes.c_double), ("theta_star", ctypes.c_double), ("eps_apo", ctypes.c_double),
+        ("theta_max", ctypes.c_double), ("alpha", ctypes.c_double), ("dTheta", ctypes.c_double),
+        ("Lmax", ctypes.c_int), ("L", ctypes.c_int), ("nring", ctypes.c_int),
+        ("M", ctypes.c_int), ("W", ctypes.c_int), ("beta_es", ctypes.c_double),
+        ("nTheta", ctypes.c_int), ("nphi", ctypes.c_int), ("r_lo", ctypes.c_int), ("nrows", ctypes.c_int),
+        ("npts", ctypes.c_int64), ("ring_mode_pairs", ctypes.c_int64), ("recursion_triples", ctypes.c_int64),
+        ("device_bytes", ctypes.c_size_t),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load the in-tree libpsht.so; raise if it has not been built (there is no fallback)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                               "(python -m paper_2603_17166_gb300.build)")
+        L = ctypes.CDLL(path)
+        P, I, D, I64, U32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64, ctypes.c_uint32
+        L.psht_plan_create.argtypes = [I, I, P, P, I64, D, U32, P, ctypes.POINTER(P)]
+        L.psht_plan_info.argtypes = [P, ctypes.POINTER(PshtInfo)]
+        for name in ("psht_plan_synthesis", "psht_plan_adjoint", "psht_plan_synthesis_host",
+                     "psht_plan_adjoint_host", "psht_plan_ring_coeffs"):
+            getattr(L, name).argtypes = [P, P, P, P, P]
+        L.psht_plan_destroy.argtypes = [P]
+        L.psht_plan_rings.argtypes = [P, P, P, P]
+        L.psht_synthesis.argtypes = [P, P, I, I, P, P, I64, D, P, P]
+        L.psht_adjoint_synthesis.argtypes = [P, I, I, P, P, I64, D, P, P, P]
+        L.psht_estimate_bytes.argtypes = [I, I, D, I64, D, U32]
+        L.psht_estimate_bytes.restype = ctypes.c_size_t
+        L.psht_last_error.restype = ctypes.c_char_p
+        L.psht_version.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise PshtError(rc, lib().psht_last_error().decode())
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _stream(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def nalm(lmax: int) -> int:
+    return (lmax + 1) * (lmax + 2) // 2
+
+
+class Plan:
+    """A plan for synthesis general and its adjoint at fixed points (psht_plan_create)."""
+
+    def __init__(self, spin: int, lmax: int, theta, phi, eps: float, precision="auto", stream=None):
+        torch = _torch()
+        theta = torch.as_tensor(theta, dtype=torch.float64, device="cuda").contiguous()
+        phi = torch.as_tensor(phi, dtype=torch.float64, device="cuda").contiguous()
+        if theta.shape != phi.shape or theta.dim() != 1:
+            raise ValueError("theta and phi must be 1-D tensors of equal length")
+        self._h = ctypes.c_void_p()
+        _check(lib().psht_plan_create(int(spin), int(lmax), _ptr(theta), _ptr(phi), theta.numel(), float(eps),
+                                      _PREC[precision], _stream(stream), ctypes.byref(self._h)))
+        self.spin, self.lmax, self.eps, self.npts = int(spin), int(lmax), float(eps), theta.numel()
+        i = self.info
+        self.precision = i["precision"]
+        self.cdtype = torch.complex128 if self.precision == 64 else torch.complex64
+        self.np_cdtype = np.complex128 if self.precision == 64 else np.complex64
+
+    @property
+    def info(self) -> dict:
+        inf = PshtInfo()
+        _check(lib().psht_plan_info(self._h, ctypes.byref(inf)))
+        return {name: getattr(inf, name) for name, _ in PshtInfo._fields_}
+
+    def _alm_in(self, a):
+        torch = _torch()
+        if a is None:
+            return None
+        a = torch.as_tensor(a, device="cuda").to(self.cdtype).contiguous()
+        if a.numel() != nalm(self.lmax):
+            raise ValueError(f"a_lm must hold {nalm(self.lmax)} packed coefficients")
+        return a
+
+    def synthesis(self, g, c=None, out=None, stream=None):
+        """f_p = -sum (g_lm + i c_lm) sY_lm(theta_p, phi_p) (psht_plan_synthesis)."""
+        torch = _torch()
+        g, c = self._alm_in(g), self._alm_in(c)
+        f = out if out is not None else torch.empty(self.npts, dtype=self.cdtype, device="cuda")
+        _check(lib().psht_plan_synthesis(self._h, _ptr(g), _ptr(c), _ptr(f), _stream(stream)))
+        return f
+
+    def adjoint(self, f, g_out=None, c_out=None, want_c: bool = True, stream=None):
+        """(g~, c~) of adjoint synthesis general (psht_plan_adjoint)."""
+        torch = _torch()
+        f = torch.as_tensor(f, device="cuda").to(self.cdtype).contiguous()
+        if f.numel() != self.npts:
+            raise ValueError("f must hold one value per point")
+        n = nalm(self.lmax)
+        g = g_out if g_out is not None else torch.empty(n, dtype=self.cdtype, device="cuda")
+        c = (c_out if c_out is not None else torch.empty(n, dtype=self.cdtype, device="cuda")) if want_c else None
+        _check(lib().psht_plan_adjoint(self._h, _ptr(f), _ptr(g), _ptr(c), _stream(stream)))
+        return g, c
+
+    def synthesis_host(self, g: np.ndarray, c, f: np.ndarray, stream=None):
+        """Host-buffer synthesis (psht_plan_synthesis_host); g, c, f numpy arrays (pinned memory ok)."""
+        _check(lib().psht_plan_synthesis_host(self._h, ctypes.c_void_p(g.ctypes.data),
+                                              None if c is None else ctypes.c_void_p(c.ctypes.data),
+                                              ctypes.c_void_p(f.ctypes.data), _stream(stream)))
+        return f
+
+    def adjoint_host(self, f: np.ndarray, g: np.ndarray, c, stream=None):
+        _check(lib().psht_plan_adjoint_host(self._h, ctypes.c_void_p(f.ctypes.data), ctypes.c_void_p(g.ctypes.data),
+                                            None if c is None else ctypes.c_void_p(c.ctypes.data), _stream(stream)))
+        return g, c
+
+    def rings(self):
+        """(theta_j, w_j, M_j) of the planner (psht_plan_rings)."""
+        n = self.info["nring"]
+        th, w, mj = np.zeros(n), np.zeros(n), np.zeros(n, dtype=np.int32)
+        _check(lib().psht_plan_rings(self._h, ctypes.c_void_p(th.ctypes.data), ctypes.c_void_p(w.ctypes.data),
+                                     ctypes.c_void_p(mj.ctypes.data)))
+        return th, w, mj
+
+    def ring_coeffs(self, g, c=None, stream=None):
+        """Ring Fourier coefficients F[j, m + M] (psht_plan_ring_coeffs)."""
+        torch = _torch()
+        i = self.info
+        g, c = self._alm_in(g), self._alm_in(c)
+        F = torch.empty((i["nring"], 2 * i["M"] + 1), dtype=self.cdtype, device="cuda")
+        _check(lib().psht_plan_ring_coeffs(self._h, _ptr(g), _ptr(c), _ptr(F), _stream(stream)))
+        return F
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().psht_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def synthesis(g, c, spin: int, lmax: int, theta, phi, eps: float, stream=None):
+    """One-shot synthesis general (psht_synthesis); precision chosen from eps."""
+    torch = _torch()
+    theta = torch.as_tensor(theta, dtype=torch.float64, device="cuda").contiguous()
+    phi = torch.as_tensor(phi, dtype=torch.float64, device="cuda").contiguous()
+    cd = torch.complex64 if eps >= 1e-5 else torch.complex128
+    g = torch.as_tensor(g, device="cuda").to(cd).contiguous()
+    c = None if c is None else torch.as_tensor(c, device="cuda").to(cd).contiguous()
+    f = torch.empty(theta.numel(), dtype=cd, device="cuda")
+    _check(lib().psht_synthesis(_ptr(g), _ptr(c), int(spin), int(lmax), _ptr(theta), _ptr(phi), theta.numel(),
+                                float(eps), _ptr(f), _stream(stream)))
+    return f
+
+
+def adjoint_synthesis(f, spin: int, lmax: int, theta, phi, eps: float, stream=None):
+    """One-shot adjoint synthesis general (psht_adjoint_synthesis) -> (g~, c~)."""
+    torch = _torch()
+    theta = torch.as_tensor(theta, dtype=torch.float64, device="cuda").contiguous()
+    phi = torch.as_tensor(phi, dtype=torch.float64, device="cuda").contiguous()
+    cd = torch.complex64 if eps >= 1e-5 else torch.complex128
+    f = torch.as_tensor(f, device="cuda").to(cd).contiguous()
+    g = torch.empty(nalm(lmax), dtype=cd, device="cuda")
+    c = torch.empty(nalm(lmax), dtype=cd, device="cuda")
+    _check(lib().psht_adjoint_synthesis(_ptr(f), int(spin), int(lmax), _ptr(theta), _ptr(phi), theta.numel(),
+                                        float(eps), _ptr(g), _ptr(c), _stream(stream)))
+    return g, c
+
+
+def estimate_bytes(spin: int, lmax: int, theta_star: float, npts: int, eps: float, precision="auto") -> int:
+    return int(lib().psht_estimate_bytes(int(spin), int(lmax), float(theta_star), int(npts), float(eps),
+                                         _PREC[precision]))

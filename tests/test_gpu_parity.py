@@ -1,0 +1,199 @@
+"""CUDA path against the FP64 oracle through the C ABI (marked gpu).
+
+Small cases that the oracle finishes in seconds but that span several tiles, several FFT
+stages and ragged ring chunks: plan parameters, ring coefficients (stage parity), end-to-end
+synthesis and adjoint against direct summation (<= 10 eps), against the oracle pipeline
+(same plan, FP64 to 1e-11), the adjoint identity, and the edge cases."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _alm(rng, lmax, s):
+    n = O.nalm(lmax)
+    return O.canonical_alm(rng.standard_normal(n) + 1j * rng.standard_normal(n), lmax, s)
+
+
+def _cap(rng, n, radius, pole="N"):
+    th = np.arccos(rng.uniform(math.cos(radius), 1.0, n))
+    if pole == "S":
+        th = math.pi - th
+    return th, rng.uniform(-math.pi, 3 * math.pi, n)
+
+
+def _plan(s, lmax, th, ph, eps, prec):
+    from paper_2603_17166_gb300 import Plan
+
+    return Plan(s, lmax, torch.from_numpy(th).cuda(), torch.from_numpy(ph).cuda(), eps, precision=prec)
+
+
+def _cu(a, plan):
+    return None if a is None else torch.from_numpy(np.asarray(a)).cuda().to(plan.cdtype)
+
+
+CASES = [
+    # lmax, s, cap radius, pole, eps, precision
+    (64, 0, math.radians(10), "S", 1e-10, "fp64"),
+    (64, 2, math.radians(10), "S", 1e-10, "fp64"),
+    (96, 2, 0.45, "N", 1e-7, "fp64"),
+    (160, 1, 0.3, "S", 1e-8, "fp64"),
+    (128, 3, 1.0, "N", 1e-10, "fp64"),
+    (64, 0, math.radians(10), "S", 1e-5, "fp32"),
+    (200, 2, 0.5, "N", 1e-5, "fp32"),
+    (150, 1, 0.35, "S", 1e-6, "fp32"),
+]
+
+
+@pytest.mark.parametrize("lmax,s,radius,pole,eps,prec", CASES)
+def test_plan_parameters_match_oracle(lmax, s, radius, pole, eps, prec):
+    rng = np.random.default_rng(1)
+    th, ph = _cap(rng, 3000, radius, pole)
+    plan = _plan(s, lmax, th, ph, eps, prec)
+    P = O.plan_params(lmax, s, eps, th)
+    i = plan.info
+    assert i["pole"] == (1 if P["pole"] == "N" else -1)
+    assert i["full_sky"] == int(P["full"])
+    for k in ("theta_star", "eps_apo", "theta_max", "dTheta"):
+        assert i[k] == pytest.approx(P[k], rel=1e-14, abs=1e-15)
+    for k in ("Lmax", "L", "nring", "M", "W", "nTheta", "nphi", "r_lo", "nrows"):
+        assert i[k] == P[k], k
+    tj, wj, mj = plan.rings()
+    assert np.abs(tj - P["theta_j"]).max() < 1e-15
+    assert np.abs(wj - P["w_j"]).max() < 1e-13
+    assert np.array_equal(mj, P["Mj"])
+
+
+@pytest.mark.parametrize("lmax,s,radius,pole,eps,prec", CASES)
+def test_ring_coefficients_stage_parity(lmax, s, radius, pole, eps, prec):
+    """F_j[m] of the recursion kernel against the oracle's ring synthesis at the same rings."""
+    rng = np.random.default_rng(2)
+    th, ph = _cap(rng, 500, radius, pole)
+    g, c = _alm(rng, lmax, s), (_alm(rng, lmax, s) if s else None)
+    plan = _plan(s, lmax, th, ph, eps, prec)
+    P = O.plan_params(lmax, s, eps, th)
+    F = plan.ring_coeffs(_cu(g, plan), _cu(c, plan)).cpu().numpy()
+    Fo = O.ring_synthesis(lmax, s, P["M"], g, c, P["theta_j"])
+    tol = 1e-12 if prec == "fp64" else 2e-5
+    assert O.rel_l2(F, Fo) < tol
+    # per ring, where the ring has any power
+    for j in range(0, P["nring"], max(1, P["nring"] // 7)):
+        if np.linalg.norm(Fo[j]) > 1e-8 * np.linalg.norm(Fo):
+            assert O.rel_l2(F[j], Fo[j]) < 50 * tol
+
+
+@pytest.mark.parametrize("lmax,s,radius,pole,eps,prec", CASES)
+def test_synthesis_against_direct_sum(lmax, s, radius, pole, eps, prec):
+    rng = np.random.default_rng(3)
+    th, ph = _cap(rng, 4000, radius, pole)
+    g, c = _alm(rng, lmax, s), (_alm(rng, lmax, s) if s else None)
+    plan = _plan(s, lmax, th, ph, eps, prec)
+    f = plan.synthesis(_cu(g, plan), _cu(c, plan)).cpu().numpy()
+    ref = O.direct_synthesis(lmax, s, g, c, th, ph)
+    assert O.rel_l2(f, ref) <= 10 * eps
+    if prec == "fp64":
+        P = O.plan_params(lmax, s, eps, th)
+        f2 = O.pipeline_synthesis(P, g, c, th, ph)
+        assert O.rel_l2(f, f2) < 1e-11
+
+
+@pytest.mark.parametrize("lmax,s,radius,pole,eps,prec", CASES)
+def test_adjoint_against_direct_sum(lmax, s, radius, pole, eps, prec):
+    rng = np.random.default_rng(4)
+    th, ph = _cap(rng, 4000, radius, pole)
+    g, c = _alm(rng, lmax, s), _alm(rng, lmax, s)
+    plan = _plan(s, lmax, th, ph, eps, prec)
+    f = O.direct_synthesis(lmax, s, g, c, th, ph)      # f = A a: the adjoint's accuracy target
+    gt, ct = plan.adjoint(_cu(f, plan))
+    gt, ct = gt.cpu().numpy(), ct.cpu().numpy()
+    gt1, ct1 = O.direct_adjoint(lmax, s, th, ph, f)
+    _, m = O.lm_of_index(lmax)
+    wgt = np.tile(np.where(m == 0, 1.0, 2.0), 2)
+    assert O.rel_l2(np.concatenate([gt, ct]), np.concatenate([gt1, ct1]), wgt) <= 10 * eps
+    # written zeros: Im at m = 0 and l < s
+    l, m = O.lm_of_index(lmax)
+    assert np.all(gt[m == 0].imag == 0) and np.all(ct[m == 0].imag == 0)
+    assert np.all(gt[l < s] == 0)
+    if prec == "fp64":
+        P = O.plan_params(lmax, s, eps, th)
+        gt2, ct2 = O.pipeline_adjoint(P, f, th, ph)
+        assert O.rel_l2(np.concatenate([gt, ct]), np.concatenate([gt2, ct2]), wgt) < 1e-11
+
+
+@pytest.mark.parametrize("lmax,s,radius,pole,eps,prec", CASES)
+def test_adjoint_identity(lmax, s, radius, pole, eps, prec):
+    """<f, A a> = <A^H f, a> for random a, f: every GPU stage is an exact transpose."""
+    rng = np.random.default_rng(5)
+    th, ph = _cap(rng, 3000, radius, pole)
+    g, c = _alm(rng, lmax, s), _alm(rng, lmax, s)
+    f = rng.standard_normal(th.size) + 1j * rng.standard_normal(th.size)
+    plan = _plan(s, lmax, th, ph, eps, prec)
+    Aa = plan.synthesis(_cu(g, plan), _cu(c, plan)).cpu().numpy().astype(np.complex128)
+    gt, ct = plan.adjoint(_cu(f, plan))
+    lhs = O.map_dot(f, Aa)
+    rhs = O.alm_dot(gt.cpu().numpy().astype(np.complex128), g, lmax) + \
+        O.alm_dot(ct.cpu().numpy().astype(np.complex128), c, lmax)
+    assert abs(lhs - rhs) <= (1e-12 if prec == "fp64" else 1e-5) * abs(lhs)
+
+
+def test_full_sky_mode_and_pole_points():
+    """A cap beyond the equator switches to full-sky mode; points exactly on the pole and on
+    theta = pi are valid."""
+    rng = np.random.default_rng(6)
+    lmax, s, eps = 40, 2, 1e-10
+    th, ph = _cap(rng, 1500, 2.5, "N")
+    th[:3] = [0.0, math.pi, 1e-300]
+    g, c = _alm(rng, lmax, s), _alm(rng, lmax, s)
+    plan = _plan(s, lmax, th, ph, eps, "fp64")
+    assert plan.info["full_sky"] == 1
+    f = plan.synthesis(_cu(g, plan), _cu(c, plan)).cpu().numpy()
+    assert O.rel_l2(f, O.direct_synthesis(lmax, s, g, c, th, ph)) <= 10 * eps
+
+
+def test_tiny_inputs():
+    from paper_2603_17166_gb300 import Plan
+
+    rng = np.random.default_rng(7)
+    lmax, s = 8, 0
+    g = _alm(rng, lmax, s)
+    # one point
+    th, ph = np.array([0.3]), np.array([1.0])
+    plan = _plan(s, lmax, th, ph, 1e-10, "fp64")
+    f = plan.synthesis(_cu(g, plan)).cpu().numpy()
+    assert O.rel_l2(f, O.direct_synthesis(lmax, s, g, None, th, ph)) < 1e-9
+    # no points: synthesis writes nothing, adjoint writes zeros
+    e = torch.empty(0, dtype=torch.float64, device="cuda")
+    p0 = Plan(s, lmax, e, e, 1e-10, precision="fp64")
+    assert p0.synthesis(_cu(g, p0)).numel() == 0
+    gt, ct = p0.adjoint(torch.empty(0, dtype=torch.complex128, device="cuda"))
+    assert float(gt.abs().max()) == 0.0
+    # lmax = spin = 0
+    p1 = _plan(0, 0, th, ph, 1e-10, "fp64")
+    g0 = np.array([2.0 + 0j])
+    f = p1.synthesis(_cu(g0, p1)).cpu().numpy()
+    ref = -2.0 / math.sqrt(4 * math.pi)
+    assert abs(f[0] - ref) <= 10 * 1e-10 * abs(ref)
+
+
+def test_invalid_arguments_are_rejected():
+    from paper_2603_17166_gb300 import Plan, PshtError
+
+    th = torch.tensor([0.1, 0.2], dtype=torch.float64, device="cuda")
+    ph = torch.tensor([0.0, 1.0], dtype=torch.float64, device="cuda")
+    for kw in (dict(spin=-1, lmax=8, eps=1e-8), dict(spin=3, lmax=2, eps=1e-8), dict(spin=0, lmax=8, eps=1e-20),
+               dict(spin=0, lmax=8, eps=0.5)):
+        with pytest.raises(PshtError):
+            Plan(kw["spin"], kw["lmax"], th, ph, kw["eps"])
+    bad = torch.tensor([0.1, float("nan")], dtype=torch.float64, device="cuda")
+    with pytest.raises(PshtError):
+        Plan(0, 8, bad, ph, 1e-8)
+    bad = torch.tensor([0.1, 3.5], dtype=torch.float64, device="cuda")
+    with pytest.raises(PshtError):
+        Plan(0, 8, bad, ph, 1e-8)
+    with pytest.raises(PshtError):
+        Plan(0, 8, th, ph, 1e-9, precision="fp32")   # FP32 form needs eps >= 1e-7
