@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Benchmark: spin-2 synthesis + adjoint Mpoints/s at lmax 4096 on the ~4% field (2.2e7 points).
+
+One step = one synthesis general (a_lm -> f) plus one adjoint synthesis general (f -> a_lm) on the
+same plan, i.e. every stage of the hot path.  The headline `value` is the FP32 form at eps = 1e-5;
+the FP64 form at eps = 1e-10 is timed in the same run and reported under "forms".  Inputs are
+seeded synthetic data (see paper_2603_17166_gb300/synthetic.py) and resident in HBM before the
+timed region; every step's working set (a_lm, f, grid, point tables) is larger than L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torch.distributed.run) every rank runs its own replica of the workload
+(replicas only: the transform has no exchange step on one patch) and `value` counts all ranks'
+points over the slowest rank's time.  `--impl reference` times the FP64 CPU oracle pipeline on
+this host's cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "spin-2 synth+adjoint Mpoints/s at lmax 4096, eps 1e-5 vs 1e-10; serving p99"
+UNIT = "Mpoints/s"
+LMAX, SPIN = 4096, 2
+EPS32, EPS64 = 1e-5, 1e-10
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--frame", default="R", choices=["R", "S"])
+    ap.add_argument("--step-arcmin", type=float, default=0.5)
+    ap.add_argument("--steps64", type=int, default=3)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-points", type=int, default=1_000_000)
+    ap.add_argument("--cpu-ring-stride", type=int, default=8)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="psht_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [ln.split(",") for ln in open(self.path) if ln.strip()]
+        except Exception:
+            rows = []
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for k, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(k)
+        if sm:
+            out.update(sm_mhz=float(statistics.median(sm)), sm_max_mhz=float(max(smax)), reasons=sorted(reasons),
+                       samples=len(sm))
+        return out
+
+
+# ----------------------------------------------------------------------------- peaks
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def alu_peak_tflops(prec: int) -> float:
+    """Plain-ALU FMA peak at the maximum SM clock: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz.
+    FP64 on this part runs at 1/64 of that rate (1.26 TFLOP/s)."""
+    fp32 = 152 * 128 * 2 * 2.07e9 / 1e12
+    return fp32 if prec == 32 else fp32 / 64.0
+
+
+# ----------------------------------------------------------------------------- our arm
+def flops_per_triple(spin: int) -> int:
+    """Algorithmic FLOPs of one (ring, m, l) step: a three-term recurrence step for each of the
+    two Wigner columns d_{m,-s}, d_{m,s} (2 FMA = 4 flops each) and the complex-by-real
+    accumulation into F_j[+m] and F_j[-m] (2 FMA = 4 flops each).  Spin 0 has one column."""
+    return 16 if spin else 12
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_2603_17166_gb300 import Plan, build, synthetic
+
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        dist = dist_mod
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    t0 = time.time()
+    wl = synthetic.config2(frame=args.frame, step_arcmin=args.step_arcmin, realisation=rank)
+    npts = wl["theta"].size
+    gen_s = time.time() - t0
+    theta = torch.from_numpy(wl["theta"]).to(dev)
+    phi = torch.from_numpy(wl["phi"]).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    results = {}
+    launches_per_step = 8
+    forms = [("fp32", EPS32, args.steps), ("fp64", EPS64, max(1, args.steps64))]
+    headline = None
+    for name, eps, K in forms:
+        t0 = time.time()
+        plan = Plan(SPIN, LMAX, theta, phi, eps, precision=name, stream=stream)
+        torch.cuda.synchronize(dev)
+        plan_s = time.time() - t0
+        info = plan.info
+        g = torch.from_numpy(wl["g"]).to(dev).to(plan.cdtype)
+        c = torch.from_numpy(wl["c"]).to(dev).to(plan.cdtype)
+        f = torch.empty(npts, dtype=plan.cdtype, device=dev)
+        gt = torch.empty_like(g)
+        ct = torch.empty_like(c)
+        W = args.warmup if name == "fp32" else max(1, min(args.warmup, 2))
+        for _ in range(W):
+            plan.synthesis(g, c, out=f, stream=stream)
+            plan.adjoint(f, g_out=gt, c_out=ct, stream=stream)
+        torch.cuda.synchronize(dev)
+        plan.stage_times()  # clear
+        barrier()
+        torch.cuda.synchronize(dev)
+        clk = ClockSampler(local_rank)
+        clk.start()
+        plan.profile(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            plan.synthesis(g, c, out=f, stream=stream)
+            plan.adjoint(f, g_out=gt, c_out=ct, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        plan.profile(False)
+        clocks = clk.stop()
+        ms = e0.elapsed_time(e1)
+        stages = plan.stage_times()
+        if dist is not None:
+            t = torch.tensor([ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        ms_step = ms / K
+        value = world * npts * K / (ms * 1e-3) / 1e6
+        # dominant kernel: the recursion (synthesis and adjoint launches are the same algorithm)
+        rec_ms = stages["rec_synthesis"][0] + stages["rec_adjoint"][0]
+        rec_n = stages["rec_synthesis"][1] + stages["rec_adjoint"][1]
+        flops = info["recursion_triples"] * flops_per_triple(SPIN)
+        achieved = flops / (rec_ms / rec_n * 1e-3) / 1e12 if rec_n else None
+        peak = alu_peak_tflops(64 if name == "fp64" else 32)
+        per_stage = {k: round(v[0] / max(v[1], 1), 4) for k, v in stages.items()}
+        entry = dict(value=value, ms_per_step=ms_step, steps=K, warmup=W, eps=eps, plan_s=plan_s,
+                     stage_ms=per_stage, clocks=clocks,
+                     plan=dict(L=info["L"], M=info["M"], W=info["W"], nTheta=info["nTheta"], nphi=info["nphi"],
+                               nrows=info["nrows"], theta_star_deg=math.degrees(info["theta_star"]),
+                               eps_apo=info["eps_apo"], recursion_triples=info["recursion_triples"],
+                               device_gb=info["device_bytes"] / 1e9),
+                     roofline=dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s",
+                                   frac=(achieved / peak if achieved else None), traffic=None,
+                                   kernel="k_rec_syn/k_rec_adj", flops_per_launch=flops,
+                                   peak_note="FMA lanes x 2 x 2.07 GHz max SM clock"))
+        # e2e through the host-buffer C-ABI entry points, pinned host memory
+        if name == "fp32" and not args.no_e2e:
+            hg = torch.from_numpy(wl["g"]).to(plan.cdtype).pin_memory().numpy()
+            hc = torch.from_numpy(wl["c"]).to(plan.cdtype).pin_memory().numpy()
+            hf = torch.empty(npts, dtype=plan.cdtype).pin_memory().numpy()
+            hgt = torch.empty(g.numel(), dtype=plan.cdtype).pin_memory().numpy()
+            hct = torch.empty(g.numel(), dtype=plan.cdtype).pin_memory().numpy()
+            for _ in range(2):
+                plan.synthesis_host(hg, hc, hf, stream=stream)
+                plan.adjoint_host(hf, hgt, hct, stream=stream)
+            barrier()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            for _ in range(K):
+                plan.synthesis_host(hg, hc, hf, stream=stream)
+                plan.adjoint_host(hf, hgt, hct, stream=stream)
+            torch.cuda.synchronize(dev)
+            el = time.perf_counter() - t0
+            barrier()
+            if dist is not None:
+                t = torch.tensor([el], device=dev, dtype=torch.float64)
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                el = float(t.item())
+            cb = hf.itemsize
+            entry["e2e"] = dict(value=world * npts * K / el / 1e6, unit=UNIT,
+                                h2d_bytes_per_step=int(hg.nbytes + hc.nbytes + npts * cb),
+                                d2h_bytes_per_step=int(npts * cb + hgt.nbytes + hct.nbytes))
+        results[name] = entry
+        if name == "fp32":
+            headline = entry
+        plan.close()
+        del g, c, f, gt, ct
+        torch.cuda.empty_cache()
+
+    line = {
+        "metric": METRIC, "value": headline["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": headline["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "spin-2 synthesis+adjoint, lmax 4096, ~4% field RA -50..50 dec -70..-42, "
+                               f"regular {args.step_arcmin}' grid + 2.5' rms deflections, frame {args.frame}",
+                   "npts": npts, "lmax": LMAX, "spin": SPIN, "eps": EPS32, "form": "fp32",
+                   "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "l2": "per-step working set larger than L2 (no flush)"},
+        "roofline": headline["roofline"], "clocks": headline["clocks"], "e2e": headline.get("e2e"),
+        "gpu_launches": launches_per_step * args.steps,
+        "forms": {k: {kk: vv for kk, vv in v.items() if kk not in ("e2e",)} for k, v in results.items()},
+        "input_generation_s": gen_s,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, wl, steps=1)
+    if dist is not None:
+        dist.destroy_process_group()
+    return line
+
+
+# ----------------------------------------------------------------------------- oracle arm
+def cpu_baseline(args, wl, steps: int = 1) -> dict:
+    """The FP64 CPU oracle pipeline (as it stands) on a bounded sample of the same workload:
+    every `cpu_ring_stride`-th ring for the two recursion stages, the full FFT stages, and
+    `cpu_sample_points` points for interpolation and spreading; each part's time is scaled to the
+    full workload linearly (ring count, point count)."""
+    import oracle as O
+
+    lmax, s = LMAX, SPIN
+    th, ph = wl["theta"], wl["phi"]
+    N = th.size
+    rng = np.random.default_rng(0)
+    sel = rng.choice(N, size=min(args.cpu_sample_points, N), replace=False)
+    P = O.plan_params(lmax, s, EPS32, th)
+    ring_sel = np.arange(0, P["nring"], args.cpu_ring_stride)
+    ring_scale = P["nring"] / ring_sel.size
+    pt_scale = N / sel.size
+    times = []
+    for _ in range(steps):
+        t = {}
+        a = time.perf_counter()
+        F = O.ring_synthesis(lmax, s, P["M"], wl["g"], wl["c"], P["theta_j"][ring_sel])
+        t["rings"] = (time.perf_counter() - a) * ring_scale
+        Ffull = np.zeros((P["nring"], 2 * P["M"] + 1), complex)
+        Ffull[ring_sel] = F
+        a = time.perf_counter()
+        H = O.theta_coefficients(P, Ffull)
+        G = O.fourier_to_grid(P, H)
+        t["fft"] = time.perf_counter() - a
+        _, _, tt, uu = O.point_coords(P, th[sel], ph[sel])
+        a = time.perf_counter()
+        f = O.interp(P, tt, uu, G)
+        t["interp"] = (time.perf_counter() - a) * pt_scale
+        a = time.perf_counter()
+        Gt = O.spread(P, tt, uu, f)
+        t["spread"] = (time.perf_counter() - a) * pt_scale
+        a = time.perf_counter()
+        Ht = O.grid_to_fourier(P, Gt)
+        Ft = O.theta_coefficients_adjoint(P, Ht)
+        t["fft_adj"] = time.perf_counter() - a
+        a = time.perf_counter()
+        O.ring_adjoint(lmax, s, P["M"], P["theta_j"][ring_sel], Ft[ring_sel])
+        t["rings_adj"] = (time.perf_counter() - a) * ring_scale
+        times.append(t)
+    tot = statistics.median(sum(t.values()) for t in times)
+    return {"value": N / tot / 1e6, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": (f"FP64 oracle pipeline at eps {EPS32:g} (W={P['W']}, L={P['L']}, M={P['M']}): "
+                       f"every {args.cpu_ring_stride}th ring for both recursions, full FFTs, "
+                       f"{sel.size} of {N} points for interp/spread; times scaled to the full workload"),
+            "est_seconds_per_step": tot, "parts_s": {k: round(v, 3) for k, v in times[-1].items()}}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    from paper_2603_17166_gb300 import synthetic
+
+    wl = synthetic.config2(frame=args.frame, step_arcmin=args.step_arcmin)
+    a = time.perf_counter()
+    base = cpu_baseline(args, wl, steps=max(1, args.steps))
+    wall = time.perf_counter() - a
+    return {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": base["est_seconds_per_step"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "spin-2 synthesis+adjoint, lmax 4096, ~4% field (same generator as ours)",
+                       "npts": int(wl["theta"].size), "eps": EPS32},
+            "cpu_baseline": {"kind": base["kind"], "cores": base["cores"], "sample": base["sample"],
+                             "value": base["value"], "unit": UNIT},
+            "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        line = run_ours(args, rank, world, local_rank)
+    if rank == 0 and line is not None:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

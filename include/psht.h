@@ -123,6 +123,18 @@ int psht_plan_rings(const psht_plan* plan, double* theta_j, double* w_j, int32_t
 int psht_plan_ring_coeffs(psht_plan* plan, const void* g, const void* c, void* F, void* stream);
 
 /*
+ * Stage timing.  psht_plan_profile(plan, 1) makes every later execute call record CUDA events on
+ * its stream around each stage (0 recursion, 1 Theta FFT, 2 phi FFT, 3 gather; adjoint: 4 scatter
+ * incl. grid clearing, 5 phi FFT, 6 Theta FFT, 7 recursion); 0 stops recording.
+ * psht_plan_stage_times synchronises the recorded events and writes, per stage, the summed
+ * milliseconds into ms[PSHT_NSTAGES] and the number of launches into calls[PSHT_NSTAGES] (either may
+ * be NULL), then clears the record.
+ */
+#define PSHT_NSTAGES 8
+int psht_plan_profile(psht_plan* plan, int enable);
+int psht_plan_stage_times(psht_plan* plan, double* ms, int64_t* calls);
+
+/*
  * One-shot forms with the paper's argument list (g, c, spin, lmax, theta, phi, eps): plan,
  * execute and destroy.  All pointers DEVICE.  Precision PSHT_AUTO.  Synchronise `stream`.
  */

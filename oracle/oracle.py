@@ -78,6 +78,7 @@ def _lib():
         lib.orc_direct_adjoint.argtypes = [I, I, L, P, P, P, P, P]
         lib.orc_interp.argtypes = [L, P, P, I, D, L, L, L, P, P]
         lib.orc_spread.argtypes = [L, P, P, P, I, D, L, L, L, P, P]
+        lib.orc_direct_adjoint_lm.argtypes = [I, L, P, P, P, I, P, P, P, P]
         lib.orc_num_threads.restype = I
         _lib_handle = lib
     return _lib_handle
@@ -196,6 +197,20 @@ def direct_adjoint(lmax: int, s: int, theta, phi, f):
     gt = np.zeros(nalm(lmax), dtype=np.complex128)
     ct = np.zeros(nalm(lmax), dtype=np.complex128)
     _lib().orc_direct_adjoint(lmax, s, theta.size, _ptr(theta), _ptr(phi), _ptr(f), _ptr(gt), _ptr(ct))
+    return gt, ct
+
+
+def direct_adjoint_lm(s: int, theta, phi, f, ls, ms):
+    """O1 adjoint restricted to selected (l, m >= 0): (g~, c~) at those coefficients only."""
+    theta = np.ascontiguousarray(theta, dtype=np.float64)
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    f = _c128(f)
+    ls = np.ascontiguousarray(ls, dtype=np.int32)
+    ms = np.ascontiguousarray(ms, dtype=np.int32)
+    gt = np.zeros(ls.size, dtype=np.complex128)
+    ct = np.zeros(ls.size, dtype=np.complex128)
+    _lib().orc_direct_adjoint_lm(s, theta.size, _ptr(theta), _ptr(phi), _ptr(f), ls.size, _ptr(ls), _ptr(ms),
+                                 _ptr(gt), _ptr(ct))
     return gt, ct
 
 

@@ -341,3 +341,48 @@ int orc_num_threads(void) {
   return 1;
 #endif
 }
+
+/*
+ * Selected outputs of the direct adjoint synthesis general: for each (l_k, m_k), m_k >= 0,
+ *   ut_{l,m}  = -sum_p f_p N_l d^l_{m,-s}(theta_p) e^{-i m phi_p}
+ *   ut_{l,-m} = -(-1)^(m-s) sum_p f_p N_l d^l_{m,s}(theta_p) e^{+i m phi_p}
+ * projected as in orc_ring_adjoint.  Cost per point O(l_k - max(m_k, s)), so the full point set
+ * of a large workload can be summed for coefficients close to the diagonal or of low degree.
+ */
+void orc_direct_adjoint_lm(int s, int64_t npts, const double* theta, const double* phi, const double* f, int nsel,
+                           const int* ls, const int* ms, double* gt, double* ct) {
+  for (int k = 0; k < nsel; ++k) {
+    const int l = ls[k], m = ms[k];
+    double ar = 0, ai = 0, br = 0, bi = 0;
+    if (l >= (m > s ? m : s)) {
+#pragma omp parallel reduction(+ : ar, ai, br, bi)
+      {
+        double* d1 = (double*)malloc(sizeof(double) * (l + 1));
+        double* d2 = (double*)malloc(sizeof(double) * (l + 1));
+#pragma omp for schedule(static)
+        for (int64_t p = 0; p < npts; ++p) {
+          double cb, ch, sh; half_angles(theta[p], &cb, &ch, &sh);
+          orc_wigner_d_column(l, m, -s, cb, ch, sh, d1);
+          orc_wigner_d_column(l, m, s, cb, ch, sh, d2);
+          const double cr = cos(m * phi[p]), si = sin(m * phi[p]);
+          const double fr = f[2 * p], fi = f[2 * p + 1];
+          /* f e^{-i m phi} and f e^{+i m phi} */
+          ar += d1[l] * (fr * cr + fi * si); ai += d1[l] * (fi * cr - fr * si);
+          br += d2[l] * (fr * cr - fi * si); bi += d2[l] * (fi * cr + fr * si);
+        }
+        free(d1); free(d2);
+      }
+    }
+    const double nl = sqrt((2.0 * l + 1.0) / (4.0 * M_PI));
+    const double sg = (((m - s) % 2) != 0) ? -1.0 : 1.0, sm = (m & 1) ? -1.0 : 1.0;
+    const double a_r = -nl * ar, a_i = -nl * ai, b_r = -sg * nl * br, b_i = -sg * nl * bi;
+    const double w_r = sm * b_r, w_i = -sm * b_i;
+    if (l < s) { gt[2 * k] = gt[2 * k + 1] = ct[2 * k] = ct[2 * k + 1] = 0.0; continue; }
+    if (m == 0) {
+      gt[2 * k] = a_r; gt[2 * k + 1] = 0.0; ct[2 * k] = a_i; ct[2 * k + 1] = 0.0;
+    } else {
+      gt[2 * k] = 0.5 * (a_r + w_r); gt[2 * k + 1] = 0.5 * (a_i + w_i);
+      ct[2 * k] = 0.5 * (a_i - w_i); ct[2 * k + 1] = -0.5 * (a_r - w_r);
+    }
+  }
+}

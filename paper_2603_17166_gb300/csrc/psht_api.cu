@@ -254,6 +254,11 @@ void destroy(Plan* p) {
   if (!p) return;
   cudaDeviceSynchronize();
   for (void* a : p->allocs) cudaFree(a);
+  for (auto& r : p->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (cudaEvent_t e : p->evpool) cudaEventDestroy(e);
   delete p;
 }
 
@@ -425,20 +430,47 @@ int guarded(F&& f) {
   }
 }
 
+cudaEvent_t take_event(Plan& p) {
+  if (!p.evpool.empty()) {
+    cudaEvent_t e = p.evpool.back();
+    p.evpool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  PSHT_CUDA_TRY(cudaEventCreate(&e));
+  return e;
+}
+
+// run fn() as stage `stage`, bracketed by events when profiling is on
+template <class F>
+void staged(Plan& p, int stage, cudaStream_t st, F&& fn) {
+  if (!p.profile) {
+    fn();
+    return;
+  }
+  Plan::StageRec r{stage, take_event(p), take_event(p)};
+  PSHT_CUDA_TRY(cudaEventRecord(r.a, st));
+  fn();
+  PSHT_CUDA_TRY(cudaEventRecord(r.b, st));
+  p.recs.push_back(r);
+}
+
 void run_synthesis(Plan& p, const void* g, const void* c, void* f, cudaStream_t st) {
-  launch_rec_synthesis(p, g, c, st);
-  launch_theta_synthesis(p, st);
-  launch_phi_synthesis(p, st);
-  launch_gather(p, f, st);
+  staged(p, 0, st, [&] { launch_rec_synthesis(p, g, c, st); });
+  staged(p, 1, st, [&] { launch_theta_synthesis(p, st); });
+  staged(p, 2, st, [&] { launch_phi_synthesis(p, st); });
+  staged(p, 3, st, [&] { launch_gather(p, f, st); });
 }
 
 void run_adjoint(Plan& p, const void* f, void* g, void* c, cudaStream_t st) {
   const size_t cb = p.prec == 64 ? 16 : 8;
-  PSHT_CUDA_TRY(cudaMemsetAsync(p.d_G, 0, (size_t)p.nrows * p.gstride * cb, st));
-  launch_scatter(p, f, st);
-  launch_phi_adjoint(p, st);
-  launch_theta_adjoint(p, st);
-  launch_rec_adjoint(p, g, c, st);
+  staged(p, 4, st, [&] {
+    PSHT_CUDA_TRY(cudaMemsetAsync(p.d_G, 0, (size_t)p.nrows * p.gstride * cb, st));
+    launch_scatter(p, f, st);
+  });
+  staged(p, 5, st, [&] { launch_phi_adjoint(p, st); });
+  staged(p, 6, st, [&] { launch_theta_adjoint(p, st); });
+  staged(p, 7, st, [&] { launch_rec_adjoint(p, g, c, st); });
 }
 
 void ensure_io(Plan& p) {
@@ -575,6 +607,36 @@ int psht_plan_ring_coeffs(psht_plan* plan, const void* g, const void* c, void* F
     PSHT_REQUIRE(plan && g && F, PSHT_EINVAL, "plan, g and F must not be NULL");
     launch_rec_synthesis(*plan->p, g, c, (cudaStream_t)stream);
     launch_ring_coeffs_export(*plan->p, F, (cudaStream_t)stream);
+  });
+}
+
+int psht_plan_profile(psht_plan* plan, int enable) {
+  return guarded([&] {
+    PSHT_REQUIRE(plan, PSHT_EINVAL, "plan must not be NULL");
+    plan->p->profile = enable != 0;
+  });
+}
+
+int psht_plan_stage_times(psht_plan* plan, double* ms, int64_t* calls) {
+  return guarded([&] {
+    PSHT_REQUIRE(plan, PSHT_EINVAL, "plan must not be NULL");
+    Plan& p = *plan->p;
+    double acc[PSHT_NSTAGES] = {0};
+    int64_t cnt[PSHT_NSTAGES] = {0};
+    for (auto& r : p.recs) {
+      PSHT_CUDA_TRY(cudaEventSynchronize(r.b));
+      float t = 0.f;
+      PSHT_CUDA_TRY(cudaEventElapsedTime(&t, r.a, r.b));
+      acc[r.stage] += t;
+      cnt[r.stage] += 1;
+      p.evpool.push_back(r.a);
+      p.evpool.push_back(r.b);
+    }
+    p.recs.clear();
+    for (int i = 0; i < PSHT_NSTAGES; ++i) {
+      if (ms) ms[i] = acc[i];
+      if (calls) calls[i] = cnt[i];
+    }
   });
 }
 

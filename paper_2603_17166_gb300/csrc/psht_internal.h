@@ -126,6 +126,14 @@ struct Plan {
   void* d_io_f = nullptr;
   size_t bytes = 0;
   std::vector<void*> allocs;
+  // stage timing (psht_plan_profile)
+  bool profile = false;
+  struct StageRec {
+    int stage;
+    cudaEvent_t a, b;
+  };
+  std::vector<StageRec> recs;
+  std::vector<cudaEvent_t> evpool;
 };
 
 // kernels / launchers ---------------------------------------------------------------------------

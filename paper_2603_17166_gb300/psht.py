@@ -58,6 +58,8 @@ def lib():
         L.psht_plan_rings.argtypes = [P, P, P, P]
         L.psht_synthesis.argtypes = [P, P, I, I, P, P, I64, D, P, P]
         L.psht_adjoint_synthesis.argtypes = [P, I, I, P, P, I64, D, P, P, P]
+        L.psht_plan_profile.argtypes = [P, I]
+        L.psht_plan_stage_times.argtypes = [P, P, P]
         L.psht_estimate_bytes.argtypes = [I, I, D, I64, D, U32]
         L.psht_estimate_bytes.restype = ctypes.c_size_t
         L.psht_last_error.restype = ctypes.c_char_p
@@ -173,6 +175,20 @@ class Plan:
         F = torch.empty((i["nring"], 2 * i["M"] + 1), dtype=self.cdtype, device="cuda")
         _check(lib().psht_plan_ring_coeffs(self._h, _ptr(g), _ptr(c), _ptr(F), _stream(stream)))
         return F
+
+    STAGES = ("rec_synthesis", "theta_synthesis", "phi_synthesis", "gather", "scatter", "phi_adjoint",
+              "theta_adjoint", "rec_adjoint")
+
+    def profile(self, enable: bool = True):
+        """Record CUDA events around each stage of later calls (psht_plan_profile)."""
+        _check(lib().psht_plan_profile(self._h, 1 if enable else 0))
+
+    def stage_times(self) -> dict:
+        """{stage: (summed ms, launches)} since the last call (psht_plan_stage_times)."""
+        ms = np.zeros(8)
+        calls = np.zeros(8, dtype=np.int64)
+        _check(lib().psht_plan_stage_times(self._h, ctypes.c_void_p(ms.ctypes.data), ctypes.c_void_p(calls.ctypes.data)))
+        return {name: (float(ms[i]), int(calls[i])) for i, name in enumerate(self.STAGES)}
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

@@ -291,3 +291,18 @@ def test_error_envelope_and_QU_asymmetry():
     P = O.plan_params(lmax, 2, 1e-5, th)
     d = O.pipeline_synthesis(P, g, None, th, ph, exact=True) - O.direct_synthesis(lmax, 2, g, None, th, ph)
     assert np.sqrt(np.mean(d.real ** 2)) > 1.1 * np.sqrt(np.mean(d.imag ** 2))
+
+
+def test_direct_adjoint_selected_coefficients():
+    """The restricted direct adjoint equals the full direct adjoint at the selected (l, m)."""
+    rng = np.random.default_rng(9)
+    lmax, s = 20, 2
+    th, ph = _cap(rng, 300, 0.8, "S")
+    f = rng.standard_normal(300) + 1j * rng.standard_normal(300)
+    gt, ct = O.direct_adjoint(lmax, s, th, ph, f)
+    sel = [(2, 0), (2, 2), (5, 1), (20, 20), (13, 7), (1, 0)]
+    ls, ms = np.array([a for a, _ in sel]), np.array([b for _, b in sel])
+    g2, c2 = O.direct_adjoint_lm(s, th, ph, f, ls, ms)
+    idx = O.alm_index(lmax, ls, ms)
+    assert np.abs(g2 - gt[idx]).max() < 1e-13 * np.abs(gt).max()
+    assert np.abs(c2 - ct[idx]).max() < 1e-13 * np.abs(ct).max()
