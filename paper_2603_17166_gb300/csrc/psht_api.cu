@@ -240,7 +240,7 @@ void layout(Plan& p, double theta_star) {
 size_t planned_bytes(const Plan& p) {
   const size_t cb = p.prec == 64 ? 16 : 8, rb = p.prec == 64 ? 8 : 4;
   size_t b = 0;
-  b += 3 * (size_t)p.nalm * rb;                                // recursion table
+  b += (size_t)rec_table_width(p.prec) * p.nalm * rb;           // recursion table
   b += (size_t)p.ncols * p.Lpad * cb;                          // ring coefficients
   b += (size_t)p.nrows * p.ncols * cb;                         // Theta-stage rows
   b += (size_t)p.nrows * p.gstride * cb;                       // grid
@@ -290,18 +290,22 @@ Plan* create(int spin, int lmax, const double* theta, const double* phi, int64_t
     layout(*p, p->pole > 0 ? red[0] : red[1]);
 
     // ring table
+    // A ring at colatitude theta_j > pi/2 is evaluated at pi - theta_j by the reflection
+    // d^l_{m,-s}(pi - b) = (-1)^(l+m) d^l_{m,s}(b), so every recurrence runs at b <= pi/2.
     std::vector<RingDev> rings(p->nring);
+    std::vector<int> refl(p->nring);
     for (int j = 0; j < p->nring; ++j) {
-      const double b = p->beta_j[j];
+      const double bj = p->beta_j[j];
+      const double b = bj <= 0.5 * M_PI ? bj : M_PI - bj;
+      refl[j] = p->pole > 0 ? (bj > 0.5 * M_PI) : (bj < 0.5 * M_PI);
+      p->has_refl |= refl[j];
       RingDev r;
-      // cos and half angles from beta (accurate near either pole)
-      r.x = p->pole > 0 ? cos(b) : -cos(b);
-      const double ch = p->pole > 0 ? cos(0.5 * b) : sin(0.5 * b);
-      const double sh = p->pole > 0 ? sin(0.5 * b) : cos(0.5 * b);
+      const double sb = sin(0.5 * b), ch = cos(0.5 * b);
+      r.omx = 2.0 * sb * sb;
       r.l2c = ch > 0 ? log2(ch) : -INFINITY;
-      r.l2s = sh > 0 ? log2(sh) : -INFINITY;
-      r.xhi = (float)r.x;
-      r.xlo = (float)(r.x - (double)r.xhi);
+      r.l2s = sb > 0 ? log2(sb) : -INFINITY;
+      r.ohi = (float)r.omx;
+      r.olo = (float)(r.omx - (double)r.ohi);
       rings[j] = r;
     }
     p->d_ring = (RingDev*)upload(*p, rings, st);
@@ -329,25 +333,29 @@ Plan* create(int spin, int lmax, const double* theta, const double* phi, int64_t
     }
     p->d_mseed = (MSeed*)upload(*p, ms, st);
     // active ring ranges and synthesis work items
-    std::vector<int2> mr(lmax + 1, make_int2(0, 0));
+    // per order m and ring part (0: direct, 1: reflected) the active rings M_j >= m form one
+    // contiguous range (M_j is unimodal in j, the reflection flag monotone)
+    std::vector<int2> mr(2 * (size_t)(lmax + 1), make_int2(0, 0));
     std::vector<RecItem> items;
     const int cap = p->syn_rpt * p->syn_threads;
     for (int m = 0; m <= p->M; ++m) {
-      int lo = -1, hi = -1;
-      for (int j = 0; j < p->nring; ++j)
-        if (p->Mj[j] >= m) {
-          if (lo < 0) lo = j;
-          hi = j + 1;
+      for (int part = 0; part < 2; ++part) {
+        int lo = -1, hi = -1;
+        for (int j = 0; j < p->nring; ++j)
+          if (p->Mj[j] >= m && refl[j] == part) {
+            if (lo < 0) lo = j;
+            hi = j + 1;
+          }
+        if (lo < 0) continue;
+        mr[(size_t)part * (lmax + 1) + m] = make_int2(lo, hi);
+        const int n = hi - lo, nchunk = (n + cap - 1) / cap;
+        for (int c = 0; c < nchunk; ++c) {
+          const int a = lo + (int)((int64_t)n * c / nchunk), b = lo + (int)((int64_t)n * (c + 1) / nchunk);
+          items.push_back(RecItem{m, a, b - a, part});
         }
-      if (lo < 0) continue;
-      mr[m] = make_int2(lo, hi);
-      const int n = hi - lo, nchunk = (n + cap - 1) / cap;
-      for (int c = 0; c < nchunk; ++c) {
-        const int a = lo + (int)((int64_t)n * c / nchunk), b = lo + (int)((int64_t)n * (c + 1) / nchunk);
-        items.push_back(RecItem{m, a, b - a, 0});
+        p->pairs += n;
+        p->triples += (int64_t)n * (lmax - std::max(m, spin) + 1);
       }
-      p->pairs += n;
-      p->triples += (int64_t)n * (lmax - std::max(m, spin) + 1);
     }
     p->d_mrange = (int2*)upload(*p, mr, st);
     p->nitems = (int)items.size();
@@ -391,7 +399,7 @@ Plan* create(int spin, int lmax, const double* theta, const double* phi, int64_t
     }
     // work buffers
     const size_t cb = prec == 64 ? 16 : 8, rb = prec == 64 ? 8 : 4;
-    p->d_rtab = dalloc(*p, 3 * (size_t)p->nalm * rb);
+    p->d_rtab = dalloc(*p, (size_t)rec_table_width(prec) * p->nalm * rb);
     p->d_F = dalloc(*p, (size_t)p->ncols * p->Lpad * cb);
     p->d_X = dalloc(*p, (size_t)p->nrows * p->ncols * cb);
     p->d_G = dalloc(*p, (size_t)p->nrows * p->gstride * cb);

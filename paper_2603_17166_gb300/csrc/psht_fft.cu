@@ -28,7 +28,7 @@ struct QPer {
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads) k_theta_syn(const typename Cx<T>::V* __restrict__ F, int Lpad,
                                                            const T* __restrict__ w, int nring,
-                                                           const int2* __restrict__ mrange, int s, int L,
+                                                           const int2* __restrict__ mrange, int mstride, int s, int L,
                                                            const T* __restrict__ sT, const T* __restrict__ sP, int M,
                                                            FftDev f2L, const typename Cx<T>::V* __restrict__ tw2L,
                                                            const int* __restrict__ perm2L, FftDev f4L,
@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(kFftThreads) k_theta_syn(const typename Cx<T>:
   const int mi = blockIdx.x;
   const int m = col_m(mi), am = m < 0 ? -m : m;
   const T sigma = ((s + am) & 1) ? (T)-1 : (T)1;
-  const int2 rr = mrange[am];
+  const int2 rr = mrange[am], rr1 = mrange[mstride + am];  // active rings: direct part, reflected part
   const int N2 = 2 * L, N4 = 4 * L;
   const V* Fc = F + (int64_t)mi * Lpad;
   for (int k = threadIdx.x; k < N2; k += blockDim.x) {
@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(kFftThreads) k_theta_syn(const typename Cx<T>:
       sg = sigma;
     }
     V v = mk((T)0, (T)0);
-    if (j < nring && j >= rr.x && j < rr.y) v = cscale(Fc[j], sg * w[j]);
+    if (j < nring && ((j >= rr.x && j < rr.y) || (j >= rr1.x && j < rr1.y))) v = cscale(Fc[j], sg * w[j]);
     buf[k] = v;
   }
   __syncthreads();
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(kFftThreads) k_theta_adj(const typename Cx<T>:
 // F[mi][j] (column layout, active rings only) -> out[j][m + M], zero outside the active range
 template <typename T>
 __global__ void k_export_rings(const typename Cx<T>::V* __restrict__ F, int Lpad, const int2* __restrict__ mrange,
-                               int nring, int M, typename Cx<T>::V* __restrict__ out) {
+                               int mstride, int nring, int M, typename Cx<T>::V* __restrict__ out) {
   using V = typename Cx<T>::V;
   const int ncols = 2 * M + 1;
   const int64_t tot = (int64_t)nring * ncols;
@@ -215,9 +215,9 @@ __global__ void k_export_rings(const typename Cx<T>::V* __restrict__ F, int Lpad
     const int j = (int)(e / ncols);
     const int m = (int)(e % ncols) - M;
     const int am = m < 0 ? -m : m;
-    const int2 rr = mrange[am];
+    const int2 rr = mrange[am], rr1 = mrange[mstride + am];
     V v = mk((T)0, (T)0);
-    if (j >= rr.x && j < rr.y) v = F[(int64_t)col_of(m) * Lpad + j];
+    if ((j >= rr.x && j < rr.y) || (j >= rr1.x && j < rr1.y)) v = F[(int64_t)col_of(m) * Lpad + j];
     out[e] = v;
   }
 }
@@ -237,14 +237,14 @@ void launch_theta_synthesis(Plan& p, cudaStream_t st) {
     using V = double2;
     set_smem<double>((const void*)k_theta_syn<double>, smem);
     k_theta_syn<double><<<p.ncols, kFftThreads, smem, st>>>(
-        (const V*)p.d_F, p.Lpad, (const double*)p.d_w, p.nring, p.d_mrange, p.spin, p.L, (const double*)p.d_sT,
+        (const V*)p.d_F, p.Lpad, (const double*)p.d_w, p.nring, p.d_mrange, p.lmax + 1, p.spin, p.L, (const double*)p.d_sT,
         (const double*)p.d_sP, p.M, p.f2L, (const V*)p.d_tw2L, p.d_perm2L, p.f4L, (const V*)p.d_tw4L, p.d_perm4L,
         p.r_lo, p.nrows, (V*)p.d_X, p.ncols);
   } else {
     using V = float2;
     set_smem<float>((const void*)k_theta_syn<float>, smem);
     k_theta_syn<float><<<p.ncols, kFftThreads, smem, st>>>(
-        (const V*)p.d_F, p.Lpad, (const float*)p.d_w, p.nring, p.d_mrange, p.spin, p.L, (const float*)p.d_sT,
+        (const V*)p.d_F, p.Lpad, (const float*)p.d_w, p.nring, p.d_mrange, p.lmax + 1, p.spin, p.L, (const float*)p.d_sT,
         (const float*)p.d_sP, p.M, p.f2L, (const V*)p.d_tw2L, p.d_perm2L, p.f4L, (const V*)p.d_tw4L, p.d_perm4L,
         p.r_lo, p.nrows, (V*)p.d_X, p.ncols);
   }
@@ -305,10 +305,10 @@ void launch_theta_adjoint(Plan& p, cudaStream_t st) {
 void launch_ring_coeffs_export(Plan& p, void* out, cudaStream_t st) {
   const int nth = 256, nbl = 152 * 8;
   if (p.prec == 64)
-    k_export_rings<double><<<nbl, nth, 0, st>>>((const double2*)p.d_F, p.Lpad, p.d_mrange, p.nring, p.M,
+    k_export_rings<double><<<nbl, nth, 0, st>>>((const double2*)p.d_F, p.Lpad, p.d_mrange, p.lmax + 1, p.nring, p.M,
                                                 (double2*)out);
   else
-    k_export_rings<float><<<nbl, nth, 0, st>>>((const float2*)p.d_F, p.Lpad, p.d_mrange, p.nring, p.M,
+    k_export_rings<float><<<nbl, nth, 0, st>>>((const float2*)p.d_F, p.Lpad, p.d_mrange, p.lmax + 1, p.nring, p.M,
                                                (float2*)out);
   PSHT_CUDA_TRY(cudaGetLastError());
 }

@@ -46,10 +46,10 @@ struct ScaleConst<float> {
 
 // ---------------------------------------------------------------------------------------------
 // device-side tables
-struct RingDev {
-  double x;         // cos(theta_j)
-  double l2c, l2s;  // log2 cos(theta_j/2), log2 sin(theta_j/2)  (-inf allowed)
-  float xhi, xlo;   // x split into two floats (FP32 form)
+struct RingDev {    // ring j evaluated at b = min(theta_j, pi - theta_j), its distance from the nearer pole
+  double omx;       // 1 - cos(b) = 2 sin^2(b/2)
+  double l2c, l2s;  // log2 cos(b/2), log2 sin(b/2)  (-inf allowed)
+  float ohi, olo;   // omx split into two floats (FP32 form)
 };
 
 struct MSeed {      // per order m, for the two recursions m' = -s (e1) and m' = +s (e2)
@@ -60,7 +60,8 @@ struct MSeed {      // per order m, for the two recursions m' = -s (e1) and m' =
 };
 
 struct RecItem {    // one CTA of the synthesis recursion: order m, rings [j0, j0 + nj)
-  int m, j0, nj, pad;
+  int m, j0, nj;
+  int refl;         // 1: the rings lie at theta > pi/2 and are evaluated at pi - theta (reflection)
 };
 
 struct TileItem {   // one CTA of the gather/scatter: a tile and a slice of its sorted points
@@ -98,8 +99,9 @@ struct Plan {
   // device memory
   RingDev* d_ring = nullptr;
   MSeed* d_mseed = nullptr;
-  int2* d_mrange = nullptr;     // active ring range [j_lo, j_hi) per m
-  void* d_rtab = nullptr;       // (A', B', kappa) per packed (l, m), precision T, 3 arrays
+  int2* d_mrange = nullptr;     // active ring range [j_lo, j_hi) per m: part 0 (theta <= pi/2), then part 1
+  int has_refl = 0;             // any ring at theta > pi/2 (part 1 non-empty)
+  void* d_rtab = nullptr;       // recurrence table per packed (l, m), rec_table_width(prec) arrays of T
   RecItem* d_items = nullptr;
   int nitems = 0;
   void* d_F = nullptr;          // complex T [ncols][Lpad]
@@ -137,6 +139,7 @@ struct Plan {
 };
 
 // kernels / launchers ---------------------------------------------------------------------------
+int rec_table_width(int prec);  // arrays of nalm values in the recurrence table
 void build_rec_table(Plan& p, cudaStream_t st);
 void launch_rec_synthesis(Plan& p, const void* g, const void* c, cudaStream_t st);
 void launch_rec_adjoint(Plan& p, void* g, void* c, cudaStream_t st);

@@ -1,19 +1,25 @@
 // Wigner-d recursion onto the apodised rings (synthesis, "K-REC") and its transpose
 // (adjoint, "K-REC-ADJ").
 //
-// Per order m and ring j the two columns e1_l = N_l d^l_{m,-s}(theta_j) and e2_l = N_l d^l_{m,s}(theta_j)
-// follow the textbook three-term recurrence in l (the appendix's eq. Ylm gives
-// sY_lm = N_l d^l_{m,-s} e^{im phi}).  The recurrence coefficients, N_l and a per-(l, m) rescaling
-// kappa_l are folded into one table so that one step is y_{l+1} = (A'_l x +- B'_l) y_l - y_{l-1},
-// with e_l = kappa_l y_l (kappa_{l0} = kappa_{l0+1} = 1, kappa_{l+1} = C_l kappa_{l-1}).
-// Seeds are Wigner's closed form at l0 = max(m, s), evaluated in FP64 in log2 form; values too
-// small for the working precision are carried as y * 2^(-F k) and join the sums once k = 0.
+// Per order m and ring j the two columns e1_l = N_l d^l_{m,-s}(beta_j) and e2_l = N_l d^l_{m,s}(beta_j)
+// (sY_lm = N_l d^l_{m,-s} e^{im phi}, appendix eq. Ylm; N_l = sqrt((2l+1)/4pi)) obey the textbook
+// three-term recurrence in l, written for the normalised columns as
+//     e_{l+1} = (A_l x +- B_l) e_l - C_l e_{l-1},   x = cos(beta_j),
+// and evaluated in Reinsch's form for x near 1: with D_l = A_l - 1 - C_l and Delta_l = e_l - e_{l-1},
+//     Delta_{l+1} = (D_l +- B_l - A_l (1 - x)) e_l + C_l Delta_l,   e_{l+1} = e_l + Delta_{l+1},
+// where 1 - x = 2 sin^2(beta/2) is exact on the host.  This keeps the recurrence accurate on the
+// rings next to the pole, where A x + B - 2 is far below the rounding of A x + B.  In the FP32
+// form A, D and 1 - x are carried as float pairs (hi + lo).
+// Rings of a south-pole plan sit at theta_j = pi - beta_j; they are evaluated at beta_j with
+// d^l_{m,-s}(pi - beta) = (-1)^(l+m) d^l_{m,s}(beta), i.e. with the two columns swapped and the
+// coefficients signed by (-1)^(l+m).
+// Seeds are Wigner's closed form at l0 = max(m, s) in FP64 log2 form; values too small for the
+// working precision are carried as e 2^(-F k) and join the sums once k = 0.
 //
-// Synthesis (eq. syn restricted to ring j):
-//   F_j[m]  = -sum_l kappa_l (g + i c)_lm y1_l,   F_j[-m] = -(-1)^s sum_l kappa_l (g* + i c*)_lm y2_l
-// Adjoint (transpose, then the adjoint synthesis general projection of Sec. I):
-//   ut_{l,m} = -kappa_l sum_j y1_l(j) Ft_j[m],  ut_{l,-m} = -(-1)^(m-s) kappa_l sum_j y2_l(j) Ft_j[-m]
-//   g~ = (ut_lm + (-1)^m conj ut_{l,-m})/2,  c~ = (ut_lm - (-1)^m conj ut_{l,-m})/(2i)
+// Synthesis (eq. syn on ring j):   F_j[m] = -sum_l (g + i c)_lm e1_l,   F_j[-m] = -(-1)^s sum_l (g* + i c*)_lm e2_l
+// Adjoint (transpose, then the projection of the adjoint synthesis general formula, Sec. I):
+//   ut_{l,m} = -sum_j e1_l(j) Ft_j[m],   ut_{l,-m} = -(-1)^(m-s) sum_j e2_l(j) Ft_j[-m]
+//   g~ = (ut_lm + (-1)^m conj ut_{l,-m})/2,   c~ = (ut_lm - (-1)^m conj ut_{l,-m})/(2i)
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -28,38 +34,44 @@ constexpr int kCH = 64;  // l values staged in shared memory per chunk
 __device__ __forceinline__ int64_t alm_base(int lmax, int m) { return (int64_t)m * (2 * lmax + 1 - m) / 2; }
 
 // ---------------------------------------------------------------------------------------------
-// table (A'_l, B'_l, kappa_l) for every packed (l, m); one thread per m, FP64 throughout.
+// recurrence table per packed (l, m), FP64 arithmetic, one thread per m.
+//   FP64 form: t[0] = A, t[1] = D, t[2] = B, t[3] = C
+//   FP32 form: t[0] = A_hi, t[1] = A_lo, t[2] = D_hi, t[3] = D_lo, t[4] = B, t[5] = C
 template <typename T>
-__global__ void k_rec_table(int lmax, int s, T* __restrict__ tA, T* __restrict__ tB, T* __restrict__ tK) {
+__global__ void k_rec_table(int lmax, int s, T* __restrict__ tab, int64_t nalm) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m > lmax) return;
   const int l0 = max(m, s);
   const int64_t base = alm_base(lmax, m);
-  for (int l = m; l < l0 && l <= lmax; ++l) {
-    tA[base + l] = 0;
-    tB[base + l] = 0;
-    tK[base + l] = 0;
-  }
   const double m2 = (double)m * m, s2 = (double)s * s;
-  double kprev = 1.0, kcur = 1.0;
-  for (int l = l0; l <= lmax; ++l) {
-    const double lp1 = l + 1.0;
-    const double a = lp1 * (2.0 * l + 1.0) / sqrt((lp1 * lp1 - m2) * (lp1 * lp1 - s2));
-    const double Ac = sqrt((2.0 * l + 3.0) / (2.0 * l + 1.0)) * a;
-    const double Bt = (l == 0) ? 0.0 : Ac * (double)m * (double)s / ((double)l * lp1);
-    double knext;
-    if (l == l0) {
-      knext = 1.0;
-    } else {
-      const double c = sqrt(((double)l * l - m2) * ((double)l * l - s2)) / ((double)l * (2.0 * l + 1.0));
-      const double C = sqrt((2.0 * l + 3.0) / (2.0 * l - 1.0)) * a * c;
-      knext = C * kprev;
+  for (int l = m; l <= lmax; ++l) {
+    double A = 0, B = 0, C = 0, D = 0;
+    if (l >= l0 && l < lmax) {
+      const double lp1 = l + 1.0;
+      const double a = lp1 * (2.0 * l + 1.0) / sqrt((lp1 * lp1 - m2) * (lp1 * lp1 - s2));
+      A = sqrt((2.0 * l + 3.0) / (2.0 * l + 1.0)) * a;
+      B = (l == 0) ? 0.0 : A * (double)m * (double)s / ((double)l * lp1);
+      if (l > l0) {
+        const double c = sqrt(((double)l * l - m2) * ((double)l * l - s2)) / ((double)l * (2.0 * l + 1.0));
+        C = sqrt((2.0 * l + 3.0) / (2.0 * l - 1.0)) * a * c;
+      }
+      D = (A - 1.0) - C;
     }
-    tK[base + l] = (T)kcur;
-    tA[base + l] = (T)(l < lmax ? Ac * kcur / knext : 0.0);
-    tB[base + l] = (T)(l < lmax ? Bt * kcur / knext : 0.0);
-    kprev = kcur;
-    kcur = knext;
+    const int64_t id = base + l;
+    if (sizeof(T) == 8) {
+      tab[id] = (T)A;
+      tab[nalm + id] = (T)D;
+      tab[2 * nalm + id] = (T)B;
+      tab[3 * nalm + id] = (T)C;
+    } else {
+      const float ah = (float)A, dh = (float)D;
+      tab[id] = ah;
+      tab[nalm + id] = (float)(A - (double)ah);
+      tab[2 * nalm + id] = dh;
+      tab[3 * nalm + id] = (float)(D - (double)dh);
+      tab[4 * nalm + id] = (float)B;
+      tab[5 * nalm + id] = (float)C;
+    }
   }
 }
 
@@ -108,48 +120,95 @@ __device__ __forceinline__ double seed_log2(double lbin, int p, int q, double l2
   return v;
 }
 
+// staged recurrence coefficients of one l, and the shared part t = D - A (1 - x) of the multiplier
 template <typename T>
-__device__ __forceinline__ T ring_ax(T A, const RingDev& r, T xr, T xlo);
+struct Coef;
 template <>
-__device__ __forceinline__ double ring_ax<double>(double A, const RingDev&, double x, double) {
-  return A * x;
+struct Coef<double> {
+  double A, D, B, C;
+  __device__ __forceinline__ double t(double omx, double) const { return fma(-A, omx, D); }
+};
+template <>
+struct Coef<float> {
+  float Ah, Al, Dh, Dl, B, C;
+  __device__ __forceinline__ float t(float oh, float ol) const {
+    return fmaf(-Ah, oh, Dh) + fmaf(-Ah, ol, fmaf(-Al, oh, Dl));
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ Coef<T> load_coef(const T* __restrict__ tab, int64_t nalm, int64_t id);
+template <>
+__device__ __forceinline__ Coef<double> load_coef<double>(const double* __restrict__ tab, int64_t nalm, int64_t id) {
+  return Coef<double>{tab[id], tab[nalm + id], tab[2 * nalm + id], tab[3 * nalm + id]};
 }
 template <>
-__device__ __forceinline__ float ring_ax<float>(float A, const RingDev&, float xhi, float xlo) {
-  // x carried as xhi + xlo so that the ring position is exact to FP64 level
-  return fmaf(A, xhi, A * xlo);
+__device__ __forceinline__ Coef<float> load_coef<float>(const float* __restrict__ tab, int64_t nalm, int64_t id) {
+  return Coef<float>{tab[id], tab[nalm + id], tab[2 * nalm + id], tab[3 * nalm + id], tab[4 * nalm + id],
+                     tab[5 * nalm + id]};
 }
 
 template <typename T>
-__device__ __forceinline__ void ring_x(const RingDev& r, T& x, T& xlo);
+__device__ __forceinline__ void ring_omx(const RingDev& r, T& oh, T& ol);
 template <>
-__device__ __forceinline__ void ring_x<double>(const RingDev& r, double& x, double& xlo) {
-  x = r.x;
-  xlo = 0.0;
+__device__ __forceinline__ void ring_omx<double>(const RingDev& r, double& oh, double& ol) {
+  oh = r.omx;
+  ol = 0.0;
 }
 template <>
-__device__ __forceinline__ void ring_x<float>(const RingDev& r, float& x, float& xlo) {
-  x = r.xhi;
-  xlo = r.xlo;
+__device__ __forceinline__ void ring_omx<float>(const RingDev& r, float& oh, float& ol) {
+  oh = r.ohi;
+  ol = r.olo;
+}
+
+// one Reinsch step of a column: Delta <- (t) e + C Delta, e <- e + Delta, with the rescale guard
+template <typename T>
+__device__ __forceinline__ void reinsch_step(T t, T C, T& e, T& d, int& k) {
+  d = fma(t, e, C * d);
+  e = e + d;
+  if (k > 0 && Rc<T>::big(e)) {
+    e *= Rc<T>::down();
+    d *= Rc<T>::down();
+    --k;
+  }
+}
+
+// staged a_lm combination for the two columns: north  P = g + i c (col 1), Q = g* + i c* (col 2);
+// south (reflected rings) P = (-1)^(l+m) (g* + i c*), Q = (-1)^(l+m) (g + i c)
+template <typename V, typename T>
+__device__ __forceinline__ void stage_pq(V gv, V cv, bool m0, bool refl, int lpm, V& P, V& Q) {
+  if (m0) {
+    gv.y = (T)0;
+    cv.y = (T)0;
+  }
+  V u = mk(gv.x - cv.y, gv.y + cv.x);
+  V v = mk(gv.x + cv.y, cv.x - gv.y);
+  if (refl) {
+    const T sg = (lpm & 1) ? (T)-1 : (T)1;
+    P = mk(sg * v.x, sg * v.y);
+    Q = mk(sg * u.x, sg * u.y);
+  } else {
+    P = u;
+    Q = v;
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
 // synthesis: one CTA per RecItem (order m, rings j0 .. j0+nj-1), RPT rings per thread.
 template <typename T, bool SPIN, int RPT>
 __global__ void __launch_bounds__(128) k_rec_syn(const RecItem* __restrict__ items, const RingDev* __restrict__ rings,
-                                                 const MSeed* __restrict__ mseed, const T* __restrict__ tA,
-                                                 const T* __restrict__ tB, const T* __restrict__ tK,
-                                                 const typename Cx<T>::V* __restrict__ g,
+                                                 const MSeed* __restrict__ mseed, const T* __restrict__ tab,
+                                                 int64_t nalm, const typename Cx<T>::V* __restrict__ g,
                                                  const typename Cx<T>::V* __restrict__ c, int lmax, int s,
                                                  typename Cx<T>::V* __restrict__ F, int Lpad) {
   using V = typename Cx<T>::V;
   const RecItem it = items[blockIdx.x];
   const int m = it.m;
   const MSeed sd = mseed[m];
-  __shared__ T sA[kCH], sB[kCH];
-  __shared__ V sU[kCH], sV[kCH];
+  __shared__ Coef<T> sC[kCH];
+  __shared__ V sP[kCH], sQ[kCH];
 
-  T x[RPT], xlo[RPT], y1[RPT], y1p[RPT], y2[RPT], y2p[RPT];
+  T oh[RPT], ol[RPT], e1[RPT], d1[RPT], e2[RPT], d2[RPT];
   T a0[RPT], a1[RPT], a2[RPT], a3[RPT];
   int k1[RPT], k2[RPT];
   bool any = false;
@@ -157,73 +216,56 @@ __global__ void __launch_bounds__(128) k_rec_syn(const RecItem* __restrict__ ite
   for (int r = 0; r < RPT; ++r) {
     const int jj = threadIdx.x + r * blockDim.x;
     a0[r] = a1[r] = a2[r] = a3[r] = (T)0;
-    y1p[r] = y2p[r] = (T)0;
     if (jj < it.nj) {
       const RingDev rg = rings[it.j0 + jj];
-      ring_x<T>(rg, x[r], xlo[r]);
-      seed_scaled<T>(seed_log2(sd.lbin, sd.p1, sd.q1, rg.l2c, rg.l2s), sd.sign1, y1[r], k1[r]);
-      if (SPIN) seed_scaled<T>(seed_log2(sd.lbin, sd.q1, sd.p1, rg.l2c, rg.l2s), sd.sign2, y2[r], k2[r]);
+      ring_omx<T>(rg, oh[r], ol[r]);
+      seed_scaled<T>(seed_log2(sd.lbin, sd.p1, sd.q1, rg.l2c, rg.l2s), sd.sign1, e1[r], k1[r]);
+      if (SPIN) seed_scaled<T>(seed_log2(sd.lbin, sd.q1, sd.p1, rg.l2c, rg.l2s), sd.sign2, e2[r], k2[r]);
       any = true;
     } else {
-      x[r] = xlo[r] = y1[r] = y2[r] = (T)0;
+      oh[r] = ol[r] = e1[r] = e2[r] = (T)0;
       k1[r] = k2[r] = 1;
     }
+    d1[r] = e1[r];  // Delta_{l0} = e_{l0} - e_{l0-1}, e_{l0-1} = 0
+    d2[r] = e2[r];
   }
   const bool warp_any = __any_sync(0xffffffffu, any);
   const int64_t base = alm_base(lmax, m);
   const bool m0 = (m == 0);
+  const bool rf = it.refl != 0;
 
   for (int lc = sd.l0; lc <= lmax; lc += kCH) {
     const int n = min(kCH, lmax - lc + 1);
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const int64_t id = base + lc + i;
-      const T kap = tK[id];
-      sA[i] = tA[id];
-      sB[i] = tB[id];
-      V gv = g[id];
-      V cv = c ? c[id] : mk((T)0, (T)0);
-      if (m0) {
-        gv.y = (T)0;
-        cv.y = (T)0;
-      }
-      sU[i] = mk(kap * (gv.x - cv.y), kap * (gv.y + cv.x));  // kappa (g + i c)
-      sV[i] = mk(kap * (gv.x + cv.y), kap * (cv.x - gv.y));  // kappa (g* + i c*)
+      sC[i] = load_coef<T>(tab, nalm, id);
+      V P, Q;
+      stage_pq<V, T>(g[id], c ? c[id] : mk((T)0, (T)0), m0, rf, lc + i + m, P, Q);
+      sP[i] = P;
+      sQ[i] = Q;
     }
     __syncthreads();
     if (!warp_any) continue;
     for (int i = 0; i < n; ++i) {
-      const T A = sA[i], B = sB[i];
-      const V u = sU[i], v = sV[i];
+      const Coef<T> cf = sC[i];
+      const V P = sP[i], Q = sQ[i];
 #pragma unroll
       for (int r = 0; r < RPT; ++r) {
-        const T o1 = (k1[r] == 0) ? y1[r] : (T)0;
-        a0[r] = fma(u.x, o1, a0[r]);
-        a1[r] = fma(u.y, o1, a1[r]);
-        const T ax = ring_ax<T>(A, RingDev{}, x[r], xlo[r]);
-        const T n1 = fma(ax + B, y1[r], -y1p[r]);
-        y1p[r] = y1[r];
-        y1[r] = n1;
+        const T o1 = (k1[r] == 0) ? e1[r] : (T)0;
+        a0[r] = fma(P.x, o1, a0[r]);
+        a1[r] = fma(P.y, o1, a1[r]);
+        const T t = cf.t(oh[r], ol[r]);
         if (SPIN) {
-          const T o2 = (k2[r] == 0) ? y2[r] : (T)0;
-          a2[r] = fma(v.x, o2, a2[r]);
-          a3[r] = fma(v.y, o2, a3[r]);
-          const T n2 = fma(ax - B, y2[r], -y2p[r]);
-          y2p[r] = y2[r];
-          y2[r] = n2;
-          if (k2[r] > 0 && Rc<T>::big(n2)) {
-            y2[r] *= Rc<T>::down();
-            y2p[r] *= Rc<T>::down();
-            --k2[r];
-          }
+          const T o2 = (k2[r] == 0) ? e2[r] : (T)0;
+          a2[r] = fma(Q.x, o2, a2[r]);
+          a3[r] = fma(Q.y, o2, a3[r]);
+          reinsch_step<T>(t + cf.B, cf.C, e1[r], d1[r], k1[r]);
+          reinsch_step<T>(t - cf.B, cf.C, e2[r], d2[r], k2[r]);
         } else {
-          a2[r] = fma(v.x, o1, a2[r]);
-          a3[r] = fma(v.y, o1, a3[r]);
-        }
-        if (k1[r] > 0 && Rc<T>::big(n1)) {
-          y1[r] *= Rc<T>::down();
-          y1p[r] *= Rc<T>::down();
-          --k1[r];
+          a2[r] = fma(Q.x, o1, a2[r]);
+          a3[r] = fma(Q.y, o1, a3[r]);
+          reinsch_step<T>(t, cf.C, e1[r], d1[r], k1[r]);
         }
       }
     }
@@ -234,8 +276,11 @@ __global__ void __launch_bounds__(128) k_rec_syn(const RecItem* __restrict__ ite
     const int jj = threadIdx.x + r * blockDim.x;
     if (jj < it.nj) {
       const int j = it.j0 + jj;
-      F[(int64_t)col_of(m) * Lpad + j] = mk(-a0[r], -a1[r]);
-      if (!m0) F[(int64_t)col_of(-m) * Lpad + j] = mk(sgn_s * a2[r], sgn_s * a3[r]);
+      // north: F[m] <- column 1, F[-m] <- column 2; south: swapped
+      const V fpos = rf ? mk(-a2[r], -a3[r]) : mk(-a0[r], -a1[r]);
+      const V fneg = rf ? mk(sgn_s * a0[r], sgn_s * a1[r]) : mk(sgn_s * a2[r], sgn_s * a3[r]);
+      F[(int64_t)col_of(m) * Lpad + j] = fpos;
+      if (!m0) F[(int64_t)col_of(-m) * Lpad + j] = fneg;
     }
   }
 }
@@ -251,15 +296,16 @@ __device__ __forceinline__ T warp_sum(T v) {
 
 template <typename T, bool SPIN, int RPT>
 __global__ void __launch_bounds__(512) k_rec_adj(const RingDev* __restrict__ rings, const MSeed* __restrict__ mseed,
-                                                 const int2* __restrict__ mrange, const T* __restrict__ tA,
-                                                 const T* __restrict__ tB, const T* __restrict__ tK,
-                                                 const typename Cx<T>::V* __restrict__ Ft, int Lpad, int lmax, int s,
-                                                 int M, typename Cx<T>::V* __restrict__ gt,
+                                                 const int2* __restrict__ mrange, const T* __restrict__ tab,
+                                                 int64_t nalm, const typename Cx<T>::V* __restrict__ Ft, int Lpad,
+                                                 int lmax, int s, int M, int refl, int accumulate,
+                                                 typename Cx<T>::V* __restrict__ gt,
                                                  typename Cx<T>::V* __restrict__ ct) {
   using V = typename Cx<T>::V;
   const int m = blockIdx.x;
   const int64_t base = alm_base(lmax, m);
-  if (m > M) {  // beyond the polar-optimisation cutoff on every ring: exact transpose of a zero block
+  if (m > M) {  // beyond the polar-optimisation cutoff on every ring: transpose of a zero block
+    if (accumulate) return;
     for (int l = m + threadIdx.x; l <= lmax; l += blockDim.x) {
       gt[base + l] = mk((T)0, (T)0);
       if (ct) ct[base + l] = mk((T)0, (T)0);
@@ -270,38 +316,42 @@ __global__ void __launch_bounds__(512) k_rec_adj(const RingDev* __restrict__ rin
   const int2 rr = mrange[m];
   const int nact = rr.y - rr.x;
   constexpr int NW = 512 / 32;
-  __shared__ T sA[kCH], sB[kCH], sK[kCH];
+  __shared__ Coef<T> sC[kCH];
   __shared__ T red[NW][kCH][4];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = blockDim.x >> 5;
-  for (int l = m + threadIdx.x; l < sd.l0 && l <= lmax; l += blockDim.x) {
+  for (int l = m + threadIdx.x; !accumulate && l < sd.l0 && l <= lmax; l += blockDim.x) {
     gt[base + l] = mk((T)0, (T)0);
     if (ct) ct[base + l] = mk((T)0, (T)0);
   }
+  const bool m0 = (m == 0);
+  const bool rf = refl != 0;
 
-  T x[RPT], xlo[RPT], y1[RPT], y1p[RPT], y2[RPT], y2p[RPT];
-  V fp[RPT], fm[RPT];
+  T oh[RPT], ol[RPT], e1[RPT], d1[RPT], e2[RPT], d2[RPT];
+  V f1[RPT], f2[RPT];  // ring values paired with column 1 / column 2
   int k1[RPT], k2[RPT];
   bool any = false;
-  const bool m0 = (m == 0);
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
     const int jj = threadIdx.x + r * blockDim.x;
-    y1p[r] = y2p[r] = (T)0;
     if (jj < nact) {
       const int j = rr.x + jj;
       const RingDev rg = rings[j];
-      ring_x<T>(rg, x[r], xlo[r]);
-      seed_scaled<T>(seed_log2(sd.lbin, sd.p1, sd.q1, rg.l2c, rg.l2s), sd.sign1, y1[r], k1[r]);
-      if (SPIN) seed_scaled<T>(seed_log2(sd.lbin, sd.q1, sd.p1, rg.l2c, rg.l2s), sd.sign2, y2[r], k2[r]);
-      fp[r] = Ft[(int64_t)col_of(m) * Lpad + j];
-      fm[r] = m0 ? mk((T)0, (T)0) : Ft[(int64_t)col_of(-m) * Lpad + j];
+      ring_omx<T>(rg, oh[r], ol[r]);
+      seed_scaled<T>(seed_log2(sd.lbin, sd.p1, sd.q1, rg.l2c, rg.l2s), sd.sign1, e1[r], k1[r]);
+      if (SPIN) seed_scaled<T>(seed_log2(sd.lbin, sd.q1, sd.p1, rg.l2c, rg.l2s), sd.sign2, e2[r], k2[r]);
+      const V fp = Ft[(int64_t)col_of(m) * Lpad + j];
+      const V fm = m0 ? mk((T)0, (T)0) : Ft[(int64_t)col_of(-m) * Lpad + j];
+      f1[r] = rf ? fm : fp;
+      f2[r] = rf ? fp : fm;
       any = true;
     } else {
-      x[r] = xlo[r] = y1[r] = y2[r] = (T)0;
+      oh[r] = ol[r] = e1[r] = e2[r] = (T)0;
       k1[r] = k2[r] = 1;
-      fp[r] = fm[r] = mk((T)0, (T)0);
+      f1[r] = f2[r] = mk((T)0, (T)0);
     }
+    d1[r] = e1[r];
+    d2[r] = e2[r];
   }
   const bool warp_any = __any_sync(0xffffffffu, any);
   const T sg = (((m - s) & 1) ? (T)1 : (T)-1);  // -(-1)^(m-s)
@@ -310,46 +360,28 @@ __global__ void __launch_bounds__(512) k_rec_adj(const RingDev* __restrict__ rin
   for (int lc = sd.l0; lc <= lmax; lc += kCH) {
     const int n = min(kCH, lmax - lc + 1);
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const int64_t id = base + lc + i;
-      sA[i] = tA[id];
-      sB[i] = tB[id];
-      sK[i] = tK[id];
-    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sC[i] = load_coef<T>(tab, nalm, base + lc + i);
     __syncthreads();
     for (int i = 0; i < n; ++i) {
       T p0 = 0, p1 = 0, p2 = 0, p3 = 0;
       if (warp_any) {
-        const T A = sA[i], B = sB[i];
+        const Coef<T> cf = sC[i];
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
-          const T o1 = (k1[r] == 0) ? y1[r] : (T)0;
-          p0 = fma(o1, fp[r].x, p0);
-          p1 = fma(o1, fp[r].y, p1);
-          const T ax = ring_ax<T>(A, RingDev{}, x[r], xlo[r]);
-          const T n1 = fma(ax + B, y1[r], -y1p[r]);
-          y1p[r] = y1[r];
-          y1[r] = n1;
+          const T o1 = (k1[r] == 0) ? e1[r] : (T)0;
+          p0 = fma(o1, f1[r].x, p0);
+          p1 = fma(o1, f1[r].y, p1);
+          const T t = cf.t(oh[r], ol[r]);
           if (SPIN) {
-            const T o2 = (k2[r] == 0) ? y2[r] : (T)0;
-            p2 = fma(o2, fm[r].x, p2);
-            p3 = fma(o2, fm[r].y, p3);
-            const T n2 = fma(ax - B, y2[r], -y2p[r]);
-            y2p[r] = y2[r];
-            y2[r] = n2;
-            if (k2[r] > 0 && Rc<T>::big(n2)) {
-              y2[r] *= Rc<T>::down();
-              y2p[r] *= Rc<T>::down();
-              --k2[r];
-            }
+            const T o2 = (k2[r] == 0) ? e2[r] : (T)0;
+            p2 = fma(o2, f2[r].x, p2);
+            p3 = fma(o2, f2[r].y, p3);
+            reinsch_step<T>(t + cf.B, cf.C, e1[r], d1[r], k1[r]);
+            reinsch_step<T>(t - cf.B, cf.C, e2[r], d2[r], k2[r]);
           } else {
-            p2 = fma(o1, fm[r].x, p2);
-            p3 = fma(o1, fm[r].y, p3);
-          }
-          if (k1[r] > 0 && Rc<T>::big(n1)) {
-            y1[r] *= Rc<T>::down();
-            y1p[r] *= Rc<T>::down();
-            --k1[r];
+            p2 = fma(o1, f2[r].x, p2);
+            p3 = fma(o1, f2[r].y, p3);
+            reinsch_step<T>(t, cf.C, e1[r], d1[r], k1[r]);
           }
         }
         p0 = warp_sum(p0);
@@ -373,19 +405,36 @@ __global__ void __launch_bounds__(512) k_rec_adj(const RingDev* __restrict__ rin
         q2 += red[w][i][2];
         q3 += red[w][i][3];
       }
-      const T kap = sK[i];
-      // ut_{l,m} = -kappa (q0 + i q1);  ut_{l,-m} = -(-1)^(m-s) kappa (q2 + i q3)
-      const T ar = -kap * q0, ai = -kap * q1;
-      const T br = sg * kap * q2, bi = sg * kap * q3;
-      const int64_t id = base + lc + i;
+      const int l = lc + i;
+      // sums against d_{m,-s}(theta) (Qp) and d_{m,s}(theta) (Qm); reflected rings swap the columns
+      // and carry (-1)^(l+m)
+      T Qpr = q0, Qpi = q1, Qmr = q2, Qmi = q3;
+      if (rf) {
+        const T sl = ((l + m) & 1) ? (T)-1 : (T)1;
+        Qpr = sl * q2;
+        Qpi = sl * q3;
+        Qmr = sl * q0;
+        Qmi = sl * q1;
+      }
+      // ut_{l,m} = -Qp;  ut_{l,-m} = -(-1)^(m-s) Qm
+      const T ar = -Qpr, ai = -Qpi;
+      const T br = sg * Qmr, bi = sg * Qmi;
+      const int64_t id = base + l;
+      V gv, cv;
       if (m0) {
-        gt[id] = mk(ar, (T)0);
-        if (ct) ct[id] = mk(ai, (T)0);
+        gv = mk(ar, (T)0);
+        cv = mk(ai, (T)0);
       } else {
         const T wr = sm * br, wi = -sm * bi;  // (-1)^m conj(ut_{l,-m})
-        gt[id] = mk((T)0.5 * (ar + wr), (T)0.5 * (ai + wi));
-        if (ct) ct[id] = mk((T)0.5 * (ai - wi), (T)-0.5 * (ar - wr));
+        gv = mk((T)0.5 * (ar + wr), (T)0.5 * (ai + wi));
+        cv = mk((T)0.5 * (ai - wi), (T)-0.5 * (ar - wr));
       }
+      if (accumulate) {  // the projection is linear: the second ring part adds its share
+        gv = cadd(gv, gt[id]);
+        if (ct) cv = cadd(cv, ct[id]);
+      }
+      gt[id] = gv;
+      if (ct) ct[id] = cv;
     }
   }
 }
@@ -393,22 +442,20 @@ __global__ void __launch_bounds__(512) k_rec_adj(const RingDev* __restrict__ rin
 template <typename T, bool SPIN, int RPT>
 void launch_syn_t(Plan& p, const void* g, const void* c, cudaStream_t st) {
   using V = typename Cx<T>::V;
-  const T* tA = (const T*)p.d_rtab;
-  const T* tB = tA + p.nalm;
-  const T* tK = tB + p.nalm;
-  k_rec_syn<T, SPIN, RPT><<<p.nitems, 128, 0, st>>>(p.d_items, p.d_ring, p.d_mseed, tA, tB, tK, (const V*)g,
-                                                     (const V*)c, p.lmax, p.spin, (V*)p.d_F, p.Lpad);
+  k_rec_syn<T, SPIN, RPT><<<p.nitems, 128, 0, st>>>(p.d_items, p.d_ring, p.d_mseed, (const T*)p.d_rtab, p.nalm,
+                                                     (const V*)g, (const V*)c, p.lmax, p.spin, (V*)p.d_F, p.Lpad);
 }
 
 template <typename T, bool SPIN, int RPT>
 void launch_adj_t(Plan& p, void* g, void* c, cudaStream_t st) {
   using V = typename Cx<T>::V;
-  const T* tA = (const T*)p.d_rtab;
-  const T* tB = tA + p.nalm;
-  const T* tK = tB + p.nalm;
-  k_rec_adj<T, SPIN, RPT><<<p.lmax + 1, p.adj_threads, 0, st>>>(p.d_ring, p.d_mseed, p.d_mrange, tA, tB, tK,
-                                                                (const V*)p.d_F, p.Lpad, p.lmax, p.spin, p.M,
-                                                                (V*)g, (V*)c);
+  // one launch per ring part (rings at theta <= pi/2, then reflected rings at theta > pi/2)
+  for (int part = 0; part < 2; ++part) {
+    if (part == 1 && !p.has_refl) break;
+    k_rec_adj<T, SPIN, RPT><<<p.lmax + 1, p.adj_threads, 0, st>>>(
+        p.d_ring, p.d_mseed, p.d_mrange + part * (p.lmax + 1), (const T*)p.d_rtab, p.nalm, (const V*)p.d_F, p.Lpad,
+        p.lmax, p.spin, p.M, part, part, (V*)g, (V*)c);
+  }
 }
 
 template <typename T, bool SPIN>
@@ -431,15 +478,12 @@ void launch_adj_s(Plan& p, void* g, void* c, cudaStream_t st) {
 
 }  // namespace
 
+int rec_table_width(int prec) { return prec == 64 ? 4 : 6; }
+
 void build_rec_table(Plan& p, cudaStream_t st) {
   const int nth = 128, nbl = (p.lmax + 1 + nth - 1) / nth;
-  if (p.prec == 64) {
-    double* t = (double*)p.d_rtab;
-    k_rec_table<double><<<nbl, nth, 0, st>>>(p.lmax, p.spin, t, t + p.nalm, t + 2 * p.nalm);
-  } else {
-    float* t = (float*)p.d_rtab;
-    k_rec_table<float><<<nbl, nth, 0, st>>>(p.lmax, p.spin, t, t + p.nalm, t + 2 * p.nalm);
-  }
+  if (p.prec == 64) k_rec_table<double><<<nbl, nth, 0, st>>>(p.lmax, p.spin, (double*)p.d_rtab, p.nalm);
+  else k_rec_table<float><<<nbl, nth, 0, st>>>(p.lmax, p.spin, (float*)p.d_rtab, p.nalm);
   PSHT_CUDA_TRY(cudaGetLastError());
 }
 

@@ -197,3 +197,25 @@ def test_invalid_arguments_are_rejected():
         Plan(0, 8, bad, ph, 1e-8)
     with pytest.raises(PshtError):
         Plan(0, 8, th, ph, 1e-9, precision="fp32")   # FP32 form needs eps >= 1e-7
+
+
+@pytest.mark.parametrize("prec,eps", [("fp32", 1e-5), ("fp64", 1e-9)])
+def test_full_sky_both_poles_reflection(prec, eps):
+    """Full-sky plan with points next to both poles: rings beyond the equator run reflected."""
+    rng = np.random.default_rng(8)
+    lmax, s = 48, 2
+    th = np.concatenate([np.arccos(rng.uniform(0.98, 1.0, 600)), math.pi - np.arccos(rng.uniform(0.98, 1.0, 600)),
+                         np.arccos(rng.uniform(-1, 1, 600))])
+    ph = rng.uniform(0, 2 * math.pi, th.size)
+    g, c = _alm(rng, lmax, s), _alm(rng, lmax, s)
+    plan = _plan(s, lmax, th, ph, eps, prec)
+    assert plan.info["full_sky"] == 1
+    f = plan.synthesis(_cu(g, plan), _cu(c, plan)).cpu().numpy().astype(np.complex128)
+    ref = O.direct_synthesis(lmax, s, g, c, th, ph)
+    assert O.rel_l2(f, ref) <= 10 * eps
+    gt, ct = plan.adjoint(_cu(ref, plan))
+    gt1, ct1 = O.direct_adjoint(lmax, s, th, ph, ref)
+    _, m = O.lm_of_index(lmax)
+    wgt = np.tile(np.where(m == 0, 1.0, 2.0), 2)
+    got = np.concatenate([gt.cpu().numpy(), ct.cpu().numpy()]).astype(np.complex128)
+    assert O.rel_l2(got, np.concatenate([gt1, ct1]), wgt) <= 10 * eps

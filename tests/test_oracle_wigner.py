@@ -130,3 +130,16 @@ def test_orthonormality_gauss_legendre(s):
             Y[a, i * nph:(i + 1) * nph] = d * np.exp(1j * m * phis) * math.sqrt(w[i] * 2 * math.pi / nph)
     gram = Y @ Y.conj().T
     assert np.abs(gram - np.eye(len(idx))).max() < 1e-13
+
+
+def test_reflection_identity():
+    """d^l_{m,-s}(pi - b) = (-1)^(l+m) d^l_{m,s}(b): the symmetry the CUDA recursion uses to run
+    every ring at a distance <= pi/2 from a pole (follows from the appendix's d(pi + b) relation
+    and d^l_{m'm}(-b) = d^l_{mm'}(b))."""
+    for l in range(0, 10):
+        for m in range(0, l + 1):
+            for s in range(0, l + 1):
+                for b in (0.2, 1.1, 2.3):
+                    lhs = wigner_explicit(l, m, -s, math.pi - b)
+                    rhs = (-1) ** (l + m) * wigner_explicit(l, m, s, b)
+                    assert abs(lhs - rhs) < 1e-14
