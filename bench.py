@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--frame", default="R", choices=["R", "S"])
     ap.add_argument("--step-arcmin", type=float, default=0.5)
     ap.add_argument("--steps64", type=int, default=3)
+    ap.add_argument("--forms", default="fp32,fp64", help="comma list of forms to time (fp32 is the headline)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-points", type=int, default=1_000_000)
@@ -165,7 +166,10 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
     results = {}
     launches_per_step = 8
-    forms = [("fp32", EPS32, args.steps), ("fp64", EPS64, max(1, args.steps64))]
+    want = set(args.forms.split(","))
+    forms = [f for f in (("fp32", EPS32, args.steps), ("fp64", EPS64, max(1, args.steps64))) if f[0] in want]
+    if not forms or forms[0][0] != "fp32":
+        raise SystemExit("--forms must include fp32 (the headline form)")
     headline = None
     for name, eps, K in forms:
         t0 = time.time()
@@ -189,14 +193,15 @@ def run_ours(args, rank, world, local_rank):
         clk = ClockSampler(local_rank)
         clk.start()
         plan.profile(True)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(K):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+        evs[0].record(stream)
+        for k in range(K):
             plan.synthesis(g, c, out=f, stream=stream)
             plan.adjoint(f, g_out=gt, c_out=ct, stream=stream)
-        e1.record(stream)
+            evs[k + 1].record(stream)
+        e0, e1 = evs[0], evs[-1]
         torch.cuda.synchronize(dev)
+        step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(K)]
         barrier()
         plan.profile(False)
         clocks = clk.stop()
@@ -216,6 +221,7 @@ def run_ours(args, rank, world, local_rank):
         peak = alu_peak_tflops(64 if name == "fp64" else 32)
         per_stage = {k: round(v[0] / max(v[1], 1), 4) for k, v in stages.items()}
         entry = dict(value=value, ms_per_step=ms_step, steps=K, warmup=W, eps=eps, plan_s=plan_s,
+                     step_ms_min=min(step_ms), step_ms_max=max(step_ms),
                      stage_ms=per_stage, clocks=clocks,
                      plan=dict(L=info["L"], M=info["M"], W=info["W"], nTheta=info["nTheta"], nphi=info["nphi"],
                                nrows=info["nrows"], theta_star_deg=math.degrees(info["theta_star"]),

@@ -225,10 +225,15 @@ void layout(Plan& p, double theta_star) {
   // launch shapes of the recursion
   p.syn_rpt = (p.prec == 64) ? 1 : 4;
   p.syn_threads = 128;
-  int rpt = (p.prec == 64) ? 1 : 2;
-  while (rpt * 512 < p.nring && rpt < 8) rpt *= 2;
-  p.adj_rpt = rpt;
-  p.adj_threads = std::min(512, ((p.nring + rpt - 1) / rpt + 31) / 32 * 32);
+  // adjoint: all active rings of one order m in one CTA, (rings per thread, threads) from the
+  // instantiated shapes, more rings per thread in FP32 to amortise the per-l warp reduction
+  if (p.prec == 32) {
+    p.adj_rpt = 8;
+    p.adj_threads = p.nring <= 1024 ? 128 : (p.nring <= 2048 ? 256 : 512);
+  } else {
+    p.adj_rpt = p.nring <= 1024 ? 4 : 8;
+    p.adj_threads = p.nring <= 512 ? 128 : (p.nring <= 2048 ? 256 : 512);
+  }
   PSHT_REQUIRE(p.nring <= 8 * 512, PSHT_ENOTSUP, "more than 4096 rings (lmax theta* too large for this build)");
   const int maxlen = max_fft_len(p.prec);
   PSHT_REQUIRE(p.nTheta <= maxlen, PSHT_ENOTSUP,

@@ -29,19 +29,20 @@ struct Error {
   } while (0)
 
 // ---------------------------------------------------------------------------------------------
-// constants of the scaled recursion.  A value is held as y * 2^(-SCALE_F * k) with k >= 0;
-// while k > 0 the true value is below 2^(SCALE_R - SCALE_F) and its contribution is dropped.
+// constants of the scaled recursion.  A value is held as y * 2^(-F k) with k >= 0; while k > 0 the
+// true value is below 2^(R_EXP - F) and its contribution is dropped.  The rescale test runs every
+// 4 steps of l, so values may pass 2^R_EXP by the growth of 4 steps (< 2^32) before rescaling.
 template <typename T>
 struct ScaleConst;
 template <>
 struct ScaleConst<double> {
   static constexpr int F = 500;      // exponent step of one rescale
-  static constexpr int R_EXP = 400;  // rescale when |y| >= 2^400
+  static constexpr int R_EXP = 400;  // rescale when |y| >= 2^400; dropped region below 2^-100
 };
 template <>
 struct ScaleConst<float> {
   static constexpr int F = 80;
-  static constexpr int R_EXP = 50;   // threshold of the dropped region: 2^(50-80) = 2^-30
+  static constexpr int R_EXP = 20;   // dropped region below 2^(20-80) = 2^-60
 };
 
 // ---------------------------------------------------------------------------------------------

@@ -161,11 +161,15 @@ __device__ __forceinline__ void ring_omx<float>(const RingDev& r, float& oh, flo
   ol = r.olo;
 }
 
-// one Reinsch step of a column: Delta <- (t) e + C Delta, e <- e + Delta, with the rescale guard
+// one Reinsch step of a column: Delta <- t e + C Delta, e <- e + Delta
 template <typename T>
-__device__ __forceinline__ void reinsch_step(T t, T C, T& e, T& d, int& k) {
+__device__ __forceinline__ void reinsch_step(T t, T C, T& e, T& d) {
   d = fma(t, e, C * d);
   e = e + d;
+}
+// rescale guard, run once per quad of l steps while a column is in its dropped region
+template <typename T>
+__device__ __forceinline__ void rescale(T& e, T& d, int& k) {
   if (k > 0 && Rc<T>::big(e)) {
     e *= Rc<T>::down();
     d *= Rc<T>::down();
@@ -173,8 +177,8 @@ __device__ __forceinline__ void reinsch_step(T t, T C, T& e, T& d, int& k) {
   }
 }
 
-// staged a_lm combination for the two columns: north  P = g + i c (col 1), Q = g* + i c* (col 2);
-// south (reflected rings) P = (-1)^(l+m) (g* + i c*), Q = (-1)^(l+m) (g + i c)
+// staged a_lm combination for the two columns: direct rings P = g + i c (col 1), Q = g* + i c* (col 2);
+// reflected rings P = (-1)^(l+m) (g* + i c*), Q = (-1)^(l+m) (g + i c)
 template <typename V, typename T>
 __device__ __forceinline__ void stage_pq(V gv, V cv, bool m0, bool refl, int lpm, V& P, V& Q) {
   if (m0) {
@@ -193,8 +197,45 @@ __device__ __forceinline__ void stage_pq(V gv, V cv, bool m0, bool refl, int lpm
   }
 }
 
+// Shared-memory staging of one chunk of l values.  Entries past lmax get zero coefficients, which
+// leave the state unchanged and add nothing, so every chunk is a whole number of quads.
+template <typename T>
+struct Stage {
+  Coef<T> cf[kCH];
+  typename Cx<T>::V P[kCH], Q[kCH];
+};
+
+template <typename T, bool WITH_PQ>
+__device__ __forceinline__ void stage_chunk(Stage<T>& S, const T* __restrict__ tab, int64_t nalm, int64_t base,
+                                            int lc, int lmax, int m,
+                                            const typename Cx<T>::V* __restrict__ g,
+                                            const typename Cx<T>::V* __restrict__ c, bool refl) {
+  using V = typename Cx<T>::V;
+  for (int i = threadIdx.x; i < kCH; i += blockDim.x) {
+    const int l = lc + i;
+    if (l <= lmax) {
+      const int64_t id = base + l;
+      S.cf[i] = load_coef<T>(tab, nalm, id);
+      if (WITH_PQ) {
+        V P, Q;
+        stage_pq<V, T>(g[id], c ? c[id] : mk((T)0, (T)0), m == 0, refl, l + m, P, Q);
+        S.P[i] = P;
+        S.Q[i] = Q;
+      }
+    } else {
+      S.cf[i] = Coef<T>{};
+      if (WITH_PQ) {
+        S.P[i] = mk((T)0, (T)0);
+        S.Q[i] = mk((T)0, (T)0);
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------------------------
 // synthesis: one CTA per RecItem (order m, rings j0 .. j0+nj-1), RPT rings per thread.
+// Work proceeds in quads of 4 l steps; per quad each warp takes one of three uniform paths:
+// all its columns past the dropped region (no tests), all still inside it (no sums), or mixed.
 template <typename T, bool SPIN, int RPT>
 __global__ void __launch_bounds__(128) k_rec_syn(const RecItem* __restrict__ items, const RingDev* __restrict__ rings,
                                                  const MSeed* __restrict__ mseed, const T* __restrict__ tab,
@@ -205,8 +246,7 @@ __global__ void __launch_bounds__(128) k_rec_syn(const RecItem* __restrict__ ite
   const RecItem it = items[blockIdx.x];
   const int m = it.m;
   const MSeed sd = mseed[m];
-  __shared__ Coef<T> sC[kCH];
-  __shared__ V sP[kCH], sQ[kCH];
+  __shared__ Stage<T> S;
 
   T oh[RPT], ol[RPT], e1[RPT], d1[RPT], e2[RPT], d2[RPT];
   T a0[RPT], a1[RPT], a2[RPT], a3[RPT];
@@ -221,51 +261,69 @@ __global__ void __launch_bounds__(128) k_rec_syn(const RecItem* __restrict__ ite
       ring_omx<T>(rg, oh[r], ol[r]);
       seed_scaled<T>(seed_log2(sd.lbin, sd.p1, sd.q1, rg.l2c, rg.l2s), sd.sign1, e1[r], k1[r]);
       if (SPIN) seed_scaled<T>(seed_log2(sd.lbin, sd.q1, sd.p1, rg.l2c, rg.l2s), sd.sign2, e2[r], k2[r]);
+      else k2[r] = 0;
       any = true;
     } else {
       oh[r] = ol[r] = e1[r] = e2[r] = (T)0;
-      k1[r] = k2[r] = 1;
+      k1[r] = 1;
+      k2[r] = SPIN ? 1 : 0;
     }
     d1[r] = e1[r];  // Delta_{l0} = e_{l0} - e_{l0-1}, e_{l0-1} = 0
     d2[r] = e2[r];
   }
   const bool warp_any = __any_sync(0xffffffffu, any);
   const int64_t base = alm_base(lmax, m);
-  const bool m0 = (m == 0);
   const bool rf = it.refl != 0;
 
   for (int lc = sd.l0; lc <= lmax; lc += kCH) {
-    const int n = min(kCH, lmax - lc + 1);
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const int64_t id = base + lc + i;
-      sC[i] = load_coef<T>(tab, nalm, id);
-      V P, Q;
-      stage_pq<V, T>(g[id], c ? c[id] : mk((T)0, (T)0), m0, rf, lc + i + m, P, Q);
-      sP[i] = P;
-      sQ[i] = Q;
-    }
+    stage_chunk<T, true>(S, tab, nalm, base, lc, lmax, m, g, c, rf);
     __syncthreads();
     if (!warp_any) continue;
-    for (int i = 0; i < n; ++i) {
-      const Coef<T> cf = sC[i];
-      const V P = sP[i], Q = sQ[i];
+    const int nq = (min(kCH, lmax - lc + 1) + 3) >> 2;
+    for (int q = 0; q < nq; ++q) {
+      bool in2 = true, in1 = true;  // all columns summing / all columns still dropped
 #pragma unroll
       for (int r = 0; r < RPT; ++r) {
-        const T o1 = (k1[r] == 0) ? e1[r] : (T)0;
-        a0[r] = fma(P.x, o1, a0[r]);
-        a1[r] = fma(P.y, o1, a1[r]);
-        const T t = cf.t(oh[r], ol[r]);
-        if (SPIN) {
-          const T o2 = (k2[r] == 0) ? e2[r] : (T)0;
-          a2[r] = fma(Q.x, o2, a2[r]);
-          a3[r] = fma(Q.y, o2, a3[r]);
-          reinsch_step<T>(t + cf.B, cf.C, e1[r], d1[r], k1[r]);
-          reinsch_step<T>(t - cf.B, cf.C, e2[r], d2[r], k2[r]);
-        } else {
-          a2[r] = fma(Q.x, o1, a2[r]);
-          a3[r] = fma(Q.y, o1, a3[r]);
-          reinsch_step<T>(t, cf.C, e1[r], d1[r], k1[r]);
+        in2 = in2 && k1[r] == 0 && k2[r] == 0;
+        in1 = in1 && k1[r] > 0 && (!SPIN || k2[r] > 0);
+      }
+      const bool fast = __all_sync(0xffffffffu, in2);
+      const bool skip = !fast && __all_sync(0xffffffffu, in1);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = 4 * q + u;
+        const Coef<T> cf = S.cf[i];
+        const V P = S.P[i], Q = S.Q[i];
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+          if (!skip) {
+            const T o1 = (fast || k1[r] == 0) ? e1[r] : (T)0;
+            a0[r] = fma(P.x, o1, a0[r]);
+            a1[r] = fma(P.y, o1, a1[r]);
+            if (SPIN) {
+              const T o2 = (fast || k2[r] == 0) ? e2[r] : (T)0;
+              a2[r] = fma(Q.x, o2, a2[r]);
+              a3[r] = fma(Q.y, o2, a3[r]);
+            } else {
+              a2[r] = fma(Q.x, o1, a2[r]);
+              a3[r] = fma(Q.y, o1, a3[r]);
+            }
+          }
+          const T t = cf.t(oh[r], ol[r]);
+          if (SPIN) {
+            reinsch_step<T>(t + cf.B, cf.C, e1[r], d1[r]);
+            reinsch_step<T>(t - cf.B, cf.C, e2[r], d2[r]);
+          } else {
+            reinsch_step<T>(t, cf.C, e1[r], d1[r]);
+          }
+        }
+      }
+      if (!fast) {
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+          rescale<T>(e1[r], d1[r], k1[r]);
+          if (SPIN) rescale<T>(e2[r], d2[r], k2[r]);
         }
       }
     }
@@ -276,31 +334,41 @@ __global__ void __launch_bounds__(128) k_rec_syn(const RecItem* __restrict__ ite
     const int jj = threadIdx.x + r * blockDim.x;
     if (jj < it.nj) {
       const int j = it.j0 + jj;
-      // north: F[m] <- column 1, F[-m] <- column 2; south: swapped
+      // direct rings: F[m] <- column 1, F[-m] <- column 2; reflected rings: swapped
       const V fpos = rf ? mk(-a2[r], -a3[r]) : mk(-a0[r], -a1[r]);
       const V fneg = rf ? mk(sgn_s * a0[r], sgn_s * a1[r]) : mk(sgn_s * a2[r], sgn_s * a3[r]);
       F[(int64_t)col_of(m) * Lpad + j] = fpos;
-      if (!m0) F[(int64_t)col_of(-m) * Lpad + j] = fneg;
+      if (m != 0) F[(int64_t)col_of(-m) * Lpad + j] = fneg;
     }
   }
 }
 
 // ---------------------------------------------------------------------------------------------
-// adjoint: one CTA per order m (blockIdx.x = m), all active rings, RPT rings per thread.
+// adjoint: one CTA per order m (blockIdx.x = m), the active rings of one ring part, RPT rings
+// per thread.  Per quad the 4 l values x 4 partial sums of each thread are reduced across the
+// warp by a reduce-scatter (16 values over 32 lanes: 4 halving exchanges and one final add).
 template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
+__device__ __forceinline__ T reduce_scatter16(T (&v)[16], int lane) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+  for (int o = 8; o >= 1; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int k = 0; k < o; ++k) {
+      const T send = up ? v[k] : v[k + o];
+      const T keep = up ? v[k + o] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);  // lane holds value (lane & 15)
 }
 
-template <typename T, bool SPIN, int RPT>
-__global__ void __launch_bounds__(512) k_rec_adj(const RingDev* __restrict__ rings, const MSeed* __restrict__ mseed,
-                                                 const int2* __restrict__ mrange, const T* __restrict__ tab,
-                                                 int64_t nalm, const typename Cx<T>::V* __restrict__ Ft, int Lpad,
-                                                 int lmax, int s, int M, int refl, int accumulate,
-                                                 typename Cx<T>::V* __restrict__ gt,
-                                                 typename Cx<T>::V* __restrict__ ct) {
+template <typename T, bool SPIN, int RPT, int NT>
+__global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ rings, const MSeed* __restrict__ mseed,
+                                                const int2* __restrict__ mrange, const T* __restrict__ tab,
+                                                int64_t nalm, const typename Cx<T>::V* __restrict__ Ft, int Lpad,
+                                                int lmax, int s, int M, int refl, int accumulate,
+                                                typename Cx<T>::V* __restrict__ gt,
+                                                typename Cx<T>::V* __restrict__ ct) {
   using V = typename Cx<T>::V;
   const int m = blockIdx.x;
   const int64_t base = alm_base(lmax, m);
@@ -315,11 +383,10 @@ __global__ void __launch_bounds__(512) k_rec_adj(const RingDev* __restrict__ rin
   const MSeed sd = mseed[m];
   const int2 rr = mrange[m];
   const int nact = rr.y - rr.x;
-  constexpr int NW = 512 / 32;
-  __shared__ Coef<T> sC[kCH];
+  constexpr int NW = NT / 32;
+  __shared__ Stage<T> S;
   __shared__ T red[NW][kCH][4];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nwarps = blockDim.x >> 5;
   for (int l = m + threadIdx.x; !accumulate && l < sd.l0 && l <= lmax; l += blockDim.x) {
     gt[base + l] = mk((T)0, (T)0);
     if (ct) ct[base + l] = mk((T)0, (T)0);
@@ -340,6 +407,7 @@ __global__ void __launch_bounds__(512) k_rec_adj(const RingDev* __restrict__ rin
       ring_omx<T>(rg, oh[r], ol[r]);
       seed_scaled<T>(seed_log2(sd.lbin, sd.p1, sd.q1, rg.l2c, rg.l2s), sd.sign1, e1[r], k1[r]);
       if (SPIN) seed_scaled<T>(seed_log2(sd.lbin, sd.q1, sd.p1, rg.l2c, rg.l2s), sd.sign2, e2[r], k2[r]);
+      else k2[r] = 0;
       const V fp = Ft[(int64_t)col_of(m) * Lpad + j];
       const V fm = m0 ? mk((T)0, (T)0) : Ft[(int64_t)col_of(-m) * Lpad + j];
       f1[r] = rf ? fm : fp;
@@ -347,7 +415,8 @@ __global__ void __launch_bounds__(512) k_rec_adj(const RingDev* __restrict__ rin
       any = true;
     } else {
       oh[r] = ol[r] = e1[r] = e2[r] = (T)0;
-      k1[r] = k2[r] = 1;
+      k1[r] = 1;
+      k2[r] = SPIN ? 1 : 0;
       f1[r] = f2[r] = mk((T)0, (T)0);
     }
     d1[r] = e1[r];
@@ -359,47 +428,70 @@ __global__ void __launch_bounds__(512) k_rec_adj(const RingDev* __restrict__ rin
 
   for (int lc = sd.l0; lc <= lmax; lc += kCH) {
     const int n = min(kCH, lmax - lc + 1);
+    const int nq = (n + 3) >> 2;
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) sC[i] = load_coef<T>(tab, nalm, base + lc + i);
+    stage_chunk<T, false>(S, tab, nalm, base, lc, lmax, m, nullptr, nullptr, rf);
     __syncthreads();
-    for (int i = 0; i < n; ++i) {
-      T p0 = 0, p1 = 0, p2 = 0, p3 = 0;
-      if (warp_any) {
-        const Coef<T> cf = sC[i];
+    for (int q = 0; q < nq; ++q) {
+      if (!warp_any) {
+        if (lane < 16) red[warp][4 * q + (lane >> 2)][lane & 3] = (T)0;
+        continue;
+      }
+      bool in2 = true, in1 = true;
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        in2 = in2 && k1[r] == 0 && k2[r] == 0;
+        in1 = in1 && k1[r] > 0 && (!SPIN || k2[r] > 0);
+      }
+      const bool fast = __all_sync(0xffffffffu, in2);
+      const bool skip = !fast && __all_sync(0xffffffffu, in1);
+      T v[16];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const Coef<T> cf = S.cf[4 * q + u];
+        T p0 = 0, p1 = 0, p2 = 0, p3 = 0;
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
-          const T o1 = (k1[r] == 0) ? e1[r] : (T)0;
-          p0 = fma(o1, f1[r].x, p0);
-          p1 = fma(o1, f1[r].y, p1);
-          const T t = cf.t(oh[r], ol[r]);
-          if (SPIN) {
-            const T o2 = (k2[r] == 0) ? e2[r] : (T)0;
+          if (!skip) {
+            const T o1 = (fast || k1[r] == 0) ? e1[r] : (T)0;
+            p0 = fma(o1, f1[r].x, p0);
+            p1 = fma(o1, f1[r].y, p1);
+            const T o2 = SPIN ? ((fast || k2[r] == 0) ? e2[r] : (T)0) : o1;
             p2 = fma(o2, f2[r].x, p2);
             p3 = fma(o2, f2[r].y, p3);
-            reinsch_step<T>(t + cf.B, cf.C, e1[r], d1[r], k1[r]);
-            reinsch_step<T>(t - cf.B, cf.C, e2[r], d2[r], k2[r]);
+          }
+          const T t = cf.t(oh[r], ol[r]);
+          if (SPIN) {
+            reinsch_step<T>(t + cf.B, cf.C, e1[r], d1[r]);
+            reinsch_step<T>(t - cf.B, cf.C, e2[r], d2[r]);
           } else {
-            p2 = fma(o1, f2[r].x, p2);
-            p3 = fma(o1, f2[r].y, p3);
-            reinsch_step<T>(t, cf.C, e1[r], d1[r], k1[r]);
+            reinsch_step<T>(t, cf.C, e1[r], d1[r]);
           }
         }
-        p0 = warp_sum(p0);
-        p1 = warp_sum(p1);
-        p2 = warp_sum(p2);
-        p3 = warp_sum(p3);
+        v[4 * u + 0] = p0;
+        v[4 * u + 1] = p1;
+        v[4 * u + 2] = p2;
+        v[4 * u + 3] = p3;
       }
-      if (lane == 0) {
-        red[warp][i][0] = p0;
-        red[warp][i][1] = p1;
-        red[warp][i][2] = p2;
-        red[warp][i][3] = p3;
+      if (!fast) {
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+          rescale<T>(e1[r], d1[r], k1[r]);
+          if (SPIN) rescale<T>(e2[r], d2[r], k2[r]);
+        }
+      }
+      if (skip) {
+        if (lane < 16) red[warp][4 * q + (lane >> 2)][lane & 3] = (T)0;
+      } else {
+        const T tot = reduce_scatter16<T>(v, lane);
+        if (lane < 16) red[warp][4 * q + (lane >> 2)][lane & 3] = tot;
       }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       T q0 = 0, q1 = 0, q2 = 0, q3 = 0;
-      for (int w = 0; w < nwarps; ++w) {
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
         q0 += red[w][i][0];
         q1 += red[w][i][1];
         q2 += red[w][i][2];
@@ -446,13 +538,13 @@ void launch_syn_t(Plan& p, const void* g, const void* c, cudaStream_t st) {
                                                      (const V*)g, (const V*)c, p.lmax, p.spin, (V*)p.d_F, p.Lpad);
 }
 
-template <typename T, bool SPIN, int RPT>
+template <typename T, bool SPIN, int RPT, int NT>
 void launch_adj_t(Plan& p, void* g, void* c, cudaStream_t st) {
   using V = typename Cx<T>::V;
   // one launch per ring part (rings at theta <= pi/2, then reflected rings at theta > pi/2)
   for (int part = 0; part < 2; ++part) {
     if (part == 1 && !p.has_refl) break;
-    k_rec_adj<T, SPIN, RPT><<<p.lmax + 1, p.adj_threads, 0, st>>>(
+    k_rec_adj<T, SPIN, RPT, NT><<<p.lmax + 1, NT, 0, st>>>(
         p.d_ring, p.d_mseed, p.d_mrange + part * (p.lmax + 1), (const T*)p.d_rtab, p.nalm, (const V*)p.d_F, p.Lpad,
         p.lmax, p.spin, p.M, part, part, (V*)g, (V*)c);
   }
@@ -468,11 +560,15 @@ void launch_syn_s(Plan& p, const void* g, const void* c, cudaStream_t st) {
 }
 template <typename T, bool SPIN>
 void launch_adj_s(Plan& p, void* g, void* c, cudaStream_t st) {
-  switch (p.adj_rpt) {
-    case 1: launch_adj_t<T, SPIN, 1>(p, g, c, st); break;
-    case 2: launch_adj_t<T, SPIN, 2>(p, g, c, st); break;
-    case 4: launch_adj_t<T, SPIN, 4>(p, g, c, st); break;
-    default: launch_adj_t<T, SPIN, 8>(p, g, c, st); break;
+  // (rings per thread, threads) covering up to 4096 rings; chosen by the planner
+  switch (p.adj_rpt * 10000 + p.adj_threads) {
+    case 10128: launch_adj_t<T, SPIN, 1, 128>(p, g, c, st); break;
+    case 20128: launch_adj_t<T, SPIN, 2, 128>(p, g, c, st); break;
+    case 40128: launch_adj_t<T, SPIN, 4, 128>(p, g, c, st); break;
+    case 40256: launch_adj_t<T, SPIN, 4, 256>(p, g, c, st); break;
+    case 80128: launch_adj_t<T, SPIN, 8, 128>(p, g, c, st); break;
+    case 80256: launch_adj_t<T, SPIN, 8, 256>(p, g, c, st); break;
+    default: launch_adj_t<T, SPIN, 8, 512>(p, g, c, st); break;
   }
 }
 
