@@ -108,6 +108,13 @@ int psht_plan_adjoint(psht_plan* plan, const void* f, void* g, void* c, void* st
 int psht_plan_synthesis_host(psht_plan* plan, const void* g, const void* c, void* f, void* stream);
 int psht_plan_adjoint_host(psht_plan* plan, const void* f, void* g, void* c, void* stream);
 
+/*
+ * Device status of the plan: synchronises `stream` and writes 0 to *status if every kernel wait of
+ * earlier calls completed, or 1 if a wait on an asynchronous copy gave up after its iteration
+ * limit (the kernel then stopped early and the call's outputs are invalid).  Clears the word.
+ */
+int psht_plan_status(psht_plan* plan, int* status, void* stream);
+
 /* Release the plan and all device memory it holds.  Synchronises the device. NULL is a no-op. */
 int psht_plan_destroy(psht_plan* plan);
 

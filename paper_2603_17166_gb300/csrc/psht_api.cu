@@ -222,6 +222,7 @@ void layout(Plan& p, double theta_star) {
   p.ntr = (p.nrows - 1) / p.TR + 1;
   p.ntq = (p.nphi + p.padq) / p.TQ + 1;
   p.nalm = (int64_t)(p.lmax + 1) * (p.lmax + 2) / 2;
+  p.tstride = (p.nalm + 72 + 7) / 8 * 8;  // room for the aligned over-read of the last chunk
   // launch shapes of the recursion
   p.syn_rpt = (p.prec == 64) ? 1 : 4;
   p.syn_threads = 128;
@@ -245,7 +246,7 @@ void layout(Plan& p, double theta_star) {
 size_t planned_bytes(const Plan& p) {
   const size_t cb = p.prec == 64 ? 16 : 8, rb = p.prec == 64 ? 8 : 4;
   size_t b = 0;
-  b += (size_t)rec_table_width(p.prec) * p.nalm * rb;           // recursion table
+  b += (size_t)rec_table_width(p.prec) * p.tstride * rb;        // recursion table
   b += (size_t)p.ncols * p.Lpad * cb;                          // ring coefficients
   b += (size_t)p.nrows * p.ncols * cb;                         // Theta-stage rows
   b += (size_t)p.nrows * p.gstride * cb;                       // grid
@@ -404,7 +405,10 @@ Plan* create(int spin, int lmax, const double* theta, const double* phi, int64_t
     }
     // work buffers
     const size_t cb = prec == 64 ? 16 : 8, rb = prec == 64 ? 8 : 4;
-    p->d_rtab = dalloc(*p, (size_t)rec_table_width(prec) * p->nalm * rb);
+    p->d_rtab = dalloc(*p, (size_t)rec_table_width(prec) * p->tstride * rb);
+    PSHT_CUDA_TRY(cudaMemsetAsync(p->d_rtab, 0, (size_t)rec_table_width(prec) * p->tstride * rb, st));
+    p->d_status = (int*)dalloc(*p, sizeof(int));
+    PSHT_CUDA_TRY(cudaMemsetAsync(p->d_status, 0, sizeof(int), st));
     p->d_F = dalloc(*p, (size_t)p->ncols * p->Lpad * cb);
     p->d_X = dalloc(*p, (size_t)p->nrows * p->ncols * cb);
     p->d_G = dalloc(*p, (size_t)p->nrows * p->gstride * cb);
@@ -620,6 +624,18 @@ int psht_plan_ring_coeffs(psht_plan* plan, const void* g, const void* c, void* F
     PSHT_REQUIRE(plan && g && F, PSHT_EINVAL, "plan, g and F must not be NULL");
     launch_rec_synthesis(*plan->p, g, c, (cudaStream_t)stream);
     launch_ring_coeffs_export(*plan->p, F, (cudaStream_t)stream);
+  });
+}
+
+int psht_plan_status(psht_plan* plan, int* status, void* stream) {
+  return guarded([&] {
+    PSHT_REQUIRE(plan && status, PSHT_EINVAL, "plan and status must not be NULL");
+    int h = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    PSHT_CUDA_TRY(cudaMemcpyAsync(&h, plan->p->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PSHT_CUDA_TRY(cudaMemsetAsync(plan->p->d_status, 0, sizeof(int), st));
+    PSHT_CUDA_TRY(cudaStreamSynchronize(st));
+    *status = h;
   });
 }
 

@@ -103,6 +103,8 @@ struct Plan {
   int2* d_mrange = nullptr;     // active ring range [j_lo, j_hi) per m: part 0 (theta <= pi/2), then part 1
   int has_refl = 0;             // any ring at theta > pi/2 (part 1 non-empty)
   void* d_rtab = nullptr;       // recurrence table per packed (l, m), rec_table_width(prec) arrays of T
+  int64_t tstride = 0;          // element stride between the table's arrays (nalm padded for bulk copies)
+  int* d_status = nullptr;      // device error word (bounded waits that gave up), read by psht_plan_status
   RecItem* d_items = nullptr;
   int nitems = 0;
   void* d_F = nullptr;          // complex T [ncols][Lpad]

@@ -67,21 +67,79 @@ __device__ __forceinline__ void point_tu(const BinGeom& g, double th, double ph,
   if (u < 0.0) u = 0.0;
 }
 
+// fine binning key of a point: tile (tr, tq) and base cell (lr, lq) inside it, so that sorting by
+// the key groups points by tile and orders each tile's points by base cell
 __global__ void k_bin_count(const double* __restrict__ theta, const double* __restrict__ phi, int64_t n, BinGeom g,
-                            int* __restrict__ tile_of, int* __restrict__ counts) {
+                            int* __restrict__ key_of, int* __restrict__ counts) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double t, u;
     point_tu(g, theta[i], phi[i], t, u);
     const int r0 = (int)ceil(t - 0.5 * g.W), q0 = (int)ceil(u - 0.5 * g.W);
     const int dr = r0 - g.r_lo, dq = q0 + g.padq;
     if (dr < 0 || dq < 0 || dr / g.TR >= g.ntr || dq / g.TQ >= g.ntq) {  // outside the planned rows: reported
-      tile_of[i] = -1;
+      key_of[i] = -1;
       continue;
     }
-    const int tile = (dr / g.TR) * g.ntq + dq / g.TQ;
-    tile_of[i] = tile;
-    atomicAdd(&counts[tile], 1);
+    const int tr = dr / g.TR, tq = dq / g.TQ;
+    const int key = ((tr * g.ntq + tq) * g.TR + (dr - tr * g.TR)) * g.TQ + (dq - tq * g.TQ);
+    key_of[i] = key;
+    atomicAdd(&counts[key], 1);
   }
+}
+
+// exclusive scan of n ints in place, three passes: per-block scan, scan of block sums, add back
+constexpr int kScanThreads = 1024, kScanPer = 4, kScanBlock = kScanThreads * kScanPer;
+__global__ void k_scan_blocks(int* __restrict__ a, int64_t n, int* __restrict__ bsum) {
+  __shared__ int ws[kScanThreads / 32];
+  const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanPer;
+  int v[kScanPer], tot = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    v[k] = (base + k < n) ? a[base + k] : 0;
+    tot += v[k];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int incl = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) ws[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int w = (lane < kScanThreads / 32) ? ws[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < kScanThreads / 32) ws[lane] = w;
+  }
+  __syncthreads();
+  int run = incl - tot + (warp > 0 ? ws[warp - 1] : 0);
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    if (base + k < n) a[base + k] = run;
+    run += v[k];
+  }
+  if (threadIdx.x == kScanThreads - 1) bsum[blockIdx.x] = run;
+}
+__global__ void k_scan_sums(int* __restrict__ bsum, int nb) {  // one thread: nb is small
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int run = 0;
+    for (int i = 0; i < nb; ++i) {
+      const int v = bsum[i];
+      bsum[i] = run;
+      run += v;
+    }
+  }
+}
+__global__ void k_scan_add(int* __restrict__ a, int64_t n, const int* __restrict__ bsum) {
+  const int64_t base = (int64_t)blockIdx.x * kScanBlock;
+  const int add = bsum[blockIdx.x];
+  for (int k = threadIdx.x; k < kScanBlock; k += blockDim.x)
+    if (base + k < n) a[base + k] += add;
 }
 
 __device__ __forceinline__ double es_psi(double z, double beta) {
@@ -89,20 +147,24 @@ __device__ __forceinline__ double es_psi(double z, double beta) {
   return exp(beta * (sqrt(1.0 - z * z) - 1.0));
 }
 
+__global__ void k_tile_offsets(const int* __restrict__ cnt, int ntiles, int per_tile, int* __restrict__ toff) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t <= ntiles) toff[t] = cnt[(int64_t)t * per_tile];
+}
+
 __global__ void k_bin_scatter(const double* __restrict__ theta, const double* __restrict__ phi, int64_t n, BinGeom g,
-                              const int* __restrict__ tile_of, const int* __restrict__ offsets,
+                              const int* __restrict__ key_of, const int* __restrict__ offsets,
                               int* __restrict__ cursor, int32_t* __restrict__ pidx, int32_t* __restrict__ pcell,
                               double* __restrict__ pw, float* __restrict__ pfrac, double beta_es) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int key = key_of[i];
+    if (key < 0) continue;
     double t, u;
     point_tu(g, theta[i], phi[i], t, u);
     const int r0 = (int)ceil(t - 0.5 * g.W), q0 = (int)ceil(u - 0.5 * g.W);
-    const int tile = tile_of[i];
-    if (tile < 0) continue;
-    const int tr = tile / g.ntq, tq = tile - tr * g.ntq;
-    const int pos = offsets[tile] + atomicAdd(&cursor[tile], 1);
+    const int pos = offsets[key] + atomicAdd(&cursor[key], 1);
     pidx[pos] = (int32_t)i;
-    const int lr = r0 - g.r_lo - tr * g.TR, lq = q0 + g.padq - tq * g.TQ;
+    const int lq = key % g.TQ, lr = (key / g.TQ) % g.TR;
     pcell[pos] = (int32_t)(lr | (lq << 16));
     if (pw) {
       for (int a = 0; a < g.W; ++a) {
@@ -190,43 +252,77 @@ __global__ void __launch_bounds__(kInterpThreads) k_gather(const TileItem* __res
   }
 }
 
-template <typename T, int W>
-__global__ void __launch_bounds__(kInterpThreads) k_scatter(const TileItem* __restrict__ items,
-                                                            const int32_t* __restrict__ pidx,
-                                                            const int32_t* __restrict__ pcell,
-                                                            const double* __restrict__ pw,
-                                                            const float* __restrict__ pf, int64_t npts,
-                                                            const typename Cx<T>::V* __restrict__ f,
-                                                            typename Cx<T>::V* __restrict__ G, int nrows, int gstride,
-                                                            int TR, int TQ, T beta) {
+// Spreading (transpose of k_gather).  Each warp owns a private copy of the tile; it spreads 32
+// consecutive (cell-sorted) points at a time, one per lane.  Lanes whose points share a base cell
+// take separate rounds, so within one window offset (a, b) all lanes write distinct cells; a
+// __syncwarp after every offset orders the read-modify-writes of successive offsets.  The warp
+// copies are summed at the end and added to the grid with one global atomic per nonzero cell.
+template <typename T, int W, int NT>
+__global__ void __launch_bounds__(NT) k_scatter(const TileItem* __restrict__ items, const int32_t* __restrict__ pidx,
+                                                const int32_t* __restrict__ pcell, const double* __restrict__ pw,
+                                                const float* __restrict__ pf, int64_t npts,
+                                                const typename Cx<T>::V* __restrict__ f,
+                                                typename Cx<T>::V* __restrict__ G, int nrows, int gstride, int TR,
+                                                int TQ, T beta) {
   using V = typename Cx<T>::V;
+  constexpr int NWARP = NT / 32;
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* tile = reinterpret_cast<T*>(smraw);  // interleaved re, im
+  V* tiles = reinterpret_cast<V*>(smraw);
   const TileItem it = items[blockIdx.x];
-  const int pitch = TQ + W - 1, rows = TR + W - 1;
+  const int pitch = TQ + W - 1, rows = TR + W - 1, cells = rows * pitch;
   const int row0 = it.tr * TR, col0 = it.tq * TQ;
-  for (int e = threadIdx.x; e < 2 * rows * pitch; e += blockDim.x) tile[e] = (T)0;
+  for (int e = threadIdx.x; e < NWARP * cells; e += NT) tiles[e] = mk((T)0, (T)0);
   __syncthreads();
-  for (int pt = it.p0 + threadIdx.x; pt < it.p0 + it.np; pt += blockDim.x) {
-    const int cell = pcell[pt];
-    const int lr = cell & 0xffff, lq = cell >> 16;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  V* tw = tiles + warp * cells;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int g0 = it.p0 + warp * 32; g0 < it.p0 + it.np; g0 += NT) {
+    const int pt = g0 + lane;
+    const bool valid = pt < it.p0 + it.np;
+    int lr = 0, lq = 0, key = -1 - lane;
     T wr[W], wq[W];
-    Weights<T, W>::get(pw, pf, npts, pt, beta, wr, wq);
-    const V fv = f[pidx[pt]];
+    V fv = mk((T)0, (T)0);
+    if (valid) {
+      const int cell = pcell[pt];
+      lr = cell & 0xffff;
+      lq = cell >> 16;
+      key = lr * pitch + lq;
+      Weights<T, W>::get(pw, pf, npts, pt, beta, wr, wq);
+      fv = f[pidx[pt]];
+    } else {
 #pragma unroll
-    for (int a = 0; a < W; ++a) {
-      const T vr = wr[a] * fv.x, vi = wr[a] * fv.y;
-      T* tp = tile + 2 * ((lr + a) * pitch + lq);
+      for (int a = 0; a < W; ++a) wr[a] = wq[a] = (T)0;
+    }
+    const unsigned same = __match_any_sync(0xffffffffu, key);
+    const unsigned rank = __popc(same & lt);
+    const unsigned rounds = __reduce_max_sync(0xffffffffu, rank) + 1u;
+    for (unsigned rd = 0; rd < rounds; ++rd) {
+      const bool on = valid && rank == rd;
 #pragma unroll
-      for (int b = 0; b < W; ++b) {
-        atomicAdd(tp + 2 * b, wq[b] * vr);
-        atomicAdd(tp + 2 * b + 1, wq[b] * vi);
+      for (int a = 0; a < W; ++a) {
+        const T vr = wr[a] * fv.x, vi = wr[a] * fv.y;
+        V* tp = tw + (lr + a) * pitch + lq;
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+          if (on) {
+            V x = tp[b];
+            x.x = fma(wq[b], vr, x.x);
+            x.y = fma(wq[b], vi, x.y);
+            tp[b] = x;
+          }
+          __syncwarp();
+        }
       }
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < rows * pitch; e += blockDim.x) {
-    const T vr = tile[2 * e], vi = tile[2 * e + 1];
+  for (int e = threadIdx.x; e < cells; e += NT) {
+    T vr = 0, vi = 0;
+#pragma unroll
+    for (int w = 0; w < NWARP; ++w) {
+      vr += tiles[w * cells + e].x;
+      vi += tiles[w * cells + e].y;
+    }
     if (vr == (T)0 && vi == (T)0) continue;
     const int rr = e / pitch, cc = e - rr * pitch;
     const int gr = row0 + rr, gc = col0 + cc;
@@ -251,12 +347,13 @@ void run_gather(Plan& p, void* f, cudaStream_t st) {
 template <typename T, int W>
 void run_scatter(Plan& p, const void* f, cudaStream_t st) {
   using V = typename Cx<T>::V;
-  const size_t smem = (size_t)(p.TR + W - 1) * (p.TQ + W - 1) * sizeof(V);
-  PSHT_CUDA_TRY(cudaFuncSetAttribute((const void*)k_scatter<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  constexpr int NT = sizeof(T) == 8 ? 128 : 256;
+  const size_t smem = (size_t)(NT / 32) * (p.TR + W - 1) * (p.TQ + W - 1) * sizeof(V);
+  PSHT_CUDA_TRY(cudaFuncSetAttribute((const void*)k_scatter<T, W, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
-  k_scatter<T, W><<<p.ntitems, kInterpThreads, smem, st>>>(p.d_titems, p.d_pidx, p.d_pcell, (const double*)p.d_pw,
-                                                           p.d_pfrac, p.npts, (const V*)f, (V*)p.d_G, p.nrows,
-                                                           p.gstride, p.TR, p.TQ, (T)p.beta_es);
+  k_scatter<T, W, NT><<<p.ntitems, NT, smem, st>>>(p.d_titems, p.d_pidx, p.d_pcell, (const double*)p.d_pw,
+                                                   p.d_pfrac, p.npts, (const V*)f, (V*)p.d_G, p.nrows, p.gstride,
+                                                   p.TR, p.TQ, (T)p.beta_es);
 }
 
 template <typename T, bool GATHER>
@@ -317,35 +414,46 @@ void bin_points(Plan& p, const double* theta, const double* phi, cudaStream_t st
   g.ntr = p.ntr;
   g.ntq = p.ntq;
   const int ntiles = p.ntr * p.ntq;
-  int *d_tile = nullptr, *d_cnt = nullptr, *d_off = nullptr;
-  PSHT_CUDA_TRY(cudaMallocAsync((void**)&d_tile, sizeof(int) * std::max<int64_t>(n, 1), st));
-  PSHT_CUDA_TRY(cudaMallocAsync((void**)&d_cnt, sizeof(int) * ntiles, st));
-  PSHT_CUDA_TRY(cudaMallocAsync((void**)&d_off, sizeof(int) * ntiles, st));
-  PSHT_CUDA_TRY(cudaMemsetAsync(d_cnt, 0, sizeof(int) * ntiles, st));
+  const int64_t nkeys = (int64_t)ntiles * p.TR * p.TQ;
+  PSHT_REQUIRE(nkeys < ((int64_t)1 << 31), PSHT_ENOTSUP, "grid too large for 32-bit point binning keys");
+  const int64_t nsb = (nkeys + 1 + kScanBlock - 1) / kScanBlock;  // blocks of the scan over nkeys + 1 entries
+  int *d_key = nullptr, *d_cnt = nullptr, *d_cur = nullptr, *d_bs = nullptr, *d_toff = nullptr;
+  PSHT_CUDA_TRY(cudaMallocAsync((void**)&d_key, sizeof(int) * std::max<int64_t>(n, 1), st));
+  PSHT_CUDA_TRY(cudaMallocAsync((void**)&d_cnt, sizeof(int) * (nkeys + 1), st));
+  PSHT_CUDA_TRY(cudaMallocAsync((void**)&d_cur, sizeof(int) * nkeys, st));
+  PSHT_CUDA_TRY(cudaMallocAsync((void**)&d_bs, sizeof(int) * std::max<int64_t>(nsb, 1), st));
+  PSHT_CUDA_TRY(cudaMallocAsync((void**)&d_toff, sizeof(int) * (ntiles + 1), st));
+  PSHT_CUDA_TRY(cudaMemsetAsync(d_cnt, 0, sizeof(int) * (nkeys + 1), st));
   const int nbl = (int)std::max<int64_t>(1, std::min<int64_t>((n + kBinThreads - 1) / kBinThreads, 152 * 32));
-  if (n > 0) k_bin_count<<<nbl, kBinThreads, 0, st>>>(theta, phi, n, g, d_tile, d_cnt);
+  if (n > 0) k_bin_count<<<nbl, kBinThreads, 0, st>>>(theta, phi, n, g, d_key, d_cnt);
   PSHT_CUDA_TRY(cudaGetLastError());
-  std::vector<int> cnt(ntiles), off(ntiles);
-  PSHT_CUDA_TRY(cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int) * ntiles, cudaMemcpyDeviceToHost, st));
+  // counting sort: exclusive scan of the per-key counts (entry nkeys becomes the total)
+  const int nb = (int)nsb;
+  k_scan_blocks<<<nb, kScanThreads, 0, st>>>(d_cnt, nkeys + 1, d_bs);
+  k_scan_sums<<<1, 32, 0, st>>>(d_bs, nb);
+  k_scan_add<<<nb, 256, 0, st>>>(d_cnt, nkeys + 1, d_bs);
+  PSHT_CUDA_TRY(cudaGetLastError());
+  // tile boundaries on the host: offsets of each tile's first key
+  std::vector<int> toff(ntiles + 1);
+  k_tile_offsets<<<(ntiles + 1 + 255) / 256, 256, 0, st>>>(d_cnt, ntiles, p.TR * p.TQ, d_toff);
+  PSHT_CUDA_TRY(cudaGetLastError());
+  PSHT_CUDA_TRY(cudaMemcpyAsync(toff.data(), d_toff, sizeof(int) * (ntiles + 1), cudaMemcpyDeviceToHost, st));
   PSHT_CUDA_TRY(cudaStreamSynchronize(st));
+  PSHT_REQUIRE(toff[ntiles] == n, PSHT_EINVAL, "a point falls outside the planned grid rows (theta* inconsistent)");
   // tile work items, dense tiles split so that no CTA holds more than kMaxPts points
   const int kMaxPts = 2048;
   std::vector<TileItem> items;
-  int64_t acc = 0;
   for (int t = 0; t < ntiles; ++t) {
-    off[t] = (int)acc;
-    const int c = cnt[t];
+    const int c = toff[t + 1] - toff[t];
     for (int b = 0; b < c; b += kMaxPts) {
       TileItem it;
       it.tr = t / p.ntq;
       it.tq = t % p.ntq;
-      it.p0 = (int)(acc + b);
+      it.p0 = toff[t] + b;
       it.np = std::min(kMaxPts, c - b);
       items.push_back(it);
     }
-    acc += c;
   }
-  PSHT_REQUIRE(acc == n, PSHT_EINVAL, "a point falls outside the planned grid rows (theta* inconsistent)");
   p.ntitems = (int)items.size();
   if (p.ntitems > 0) {
     PSHT_CUDA_TRY(cudaMalloc((void**)&p.d_titems, sizeof(TileItem) * items.size()));
@@ -353,15 +461,16 @@ void bin_points(Plan& p, const double* theta, const double* phi, cudaStream_t st
     p.bytes += sizeof(TileItem) * items.size();
     PSHT_CUDA_TRY(cudaMemcpyAsync(p.d_titems, items.data(), sizeof(TileItem) * items.size(), cudaMemcpyHostToDevice, st));
   }
-  PSHT_CUDA_TRY(cudaMemcpyAsync(d_off, off.data(), sizeof(int) * ntiles, cudaMemcpyHostToDevice, st));
-  PSHT_CUDA_TRY(cudaMemsetAsync(d_cnt, 0, sizeof(int) * ntiles, st));
+  PSHT_CUDA_TRY(cudaMemsetAsync(d_cur, 0, sizeof(int) * nkeys, st));
   if (n > 0)
-    k_bin_scatter<<<nbl, kBinThreads, 0, st>>>(theta, phi, n, g, d_tile, d_off, d_cnt, p.d_pidx, p.d_pcell,
+    k_bin_scatter<<<nbl, kBinThreads, 0, st>>>(theta, phi, n, g, d_key, d_cnt, d_cur, p.d_pidx, p.d_pcell,
                                                (double*)p.d_pw, p.d_pfrac, p.beta_es);
   PSHT_CUDA_TRY(cudaGetLastError());
-  PSHT_CUDA_TRY(cudaFreeAsync(d_tile, st));
+  PSHT_CUDA_TRY(cudaFreeAsync(d_key, st));
   PSHT_CUDA_TRY(cudaFreeAsync(d_cnt, st));
-  PSHT_CUDA_TRY(cudaFreeAsync(d_off, st));
+  PSHT_CUDA_TRY(cudaFreeAsync(d_cur, st));
+  PSHT_CUDA_TRY(cudaFreeAsync(d_bs, st));
+  PSHT_CUDA_TRY(cudaFreeAsync(d_toff, st));
   PSHT_CUDA_TRY(cudaStreamSynchronize(st));
 }
 

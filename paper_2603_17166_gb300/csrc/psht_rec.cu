@@ -1,17 +1,17 @@
 // Wigner-d recursion onto the apodised rings (synthesis, "K-REC") and its transpose
 // (adjoint, "K-REC-ADJ").
 //
-// Per order m and ring j the two columns e1_l = N_l d^l_{m,-s}(beta_j) and e2_l = N_l d^l_{m,s}(beta_j)
+// Per order m and ring j the two columns e1_l = N_l d^l_{m,-s}(b_j) and e2_l = N_l d^l_{m,s}(b_j)
 // (sY_lm = N_l d^l_{m,-s} e^{im phi}, appendix eq. Ylm; N_l = sqrt((2l+1)/4pi)) obey the textbook
 // three-term recurrence in l, written for the normalised columns as
-//     e_{l+1} = (A_l x +- B_l) e_l - C_l e_{l-1},   x = cos(beta_j),
+//     e_{l+1} = (A_l x +- B_l) e_l - C_l e_{l-1},   x = cos(b_j),
 // and evaluated in Reinsch's form for x near 1: with D_l = A_l - 1 - C_l and Delta_l = e_l - e_{l-1},
 //     Delta_{l+1} = (D_l +- B_l - A_l (1 - x)) e_l + C_l Delta_l,   e_{l+1} = e_l + Delta_{l+1},
-// where 1 - x = 2 sin^2(beta/2) is exact on the host.  This keeps the recurrence accurate on the
+// where 1 - x = 2 sin^2(b/2) is exact on the host.  This keeps the recurrence accurate on the
 // rings next to the pole, where A x + B - 2 is far below the rounding of A x + B.  In the FP32
 // form A, D and 1 - x are carried as float pairs (hi + lo).
-// Rings of a south-pole plan sit at theta_j = pi - beta_j; they are evaluated at beta_j with
-// d^l_{m,-s}(pi - beta) = (-1)^(l+m) d^l_{m,s}(beta), i.e. with the two columns swapped and the
+// Every ring is evaluated at b = min(theta_j, pi - theta_j): a ring at theta_j > pi/2 uses
+// d^l_{m,-s}(pi - b) = (-1)^(l+m) d^l_{m,s}(b), i.e. the two columns swapped and the
 // coefficients signed by (-1)^(l+m).
 // Seeds are Wigner's closed form at l0 = max(m, s) in FP64 log2 form; values too small for the
 // working precision are carried as e 2^(-F k) and join the sums once k = 0.
@@ -20,6 +20,10 @@
 // Adjoint (transpose, then the projection of the adjoint synthesis general formula, Sec. I):
 //   ut_{l,m} = -sum_j e1_l(j) Ft_j[m],   ut_{l,-m} = -(-1)^(m-s) sum_j e2_l(j) Ft_j[-m]
 //   g~ = (ut_lm + (-1)^m conj ut_{l,-m})/2,   c~ = (ut_lm - (-1)^m conj ut_{l,-m})/(2i)
+//
+// Data movement: per CTA the recurrence table of its order m is streamed through shared memory
+// in chunks of 64 l by TMA bulk copies (cp.async.bulk, completion on an mbarrier, two stages in
+// flight); the a_lm column is prefetched through registers two chunks ahead.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -29,16 +33,27 @@ namespace psht {
 
 namespace {
 
-constexpr int kCH = 64;  // l values staged in shared memory per chunk
+constexpr int kCH = 64;              // l values per chunk
+constexpr int kPadE = 8;             // extra table elements per staged array (aligned over-read)
+constexpr int kSpinLimit = 1 << 26;  // bounded mbarrier waits
 
 __device__ __forceinline__ int64_t alm_base(int lmax, int m) { return (int64_t)m * (2 * lmax + 1 - m) / 2; }
 
-// ---------------------------------------------------------------------------------------------
-// recurrence table per packed (l, m), FP64 arithmetic, one thread per m.
-//   FP64 form: t[0] = A, t[1] = D, t[2] = B, t[3] = C
-//   FP32 form: t[0] = A_hi, t[1] = A_lo, t[2] = D_hi, t[3] = D_lo, t[4] = B, t[5] = C
 template <typename T>
-__global__ void k_rec_table(int lmax, int s, T* __restrict__ tab, int64_t nalm) {
+struct TabWidth;
+template <>
+struct TabWidth<double> {
+  static constexpr int v = 4;  // A, D, B, C
+};
+template <>
+struct TabWidth<float> {
+  static constexpr int v = 6;  // A_hi, A_lo, D_hi, D_lo, B, C
+};
+
+// ---------------------------------------------------------------------------------------------
+// recurrence table per packed (l, m), FP64 arithmetic, one thread per m; array k at k * ts.
+template <typename T>
+__global__ void k_rec_table(int lmax, int s, T* __restrict__ tab, int64_t ts) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m > lmax) return;
   const int l0 = max(m, s);
@@ -60,19 +75,99 @@ __global__ void k_rec_table(int lmax, int s, T* __restrict__ tab, int64_t nalm) 
     const int64_t id = base + l;
     if (sizeof(T) == 8) {
       tab[id] = (T)A;
-      tab[nalm + id] = (T)D;
-      tab[2 * nalm + id] = (T)B;
-      tab[3 * nalm + id] = (T)C;
+      tab[ts + id] = (T)D;
+      tab[2 * ts + id] = (T)B;
+      tab[3 * ts + id] = (T)C;
     } else {
       const float ah = (float)A, dh = (float)D;
       tab[id] = ah;
-      tab[nalm + id] = (float)(A - (double)ah);
-      tab[2 * nalm + id] = dh;
-      tab[3 * nalm + id] = (float)(D - (double)dh);
-      tab[4 * nalm + id] = (float)B;
-      tab[5 * nalm + id] = (float)C;
+      tab[ts + id] = (float)(A - (double)ah);
+      tab[2 * ts + id] = dh;
+      tab[3 * ts + id] = (float)(D - (double)dh);
+      tab[4 * ts + id] = (float)B;
+      tab[5 * ts + id] = (float)C;
     }
   }
+}
+
+// ---------------------------------------------------------------------------------------------
+// mbarrier + bulk copy helpers (inline PTX)
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: false after kSpinLimit polls (the caller reports it and leaves)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (int i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// One staged chunk of the table: array k holds elements [a0, a0 + cnt) of table array k; the
+// chunk's first l sits at offset `off` (a0 is the 16-byte aligned start of the copy).
+template <typename T>
+struct TabStage {
+  T v[TabWidth<T>::v][kCH + kPadE];
+};
+template <typename T>
+__device__ __forceinline__ int chunk_off(int64_t start) {
+  return (int)(start & (16 / (int)sizeof(T) - 1));
+}
+
+// Issue the bulk copies of table elements start .. start + 63 of every array into st (one thread).
+// The table arrays are padded, so the aligned over-read stays inside the allocation.
+template <typename T>
+__device__ __forceinline__ void issue_chunk(TabStage<T>& st, uint64_t* bar, const T* __restrict__ tab, int64_t ts,
+                                            int64_t start) {
+  constexpr int A = 16 / sizeof(T);  // elements per 16 bytes
+  const int64_t a0 = start & ~(int64_t)(A - 1);
+  const int cnt = ((int)(start - a0) + kCH + A - 1) / A * A;
+  const uint32_t bytes = (uint32_t)(cnt * sizeof(T));
+  fence_proxy_async();  // earlier generic reads of this stage before the async-proxy writes
+  mbar_expect_tx(bar, bytes * TabWidth<T>::v);
+#pragma unroll
+  for (int k = 0; k < TabWidth<T>::v; ++k) bulk_g2s(st.v[k], tab + k * ts + a0, bytes, bar);
+}
+
+template <typename T>
+struct Coef;
+template <>
+struct Coef<double> {
+  double A, D, B, C;
+  __device__ __forceinline__ double t(double omx, double) const { return fma(-A, omx, D); }
+};
+template <>
+struct Coef<float> {
+  float Ah, Al, Dh, Dl, B, C;
+  __device__ __forceinline__ float t(float oh, float ol) const {
+    return fmaf(-Ah, oh, Dh) + fmaf(-Ah, ol, fmaf(-Al, oh, Dl));
+  }
+};
+__device__ __forceinline__ Coef<double> get_coef(const TabStage<double>& s, int i) {
+  return Coef<double>{s.v[0][i], s.v[1][i], s.v[2][i], s.v[3][i]};
+}
+__device__ __forceinline__ Coef<float> get_coef(const TabStage<float>& s, int i) {
+  return Coef<float>{s.v[0][i], s.v[1][i], s.v[2][i], s.v[3][i], s.v[4][i], s.v[5][i]};
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -120,34 +215,6 @@ __device__ __forceinline__ double seed_log2(double lbin, int p, int q, double l2
   return v;
 }
 
-// staged recurrence coefficients of one l, and the shared part t = D - A (1 - x) of the multiplier
-template <typename T>
-struct Coef;
-template <>
-struct Coef<double> {
-  double A, D, B, C;
-  __device__ __forceinline__ double t(double omx, double) const { return fma(-A, omx, D); }
-};
-template <>
-struct Coef<float> {
-  float Ah, Al, Dh, Dl, B, C;
-  __device__ __forceinline__ float t(float oh, float ol) const {
-    return fmaf(-Ah, oh, Dh) + fmaf(-Ah, ol, fmaf(-Al, oh, Dl));
-  }
-};
-
-template <typename T>
-__device__ __forceinline__ Coef<T> load_coef(const T* __restrict__ tab, int64_t nalm, int64_t id);
-template <>
-__device__ __forceinline__ Coef<double> load_coef<double>(const double* __restrict__ tab, int64_t nalm, int64_t id) {
-  return Coef<double>{tab[id], tab[nalm + id], tab[2 * nalm + id], tab[3 * nalm + id]};
-}
-template <>
-__device__ __forceinline__ Coef<float> load_coef<float>(const float* __restrict__ tab, int64_t nalm, int64_t id) {
-  return Coef<float>{tab[id], tab[nalm + id], tab[2 * nalm + id], tab[3 * nalm + id], tab[4 * nalm + id],
-                     tab[5 * nalm + id]};
-}
-
 template <typename T>
 __device__ __forceinline__ void ring_omx(const RingDev& r, T& oh, T& ol);
 template <>
@@ -177,10 +244,10 @@ __device__ __forceinline__ void rescale(T& e, T& d, int& k) {
   }
 }
 
-// staged a_lm combination for the two columns: direct rings P = g + i c (col 1), Q = g* + i c* (col 2);
+// a_lm combination for the two columns: direct rings P = g + i c (col 1), Q = g* + i c* (col 2);
 // reflected rings P = (-1)^(l+m) (g* + i c*), Q = (-1)^(l+m) (g + i c)
 template <typename V, typename T>
-__device__ __forceinline__ void stage_pq(V gv, V cv, bool m0, bool refl, int lpm, V& P, V& Q) {
+__device__ __forceinline__ void make_pq(V gv, V cv, bool m0, bool refl, int lpm, V& P, V& Q) {
   if (m0) {
     gv.y = (T)0;
     cv.y = (T)0;
@@ -197,133 +264,205 @@ __device__ __forceinline__ void stage_pq(V gv, V cv, bool m0, bool refl, int lpm
   }
 }
 
-// Shared-memory staging of one chunk of l values.  Entries past lmax get zero coefficients, which
-// leave the state unchanged and add nothing, so every chunk is a whole number of quads.
-template <typename T>
-struct Stage {
-  Coef<T> cf[kCH];
-  typename Cx<T>::V P[kCH], Q[kCH];
+// per-thread state of RPT ring slots
+template <typename T, int RPT>
+struct Cols {
+  T oh[RPT], ol[RPT], e1[RPT], d1[RPT], e2[RPT], d2[RPT];
+  int k1[RPT], k2[RPT];
 };
 
-template <typename T, bool WITH_PQ>
-__device__ __forceinline__ void stage_chunk(Stage<T>& S, const T* __restrict__ tab, int64_t nalm, int64_t base,
-                                            int lc, int lmax, int m,
-                                            const typename Cx<T>::V* __restrict__ g,
-                                            const typename Cx<T>::V* __restrict__ c, bool refl) {
+// One quad (4 l steps) of the synthesis for the ring slots r < nr of this thread.
+// ACC: add the current column values to the sums; SEL: per column, only where k == 0.
+template <typename T, bool SPIN, int RPT, bool ACC, bool SEL>
+__device__ __forceinline__ void syn_quad(Cols<T, RPT>& S, T (&a)[RPT][4], const TabStage<T>& st, int off, int i0,
+                                         const typename Cx<T>::V* sP, const typename Cx<T>::V* sQ, int nr) {
   using V = typename Cx<T>::V;
-  for (int i = threadIdx.x; i < kCH; i += blockDim.x) {
-    const int l = lc + i;
-    if (l <= lmax) {
-      const int64_t id = base + l;
-      S.cf[i] = load_coef<T>(tab, nalm, id);
-      if (WITH_PQ) {
-        V P, Q;
-        stage_pq<V, T>(g[id], c ? c[id] : mk((T)0, (T)0), m == 0, refl, l + m, P, Q);
-        S.P[i] = P;
-        S.Q[i] = Q;
-      }
-    } else {
-      S.cf[i] = Coef<T>{};
-      if (WITH_PQ) {
-        S.P[i] = mk((T)0, (T)0);
-        S.Q[i] = mk((T)0, (T)0);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = i0 + u;
+    const Coef<T> cf = get_coef(st, off + i);
+    const V P = sP[i], Q = sQ[i];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      if (r < nr) {
+        if (ACC) {
+          const T o1 = (!SEL || S.k1[r] == 0) ? S.e1[r] : (T)0;
+          a[r][0] = fma(P.x, o1, a[r][0]);
+          a[r][1] = fma(P.y, o1, a[r][1]);
+          const T o2 = SPIN ? ((!SEL || S.k2[r] == 0) ? S.e2[r] : (T)0) : o1;
+          a[r][2] = fma(Q.x, o2, a[r][2]);
+          a[r][3] = fma(Q.y, o2, a[r][3]);
+        }
+        const T t = cf.t(S.oh[r], S.ol[r]);
+        if (SPIN) {
+          reinsch_step<T>(t + cf.B, cf.C, S.e1[r], S.d1[r]);
+          reinsch_step<T>(t - cf.B, cf.C, S.e2[r], S.d2[r]);
+        } else {
+          reinsch_step<T>(t, cf.C, S.e1[r], S.d1[r]);
+        }
       }
     }
   }
 }
 
-// ---------------------------------------------------------------------------------------------
-// synthesis: one CTA per RecItem (order m, rings j0 .. j0+nj-1), RPT rings per thread.
-// Work proceeds in quads of 4 l steps; per quad each warp takes one of three uniform paths:
-// all its columns past the dropped region (no tests), all still inside it (no sums), or mixed.
 template <typename T, bool SPIN, int RPT>
-__global__ void __launch_bounds__(128) k_rec_syn(const RecItem* __restrict__ items, const RingDev* __restrict__ rings,
-                                                 const MSeed* __restrict__ mseed, const T* __restrict__ tab,
-                                                 int64_t nalm, const typename Cx<T>::V* __restrict__ g,
-                                                 const typename Cx<T>::V* __restrict__ c, int lmax, int s,
-                                                 typename Cx<T>::V* __restrict__ F, int Lpad) {
+__device__ __forceinline__ void rescale_all(Cols<T, RPT>& S, int nr) {
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    if (r < nr) {
+      rescale<T>(S.e1[r], S.d1[r], S.k1[r]);
+      if (SPIN) rescale<T>(S.e2[r], S.d2[r], S.k2[r]);
+    }
+  }
+}
+
+// warp-uniform classification of the warp's columns: all summing / all still dropped
+template <typename T, bool SPIN, int RPT>
+__device__ __forceinline__ void classify(const Cols<T, RPT>& S, int nr, bool& fast, bool& skip) {
+  bool in2 = true, in1 = true;
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    if (r < nr) {
+      in2 = in2 && S.k1[r] == 0 && S.k2[r] == 0;
+      in1 = in1 && S.k1[r] > 0 && (!SPIN || S.k2[r] > 0);
+    }
+  }
+  fast = __all_sync(0xffffffffu, in2);
+  skip = !fast && __all_sync(0xffffffffu, in1);
+}
+
+template <typename T, bool SPIN, int RPT>
+__device__ __forceinline__ void init_col(Cols<T, RPT>& S, const RingDev* __restrict__ rings, const MSeed& sd,
+                                         int jfirst, int jj, int nj, int r) {
+  if (jj < nj) {
+    const RingDev rg = rings[jfirst + jj];
+    ring_omx<T>(rg, S.oh[r], S.ol[r]);
+    seed_scaled<T>(seed_log2(sd.lbin, sd.p1, sd.q1, rg.l2c, rg.l2s), sd.sign1, S.e1[r], S.k1[r]);
+    if (SPIN) seed_scaled<T>(seed_log2(sd.lbin, sd.q1, sd.p1, rg.l2c, rg.l2s), sd.sign2, S.e2[r], S.k2[r]);
+    else S.k2[r] = 0;
+  } else {
+    // empty slot inside a partly filled warp: zero values that count as summing, so it adds
+    // nothing and never holds the warp off the fast path
+    S.oh[r] = S.ol[r] = S.e1[r] = S.e2[r] = (T)0;
+    S.k1[r] = 0;
+    S.k2[r] = 0;
+  }
+  S.d1[r] = S.e1[r];  // Delta_{l0} = e_{l0} - e_{l0-1}, e_{l0-1} = 0
+  S.d2[r] = S.e2[r];
+}
+
+// ---------------------------------------------------------------------------------------------
+// synthesis: one CTA of NT threads per RecItem (order m, rings j0 .. j0+nj-1), RPT rings per thread.
+// Ring slots: warp w owns rings w*32*RPT + r*32 + lane (consecutive rings per warp, so the warp's
+// columns leave the dropped region together); slots r >= nr_w are empty for the whole warp.
+template <typename T, bool SPIN, int RPT, int NT>
+__global__ void __launch_bounds__(NT) k_rec_syn(const RecItem* __restrict__ items, const RingDev* __restrict__ rings,
+                                                const MSeed* __restrict__ mseed, const T* __restrict__ tab,
+                                                int64_t ts, const typename Cx<T>::V* __restrict__ g,
+                                                const typename Cx<T>::V* __restrict__ c, int lmax, int s,
+                                                typename Cx<T>::V* __restrict__ F, int Lpad, int* __restrict__ status) {
   using V = typename Cx<T>::V;
   const RecItem it = items[blockIdx.x];
   const int m = it.m;
   const MSeed sd = mseed[m];
-  __shared__ Stage<T> S;
+  __shared__ __align__(16) TabStage<T> stg[2];
+  __shared__ V sP[2][kCH], sQ[2][kCH];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int sfail;
 
-  T oh[RPT], ol[RPT], e1[RPT], d1[RPT], e2[RPT], d2[RPT];
-  T a0[RPT], a1[RPT], a2[RPT], a3[RPT];
-  int k1[RPT], k2[RPT];
-  bool any = false;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wbase = warp * 32 * RPT;
+  const int nr_w = max(0, min(RPT, (it.nj - wbase + 31) >> 5));
+  Cols<T, RPT> S;
+  T a[RPT][4];
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
-    const int jj = threadIdx.x + r * blockDim.x;
-    a0[r] = a1[r] = a2[r] = a3[r] = (T)0;
-    if (jj < it.nj) {
-      const RingDev rg = rings[it.j0 + jj];
-      ring_omx<T>(rg, oh[r], ol[r]);
-      seed_scaled<T>(seed_log2(sd.lbin, sd.p1, sd.q1, rg.l2c, rg.l2s), sd.sign1, e1[r], k1[r]);
-      if (SPIN) seed_scaled<T>(seed_log2(sd.lbin, sd.q1, sd.p1, rg.l2c, rg.l2s), sd.sign2, e2[r], k2[r]);
-      else k2[r] = 0;
-      any = true;
-    } else {
-      oh[r] = ol[r] = e1[r] = e2[r] = (T)0;
-      k1[r] = 1;
-      k2[r] = SPIN ? 1 : 0;
-    }
-    d1[r] = e1[r];  // Delta_{l0} = e_{l0} - e_{l0-1}, e_{l0-1} = 0
-    d2[r] = e2[r];
+    init_col<T, SPIN, RPT>(S, rings, sd, it.j0, wbase + r * 32 + lane, it.nj, r);
+    a[r][0] = a[r][1] = a[r][2] = a[r][3] = (T)0;
   }
-  const bool warp_any = __any_sync(0xffffffffu, any);
   const int64_t base = alm_base(lmax, m);
   const bool rf = it.refl != 0;
+  const bool m0 = (m == 0);
+  const int nchunk = (lmax - sd.l0 + kCH) / kCH;
 
-  for (int lc = sd.l0; lc <= lmax; lc += kCH) {
-    __syncthreads();
-    stage_chunk<T, true>(S, tab, nalm, base, lc, lmax, m, g, c, rf);
-    __syncthreads();
-    if (!warp_any) continue;
+  // prologue: table chunks 0 and 1 by TMA, a_lm chunks 0 and 1 into shared memory, chunk 2 into
+  // registers
+  if (threadIdx.x == 0) {
+    sfail = 0;
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    issue_chunk<T>(stg[0], &bar[0], tab, ts, base + sd.l0);
+    if (nchunk > 1) issue_chunk<T>(stg[1], &bar[1], tab, ts, base + sd.l0 + kCH);
+  }
+  for (int cc = 0; cc < 2 && cc < nchunk; ++cc) {
+    for (int i = threadIdx.x; i < kCH; i += NT) {
+      const int l = sd.l0 + cc * kCH + i;
+      V P = mk((T)0, (T)0), Q = mk((T)0, (T)0);
+      if (l <= lmax) make_pq<V, T>(g[base + l], c ? c[base + l] : mk((T)0, (T)0), m0, rf, l + m, P, Q);
+      sP[cc][i] = P;
+      sQ[cc][i] = Q;
+    }
+  }
+  V pg = mk((T)0, (T)0), pc = mk((T)0, (T)0);  // a_lm two chunks ahead
+  if (threadIdx.x < kCH) {
+    const int l = sd.l0 + 2 * kCH + threadIdx.x;
+    if (l <= lmax) {
+      pg = g[base + l];
+      if (c) pc = c[base + l];
+    }
+  }
+  int off0 = chunk_off<T>(base + sd.l0), off1 = chunk_off<T>(base + sd.l0 + kCH);
+  __syncthreads();
+
+  for (int ch = 0; ch < nchunk; ++ch) {
+    const int sidx = ch & 1;
+    const int lc = sd.l0 + ch * kCH;
+    if (!mbar_wait(&bar[sidx], (ch >> 1) & 1)) {
+      atomicExch(status, 1);
+      sfail = 1;
+    }
     const int nq = (min(kCH, lmax - lc + 1) + 3) >> 2;
-    for (int q = 0; q < nq; ++q) {
-      bool in2 = true, in1 = true;  // all columns summing / all columns still dropped
-#pragma unroll
-      for (int r = 0; r < RPT; ++r) {
-        in2 = in2 && k1[r] == 0 && k2[r] == 0;
-        in1 = in1 && k1[r] > 0 && (!SPIN || k2[r] > 0);
-      }
-      const bool fast = __all_sync(0xffffffffu, in2);
-      const bool skip = !fast && __all_sync(0xffffffffu, in1);
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int i = 4 * q + u;
-        const Coef<T> cf = S.cf[i];
-        const V P = S.P[i], Q = S.Q[i];
-#pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-          if (!skip) {
-            const T o1 = (fast || k1[r] == 0) ? e1[r] : (T)0;
-            a0[r] = fma(P.x, o1, a0[r]);
-            a1[r] = fma(P.y, o1, a1[r]);
-            if (SPIN) {
-              const T o2 = (fast || k2[r] == 0) ? e2[r] : (T)0;
-              a2[r] = fma(Q.x, o2, a2[r]);
-              a3[r] = fma(Q.y, o2, a3[r]);
-            } else {
-              a2[r] = fma(Q.x, o1, a2[r]);
-              a3[r] = fma(Q.y, o1, a3[r]);
-            }
-          }
-          const T t = cf.t(oh[r], ol[r]);
-          if (SPIN) {
-            reinsch_step<T>(t + cf.B, cf.C, e1[r], d1[r]);
-            reinsch_step<T>(t - cf.B, cf.C, e2[r], d2[r]);
-          } else {
-            reinsch_step<T>(t, cf.C, e1[r], d1[r]);
-          }
+    if (nr_w > 0 && !sfail) {
+      const TabStage<T>& st = stg[sidx];
+      const V* P = sP[sidx];
+      const V* Q = sQ[sidx];
+      const int of = sidx ? off1 : off0;
+      for (int q = 0; q < nq; ++q) {
+        bool fast, skip;
+        classify<T, SPIN, RPT>(S, nr_w, fast, skip);
+        if (fast) {
+          if (nr_w == RPT) syn_quad<T, SPIN, RPT, true, false>(S, a, st, of, 4 * q, P, Q, RPT);
+          else syn_quad<T, SPIN, RPT, true, false>(S, a, st, of, 4 * q, P, Q, nr_w);
+        } else {
+          if (skip) syn_quad<T, SPIN, RPT, false, false>(S, a, st, of, 4 * q, P, Q, nr_w);
+          else syn_quad<T, SPIN, RPT, true, true>(S, a, st, of, 4 * q, P, Q, nr_w);
+          rescale_all<T, SPIN, RPT>(S, nr_w);
         }
       }
-      if (!fast) {
-#pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-          rescale<T>(e1[r], d1[r], k1[r]);
-          if (SPIN) rescale<T>(e2[r], d2[r], k2[r]);
+    }
+    __syncthreads();  // everyone is done with stage sidx
+    if (sfail) {
+      if (threadIdx.x == 0) mbar_wait(&bar[sidx ^ 1], ((ch + 1) >> 1) & 1);  // drain the other stage
+      return;
+    }
+    if (ch + 2 < nchunk) {
+      if (threadIdx.x == 0) issue_chunk<T>(stg[sidx], &bar[sidx], tab, ts, base + lc + 2 * kCH);
+      (sidx ? off1 : off0) = chunk_off<T>(base + lc + 2 * kCH);
+      if (threadIdx.x < kCH) {
+        const int l = lc + 2 * kCH + threadIdx.x;
+        V Pn = mk((T)0, (T)0), Qn = mk((T)0, (T)0);
+        if (l <= lmax) make_pq<V, T>(pg, pc, m0, rf, l + m, Pn, Qn);
+        sP[sidx][threadIdx.x] = Pn;
+        sQ[sidx][threadIdx.x] = Qn;
+        pg = pc = mk((T)0, (T)0);
+        const int l3 = l + kCH;
+        if (l3 <= lmax) {
+          pg = g[base + l3];
+          if (c) pc = c[base + l3];
         }
       }
     }
@@ -331,22 +470,22 @@ __global__ void __launch_bounds__(128) k_rec_syn(const RecItem* __restrict__ ite
   const T sgn_s = (s & 1) ? (T)1 : (T)-1;  // -(-1)^s
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
-    const int jj = threadIdx.x + r * blockDim.x;
+    const int jj = wbase + r * 32 + lane;
     if (jj < it.nj) {
       const int j = it.j0 + jj;
       // direct rings: F[m] <- column 1, F[-m] <- column 2; reflected rings: swapped
-      const V fpos = rf ? mk(-a2[r], -a3[r]) : mk(-a0[r], -a1[r]);
-      const V fneg = rf ? mk(sgn_s * a0[r], sgn_s * a1[r]) : mk(sgn_s * a2[r], sgn_s * a3[r]);
+      const V fpos = rf ? mk(-a[r][2], -a[r][3]) : mk(-a[r][0], -a[r][1]);
+      const V fneg = rf ? mk(sgn_s * a[r][0], sgn_s * a[r][1]) : mk(sgn_s * a[r][2], sgn_s * a[r][3]);
       F[(int64_t)col_of(m) * Lpad + j] = fpos;
-      if (m != 0) F[(int64_t)col_of(-m) * Lpad + j] = fneg;
+      if (!m0) F[(int64_t)col_of(-m) * Lpad + j] = fneg;
     }
   }
 }
 
 // ---------------------------------------------------------------------------------------------
-// adjoint: one CTA per order m (blockIdx.x = m), the active rings of one ring part, RPT rings
-// per thread.  Per quad the 4 l values x 4 partial sums of each thread are reduced across the
-// warp by a reduce-scatter (16 values over 32 lanes: 4 halving exchanges and one final add).
+// adjoint: one CTA per order m (blockIdx.x = m), the active rings of one ring part, RPT rings per
+// thread.  Per quad the 4 l values x 4 partial sums of each thread are reduced across the warp by
+// a reduce-scatter (16 values over 32 lanes: 4 halving exchanges and one final add).
 template <typename T>
 __device__ __forceinline__ T reduce_scatter16(T (&v)[16], int lane) {
 #pragma unroll
@@ -362,13 +501,65 @@ __device__ __forceinline__ T reduce_scatter16(T (&v)[16], int lane) {
   return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);  // lane holds value (lane & 15)
 }
 
+template <typename T, bool SPIN, int RPT, bool SEL>
+__device__ __forceinline__ void adj_quad_sums(Cols<T, RPT>& S, const typename Cx<T>::V (&f1)[RPT],
+                                              const typename Cx<T>::V (&f2)[RPT], const TabStage<T>& st, int off,
+                                              int i0, int nr, T (&v)[16]) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const Coef<T> cf = get_coef(st, off + i0 + u);
+    T p0 = 0, p1 = 0, p2 = 0, p3 = 0;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      if (r < nr) {
+        const T o1 = (!SEL || S.k1[r] == 0) ? S.e1[r] : (T)0;
+        p0 = fma(o1, f1[r].x, p0);
+        p1 = fma(o1, f1[r].y, p1);
+        const T o2 = SPIN ? ((!SEL || S.k2[r] == 0) ? S.e2[r] : (T)0) : o1;
+        p2 = fma(o2, f2[r].x, p2);
+        p3 = fma(o2, f2[r].y, p3);
+        const T t = cf.t(S.oh[r], S.ol[r]);
+        if (SPIN) {
+          reinsch_step<T>(t + cf.B, cf.C, S.e1[r], S.d1[r]);
+          reinsch_step<T>(t - cf.B, cf.C, S.e2[r], S.d2[r]);
+        } else {
+          reinsch_step<T>(t, cf.C, S.e1[r], S.d1[r]);
+        }
+      }
+    }
+    v[4 * u + 0] = p0;
+    v[4 * u + 1] = p1;
+    v[4 * u + 2] = p2;
+    v[4 * u + 3] = p3;
+  }
+}
+template <typename T, bool SPIN, int RPT>
+__device__ __forceinline__ void adj_quad_steps(Cols<T, RPT>& S, const TabStage<T>& st, int off, int i0, int nr) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const Coef<T> cf = get_coef(st, off + i0 + u);
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      if (r < nr) {
+        const T t = cf.t(S.oh[r], S.ol[r]);
+        if (SPIN) {
+          reinsch_step<T>(t + cf.B, cf.C, S.e1[r], S.d1[r]);
+          reinsch_step<T>(t - cf.B, cf.C, S.e2[r], S.d2[r]);
+        } else {
+          reinsch_step<T>(t, cf.C, S.e1[r], S.d1[r]);
+        }
+      }
+    }
+  }
+}
+
 template <typename T, bool SPIN, int RPT, int NT>
 __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ rings, const MSeed* __restrict__ mseed,
                                                 const int2* __restrict__ mrange, const T* __restrict__ tab,
-                                                int64_t nalm, const typename Cx<T>::V* __restrict__ Ft, int Lpad,
+                                                int64_t ts, const typename Cx<T>::V* __restrict__ Ft, int Lpad,
                                                 int lmax, int s, int M, int refl, int accumulate,
-                                                typename Cx<T>::V* __restrict__ gt,
-                                                typename Cx<T>::V* __restrict__ ct) {
+                                                typename Cx<T>::V* __restrict__ gt, typename Cx<T>::V* __restrict__ ct,
+                                                int* __restrict__ status) {
   using V = typename Cx<T>::V;
   const int m = blockIdx.x;
   const int64_t base = alm_base(lmax, m);
@@ -384,8 +575,10 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
   const int2 rr = mrange[m];
   const int nact = rr.y - rr.x;
   constexpr int NW = NT / 32;
-  __shared__ Stage<T> S;
+  __shared__ __align__(16) TabStage<T> stg[2];
   __shared__ T red[NW][kCH][4];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int sfail;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int l = m + threadIdx.x; !accumulate && l < sd.l0 && l <= lmax; l += blockDim.x) {
     gt[base + l] = mk((T)0, (T)0);
@@ -393,102 +586,83 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
   }
   const bool m0 = (m == 0);
   const bool rf = refl != 0;
+  const int wbase = warp * 32 * RPT;  // ring slots as in the synthesis kernel
+  const int nr_w = max(0, min(RPT, (nact - wbase + 31) >> 5));
 
-  T oh[RPT], ol[RPT], e1[RPT], d1[RPT], e2[RPT], d2[RPT];
+  Cols<T, RPT> S;
   V f1[RPT], f2[RPT];  // ring values paired with column 1 / column 2
-  int k1[RPT], k2[RPT];
-  bool any = false;
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
-    const int jj = threadIdx.x + r * blockDim.x;
+    const int jj = wbase + r * 32 + lane;
+    init_col<T, SPIN, RPT>(S, rings, sd, rr.x, jj, nact, r);
+    f1[r] = f2[r] = mk((T)0, (T)0);
     if (jj < nact) {
       const int j = rr.x + jj;
-      const RingDev rg = rings[j];
-      ring_omx<T>(rg, oh[r], ol[r]);
-      seed_scaled<T>(seed_log2(sd.lbin, sd.p1, sd.q1, rg.l2c, rg.l2s), sd.sign1, e1[r], k1[r]);
-      if (SPIN) seed_scaled<T>(seed_log2(sd.lbin, sd.q1, sd.p1, rg.l2c, rg.l2s), sd.sign2, e2[r], k2[r]);
-      else k2[r] = 0;
       const V fp = Ft[(int64_t)col_of(m) * Lpad + j];
       const V fm = m0 ? mk((T)0, (T)0) : Ft[(int64_t)col_of(-m) * Lpad + j];
       f1[r] = rf ? fm : fp;
       f2[r] = rf ? fp : fm;
-      any = true;
-    } else {
-      oh[r] = ol[r] = e1[r] = e2[r] = (T)0;
-      k1[r] = 1;
-      k2[r] = SPIN ? 1 : 0;
-      f1[r] = f2[r] = mk((T)0, (T)0);
     }
-    d1[r] = e1[r];
-    d2[r] = e2[r];
   }
-  const bool warp_any = __any_sync(0xffffffffu, any);
   const T sg = (((m - s) & 1) ? (T)1 : (T)-1);  // -(-1)^(m-s)
   const T sm = (m & 1) ? (T)-1 : (T)1;          // (-1)^m
+  const int nchunk = (lmax - sd.l0 + kCH) / kCH;
+  int off0 = chunk_off<T>(base + sd.l0), off1 = chunk_off<T>(base + sd.l0 + kCH);
+  if (threadIdx.x == 0) {
+    sfail = 0;
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    issue_chunk<T>(stg[0], &bar[0], tab, ts, base + sd.l0);
+    if (nchunk > 1) issue_chunk<T>(stg[1], &bar[1], tab, ts, base + sd.l0 + kCH);
+  }
 
-  for (int lc = sd.l0; lc <= lmax; lc += kCH) {
+  for (int ch = 0; ch < nchunk; ++ch) {
+    const int sidx = ch & 1;
+    const int lc = sd.l0 + ch * kCH;
     const int n = min(kCH, lmax - lc + 1);
     const int nq = (n + 3) >> 2;
-    __syncthreads();
-    stage_chunk<T, false>(S, tab, nalm, base, lc, lmax, m, nullptr, nullptr, rf);
-    __syncthreads();
-    for (int q = 0; q < nq; ++q) {
-      if (!warp_any) {
-        if (lane < 16) red[warp][4 * q + (lane >> 2)][lane & 3] = (T)0;
-        continue;
-      }
-      bool in2 = true, in1 = true;
-#pragma unroll
-      for (int r = 0; r < RPT; ++r) {
-        in2 = in2 && k1[r] == 0 && k2[r] == 0;
-        in1 = in1 && k1[r] > 0 && (!SPIN || k2[r] > 0);
-      }
-      const bool fast = __all_sync(0xffffffffu, in2);
-      const bool skip = !fast && __all_sync(0xffffffffu, in1);
-      T v[16];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const Coef<T> cf = S.cf[4 * q + u];
-        T p0 = 0, p1 = 0, p2 = 0, p3 = 0;
-#pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-          if (!skip) {
-            const T o1 = (fast || k1[r] == 0) ? e1[r] : (T)0;
-            p0 = fma(o1, f1[r].x, p0);
-            p1 = fma(o1, f1[r].y, p1);
-            const T o2 = SPIN ? ((fast || k2[r] == 0) ? e2[r] : (T)0) : o1;
-            p2 = fma(o2, f2[r].x, p2);
-            p3 = fma(o2, f2[r].y, p3);
-          }
-          const T t = cf.t(oh[r], ol[r]);
-          if (SPIN) {
-            reinsch_step<T>(t + cf.B, cf.C, e1[r], d1[r]);
-            reinsch_step<T>(t - cf.B, cf.C, e2[r], d2[r]);
-          } else {
-            reinsch_step<T>(t, cf.C, e1[r], d1[r]);
-          }
-        }
-        v[4 * u + 0] = p0;
-        v[4 * u + 1] = p1;
-        v[4 * u + 2] = p2;
-        v[4 * u + 3] = p3;
-      }
-      if (!fast) {
-#pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-          rescale<T>(e1[r], d1[r], k1[r]);
-          if (SPIN) rescale<T>(e2[r], d2[r], k2[r]);
-        }
-      }
-      if (skip) {
-        if (lane < 16) red[warp][4 * q + (lane >> 2)][lane & 3] = (T)0;
-      } else {
-        const T tot = reduce_scatter16<T>(v, lane);
-        if (lane < 16) red[warp][4 * q + (lane >> 2)][lane & 3] = tot;
-      }
+    if (!mbar_wait(&bar[sidx], (ch >> 1) & 1)) {
+      atomicExch(status, 1);
+      sfail = 1;
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const TabStage<T>& st = stg[sidx];
+    const int of = sidx ? off1 : off0;
+    for (int q = 0; q < nq; ++q) {
+      T tot = (T)0;
+      if (nr_w > 0 && !sfail) {
+        bool fast, skip;
+        classify<T, SPIN, RPT>(S, nr_w, fast, skip);
+        if (skip) {
+          adj_quad_steps<T, SPIN, RPT>(S, st, of, 4 * q, nr_w);
+          rescale_all<T, SPIN, RPT>(S, nr_w);
+        } else {
+          T v[16];
+          if (fast) {
+            if (nr_w == RPT) adj_quad_sums<T, SPIN, RPT, false>(S, f1, f2, st, of, 4 * q, RPT, v);
+            else adj_quad_sums<T, SPIN, RPT, false>(S, f1, f2, st, of, 4 * q, nr_w, v);
+          } else {
+            adj_quad_sums<T, SPIN, RPT, true>(S, f1, f2, st, of, 4 * q, nr_w, v);
+            rescale_all<T, SPIN, RPT>(S, nr_w);
+          }
+          tot = reduce_scatter16<T>(v, lane);
+        }
+      }
+      if (lane < 16) red[warp][4 * q + (lane >> 2)][lane & 3] = tot;
+    }
+    __syncthreads();  // stage sidx consumed, red complete
+    if (sfail) {
+      if (threadIdx.x == 0) mbar_wait(&bar[sidx ^ 1], ((ch + 1) >> 1) & 1);  // drain the other stage
+      return;
+    }
+    if (ch + 2 < nchunk) {
+      if (threadIdx.x == 0) issue_chunk<T>(stg[sidx], &bar[sidx], tab, ts, base + lc + 2 * kCH);
+      (sidx ? off1 : off0) = chunk_off<T>(base + lc + 2 * kCH);
+    }
+    for (int i = threadIdx.x; i < n; i += NT) {
       T q0 = 0, q1 = 0, q2 = 0, q3 = 0;
 #pragma unroll
       for (int w = 0; w < NW; ++w) {
@@ -528,14 +702,16 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
       gt[id] = gv;
       if (ct) ct[id] = cv;
     }
+    __syncthreads();  // red is rewritten by the next chunk
   }
 }
 
 template <typename T, bool SPIN, int RPT>
 void launch_syn_t(Plan& p, const void* g, const void* c, cudaStream_t st) {
   using V = typename Cx<T>::V;
-  k_rec_syn<T, SPIN, RPT><<<p.nitems, 128, 0, st>>>(p.d_items, p.d_ring, p.d_mseed, (const T*)p.d_rtab, p.nalm,
-                                                     (const V*)g, (const V*)c, p.lmax, p.spin, (V*)p.d_F, p.Lpad);
+  k_rec_syn<T, SPIN, RPT, 128><<<p.nitems, 128, 0, st>>>(p.d_items, p.d_ring, p.d_mseed, (const T*)p.d_rtab,
+                                                          p.tstride, (const V*)g, (const V*)c, p.lmax, p.spin,
+                                                          (V*)p.d_F, p.Lpad, p.d_status);
 }
 
 template <typename T, bool SPIN, int RPT, int NT>
@@ -545,8 +721,8 @@ void launch_adj_t(Plan& p, void* g, void* c, cudaStream_t st) {
   for (int part = 0; part < 2; ++part) {
     if (part == 1 && !p.has_refl) break;
     k_rec_adj<T, SPIN, RPT, NT><<<p.lmax + 1, NT, 0, st>>>(
-        p.d_ring, p.d_mseed, p.d_mrange + part * (p.lmax + 1), (const T*)p.d_rtab, p.nalm, (const V*)p.d_F, p.Lpad,
-        p.lmax, p.spin, p.M, part, part, (V*)g, (V*)c);
+        p.d_ring, p.d_mseed, p.d_mrange + part * (p.lmax + 1), (const T*)p.d_rtab, p.tstride, (const V*)p.d_F,
+        p.Lpad, p.lmax, p.spin, p.M, part, part, (V*)g, (V*)c, p.d_status);
   }
 }
 
@@ -562,8 +738,6 @@ template <typename T, bool SPIN>
 void launch_adj_s(Plan& p, void* g, void* c, cudaStream_t st) {
   // (rings per thread, threads) covering up to 4096 rings; chosen by the planner
   switch (p.adj_rpt * 10000 + p.adj_threads) {
-    case 10128: launch_adj_t<T, SPIN, 1, 128>(p, g, c, st); break;
-    case 20128: launch_adj_t<T, SPIN, 2, 128>(p, g, c, st); break;
     case 40128: launch_adj_t<T, SPIN, 4, 128>(p, g, c, st); break;
     case 40256: launch_adj_t<T, SPIN, 4, 256>(p, g, c, st); break;
     case 80128: launch_adj_t<T, SPIN, 8, 128>(p, g, c, st); break;
@@ -578,8 +752,8 @@ int rec_table_width(int prec) { return prec == 64 ? 4 : 6; }
 
 void build_rec_table(Plan& p, cudaStream_t st) {
   const int nth = 128, nbl = (p.lmax + 1 + nth - 1) / nth;
-  if (p.prec == 64) k_rec_table<double><<<nbl, nth, 0, st>>>(p.lmax, p.spin, (double*)p.d_rtab, p.nalm);
-  else k_rec_table<float><<<nbl, nth, 0, st>>>(p.lmax, p.spin, (float*)p.d_rtab, p.nalm);
+  if (p.prec == 64) k_rec_table<double><<<nbl, nth, 0, st>>>(p.lmax, p.spin, (double*)p.d_rtab, p.tstride);
+  else k_rec_table<float><<<nbl, nth, 0, st>>>(p.lmax, p.spin, (float*)p.d_rtab, p.tstride);
   PSHT_CUDA_TRY(cudaGetLastError());
 }
 

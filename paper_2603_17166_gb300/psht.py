@@ -59,6 +59,7 @@ def lib():
         L.psht_synthesis.argtypes = [P, P, I, I, P, P, I64, D, P, P]
         L.psht_adjoint_synthesis.argtypes = [P, I, I, P, P, I64, D, P, P, P]
         L.psht_plan_profile.argtypes = [P, I]
+        L.psht_plan_status.argtypes = [P, P, P]
         L.psht_plan_stage_times.argtypes = [P, P, P]
         L.psht_estimate_bytes.argtypes = [I, I, D, I64, D, U32]
         L.psht_estimate_bytes.restype = ctypes.c_size_t
@@ -189,6 +190,12 @@ class Plan:
         calls = np.zeros(8, dtype=np.int64)
         _check(lib().psht_plan_stage_times(self._h, ctypes.c_void_p(ms.ctypes.data), ctypes.c_void_p(calls.ctypes.data)))
         return {name: (float(ms[i]), int(calls[i])) for i, name in enumerate(self.STAGES)}
+
+    def status(self, stream=None) -> int:
+        """0 if every bounded wait in earlier calls completed (psht_plan_status); clears it."""
+        st = ctypes.c_int(0)
+        _check(lib().psht_plan_status(self._h, ctypes.byref(st), _stream(stream)))
+        return st.value
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

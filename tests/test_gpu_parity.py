@@ -94,6 +94,7 @@ def test_synthesis_against_direct_sum(lmax, s, radius, pole, eps, prec):
     g, c = _alm(rng, lmax, s), (_alm(rng, lmax, s) if s else None)
     plan = _plan(s, lmax, th, ph, eps, prec)
     f = plan.synthesis(_cu(g, plan), _cu(c, plan)).cpu().numpy()
+    assert plan.status() == 0
     ref = O.direct_synthesis(lmax, s, g, c, th, ph)
     assert O.rel_l2(f, ref) <= 10 * eps
     if prec == "fp64":
@@ -110,6 +111,7 @@ def test_adjoint_against_direct_sum(lmax, s, radius, pole, eps, prec):
     plan = _plan(s, lmax, th, ph, eps, prec)
     f = O.direct_synthesis(lmax, s, g, c, th, ph)      # f = A a: the adjoint's accuracy target
     gt, ct = plan.adjoint(_cu(f, plan))
+    assert plan.status() == 0
     gt, ct = gt.cpu().numpy(), ct.cpu().numpy()
     gt1, ct1 = O.direct_adjoint(lmax, s, th, ph, f)
     _, m = O.lm_of_index(lmax)
