@@ -229,8 +229,8 @@ void layout(Plan& p, double theta_star) {
   // adjoint: all active rings of one order m in one CTA, (rings per thread, threads) from the
   // instantiated shapes, more rings per thread in FP32 to amortise the per-l warp reduction
   if (p.prec == 32) {
-    p.adj_rpt = 8;
-    p.adj_threads = p.nring <= 1024 ? 128 : (p.nring <= 2048 ? 256 : 512);
+    p.adj_rpt = p.nring <= 1024 ? 4 : 8;
+    p.adj_threads = p.nring <= 2048 ? 256 : 512;
   } else {
     p.adj_rpt = p.nring <= 1024 ? 4 : 8;
     p.adj_threads = p.nring <= 512 ? 128 : (p.nring <= 2048 ? 256 : 512);

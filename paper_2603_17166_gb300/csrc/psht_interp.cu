@@ -276,9 +276,17 @@ __global__ void __launch_bounds__(NT) k_scatter(const TileItem* __restrict__ ite
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   V* tw = tiles + warp * cells;
   const unsigned lt = (1u << lane) - 1u;
-  for (int g0 = it.p0 + warp * 32; g0 < it.p0 + it.np; g0 += NT) {
-    const int pt = g0 + lane;
-    const bool valid = pt < it.p0 + it.np;
+  // warp w takes a contiguous slice of the item's points; within it lane i takes points
+  // i*ngrp .. i*ngrp + ngrp-1, so the 32 points spread at once lie in different parts of the tile and
+  // rarely share a base cell (the cell-sorted order would put equal cells side by side)
+  const int per_w = (it.np + NWARP - 1) / NWARP;
+  const int w0 = it.p0 + warp * per_w;
+  const int wn = max(0, min(per_w, it.p0 + it.np - w0));
+  const int ngrp = (wn + 31) >> 5;
+  for (int gi = 0; gi < ngrp; ++gi) {
+    const int k = lane * ngrp + gi;
+    const int pt = w0 + k;
+    const bool valid = k < wn;
     int lr = 0, lq = 0, key = -1 - lane;
     T wr[W], wq[W];
     V fv = mk((T)0, (T)0);

@@ -40,6 +40,17 @@ constexpr int kSpinLimit = 1 << 26;  // bounded mbarrier waits
 __device__ __forceinline__ int64_t alm_base(int lmax, int m) { return (int64_t)m * (2 * lmax + 1 - m) / 2; }
 
 template <typename T>
+struct Cx4;
+template <>
+struct Cx4<double> {
+  using V = double4;
+};
+template <>
+struct Cx4<float> {
+  using V = float4;
+};
+
+template <typename T>
 struct TabWidth;
 template <>
 struct TabWidth<double> {
@@ -331,6 +342,15 @@ __device__ __forceinline__ void classify(const Cols<T, RPT>& S, int nr, bool& fa
   skip = !fast && __all_sync(0xffffffffu, in1);
 }
 
+// warp w of nw takes 32-ring slots [s0, s1) of the ceil(n/32) slots: first ring wbase, wcnt rings
+__device__ __forceinline__ void slot_range(int n, int nw, int w, int& wbase, int& wcnt, int& nslot) {
+  const int ns = (n + 31) >> 5;
+  const int s0 = (w * ns) / nw, s1 = ((w + 1) * ns) / nw;
+  wbase = 32 * s0;
+  wcnt = max(0, min(32 * s1, n) - wbase);
+  nslot = s1 - s0;
+}
+
 template <typename T, bool SPIN, int RPT>
 __device__ __forceinline__ void init_col(Cols<T, RPT>& S, const RingDev* __restrict__ rings, const MSeed& sd,
                                          int jfirst, int jj, int nj, int r) {
@@ -370,14 +390,17 @@ __global__ void __launch_bounds__(NT) k_rec_syn(const RecItem* __restrict__ item
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int sfail;
 
+  // ring slots of 32 consecutive rings; the ceil(nj/32) slots are dealt to the warps in contiguous
+  // runs differing by at most one, so a warp's columns leave the dropped region together and the
+  // warps carry equal work; ring = wbase + r*32 + lane, slots r >= nr_w are empty for the warp
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int wbase = warp * 32 * RPT;
-  const int nr_w = max(0, min(RPT, (it.nj - wbase + 31) >> 5));
+  int wbase, wcnt, nr_w;
+  slot_range(it.nj, NT / 32, warp, wbase, wcnt, nr_w);
   Cols<T, RPT> S;
   T a[RPT][4];
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
-    init_col<T, SPIN, RPT>(S, rings, sd, it.j0, wbase + r * 32 + lane, it.nj, r);
+    init_col<T, SPIN, RPT>(S, rings, sd, it.j0 + wbase, r * 32 + lane, wcnt, r);
     a[r][0] = a[r][1] = a[r][2] = a[r][3] = (T)0;
   }
   const int64_t base = alm_base(lmax, m);
@@ -470,9 +493,9 @@ __global__ void __launch_bounds__(NT) k_rec_syn(const RecItem* __restrict__ item
   const T sgn_s = (s & 1) ? (T)1 : (T)-1;  // -(-1)^s
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
-    const int jj = wbase + r * 32 + lane;
-    if (jj < it.nj) {
-      const int j = it.j0 + jj;
+    const int jj = r * 32 + lane;
+    if (jj < wcnt) {
+      const int j = it.j0 + wbase + jj;
       // direct rings: F[m] <- column 1, F[-m] <- column 2; reflected rings: swapped
       const V fpos = rf ? mk(-a[r][2], -a[r][3]) : mk(-a[r][0], -a[r][1]);
       const V fneg = rf ? mk(sgn_s * a[r][0], sgn_s * a[r][1]) : mk(sgn_s * a[r][2], sgn_s * a[r][3]);
@@ -575,10 +598,12 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
   const int2 rr = mrange[m];
   const int nact = rr.y - rr.x;
   constexpr int NW = NT / 32;
+  using V4 = typename Cx4<T>::V;  // 4 partial sums of one l
   __shared__ __align__(16) TabStage<T> stg[2];
-  __shared__ T red[NW][kCH][4];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int sfail;
+  extern __shared__ __align__(16) unsigned char red_raw[];
+  V4* red = reinterpret_cast<V4*>(red_raw);  // [2][NW][kCH]: double buffer of per-warp partial sums
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int l = m + threadIdx.x; !accumulate && l < sd.l0 && l <= lmax; l += blockDim.x) {
     gt[base + l] = mk((T)0, (T)0);
@@ -586,18 +611,18 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
   }
   const bool m0 = (m == 0);
   const bool rf = refl != 0;
-  const int wbase = warp * 32 * RPT;  // ring slots as in the synthesis kernel
-  const int nr_w = max(0, min(RPT, (nact - wbase + 31) >> 5));
+  int wbase, wcnt, nr_w;  // ring slots as in the synthesis kernel
+  slot_range(nact, NW, warp, wbase, wcnt, nr_w);
 
   Cols<T, RPT> S;
   V f1[RPT], f2[RPT];  // ring values paired with column 1 / column 2
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
-    const int jj = wbase + r * 32 + lane;
-    init_col<T, SPIN, RPT>(S, rings, sd, rr.x, jj, nact, r);
+    const int jj = r * 32 + lane;
+    init_col<T, SPIN, RPT>(S, rings, sd, rr.x + wbase, jj, wcnt, r);
     f1[r] = f2[r] = mk((T)0, (T)0);
-    if (jj < nact) {
-      const int j = rr.x + jj;
+    if (jj < wcnt) {
+      const int j = rr.x + wbase + jj;
       const V fp = Ft[(int64_t)col_of(m) * Lpad + j];
       const V fm = m0 ? mk((T)0, (T)0) : Ft[(int64_t)col_of(-m) * Lpad + j];
       f1[r] = rf ? fm : fp;
@@ -631,6 +656,7 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
     }
     const TabStage<T>& st = stg[sidx];
     const int of = sidx ? off1 : off0;
+    T* redw = reinterpret_cast<T*>(red + (sidx * NW + warp) * kCH);
     for (int q = 0; q < nq; ++q) {
       T tot = (T)0;
       if (nr_w > 0 && !sfail) {
@@ -651,9 +677,9 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
           tot = reduce_scatter16<T>(v, lane);
         }
       }
-      if (lane < 16) red[warp][4 * q + (lane >> 2)][lane & 3] = tot;
+      if (lane < 16) redw[16 * q + lane] = tot;  // l = lc + 4q + (lane >> 2), sum (lane & 3)
     }
-    __syncthreads();  // stage sidx consumed, red complete
+    __syncthreads();  // stage sidx consumed, partial sums of chunk ch complete
     if (sfail) {
       if (threadIdx.x == 0) mbar_wait(&bar[sidx ^ 1], ((ch + 1) >> 1) & 1);  // drain the other stage
       return;
@@ -666,10 +692,11 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
       T q0 = 0, q1 = 0, q2 = 0, q3 = 0;
 #pragma unroll
       for (int w = 0; w < NW; ++w) {
-        q0 += red[w][i][0];
-        q1 += red[w][i][1];
-        q2 += red[w][i][2];
-        q3 += red[w][i][3];
+        const V4 x = red[(sidx * NW + w) * kCH + i];
+        q0 += x.x;
+        q1 += x.y;
+        q2 += x.z;
+        q3 += x.w;
       }
       const int l = lc + i;
       // sums against d_{m,-s}(theta) (Qp) and d_{m,s}(theta) (Qm); reflected rings swap the columns
@@ -702,7 +729,8 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
       gt[id] = gv;
       if (ct) ct[id] = cv;
     }
-    __syncthreads();  // red is rewritten by the next chunk
+    // no barrier here: the next chunk writes the other half of the double buffer, and the barrier
+    // after it orders these reads before this half is written again
   }
 }
 
@@ -720,7 +748,10 @@ void launch_adj_t(Plan& p, void* g, void* c, cudaStream_t st) {
   // one launch per ring part (rings at theta <= pi/2, then reflected rings at theta > pi/2)
   for (int part = 0; part < 2; ++part) {
     if (part == 1 && !p.has_refl) break;
-    k_rec_adj<T, SPIN, RPT, NT><<<p.lmax + 1, NT, 0, st>>>(
+    const size_t red_bytes = (size_t)2 * (NT / 32) * kCH * sizeof(typename Cx4<T>::V);
+    PSHT_CUDA_TRY(cudaFuncSetAttribute((const void*)k_rec_adj<T, SPIN, RPT, NT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red_bytes));
+    k_rec_adj<T, SPIN, RPT, NT><<<p.lmax + 1, NT, red_bytes, st>>>(
         p.d_ring, p.d_mseed, p.d_mrange + part * (p.lmax + 1), (const T*)p.d_rtab, p.tstride, (const V*)p.d_F,
         p.Lpad, p.lmax, p.spin, p.M, part, part, (V*)g, (V*)c, p.d_status);
   }
