@@ -150,6 +150,33 @@ int psht_synthesis(const void* g, const void* c, int spin, int lmax, const doubl
 int psht_adjoint_synthesis(const void* f, int spin, int lmax, const double* theta, const double* phi,
                            int64_t npts, double eps, void* g, void* c, void* stream);
 
+/*
+ * Allocation-free ring synthesis.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory — their device memory is owned by another allocator
+ * (a framework's caching pool, a memory-capped service), or they must not call cudaMalloc/cudaFree,
+ * which can synchronise the whole device, inside their own work.
+ *
+ * It computes the ring Fourier coefficients of synthesis general at arbitrary ring colatitudes,
+ *   F[j][m + lmax] = -sum_l (g_lm + i c_lm) sqrt((2l+1)/4pi) d^l_{m,-s}(theta_j),  |m| <= lmax,
+ * (the quantity psht_plan_ring_coeffs returns for a plan's rings, without the polar cutoff), in
+ * FP64, without a plan and without allocating: every intermediate lives in one fixed device array
+ * of the library (psht_noalloc_scratch_bytes(), about 4.4 MB), which every GPU that loads the
+ * library holds until the process exits.
+ *   theta: DEVICE float64[nring] in [0, pi];  g, c: DEVICE packed complex128 a_lm (c may be NULL);
+ *   F: DEVICE complex128 output [nring][2 lmax + 1], fully written.
+ * Limits: lmax <= PSHT_NOALLOC_MAX_LMAX, nring <= PSHT_NOALLOC_MAX_RINGS; larger sizes return
+ * PSHT_EINVAL with a message.  The array is shared by all calls and keeps the last call's contents
+ * (each call rewrites all it uses); calls that overlap on the GPU race on it and must be ordered
+ * by the caller.  The first call on a device looks up the array's address (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream capture.  Asynchronous on
+ * `stream`.
+ */
+#define PSHT_NOALLOC_MAX_LMAX 511
+#define PSHT_NOALLOC_MAX_RINGS 4096
+int psht_ring_synthesis_noalloc(int spin, int lmax, const double* theta, int nring, const void* g, const void* c,
+                                void* F, void* stream);
+size_t psht_noalloc_scratch_bytes(void);
+
 /* Device bytes a plan for these arguments would hold (theta_star = max distance to the pole). */
 size_t psht_estimate_bytes(int spin, int lmax, double theta_star, int64_t npts, double eps, uint32_t flags);
 

@@ -723,3 +723,14 @@ const char* psht_last_error(void) { return g_err.c_str(); }
 const char* psht_version(void) { return "psht 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+extern "C" {
+
+int psht_ring_synthesis_noalloc(int spin, int lmax, const double* theta, int nring, const void* g, const void* c,
+                                void* F, void* stream) {
+  return guarded([&] { ring_synthesis_noalloc(spin, lmax, theta, nring, g, c, F, (cudaStream_t)stream); });
+}
+
+size_t psht_noalloc_scratch_bytes(void) { return noalloc_scratch_bytes(); }
+
+}  // extern "C"

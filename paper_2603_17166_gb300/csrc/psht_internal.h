@@ -156,5 +156,8 @@ void launch_ring_coeffs_export(Plan& p, void* F, cudaStream_t st);
 void reduce_points(const double* theta, const double* phi, int64_t npts, double out[3], cudaStream_t st);
 void bin_points(Plan& p, const double* theta, const double* phi, cudaStream_t st);
 int max_fft_len(int prec);
+void ring_synthesis_noalloc(int spin, int lmax, const double* theta, int nring, const void* g, const void* c, void* F,
+                            cudaStream_t st);
+size_t noalloc_scratch_bytes();
 
 }  // namespace psht

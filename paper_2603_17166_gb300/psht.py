@@ -61,6 +61,8 @@ def lib():
         L.psht_plan_profile.argtypes = [P, I]
         L.psht_plan_status.argtypes = [P, P, P]
         L.psht_plan_stage_times.argtypes = [P, P, P]
+        L.psht_ring_synthesis_noalloc.argtypes = [I, I, P, I, P, P, P, P]
+        L.psht_noalloc_scratch_bytes.restype = ctypes.c_size_t
         L.psht_estimate_bytes.argtypes = [I, I, D, I64, D, U32]
         L.psht_estimate_bytes.restype = ctypes.c_size_t
         L.psht_last_error.restype = ctypes.c_char_p
@@ -240,3 +242,17 @@ def adjoint_synthesis(f, spin: int, lmax: int, theta, phi, eps: float, stream=No
 def estimate_bytes(spin: int, lmax: int, theta_star: float, npts: int, eps: float, precision="auto") -> int:
     return int(lib().psht_estimate_bytes(int(spin), int(lmax), float(theta_star), int(npts), float(eps),
                                          _PREC[precision]))
+
+
+def ring_synthesis_noalloc(spin: int, lmax: int, theta_rings, g, c=None, out=None, stream=None):
+    """Ring Fourier coefficients F[j, m + lmax] at the given ring colatitudes without allocating
+    inside the library (psht_ring_synthesis_noalloc): FP64, lmax <= 511, at most 4096 rings.
+    The library's fixed scratch array is shared by all calls; order overlapping calls yourself."""
+    torch = _torch()
+    th = torch.as_tensor(theta_rings, dtype=torch.float64, device="cuda").contiguous()
+    g = torch.as_tensor(g, device="cuda").to(torch.complex128).contiguous()
+    c = None if c is None else torch.as_tensor(c, device="cuda").to(torch.complex128).contiguous()
+    F = out if out is not None else torch.empty((th.numel(), 2 * lmax + 1), dtype=torch.complex128, device="cuda")
+    _check(lib().psht_ring_synthesis_noalloc(int(spin), int(lmax), _ptr(th), th.numel(), _ptr(g), _ptr(c), _ptr(F),
+                                             _stream(stream)))
+    return F
