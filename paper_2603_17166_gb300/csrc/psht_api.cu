@@ -222,7 +222,7 @@ void layout(Plan& p, double theta_star) {
   p.ntr = (p.nrows - 1) / p.TR + 1;
   p.ntq = (p.nphi + p.padq) / p.TQ + 1;
   p.nalm = (int64_t)(p.lmax + 1) * (p.lmax + 2) / 2;
-  p.tstride = (p.nalm + 72 + 7) / 8 * 8;  // room for the aligned over-read of the last chunk
+  p.tstride = p.nalm + 64;  // one chunk of zero records after the last order
   // launch shapes of the recursion
   p.syn_rpt = (p.prec == 64) ? 1 : 4;
   p.syn_threads = 128;
@@ -246,7 +246,7 @@ void layout(Plan& p, double theta_star) {
 size_t planned_bytes(const Plan& p) {
   const size_t cb = p.prec == 64 ? 16 : 8, rb = p.prec == 64 ? 8 : 4;
   size_t b = 0;
-  b += (size_t)rec_table_width(p.prec) * p.tstride * rb;        // recursion table
+  b += (size_t)rec_table_record_bytes() * p.tstride;            // recursion table
   b += (size_t)p.ncols * p.Lpad * cb;                          // ring coefficients
   b += (size_t)p.nrows * p.ncols * cb;                         // Theta-stage rows
   b += (size_t)p.nrows * p.gstride * cb;                       // grid
@@ -405,8 +405,8 @@ Plan* create(int spin, int lmax, const double* theta, const double* phi, int64_t
     }
     // work buffers
     const size_t cb = prec == 64 ? 16 : 8, rb = prec == 64 ? 8 : 4;
-    p->d_rtab = dalloc(*p, (size_t)rec_table_width(prec) * p->tstride * rb);
-    PSHT_CUDA_TRY(cudaMemsetAsync(p->d_rtab, 0, (size_t)rec_table_width(prec) * p->tstride * rb, st));
+    p->d_rtab = dalloc(*p, (size_t)rec_table_record_bytes() * p->tstride);
+    PSHT_CUDA_TRY(cudaMemsetAsync(p->d_rtab, 0, (size_t)rec_table_record_bytes() * p->tstride, st));
     p->d_status = (int*)dalloc(*p, sizeof(int));
     PSHT_CUDA_TRY(cudaMemsetAsync(p->d_status, 0, sizeof(int), st));
     p->d_F = dalloc(*p, (size_t)p->ncols * p->Lpad * cb);

@@ -34,37 +34,48 @@ namespace psht {
 namespace {
 
 constexpr int kCH = 64;              // l values per chunk
-constexpr int kPadE = 8;             // extra table elements per staged array (aligned over-read)
 constexpr int kSpinLimit = 1 << 26;  // bounded mbarrier waits
 
 __device__ __forceinline__ int64_t alm_base(int lmax, int m) { return (int64_t)m * (2 * lmax + 1 - m) / 2; }
 
+struct alignas(32) Dbl4 {
+  double x, y, z, w;
+};
 template <typename T>
 struct Cx4;
 template <>
 struct Cx4<double> {
-  using V = double4;
+  using V = Dbl4;
 };
 template <>
 struct Cx4<float> {
   using V = float4;
 };
 
+// One record of the recurrence table per packed (l, m), 32 bytes, so that a chunk of 64 l is one
+// contiguous bulk copy and one l is two vector shared-memory loads.
+__device__ __forceinline__ float4 mk4(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+__device__ __forceinline__ Dbl4 mk4(double2 a, double2 b) { return Dbl4{a.x, a.y, b.x, b.y}; }
+
 template <typename T>
-struct TabWidth;
+struct TabEntry;
 template <>
-struct TabWidth<double> {
-  static constexpr int v = 4;  // A, D, B, C
+struct TabEntry<float> {
+  float4 ad;  // A_hi, A_lo, D_hi, D_lo
+  float2 bc;  // B, C
+  float2 pad;
 };
 template <>
-struct TabWidth<float> {
-  static constexpr int v = 6;  // A_hi, A_lo, D_hi, D_lo, B, C
+struct TabEntry<double> {
+  double2 ad;  // A, D
+  double2 bc;  // B, C
 };
+static_assert(sizeof(TabEntry<float>) == 32 && sizeof(TabEntry<double>) == 32, "table records are 32 bytes");
 
 // ---------------------------------------------------------------------------------------------
-// recurrence table per packed (l, m), FP64 arithmetic, one thread per m; array k at k * ts.
+// recurrence table per packed (l, m), FP64 arithmetic, one thread per m.
 template <typename T>
-__global__ void k_rec_table(int lmax, int s, T* __restrict__ tab, int64_t ts) {
+__global__ void k_rec_table(int lmax, int s, TabEntry<T>* __restrict__ tab) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m > lmax) return;
   const int l0 = max(m, s);
@@ -83,21 +94,17 @@ __global__ void k_rec_table(int lmax, int s, T* __restrict__ tab, int64_t ts) {
       }
       D = (A - 1.0) - C;
     }
-    const int64_t id = base + l;
-    if (sizeof(T) == 8) {
-      tab[id] = (T)A;
-      tab[ts + id] = (T)D;
-      tab[2 * ts + id] = (T)B;
-      tab[3 * ts + id] = (T)C;
+    TabEntry<T> e;
+    if constexpr (sizeof(T) == 8) {
+      e.ad = make_double2(A, D);
+      e.bc = make_double2(B, C);
     } else {
       const float ah = (float)A, dh = (float)D;
-      tab[id] = ah;
-      tab[ts + id] = (float)(A - (double)ah);
-      tab[2 * ts + id] = dh;
-      tab[3 * ts + id] = (float)(D - (double)dh);
-      tab[4 * ts + id] = (float)B;
-      tab[5 * ts + id] = (float)C;
+      e.ad = make_float4(ah, (float)(A - (double)ah), dh, (float)(D - (double)dh));
+      e.bc = make_float2((float)B, (float)C);
+      e.pad = make_float2(0.f, 0.f);
     }
+    tab[base + l] = e;
   }
 }
 
@@ -134,30 +141,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
-// One staged chunk of the table: array k holds elements [a0, a0 + cnt) of table array k; the
-// chunk's first l sits at offset `off` (a0 is the 16-byte aligned start of the copy).
+// One staged chunk of the table: records of l = lc .. lc + 63 (zero records past lmax).
 template <typename T>
 struct TabStage {
-  T v[TabWidth<T>::v][kCH + kPadE];
+  TabEntry<T> v[kCH];
 };
-template <typename T>
-__device__ __forceinline__ int chunk_off(int64_t start) {
-  return (int)(start & (16 / (int)sizeof(T) - 1));
-}
 
-// Issue the bulk copies of table elements start .. start + 63 of every array into st (one thread).
-// The table arrays are padded, so the aligned over-read stays inside the allocation.
+// Issue the bulk copy of table records start .. start + 63 into st (one thread).  The table is
+// padded by one chunk of zero records, so the last chunk never reads past the allocation.
 template <typename T>
-__device__ __forceinline__ void issue_chunk(TabStage<T>& st, uint64_t* bar, const T* __restrict__ tab, int64_t ts,
+__device__ __forceinline__ void issue_chunk(TabStage<T>& st, uint64_t* bar, const TabEntry<T>* __restrict__ tab,
                                             int64_t start) {
-  constexpr int A = 16 / sizeof(T);  // elements per 16 bytes
-  const int64_t a0 = start & ~(int64_t)(A - 1);
-  const int cnt = ((int)(start - a0) + kCH + A - 1) / A * A;
-  const uint32_t bytes = (uint32_t)(cnt * sizeof(T));
+  constexpr uint32_t bytes = kCH * sizeof(TabEntry<T>);
   fence_proxy_async();  // earlier generic reads of this stage before the async-proxy writes
-  mbar_expect_tx(bar, bytes * TabWidth<T>::v);
-#pragma unroll
-  for (int k = 0; k < TabWidth<T>::v; ++k) bulk_g2s(st.v[k], tab + k * ts + a0, bytes, bar);
+  mbar_expect_tx(bar, bytes);
+  bulk_g2s(st.v, tab + start, bytes, bar);
 }
 
 template <typename T>
@@ -175,10 +173,13 @@ struct Coef<float> {
   }
 };
 __device__ __forceinline__ Coef<double> get_coef(const TabStage<double>& s, int i) {
-  return Coef<double>{s.v[0][i], s.v[1][i], s.v[2][i], s.v[3][i]};
+  const double2 ad = s.v[i].ad, bc = s.v[i].bc;
+  return Coef<double>{ad.x, ad.y, bc.x, bc.y};
 }
 __device__ __forceinline__ Coef<float> get_coef(const TabStage<float>& s, int i) {
-  return Coef<float>{s.v[0][i], s.v[1][i], s.v[2][i], s.v[3][i], s.v[4][i], s.v[5][i]};
+  const float4 ad = s.v[i].ad;
+  const float2 bc = s.v[i].bc;
+  return Coef<float>{ad.x, ad.y, ad.z, ad.w, bc.x, bc.y};
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -286,13 +287,14 @@ struct Cols {
 // ACC: add the current column values to the sums; SEL: per column, only where k == 0.
 template <typename T, bool SPIN, int RPT, bool ACC, bool SEL>
 __device__ __forceinline__ void syn_quad(Cols<T, RPT>& S, T (&a)[RPT][4], const TabStage<T>& st, int off, int i0,
-                                         const typename Cx<T>::V* sP, const typename Cx<T>::V* sQ, int nr) {
+                                         const typename Cx4<T>::V* sPQ, int nr) {
   using V = typename Cx<T>::V;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int i = i0 + u;
     const Coef<T> cf = get_coef(st, off + i);
-    const V P = sP[i], Q = sQ[i];
+    const typename Cx4<T>::V pq = sPQ[i];
+    const V P = mk(pq.x, pq.y), Q = mk(pq.z, pq.w);
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
       if (r < nr) {
@@ -377,8 +379,8 @@ __device__ __forceinline__ void init_col(Cols<T, RPT>& S, const RingDev* __restr
 // columns leave the dropped region together); slots r >= nr_w are empty for the whole warp.
 template <typename T, bool SPIN, int RPT, int NT>
 __global__ void __launch_bounds__(NT) k_rec_syn(const RecItem* __restrict__ items, const RingDev* __restrict__ rings,
-                                                const MSeed* __restrict__ mseed, const T* __restrict__ tab,
-                                                int64_t ts, const typename Cx<T>::V* __restrict__ g,
+                                                const MSeed* __restrict__ mseed, const TabEntry<T>* __restrict__ tab,
+                                                const typename Cx<T>::V* __restrict__ g,
                                                 const typename Cx<T>::V* __restrict__ c, int lmax, int s,
                                                 typename Cx<T>::V* __restrict__ F, int Lpad, int* __restrict__ status) {
   using V = typename Cx<T>::V;
@@ -386,7 +388,8 @@ __global__ void __launch_bounds__(NT) k_rec_syn(const RecItem* __restrict__ item
   const int m = it.m;
   const MSeed sd = mseed[m];
   __shared__ __align__(16) TabStage<T> stg[2];
-  __shared__ V sP[2][kCH], sQ[2][kCH];
+  using V4 = typename Cx4<T>::V;
+  __shared__ V4 sPQ[2][kCH];  // (P.x, P.y, Q.x, Q.y) per l
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int sfail;
 
@@ -418,16 +421,15 @@ __global__ void __launch_bounds__(NT) k_rec_syn(const RecItem* __restrict__ item
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    issue_chunk<T>(stg[0], &bar[0], tab, ts, base + sd.l0);
-    if (nchunk > 1) issue_chunk<T>(stg[1], &bar[1], tab, ts, base + sd.l0 + kCH);
+    issue_chunk<T>(stg[0], &bar[0], tab, base + sd.l0);
+    if (nchunk > 1) issue_chunk<T>(stg[1], &bar[1], tab, base + sd.l0 + kCH);
   }
   for (int cc = 0; cc < 2 && cc < nchunk; ++cc) {
     for (int i = threadIdx.x; i < kCH; i += NT) {
       const int l = sd.l0 + cc * kCH + i;
       V P = mk((T)0, (T)0), Q = mk((T)0, (T)0);
       if (l <= lmax) make_pq<V, T>(g[base + l], c ? c[base + l] : mk((T)0, (T)0), m0, rf, l + m, P, Q);
-      sP[cc][i] = P;
-      sQ[cc][i] = Q;
+      sPQ[cc][i] = mk4(P, Q);
     }
   }
   V pg = mk((T)0, (T)0), pc = mk((T)0, (T)0);  // a_lm two chunks ahead
@@ -438,7 +440,6 @@ __global__ void __launch_bounds__(NT) k_rec_syn(const RecItem* __restrict__ item
       if (c) pc = c[base + l];
     }
   }
-  int off0 = chunk_off<T>(base + sd.l0), off1 = chunk_off<T>(base + sd.l0 + kCH);
   __syncthreads();
 
   for (int ch = 0; ch < nchunk; ++ch) {
@@ -451,18 +452,17 @@ __global__ void __launch_bounds__(NT) k_rec_syn(const RecItem* __restrict__ item
     const int nq = (min(kCH, lmax - lc + 1) + 3) >> 2;
     if (nr_w > 0 && !sfail) {
       const TabStage<T>& st = stg[sidx];
-      const V* P = sP[sidx];
-      const V* Q = sQ[sidx];
-      const int of = sidx ? off1 : off0;
+      const V4* PQ = sPQ[sidx];
+      constexpr int of = 0;
       for (int q = 0; q < nq; ++q) {
         bool fast, skip;
         classify<T, SPIN, RPT>(S, nr_w, fast, skip);
         if (fast) {
-          if (nr_w == RPT) syn_quad<T, SPIN, RPT, true, false>(S, a, st, of, 4 * q, P, Q, RPT);
-          else syn_quad<T, SPIN, RPT, true, false>(S, a, st, of, 4 * q, P, Q, nr_w);
+          if (nr_w == RPT) syn_quad<T, SPIN, RPT, true, false>(S, a, st, of, 4 * q, PQ, RPT);
+          else syn_quad<T, SPIN, RPT, true, false>(S, a, st, of, 4 * q, PQ, nr_w);
         } else {
-          if (skip) syn_quad<T, SPIN, RPT, false, false>(S, a, st, of, 4 * q, P, Q, nr_w);
-          else syn_quad<T, SPIN, RPT, true, true>(S, a, st, of, 4 * q, P, Q, nr_w);
+          if (skip) syn_quad<T, SPIN, RPT, false, false>(S, a, st, of, 4 * q, PQ, nr_w);
+          else syn_quad<T, SPIN, RPT, true, true>(S, a, st, of, 4 * q, PQ, nr_w);
           rescale_all<T, SPIN, RPT>(S, nr_w);
         }
       }
@@ -473,14 +473,12 @@ __global__ void __launch_bounds__(NT) k_rec_syn(const RecItem* __restrict__ item
       return;
     }
     if (ch + 2 < nchunk) {
-      if (threadIdx.x == 0) issue_chunk<T>(stg[sidx], &bar[sidx], tab, ts, base + lc + 2 * kCH);
-      (sidx ? off1 : off0) = chunk_off<T>(base + lc + 2 * kCH);
+      if (threadIdx.x == 0) issue_chunk<T>(stg[sidx], &bar[sidx], tab, base + lc + 2 * kCH);
       if (threadIdx.x < kCH) {
         const int l = lc + 2 * kCH + threadIdx.x;
         V Pn = mk((T)0, (T)0), Qn = mk((T)0, (T)0);
         if (l <= lmax) make_pq<V, T>(pg, pc, m0, rf, l + m, Pn, Qn);
-        sP[sidx][threadIdx.x] = Pn;
-        sQ[sidx][threadIdx.x] = Qn;
+        sPQ[sidx][threadIdx.x] = mk4(Pn, Qn);
         pg = pc = mk((T)0, (T)0);
         const int l3 = l + kCH;
         if (l3 <= lmax) {
@@ -578,8 +576,8 @@ __device__ __forceinline__ void adj_quad_steps(Cols<T, RPT>& S, const TabStage<T
 
 template <typename T, bool SPIN, int RPT, int NT>
 __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ rings, const MSeed* __restrict__ mseed,
-                                                const int2* __restrict__ mrange, const T* __restrict__ tab,
-                                                int64_t ts, const typename Cx<T>::V* __restrict__ Ft, int Lpad,
+                                                const int2* __restrict__ mrange, const TabEntry<T>* __restrict__ tab,
+                                                const typename Cx<T>::V* __restrict__ Ft, int Lpad,
                                                 int lmax, int s, int M, int refl, int accumulate,
                                                 typename Cx<T>::V* __restrict__ gt, typename Cx<T>::V* __restrict__ ct,
                                                 int* __restrict__ status) {
@@ -632,7 +630,6 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
   const T sg = (((m - s) & 1) ? (T)1 : (T)-1);  // -(-1)^(m-s)
   const T sm = (m & 1) ? (T)-1 : (T)1;          // (-1)^m
   const int nchunk = (lmax - sd.l0 + kCH) / kCH;
-  int off0 = chunk_off<T>(base + sd.l0), off1 = chunk_off<T>(base + sd.l0 + kCH);
   if (threadIdx.x == 0) {
     sfail = 0;
     mbar_init(&bar[0], 1);
@@ -641,8 +638,8 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    issue_chunk<T>(stg[0], &bar[0], tab, ts, base + sd.l0);
-    if (nchunk > 1) issue_chunk<T>(stg[1], &bar[1], tab, ts, base + sd.l0 + kCH);
+    issue_chunk<T>(stg[0], &bar[0], tab, base + sd.l0);
+    if (nchunk > 1) issue_chunk<T>(stg[1], &bar[1], tab, base + sd.l0 + kCH);
   }
 
   for (int ch = 0; ch < nchunk; ++ch) {
@@ -655,7 +652,7 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
       sfail = 1;
     }
     const TabStage<T>& st = stg[sidx];
-    const int of = sidx ? off1 : off0;
+    constexpr int of = 0;
     T* redw = reinterpret_cast<T*>(red + (sidx * NW + warp) * kCH);
     for (int q = 0; q < nq; ++q) {
       T tot = (T)0;
@@ -685,8 +682,7 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
       return;
     }
     if (ch + 2 < nchunk) {
-      if (threadIdx.x == 0) issue_chunk<T>(stg[sidx], &bar[sidx], tab, ts, base + lc + 2 * kCH);
-      (sidx ? off1 : off0) = chunk_off<T>(base + lc + 2 * kCH);
+      if (threadIdx.x == 0) issue_chunk<T>(stg[sidx], &bar[sidx], tab, base + lc + 2 * kCH);
     }
     for (int i = threadIdx.x; i < n; i += NT) {
       T q0 = 0, q1 = 0, q2 = 0, q3 = 0;
@@ -737,8 +733,8 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
 template <typename T, bool SPIN, int RPT>
 void launch_syn_t(Plan& p, const void* g, const void* c, cudaStream_t st) {
   using V = typename Cx<T>::V;
-  k_rec_syn<T, SPIN, RPT, 128><<<p.nitems, 128, 0, st>>>(p.d_items, p.d_ring, p.d_mseed, (const T*)p.d_rtab,
-                                                          p.tstride, (const V*)g, (const V*)c, p.lmax, p.spin,
+  k_rec_syn<T, SPIN, RPT, 128><<<p.nitems, 128, 0, st>>>(p.d_items, p.d_ring, p.d_mseed,
+                                                          (const TabEntry<T>*)p.d_rtab, (const V*)g, (const V*)c, p.lmax, p.spin,
                                                           (V*)p.d_F, p.Lpad, p.d_status);
 }
 
@@ -752,7 +748,7 @@ void launch_adj_t(Plan& p, void* g, void* c, cudaStream_t st) {
     PSHT_CUDA_TRY(cudaFuncSetAttribute((const void*)k_rec_adj<T, SPIN, RPT, NT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red_bytes));
     k_rec_adj<T, SPIN, RPT, NT><<<p.lmax + 1, NT, red_bytes, st>>>(
-        p.d_ring, p.d_mseed, p.d_mrange + part * (p.lmax + 1), (const T*)p.d_rtab, p.tstride, (const V*)p.d_F,
+        p.d_ring, p.d_mseed, p.d_mrange + part * (p.lmax + 1), (const TabEntry<T>*)p.d_rtab, (const V*)p.d_F,
         p.Lpad, p.lmax, p.spin, p.M, part, part, (V*)g, (V*)c, p.d_status);
   }
 }
@@ -779,12 +775,12 @@ void launch_adj_s(Plan& p, void* g, void* c, cudaStream_t st) {
 
 }  // namespace
 
-int rec_table_width(int prec) { return prec == 64 ? 4 : 6; }
+int rec_table_record_bytes() { return 32; }
 
 void build_rec_table(Plan& p, cudaStream_t st) {
   const int nth = 128, nbl = (p.lmax + 1 + nth - 1) / nth;
-  if (p.prec == 64) k_rec_table<double><<<nbl, nth, 0, st>>>(p.lmax, p.spin, (double*)p.d_rtab, p.tstride);
-  else k_rec_table<float><<<nbl, nth, 0, st>>>(p.lmax, p.spin, (float*)p.d_rtab, p.tstride);
+  if (p.prec == 64) k_rec_table<double><<<nbl, nth, 0, st>>>(p.lmax, p.spin, (TabEntry<double>*)p.d_rtab);
+  else k_rec_table<float><<<nbl, nth, 0, st>>>(p.lmax, p.spin, (TabEntry<float>*)p.d_rtab);
   PSHT_CUDA_TRY(cudaGetLastError());
 }
 
