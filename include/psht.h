@@ -101,6 +101,21 @@ int psht_plan_synthesis(psht_plan* plan, const void* g, const void* c, void* f, 
 int psht_plan_adjoint(psht_plan* plan, const void* f, void* g, void* c, void* stream);
 
 /*
+ * Packed-gradient forms, for automatic differentiation over the packed a_lm arrays.  The transpose
+ * above pairs with the inner product that counts each m > 0 entry twice (it stands for m and -m,
+ * eq. syn's reality condition), while a gradient over the packed storage counts every stored
+ * entry once: dL/dRe a + i dL/dIm a for a real loss L.
+ *   psht_plan_adjoint_packed: as psht_plan_adjoint, with the m > 0 entries of g~ and c~ doubled,
+ *     i.e. the packed gradients of Re sum_p conj(f_p) [synthesis(g, c)]_p with respect to g and c.
+ *   psht_plan_synthesis_packed: as psht_plan_synthesis, with the m > 0 entries of g and c halved,
+ *     i.e. the gradient with respect to f of Re <(g, c), adjoint(f)> taken over the packed storage.
+ * m = 0 entries are unchanged (their imaginary parts are ignored on input and written as 0).
+ * Arguments, layout, ownership and errors as for the plain forms.
+ */
+int psht_plan_synthesis_packed(psht_plan* plan, const void* g, const void* c, void* f, void* stream);
+int psht_plan_adjoint_packed(psht_plan* plan, const void* f, void* g, void* c, void* stream);
+
+/*
  * Host-buffer forms of the two calls above: g, c, f are HOST pointers (pinned memory gives the
  * fastest copies).  Copies inputs to the device, runs the transform on `stream` and copies the
  * result back; returns after `stream` has synchronised, so the host buffers hold the result.
@@ -179,6 +194,72 @@ size_t psht_noalloc_scratch_bytes(void);
 
 /* Device bytes a plan for these arguments would hold (theta_star = max distance to the pole). */
 size_t psht_estimate_bytes(int spin, int lmax, double theta_star, int64_t npts, double eps, uint32_t flags);
+
+/*
+ * Device bytes a plan for these points would hold: one device reduction over the points (theta*
+ * and the nearer pole, Sec. II step 1), then the planner's layout.  theta, phi: DEVICE float64[npts].
+ * Synchronises `stream`.  Writes *bytes; EINVAL for invalid points, as psht_plan_create.
+ */
+int psht_plan_estimate_points(int spin, int lmax, const double* theta, const double* phi, int64_t npts, double eps,
+                              uint32_t flags, void* stream, size_t* bytes);
+
+/*
+ * Request server: a native runtime that executes many transforms concurrently on one GPU.  The
+ * paper has no counterpart; it is the serving layer over the plan API above.
+ *   - nstreams worker threads, each with its own non-blocking CUDA stream, take requests in
+ *     arrival order; a request whose plan is in use by another worker is passed over, not waited
+ *     on, so independent requests overlap on the GPU.
+ *   - Plans are cached by (points_key, spin, lmax, eps, flags): the caller names its point set by
+ *     points_key, and equal keys must denote the same theta/phi values.
+ *   - Admission: a new plan is created only if the cached plans plus its estimate fit in the
+ *     budget (bytes; 0 = 80 % of the device memory free at creation); least-recently-used idle
+ *     plans are evicted to make room; a request that cannot fit yet waits in the queue, and one
+ *     that can never fit fails with PSHT_ENOMEM.
+ * A request's device buffers (points, inputs, outputs) must stay valid until psht_server_wait has
+ * returned for its ticket.  Latencies are host wall-clock from submission to the completion of the
+ * request's stream work.
+ */
+#define PSHT_OP_SYNTHESIS 0
+#define PSHT_OP_ADJOINT 1
+typedef struct psht_server psht_server;
+typedef struct {
+  int op;              /* PSHT_OP_SYNTHESIS or PSHT_OP_ADJOINT                                 */
+  int spin, lmax;
+  double eps;
+  uint32_t flags;      /* precision flags as for psht_plan_create                              */
+  uint64_t points_key; /* caller's name of the point set                                       */
+  const double* theta; /* DEVICE float64[npts]; read when the plan is not cached               */
+  const double* phi;
+  int64_t npts;
+  const void* in_a;    /* synthesis: g; adjoint: f          (DEVICE, the plan's precision)     */
+  const void* in_b;    /* synthesis: c or NULL; adjoint: unused                                */
+  void* out_a;         /* synthesis: f; adjoint: g~                                            */
+  void* out_b;         /* synthesis: unused; adjoint: c~ or NULL                               */
+} psht_request;
+typedef struct {
+  int status;          /* PSHT_OK or the request's error code                                  */
+  int worker;          /* index of the worker (stream) that ran it                             */
+  int plan_cached;     /* 1 if the plan came from the cache                                    */
+  int precision;       /* 32 or 64                                                              */
+  double queue_ms;     /* submission to start of work                                          */
+  double plan_ms;      /* plan creation (0 when cached)                                        */
+  double exec_ms;      /* transform, until its stream completed                                */
+  double total_ms;     /* submission to completion                                             */
+} psht_result;
+typedef struct {
+  int64_t submitted, completed, failed, plans_created, cache_hits, evictions;
+  size_t budget, bytes_in_use, bytes_peak;
+} psht_server_stats;
+
+/* Start nstreams (1..64) workers on the current device.  *out receives the server. */
+int psht_server_create(int nstreams, size_t budget_bytes, psht_server** out);
+/* Queue a request (copied); *ticket identifies it for psht_server_wait. */
+int psht_server_submit(psht_server* server, const psht_request* request, int64_t* ticket);
+/* Block until the ticket's request has finished; writes its result.  Each ticket is waited once. */
+int psht_server_wait(psht_server* server, int64_t ticket, psht_result* result);
+int psht_server_get_stats(psht_server* server, psht_server_stats* stats);
+/* Finish every queued request, stop the workers and release all cached plans.  NULL is a no-op. */
+int psht_server_destroy(psht_server* server);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char* psht_last_error(void);

@@ -246,7 +246,7 @@ void layout(Plan& p, double theta_star) {
 size_t planned_bytes(const Plan& p) {
   const size_t cb = p.prec == 64 ? 16 : 8, rb = p.prec == 64 ? 8 : 4;
   size_t b = 0;
-  b += (size_t)rec_table_record_bytes() * p.tstride;            // recursion table
+  b += (size_t)rec_table_record_bytes(p.prec) * p.tstride;            // recursion table
   b += (size_t)p.ncols * p.Lpad * cb;                          // ring coefficients
   b += (size_t)p.nrows * p.ncols * cb;                         // Theta-stage rows
   b += (size_t)p.nrows * p.gstride * cb;                       // grid
@@ -405,8 +405,8 @@ Plan* create(int spin, int lmax, const double* theta, const double* phi, int64_t
     }
     // work buffers
     const size_t cb = prec == 64 ? 16 : 8, rb = prec == 64 ? 8 : 4;
-    p->d_rtab = dalloc(*p, (size_t)rec_table_record_bytes() * p->tstride);
-    PSHT_CUDA_TRY(cudaMemsetAsync(p->d_rtab, 0, (size_t)rec_table_record_bytes() * p->tstride, st));
+    p->d_rtab = dalloc(*p, (size_t)rec_table_record_bytes(p->prec) * p->tstride);
+    PSHT_CUDA_TRY(cudaMemsetAsync(p->d_rtab, 0, (size_t)rec_table_record_bytes(p->prec) * p->tstride, st));
     p->d_status = (int*)dalloc(*p, sizeof(int));
     PSHT_CUDA_TRY(cudaMemsetAsync(p->d_status, 0, sizeof(int), st));
     p->d_F = dalloc(*p, (size_t)p->ncols * p->Lpad * cb);
@@ -472,14 +472,14 @@ void staged(Plan& p, int stage, cudaStream_t st, F&& fn) {
   p.recs.push_back(r);
 }
 
-void run_synthesis(Plan& p, const void* g, const void* c, void* f, cudaStream_t st) {
-  staged(p, 0, st, [&] { launch_rec_synthesis(p, g, c, st); });
+void run_synthesis(Plan& p, const void* g, const void* c, void* f, cudaStream_t st, double msc = 1.0) {
+  staged(p, 0, st, [&] { launch_rec_synthesis(p, g, c, st, msc); });
   staged(p, 1, st, [&] { launch_theta_synthesis(p, st); });
   staged(p, 2, st, [&] { launch_phi_synthesis(p, st); });
   staged(p, 3, st, [&] { launch_gather(p, f, st); });
 }
 
-void run_adjoint(Plan& p, const void* f, void* g, void* c, cudaStream_t st) {
+void run_adjoint(Plan& p, const void* f, void* g, void* c, cudaStream_t st, double msc = 1.0) {
   const size_t cb = p.prec == 64 ? 16 : 8;
   staged(p, 4, st, [&] {
     PSHT_CUDA_TRY(cudaMemsetAsync(p.d_G, 0, (size_t)p.nrows * p.gstride * cb, st));
@@ -487,7 +487,7 @@ void run_adjoint(Plan& p, const void* f, void* g, void* c, cudaStream_t st) {
   });
   staged(p, 5, st, [&] { launch_phi_adjoint(p, st); });
   staged(p, 6, st, [&] { launch_theta_adjoint(p, st); });
-  staged(p, 7, st, [&] { launch_rec_adjoint(p, g, c, st); });
+  staged(p, 7, st, [&] { launch_rec_adjoint(p, g, c, st, msc); });
 }
 
 void ensure_io(Plan& p) {
@@ -565,6 +565,22 @@ int psht_plan_adjoint(psht_plan* plan, const void* f, void* g, void* c, void* st
     PSHT_REQUIRE(plan && g, PSHT_EINVAL, "plan and g must not be NULL");
     PSHT_REQUIRE(f || plan->p->npts == 0, PSHT_EINVAL, "f must not be NULL");
     run_adjoint(*plan->p, f, g, c, (cudaStream_t)stream);
+  });
+}
+
+int psht_plan_synthesis_packed(psht_plan* plan, const void* g, const void* c, void* f, void* stream) {
+  return guarded([&] {
+    PSHT_REQUIRE(plan && g, PSHT_EINVAL, "plan and g must not be NULL");
+    PSHT_REQUIRE(f || plan->p->npts == 0, PSHT_EINVAL, "f must not be NULL");
+    run_synthesis(*plan->p, g, c, f, (cudaStream_t)stream, 0.5);
+  });
+}
+
+int psht_plan_adjoint_packed(psht_plan* plan, const void* f, void* g, void* c, void* stream) {
+  return guarded([&] {
+    PSHT_REQUIRE(plan && g, PSHT_EINVAL, "plan and g must not be NULL");
+    PSHT_REQUIRE(f || plan->p->npts == 0, PSHT_EINVAL, "f must not be NULL");
+    run_adjoint(*plan->p, f, g, c, (cudaStream_t)stream, 2.0);
   });
 }
 
@@ -716,6 +732,30 @@ size_t psht_estimate_bytes(int spin, int lmax, double theta_star, int64_t npts, 
   } catch (...) {
     return 0;
   }
+}
+
+int psht_plan_estimate_points(int spin, int lmax, const double* theta, const double* phi, int64_t npts, double eps,
+                              uint32_t flags, void* stream, size_t* bytes) {
+  return guarded([&] {
+    PSHT_REQUIRE(bytes != nullptr, PSHT_EINVAL, "bytes must not be NULL");
+    PSHT_REQUIRE(npts >= 0 && npts < ((int64_t)1 << 31), PSHT_EINVAL, "npts must lie in [0, 2^31)");
+    PSHT_REQUIRE(npts == 0 || (theta && phi), PSHT_EINVAL, "theta and phi must be device pointers");
+    PSHT_REQUIRE(eps >= 1e-14 && eps <= 1e-1, PSHT_EINVAL, "eps must lie in [1e-14, 1e-1]");
+    PSHT_REQUIRE(spin >= 0 && lmax >= spin && lmax <= 65535, PSHT_EINVAL, "invalid spin or lmax");
+    double red[3];
+    reduce_points(theta, phi, npts, red, (cudaStream_t)stream);
+    PSHT_REQUIRE(red[2] == 0.0, PSHT_EINVAL, "theta outside [0, pi], NaN, or non-finite phi in the points");
+    Plan p;
+    p.spin = spin;
+    p.lmax = lmax;
+    p.eps = eps;
+    const uint32_t pf = flags & 3u;
+    p.prec = (pf == PSHT_FP64) ? 64 : (pf == PSHT_FP32) ? 32 : (eps >= 1e-5 ? 32 : 64);
+    p.npts = npts;
+    p.pole = (red[0] <= red[1]) ? 1 : -1;
+    layout(p, p.pole > 0 ? red[0] : red[1]);
+    *bytes = planned_bytes(p);
+  });
 }
 
 const char* psht_last_error(void) { return g_err.c_str(); }

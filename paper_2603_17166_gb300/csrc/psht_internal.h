@@ -102,7 +102,7 @@ struct Plan {
   MSeed* d_mseed = nullptr;
   int2* d_mrange = nullptr;     // active ring range [j_lo, j_hi) per m: part 0 (theta <= pi/2), then part 1
   int has_refl = 0;             // any ring at theta > pi/2 (part 1 non-empty)
-  void* d_rtab = nullptr;       // recurrence table: one 32-byte record per packed (l, m), padded by one chunk
+  void* d_rtab = nullptr;       // recurrence table: one record per packed (l, m) (32 B FP64, 48 B FP32), padded by one chunk
   int64_t tstride = 0;          // records in the table (nalm + one chunk of zero records)
   int* d_status = nullptr;      // device error word (bounded waits that gave up), read by psht_plan_status
   RecItem* d_items = nullptr;
@@ -142,10 +142,11 @@ struct Plan {
 };
 
 // kernels / launchers ---------------------------------------------------------------------------
-int rec_table_record_bytes();  // bytes per (l, m) record of the recurrence table
+int rec_table_record_bytes(int prec);  // bytes per (l, m) record of the recurrence table
 void build_rec_table(Plan& p, cudaStream_t st);
-void launch_rec_synthesis(Plan& p, const void* g, const void* c, cudaStream_t st);
-void launch_rec_adjoint(Plan& p, void* g, void* c, cudaStream_t st);
+// msc: weight of the m > 0 a_lm entries (read by the synthesis, written by the adjoint)
+void launch_rec_synthesis(Plan& p, const void* g, const void* c, cudaStream_t st, double msc = 1.0);
+void launch_rec_adjoint(Plan& p, void* g, void* c, cudaStream_t st, double msc = 1.0);
 void launch_theta_synthesis(Plan& p, cudaStream_t st);
 void launch_phi_synthesis(Plan& p, cudaStream_t st);
 void launch_phi_adjoint(Plan& p, cudaStream_t st);

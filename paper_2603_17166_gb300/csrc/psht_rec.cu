@@ -52,25 +52,29 @@ struct Cx4<float> {
   using V = float4;
 };
 
-// One record of the recurrence table per packed (l, m), 32 bytes, so that a chunk of 64 l is one
-// contiguous bulk copy and one l is two vector shared-memory loads.
-__device__ __forceinline__ float4 mk4(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
-__device__ __forceinline__ Dbl4 mk4(double2 a, double2 b) { return Dbl4{a.x, a.y, b.x, b.y}; }
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
 
+// One record of the recurrence table per packed (l, m), so that a chunk of 64 l is one contiguous
+// bulk copy and one l is a few vector shared-memory loads.  The FP32 form works on pairs of rings
+// with packed FP32x2 instructions, so its record holds every coefficient twice (one per ring of
+// the pair) and A negated: the packed operands come straight from shared memory.
 template <typename T>
 struct TabEntry;
 template <>
 struct TabEntry<float> {
-  float4 ad;  // A_hi, A_lo, D_hi, D_lo
-  float2 bc;  // B, C
-  float2 pad;
+  float4 na;  // -A_hi, -A_hi, -A_lo, -A_lo
+  float4 d;   // D_hi, D_hi, D_lo, D_lo
+  float4 bc;  // B, B, C, C
 };
 template <>
 struct TabEntry<double> {
   double2 ad;  // A, D
   double2 bc;  // B, C
 };
-static_assert(sizeof(TabEntry<float>) == 32 && sizeof(TabEntry<double>) == 32, "table records are 32 bytes");
+static_assert(sizeof(TabEntry<float>) == 48 && sizeof(TabEntry<double>) == 32, "table record sizes");
+static_assert((kCH * sizeof(TabEntry<float>)) % 16 == 0 && (kCH * sizeof(TabEntry<double>)) % 16 == 0,
+              "bulk copies are whole 16-byte units");
 
 // ---------------------------------------------------------------------------------------------
 // recurrence table per packed (l, m), FP64 arithmetic, one thread per m.
@@ -100,9 +104,10 @@ __global__ void k_rec_table(int lmax, int s, TabEntry<T>* __restrict__ tab) {
       e.bc = make_double2(B, C);
     } else {
       const float ah = (float)A, dh = (float)D;
-      e.ad = make_float4(ah, (float)(A - (double)ah), dh, (float)(D - (double)dh));
-      e.bc = make_float2((float)B, (float)C);
-      e.pad = make_float2(0.f, 0.f);
+      const float al = (float)(A - (double)ah), dl = (float)(D - (double)dh), b = (float)B, c = (float)C;
+      e.na = make_float4(-ah, -ah, -al, -al);
+      e.d = make_float4(dh, dh, dl, dl);
+      e.bc = make_float4(b, b, c, c);
     }
     tab[base + l] = e;
   }
@@ -158,28 +163,14 @@ __device__ __forceinline__ void issue_chunk(TabStage<T>& st, uint64_t* bar, cons
   bulk_g2s(st.v, tab + start, bytes, bar);
 }
 
-template <typename T>
-struct Coef;
-template <>
-struct Coef<double> {
+// FP64 coefficients of one l; t = D - A (1 - x)
+struct Coef {
   double A, D, B, C;
-  __device__ __forceinline__ double t(double omx, double) const { return fma(-A, omx, D); }
+  __device__ __forceinline__ double t(double omx) const { return fma(-A, omx, D); }
 };
-template <>
-struct Coef<float> {
-  float Ah, Al, Dh, Dl, B, C;
-  __device__ __forceinline__ float t(float oh, float ol) const {
-    return fmaf(-Ah, oh, Dh) + fmaf(-Ah, ol, fmaf(-Al, oh, Dl));
-  }
-};
-__device__ __forceinline__ Coef<double> get_coef(const TabStage<double>& s, int i) {
+__device__ __forceinline__ Coef get_coef(const TabStage<double>& s, int i) {
   const double2 ad = s.v[i].ad, bc = s.v[i].bc;
-  return Coef<double>{ad.x, ad.y, bc.x, bc.y};
-}
-__device__ __forceinline__ Coef<float> get_coef(const TabStage<float>& s, int i) {
-  const float4 ad = s.v[i].ad;
-  const float2 bc = s.v[i].bc;
-  return Coef<float>{ad.x, ad.y, ad.z, ad.w, bc.x, bc.y};
+  return Coef{ad.x, ad.y, bc.x, bc.y};
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -241,10 +232,15 @@ __device__ __forceinline__ void ring_omx<float>(const RingDev& r, float& oh, flo
 }
 
 // one Reinsch step of a column: Delta <- t e + C Delta, e <- e + Delta
-template <typename T>
-__device__ __forceinline__ void reinsch_step(T t, T C, T& e, T& d) {
+__device__ __forceinline__ void reinsch_step(double t, double C, double& e, double& d) {
   d = fma(t, e, C * d);
   e = e + d;
+}
+// the same step for the two rings of a pair in packed FP32x2 arithmetic (per element the same
+// roundings as the scalar step)
+__device__ __forceinline__ void reinsch_step2(float2 t, float2 C, float2& e, float2& d) {
+  d = __ffma2_rn(t, e, __fmul2_rn(C, d));
+  e = __fadd2_rn(e, d);
 }
 // rescale guard, run once per quad of l steps while a column is in its dropped region
 template <typename T>
@@ -257,15 +253,17 @@ __device__ __forceinline__ void rescale(T& e, T& d, int& k) {
 }
 
 // a_lm combination for the two columns: direct rings P = g + i c (col 1), Q = g* + i c* (col 2);
-// reflected rings P = (-1)^(l+m) (g* + i c*), Q = (-1)^(l+m) (g + i c)
+// reflected rings P = (-1)^(l+m) (g* + i c*), Q = (-1)^(l+m) (g + i c).  msc weights the m > 0
+// entries (1, or 1/2 for the packed-gradient form; both exact).
 template <typename V, typename T>
-__device__ __forceinline__ void make_pq(V gv, V cv, bool m0, bool refl, int lpm, V& P, V& Q) {
+__device__ __forceinline__ void make_pq(V gv, V cv, bool m0, bool refl, int lpm, T msc, V& P, V& Q) {
   if (m0) {
     gv.y = (T)0;
     cv.y = (T)0;
   }
-  V u = mk(gv.x - cv.y, gv.y + cv.x);
-  V v = mk(gv.x + cv.y, cv.x - gv.y);
+  const T w = m0 ? (T)1 : msc;
+  V u = mk(w * (gv.x - cv.y), w * (gv.y + cv.x));
+  V v = mk(w * (gv.x + cv.y), w * (cv.x - gv.y));
   if (refl) {
     const T sg = (lpm & 1) ? (T)-1 : (T)1;
     P = mk(sg * v.x, sg * v.y);
@@ -276,43 +274,173 @@ __device__ __forceinline__ void make_pq(V gv, V cv, bool m0, bool refl, int lpm,
   }
 }
 
-// per-thread state of RPT ring slots
+// Shared-memory record of P and Q for one l.  FP64: (P.x, P.y, Q.x, Q.y).  FP32: every value
+// twice, once per ring of a packed pair: (P.x, P.x, P.y, P.y), (Q.x, Q.x, Q.y, Q.y).
+struct PQ2 {
+  float4 p, q;
+};
+template <typename T>
+struct PQRec;
+template <>
+struct PQRec<double> {
+  using V = Dbl4;
+};
+template <>
+struct PQRec<float> {
+  using V = PQ2;
+};
+__device__ __forceinline__ Dbl4 pq_rec(double2 P, double2 Q) { return Dbl4{P.x, P.y, Q.x, Q.y}; }
+__device__ __forceinline__ PQ2 pq_rec(float2 P, float2 Q) {
+  return PQ2{make_float4(P.x, P.x, P.y, P.y), make_float4(Q.x, Q.x, Q.y, Q.y)};
+}
+
+// Per-thread state of RPT ring slots: 1 - x (hi + lo), the two columns e, their differences
+// Delta, and the scale counts.  FP64 keeps one value per slot.  FP32 keeps slots 2p and 2p + 1 in
+// one float2, the operand shape of the packed FP32x2 instructions, so that every arithmetic
+// instruction of a step serves two rings.  The accessors give the value of one slot.
 template <typename T, int RPT>
 struct Cols {
   T oh[RPT], ol[RPT], e1[RPT], d1[RPT], e2[RPT], d2[RPT];
   int k1[RPT], k2[RPT];
+  __device__ __forceinline__ T& OH(int r) { return oh[r]; }
+  __device__ __forceinline__ T& OL(int r) { return ol[r]; }
+  __device__ __forceinline__ T& E1(int r) { return e1[r]; }
+  __device__ __forceinline__ T& D1(int r) { return d1[r]; }
+  __device__ __forceinline__ T& E2(int r) { return e2[r]; }
+  __device__ __forceinline__ T& D2(int r) { return d2[r]; }
 };
+template <int N>
+__device__ __forceinline__ float& slot_of(float2 (&v)[N], int r) {
+  return (r & 1) ? v[r >> 1].y : v[r >> 1].x;
+}
+template <int RPT>
+struct Cols<float, RPT> {
+  static_assert(RPT % 2 == 0, "FP32 ring slots come in pairs");
+  static constexpr int NP = RPT / 2;
+  float2 oh[NP], ol[NP], e1[NP], d1[NP], e2[NP], d2[NP];
+  int k1[RPT], k2[RPT];
+  __device__ __forceinline__ float& OH(int r) { return slot_of(oh, r); }
+  __device__ __forceinline__ float& OL(int r) { return slot_of(ol, r); }
+  __device__ __forceinline__ float& E1(int r) { return slot_of(e1, r); }
+  __device__ __forceinline__ float& D1(int r) { return slot_of(d1, r); }
+  __device__ __forceinline__ float& E2(int r) { return slot_of(e2, r); }
+  __device__ __forceinline__ float& D2(int r) { return slot_of(d2, r); }
+};
+
+// synthesis sums of each slot: Re, Im of sum P e1, then of sum Q e2
+template <typename T, int RPT>
+struct SynAcc {
+  T a[RPT][4];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) a[r][0] = a[r][1] = a[r][2] = a[r][3] = (T)0;
+  }
+  __device__ __forceinline__ T get(int r, int k) const { return a[r][k]; }
+};
+template <int RPT>
+struct SynAcc<float, RPT> {
+  float2 a[RPT / 2][4];  // slot pairs
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int p = 0; p < RPT / 2; ++p) a[p][0] = a[p][1] = a[p][2] = a[p][3] = make_float2(0.f, 0.f);
+  }
+  __device__ __forceinline__ float get(int r, int k) const { return (r & 1) ? a[r >> 1][k].y : a[r >> 1][k].x; }
+};
+
+// adjoint inputs of each slot: the ring values paired with column 1 (f1) and column 2 (f2)
+template <typename T, int RPT>
+struct AdjIn {
+  using V = typename Cx<T>::V;
+  V f1[RPT], f2[RPT];
+  __device__ __forceinline__ void set(int r, V a, V b) {
+    f1[r] = a;
+    f2[r] = b;
+  }
+};
+template <int RPT>
+struct AdjIn<float, RPT> {
+  float2 x1[RPT / 2], y1[RPT / 2], x2[RPT / 2], y2[RPT / 2];  // slot pairs of Re f1, Im f1, Re f2, Im f2
+  __device__ __forceinline__ void set(int r, float2 a, float2 b) {
+    slot_of(x1, r) = a.x;
+    slot_of(y1, r) = a.y;
+    slot_of(x2, r) = b.x;
+    slot_of(y2, r) = b.y;
+  }
+};
+
+// ---------------------------------------------------------------------------------------------
+// one l step of a ring pair (FP32).  t = D - A (1 - x) with A, D and 1 - x as hi + lo:
+//   t = (D_hi - A_hi oh) + ((D_lo - A_lo oh) - A_hi ol)
+template <bool SPIN, int RPT>
+__device__ __forceinline__ void step_pair(Cols<float, RPT>& S, int p, const TabEntry<float>& cf) {
+  const float2 nah = lo2(cf.na), nal = hi2(cf.na);
+  const float2 t = __fadd2_rn(__ffma2_rn(nah, S.oh[p], lo2(cf.d)),
+                              __ffma2_rn(nah, S.ol[p], __ffma2_rn(nal, S.oh[p], hi2(cf.d))));
+  const float2 B = lo2(cf.bc), C = hi2(cf.bc);
+  if (SPIN) {
+    reinsch_step2(__fadd2_rn(t, B), C, S.e1[p], S.d1[p]);
+    reinsch_step2(__ffma2_rn(B, make_float2(-1.f, -1.f), t), C, S.e2[p], S.d2[p]);  // t - B
+  } else {
+    reinsch_step2(t, C, S.e1[p], S.d1[p]);
+  }
+}
+// column values of a pair that take part in the sums: those with scale count 0
+__device__ __forceinline__ float2 summing(float2 e, int ka, int kb) {
+  return make_float2(ka == 0 ? e.x : 0.f, kb == 0 ? e.y : 0.f);
+}
 
 // One quad (4 l steps) of the synthesis for the ring slots r < nr of this thread.
 // ACC: add the current column values to the sums; SEL: per column, only where k == 0.
-template <typename T, bool SPIN, int RPT, bool ACC, bool SEL>
-__device__ __forceinline__ void syn_quad(Cols<T, RPT>& S, T (&a)[RPT][4], const TabStage<T>& st, int off, int i0,
-                                         const typename Cx4<T>::V* sPQ, int nr) {
-  using V = typename Cx<T>::V;
+template <bool SPIN, int RPT, bool ACC, bool SEL>
+__device__ __forceinline__ void syn_quad(Cols<double, RPT>& S, SynAcc<double, RPT>& A, const TabStage<double>& st,
+                                         int i0, const Dbl4* sPQ, int nr) {
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int i = i0 + u;
-    const Coef<T> cf = get_coef(st, off + i);
-    const typename Cx4<T>::V pq = sPQ[i];
-    const V P = mk(pq.x, pq.y), Q = mk(pq.z, pq.w);
+    const Coef cf = get_coef(st, i);
+    const Dbl4 pq = sPQ[i];
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
       if (r < nr) {
         if (ACC) {
-          const T o1 = (!SEL || S.k1[r] == 0) ? S.e1[r] : (T)0;
-          a[r][0] = fma(P.x, o1, a[r][0]);
-          a[r][1] = fma(P.y, o1, a[r][1]);
-          const T o2 = SPIN ? ((!SEL || S.k2[r] == 0) ? S.e2[r] : (T)0) : o1;
-          a[r][2] = fma(Q.x, o2, a[r][2]);
-          a[r][3] = fma(Q.y, o2, a[r][3]);
+          const double o1 = (!SEL || S.k1[r] == 0) ? S.e1[r] : 0.0;
+          A.a[r][0] = fma(pq.x, o1, A.a[r][0]);
+          A.a[r][1] = fma(pq.y, o1, A.a[r][1]);
+          const double o2 = SPIN ? ((!SEL || S.k2[r] == 0) ? S.e2[r] : 0.0) : o1;
+          A.a[r][2] = fma(pq.z, o2, A.a[r][2]);
+          A.a[r][3] = fma(pq.w, o2, A.a[r][3]);
         }
-        const T t = cf.t(S.oh[r], S.ol[r]);
+        const double t = cf.t(S.oh[r]);
         if (SPIN) {
-          reinsch_step<T>(t + cf.B, cf.C, S.e1[r], S.d1[r]);
-          reinsch_step<T>(t - cf.B, cf.C, S.e2[r], S.d2[r]);
+          reinsch_step(t + cf.B, cf.C, S.e1[r], S.d1[r]);
+          reinsch_step(t - cf.B, cf.C, S.e2[r], S.d2[r]);
         } else {
-          reinsch_step<T>(t, cf.C, S.e1[r], S.d1[r]);
+          reinsch_step(t, cf.C, S.e1[r], S.d1[r]);
         }
+      }
+    }
+  }
+}
+template <bool SPIN, int RPT, bool ACC, bool SEL>
+__device__ __forceinline__ void syn_quad(Cols<float, RPT>& S, SynAcc<float, RPT>& A, const TabStage<float>& st,
+                                         int i0, const PQ2* sPQ, int nr) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = i0 + u;
+    const TabEntry<float> cf = st.v[i];
+    const PQ2 pq = sPQ[i];
+#pragma unroll
+    for (int p = 0; p < RPT / 2; ++p) {
+      if (2 * p < nr) {  // the second slot of the last pair may be empty: zero values, zero sums
+        if (ACC) {
+          const float2 o1 = SEL ? summing(S.e1[p], S.k1[2 * p], S.k1[2 * p + 1]) : S.e1[p];
+          A.a[p][0] = __ffma2_rn(lo2(pq.p), o1, A.a[p][0]);
+          A.a[p][1] = __ffma2_rn(hi2(pq.p), o1, A.a[p][1]);
+          const float2 o2 = SPIN ? (SEL ? summing(S.e2[p], S.k2[2 * p], S.k2[2 * p + 1]) : S.e2[p]) : o1;
+          A.a[p][2] = __ffma2_rn(lo2(pq.q), o2, A.a[p][2]);
+          A.a[p][3] = __ffma2_rn(hi2(pq.q), o2, A.a[p][3]);
+        }
+        step_pair<SPIN, RPT>(S, p, cf);
       }
     }
   }
@@ -323,8 +451,8 @@ __device__ __forceinline__ void rescale_all(Cols<T, RPT>& S, int nr) {
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
     if (r < nr) {
-      rescale<T>(S.e1[r], S.d1[r], S.k1[r]);
-      if (SPIN) rescale<T>(S.e2[r], S.d2[r], S.k2[r]);
+      rescale<T>(S.E1(r), S.D1(r), S.k1[r]);
+      if (SPIN) rescale<T>(S.E2(r), S.D2(r), S.k2[r]);
     }
   }
 }
@@ -358,19 +486,23 @@ __device__ __forceinline__ void init_col(Cols<T, RPT>& S, const RingDev* __restr
                                          int jfirst, int jj, int nj, int r) {
   if (jj < nj) {
     const RingDev rg = rings[jfirst + jj];
-    ring_omx<T>(rg, S.oh[r], S.ol[r]);
-    seed_scaled<T>(seed_log2(sd.lbin, sd.p1, sd.q1, rg.l2c, rg.l2s), sd.sign1, S.e1[r], S.k1[r]);
-    if (SPIN) seed_scaled<T>(seed_log2(sd.lbin, sd.q1, sd.p1, rg.l2c, rg.l2s), sd.sign2, S.e2[r], S.k2[r]);
-    else S.k2[r] = 0;
+    ring_omx<T>(rg, S.OH(r), S.OL(r));
+    seed_scaled<T>(seed_log2(sd.lbin, sd.p1, sd.q1, rg.l2c, rg.l2s), sd.sign1, S.E1(r), S.k1[r]);
+    if (SPIN) {
+      seed_scaled<T>(seed_log2(sd.lbin, sd.q1, sd.p1, rg.l2c, rg.l2s), sd.sign2, S.E2(r), S.k2[r]);
+    } else {
+      S.E2(r) = (T)0;
+      S.k2[r] = 0;
+    }
   } else {
     // empty slot inside a partly filled warp: zero values that count as summing, so it adds
     // nothing and never holds the warp off the fast path
-    S.oh[r] = S.ol[r] = S.e1[r] = S.e2[r] = (T)0;
+    S.OH(r) = S.OL(r) = S.E1(r) = S.E2(r) = (T)0;
     S.k1[r] = 0;
     S.k2[r] = 0;
   }
-  S.d1[r] = S.e1[r];  // Delta_{l0} = e_{l0} - e_{l0-1}, e_{l0-1} = 0
-  S.d2[r] = S.e2[r];
+  S.D1(r) = S.E1(r);  // Delta_{l0} = e_{l0} - e_{l0-1}, e_{l0-1} = 0
+  S.D2(r) = S.E2(r);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -381,15 +513,15 @@ template <typename T, bool SPIN, int RPT, int NT>
 __global__ void __launch_bounds__(NT) k_rec_syn(const RecItem* __restrict__ items, const RingDev* __restrict__ rings,
                                                 const MSeed* __restrict__ mseed, const TabEntry<T>* __restrict__ tab,
                                                 const typename Cx<T>::V* __restrict__ g,
-                                                const typename Cx<T>::V* __restrict__ c, int lmax, int s,
+                                                const typename Cx<T>::V* __restrict__ c, int lmax, int s, T msc,
                                                 typename Cx<T>::V* __restrict__ F, int Lpad, int* __restrict__ status) {
   using V = typename Cx<T>::V;
   const RecItem it = items[blockIdx.x];
   const int m = it.m;
   const MSeed sd = mseed[m];
   __shared__ __align__(16) TabStage<T> stg[2];
-  using V4 = typename Cx4<T>::V;
-  __shared__ V4 sPQ[2][kCH];  // (P.x, P.y, Q.x, Q.y) per l
+  using PQV = typename PQRec<T>::V;
+  __shared__ __align__(16) PQV sPQ[2][kCH];  // P and Q per l
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int sfail;
 
@@ -400,12 +532,10 @@ __global__ void __launch_bounds__(NT) k_rec_syn(const RecItem* __restrict__ item
   int wbase, wcnt, nr_w;
   slot_range(it.nj, NT / 32, warp, wbase, wcnt, nr_w);
   Cols<T, RPT> S;
-  T a[RPT][4];
+  SynAcc<T, RPT> A;
+  A.zero();
 #pragma unroll
-  for (int r = 0; r < RPT; ++r) {
-    init_col<T, SPIN, RPT>(S, rings, sd, it.j0 + wbase, r * 32 + lane, wcnt, r);
-    a[r][0] = a[r][1] = a[r][2] = a[r][3] = (T)0;
-  }
+  for (int r = 0; r < RPT; ++r) init_col<T, SPIN, RPT>(S, rings, sd, it.j0 + wbase, r * 32 + lane, wcnt, r);
   const int64_t base = alm_base(lmax, m);
   const bool rf = it.refl != 0;
   const bool m0 = (m == 0);
@@ -428,8 +558,8 @@ __global__ void __launch_bounds__(NT) k_rec_syn(const RecItem* __restrict__ item
     for (int i = threadIdx.x; i < kCH; i += NT) {
       const int l = sd.l0 + cc * kCH + i;
       V P = mk((T)0, (T)0), Q = mk((T)0, (T)0);
-      if (l <= lmax) make_pq<V, T>(g[base + l], c ? c[base + l] : mk((T)0, (T)0), m0, rf, l + m, P, Q);
-      sPQ[cc][i] = mk4(P, Q);
+      if (l <= lmax) make_pq<V, T>(g[base + l], c ? c[base + l] : mk((T)0, (T)0), m0, rf, l + m, msc, P, Q);
+      sPQ[cc][i] = pq_rec(P, Q);
     }
   }
   V pg = mk((T)0, (T)0), pc = mk((T)0, (T)0);  // a_lm two chunks ahead
@@ -452,17 +582,16 @@ __global__ void __launch_bounds__(NT) k_rec_syn(const RecItem* __restrict__ item
     const int nq = (min(kCH, lmax - lc + 1) + 3) >> 2;
     if (nr_w > 0 && !sfail) {
       const TabStage<T>& st = stg[sidx];
-      const V4* PQ = sPQ[sidx];
-      constexpr int of = 0;
+      const PQV* PQ = sPQ[sidx];
       for (int q = 0; q < nq; ++q) {
         bool fast, skip;
         classify<T, SPIN, RPT>(S, nr_w, fast, skip);
         if (fast) {
-          if (nr_w == RPT) syn_quad<T, SPIN, RPT, true, false>(S, a, st, of, 4 * q, PQ, RPT);
-          else syn_quad<T, SPIN, RPT, true, false>(S, a, st, of, 4 * q, PQ, nr_w);
+          if (nr_w == RPT) syn_quad<SPIN, RPT, true, false>(S, A, st, 4 * q, PQ, RPT);
+          else syn_quad<SPIN, RPT, true, false>(S, A, st, 4 * q, PQ, nr_w);
         } else {
-          if (skip) syn_quad<T, SPIN, RPT, false, false>(S, a, st, of, 4 * q, PQ, nr_w);
-          else syn_quad<T, SPIN, RPT, true, true>(S, a, st, of, 4 * q, PQ, nr_w);
+          if (skip) syn_quad<SPIN, RPT, false, false>(S, A, st, 4 * q, PQ, nr_w);
+          else syn_quad<SPIN, RPT, true, true>(S, A, st, 4 * q, PQ, nr_w);
           rescale_all<T, SPIN, RPT>(S, nr_w);
         }
       }
@@ -477,8 +606,8 @@ __global__ void __launch_bounds__(NT) k_rec_syn(const RecItem* __restrict__ item
       if (threadIdx.x < kCH) {
         const int l = lc + 2 * kCH + threadIdx.x;
         V Pn = mk((T)0, (T)0), Qn = mk((T)0, (T)0);
-        if (l <= lmax) make_pq<V, T>(pg, pc, m0, rf, l + m, Pn, Qn);
-        sPQ[sidx][threadIdx.x] = mk4(Pn, Qn);
+        if (l <= lmax) make_pq<V, T>(pg, pc, m0, rf, l + m, msc, Pn, Qn);
+        sPQ[sidx][threadIdx.x] = pq_rec(Pn, Qn);
         pg = pc = mk((T)0, (T)0);
         const int l3 = l + kCH;
         if (l3 <= lmax) {
@@ -495,8 +624,9 @@ __global__ void __launch_bounds__(NT) k_rec_syn(const RecItem* __restrict__ item
     if (jj < wcnt) {
       const int j = it.j0 + wbase + jj;
       // direct rings: F[m] <- column 1, F[-m] <- column 2; reflected rings: swapped
-      const V fpos = rf ? mk(-a[r][2], -a[r][3]) : mk(-a[r][0], -a[r][1]);
-      const V fneg = rf ? mk(sgn_s * a[r][0], sgn_s * a[r][1]) : mk(sgn_s * a[r][2], sgn_s * a[r][3]);
+      const T a0 = A.get(r, 0), a1 = A.get(r, 1), a2 = A.get(r, 2), a3 = A.get(r, 3);
+      const V fpos = rf ? mk(-a2, -a3) : mk(-a0, -a1);
+      const V fneg = rf ? mk(sgn_s * a0, sgn_s * a1) : mk(sgn_s * a2, sgn_s * a3);
       F[(int64_t)col_of(m) * Lpad + j] = fpos;
       if (!m0) F[(int64_t)col_of(-m) * Lpad + j] = fneg;
     }
@@ -522,29 +652,28 @@ __device__ __forceinline__ T reduce_scatter16(T (&v)[16], int lane) {
   return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);  // lane holds value (lane & 15)
 }
 
-template <typename T, bool SPIN, int RPT, bool SEL>
-__device__ __forceinline__ void adj_quad_sums(Cols<T, RPT>& S, const typename Cx<T>::V (&f1)[RPT],
-                                              const typename Cx<T>::V (&f2)[RPT], const TabStage<T>& st, int off,
-                                              int i0, int nr, T (&v)[16]) {
+template <bool SPIN, int RPT, bool SEL>
+__device__ __forceinline__ void adj_quad_sums(Cols<double, RPT>& S, const AdjIn<double, RPT>& f,
+                                              const TabStage<double>& st, int i0, int nr, double (&v)[16]) {
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
-    const Coef<T> cf = get_coef(st, off + i0 + u);
-    T p0 = 0, p1 = 0, p2 = 0, p3 = 0;
+    const Coef cf = get_coef(st, i0 + u);
+    double p0 = 0, p1 = 0, p2 = 0, p3 = 0;
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
       if (r < nr) {
-        const T o1 = (!SEL || S.k1[r] == 0) ? S.e1[r] : (T)0;
-        p0 = fma(o1, f1[r].x, p0);
-        p1 = fma(o1, f1[r].y, p1);
-        const T o2 = SPIN ? ((!SEL || S.k2[r] == 0) ? S.e2[r] : (T)0) : o1;
-        p2 = fma(o2, f2[r].x, p2);
-        p3 = fma(o2, f2[r].y, p3);
-        const T t = cf.t(S.oh[r], S.ol[r]);
+        const double o1 = (!SEL || S.k1[r] == 0) ? S.e1[r] : 0.0;
+        p0 = fma(o1, f.f1[r].x, p0);
+        p1 = fma(o1, f.f1[r].y, p1);
+        const double o2 = SPIN ? ((!SEL || S.k2[r] == 0) ? S.e2[r] : 0.0) : o1;
+        p2 = fma(o2, f.f2[r].x, p2);
+        p3 = fma(o2, f.f2[r].y, p3);
+        const double t = cf.t(S.oh[r]);
         if (SPIN) {
-          reinsch_step<T>(t + cf.B, cf.C, S.e1[r], S.d1[r]);
-          reinsch_step<T>(t - cf.B, cf.C, S.e2[r], S.d2[r]);
+          reinsch_step(t + cf.B, cf.C, S.e1[r], S.d1[r]);
+          reinsch_step(t - cf.B, cf.C, S.e2[r], S.d2[r]);
         } else {
-          reinsch_step<T>(t, cf.C, S.e1[r], S.d1[r]);
+          reinsch_step(t, cf.C, S.e1[r], S.d1[r]);
         }
       }
     }
@@ -554,23 +683,58 @@ __device__ __forceinline__ void adj_quad_sums(Cols<T, RPT>& S, const typename Cx
     v[4 * u + 3] = p3;
   }
 }
-template <typename T, bool SPIN, int RPT>
-__device__ __forceinline__ void adj_quad_steps(Cols<T, RPT>& S, const TabStage<T>& st, int off, int i0, int nr) {
+template <bool SPIN, int RPT, bool SEL>
+__device__ __forceinline__ void adj_quad_sums(Cols<float, RPT>& S, const AdjIn<float, RPT>& f,
+                                              const TabStage<float>& st, int i0, int nr, float (&v)[16]) {
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
-    const Coef<T> cf = get_coef(st, off + i0 + u);
+    const TabEntry<float> cf = st.v[i0 + u];
+    float2 p0 = make_float2(0.f, 0.f), p1 = p0, p2 = p0, p3 = p0;  // (even slot, odd slot) partial sums
+#pragma unroll
+    for (int p = 0; p < RPT / 2; ++p) {
+      if (2 * p < nr) {
+        const float2 o1 = SEL ? summing(S.e1[p], S.k1[2 * p], S.k1[2 * p + 1]) : S.e1[p];
+        p0 = __ffma2_rn(o1, f.x1[p], p0);
+        p1 = __ffma2_rn(o1, f.y1[p], p1);
+        const float2 o2 = SPIN ? (SEL ? summing(S.e2[p], S.k2[2 * p], S.k2[2 * p + 1]) : S.e2[p]) : o1;
+        p2 = __ffma2_rn(o2, f.x2[p], p2);
+        p3 = __ffma2_rn(o2, f.y2[p], p3);
+        step_pair<SPIN, RPT>(S, p, cf);
+      }
+    }
+    v[4 * u + 0] = p0.x + p0.y;
+    v[4 * u + 1] = p1.x + p1.y;
+    v[4 * u + 2] = p2.x + p2.y;
+    v[4 * u + 3] = p3.x + p3.y;
+  }
+}
+template <bool SPIN, int RPT>
+__device__ __forceinline__ void adj_quad_steps(Cols<double, RPT>& S, const TabStage<double>& st, int i0, int nr) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const Coef cf = get_coef(st, i0 + u);
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
       if (r < nr) {
-        const T t = cf.t(S.oh[r], S.ol[r]);
+        const double t = cf.t(S.oh[r]);
         if (SPIN) {
-          reinsch_step<T>(t + cf.B, cf.C, S.e1[r], S.d1[r]);
-          reinsch_step<T>(t - cf.B, cf.C, S.e2[r], S.d2[r]);
+          reinsch_step(t + cf.B, cf.C, S.e1[r], S.d1[r]);
+          reinsch_step(t - cf.B, cf.C, S.e2[r], S.d2[r]);
         } else {
-          reinsch_step<T>(t, cf.C, S.e1[r], S.d1[r]);
+          reinsch_step(t, cf.C, S.e1[r], S.d1[r]);
         }
       }
     }
+  }
+}
+template <bool SPIN, int RPT>
+__device__ __forceinline__ void adj_quad_steps(Cols<float, RPT>& S, const TabStage<float>& st, int i0, int nr) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const TabEntry<float> cf = st.v[i0 + u];
+#pragma unroll
+    for (int p = 0; p < RPT / 2; ++p)
+      if (2 * p < nr) step_pair<SPIN, RPT>(S, p, cf);
   }
 }
 
@@ -578,7 +742,7 @@ template <typename T, bool SPIN, int RPT, int NT>
 __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ rings, const MSeed* __restrict__ mseed,
                                                 const int2* __restrict__ mrange, const TabEntry<T>* __restrict__ tab,
                                                 const typename Cx<T>::V* __restrict__ Ft, int Lpad,
-                                                int lmax, int s, int M, int refl, int accumulate,
+                                                int lmax, int s, int M, int refl, int accumulate, T msc,
                                                 typename Cx<T>::V* __restrict__ gt, typename Cx<T>::V* __restrict__ ct,
                                                 int* __restrict__ status) {
   using V = typename Cx<T>::V;
@@ -613,18 +777,17 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
   slot_range(nact, NW, warp, wbase, wcnt, nr_w);
 
   Cols<T, RPT> S;
-  V f1[RPT], f2[RPT];  // ring values paired with column 1 / column 2
+  AdjIn<T, RPT> fin;  // ring values paired with column 1 / column 2
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
     const int jj = r * 32 + lane;
     init_col<T, SPIN, RPT>(S, rings, sd, rr.x + wbase, jj, wcnt, r);
-    f1[r] = f2[r] = mk((T)0, (T)0);
+    fin.set(r, mk((T)0, (T)0), mk((T)0, (T)0));
     if (jj < wcnt) {
       const int j = rr.x + wbase + jj;
       const V fp = Ft[(int64_t)col_of(m) * Lpad + j];
       const V fm = m0 ? mk((T)0, (T)0) : Ft[(int64_t)col_of(-m) * Lpad + j];
-      f1[r] = rf ? fm : fp;
-      f2[r] = rf ? fp : fm;
+      fin.set(r, rf ? fm : fp, rf ? fp : fm);
     }
   }
   const T sg = (((m - s) & 1) ? (T)1 : (T)-1);  // -(-1)^(m-s)
@@ -652,7 +815,6 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
       sfail = 1;
     }
     const TabStage<T>& st = stg[sidx];
-    constexpr int of = 0;
     T* redw = reinterpret_cast<T*>(red + (sidx * NW + warp) * kCH);
     for (int q = 0; q < nq; ++q) {
       T tot = (T)0;
@@ -660,15 +822,15 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
         bool fast, skip;
         classify<T, SPIN, RPT>(S, nr_w, fast, skip);
         if (skip) {
-          adj_quad_steps<T, SPIN, RPT>(S, st, of, 4 * q, nr_w);
+          adj_quad_steps<SPIN, RPT>(S, st, 4 * q, nr_w);
           rescale_all<T, SPIN, RPT>(S, nr_w);
         } else {
           T v[16];
           if (fast) {
-            if (nr_w == RPT) adj_quad_sums<T, SPIN, RPT, false>(S, f1, f2, st, of, 4 * q, RPT, v);
-            else adj_quad_sums<T, SPIN, RPT, false>(S, f1, f2, st, of, 4 * q, nr_w, v);
+            if (nr_w == RPT) adj_quad_sums<SPIN, RPT, false>(S, fin, st, 4 * q, RPT, v);
+            else adj_quad_sums<SPIN, RPT, false>(S, fin, st, 4 * q, nr_w, v);
           } else {
-            adj_quad_sums<T, SPIN, RPT, true>(S, f1, f2, st, of, 4 * q, nr_w, v);
+            adj_quad_sums<SPIN, RPT, true>(S, fin, st, 4 * q, nr_w, v);
             rescale_all<T, SPIN, RPT>(S, nr_w);
           }
           tot = reduce_scatter16<T>(v, lane);
@@ -718,6 +880,10 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
         gv = mk((T)0.5 * (ar + wr), (T)0.5 * (ai + wi));
         cv = mk((T)0.5 * (ai - wi), (T)-0.5 * (ar - wr));
       }
+      if (!m0) {  // weight of the m > 0 entries (1, or 2 for the packed-gradient form; exact)
+        gv = mk(msc * gv.x, msc * gv.y);
+        cv = mk(msc * cv.x, msc * cv.y);
+      }
       if (accumulate) {  // the projection is linear: the second ring part adds its share
         gv = cadd(gv, gt[id]);
         if (ct) cv = cadd(cv, ct[id]);
@@ -731,15 +897,15 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
 }
 
 template <typename T, bool SPIN, int RPT>
-void launch_syn_t(Plan& p, const void* g, const void* c, cudaStream_t st) {
+void launch_syn_t(Plan& p, const void* g, const void* c, double msc, cudaStream_t st) {
   using V = typename Cx<T>::V;
   k_rec_syn<T, SPIN, RPT, 128><<<p.nitems, 128, 0, st>>>(p.d_items, p.d_ring, p.d_mseed,
-                                                          (const TabEntry<T>*)p.d_rtab, (const V*)g, (const V*)c, p.lmax, p.spin,
+                                                          (const TabEntry<T>*)p.d_rtab, (const V*)g, (const V*)c, p.lmax, p.spin, (T)msc,
                                                           (V*)p.d_F, p.Lpad, p.d_status);
 }
 
 template <typename T, bool SPIN, int RPT, int NT>
-void launch_adj_t(Plan& p, void* g, void* c, cudaStream_t st) {
+void launch_adj_t(Plan& p, void* g, void* c, double msc, cudaStream_t st) {
   using V = typename Cx<T>::V;
   // one launch per ring part (rings at theta <= pi/2, then reflected rings at theta > pi/2)
   for (int part = 0; part < 2; ++part) {
@@ -749,33 +915,35 @@ void launch_adj_t(Plan& p, void* g, void* c, cudaStream_t st) {
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red_bytes));
     k_rec_adj<T, SPIN, RPT, NT><<<p.lmax + 1, NT, red_bytes, st>>>(
         p.d_ring, p.d_mseed, p.d_mrange + part * (p.lmax + 1), (const TabEntry<T>*)p.d_rtab, (const V*)p.d_F,
-        p.Lpad, p.lmax, p.spin, p.M, part, part, (V*)g, (V*)c, p.d_status);
+        p.Lpad, p.lmax, p.spin, p.M, part, part, (T)msc, (V*)g, (V*)c, p.d_status);
   }
 }
 
 template <typename T, bool SPIN>
-void launch_syn_s(Plan& p, const void* g, const void* c, cudaStream_t st) {
+void launch_syn_s(Plan& p, const void* g, const void* c, double msc, cudaStream_t st) {
   switch (p.syn_rpt) {
-    case 1: launch_syn_t<T, SPIN, 1>(p, g, c, st); break;
-    case 2: launch_syn_t<T, SPIN, 2>(p, g, c, st); break;
-    default: launch_syn_t<T, SPIN, 4>(p, g, c, st); break;
+    case 1: launch_syn_t<T, SPIN, sizeof(T) == 8 ? 1 : 2>(p, g, c, msc, st); break;  // FP32 slots come in pairs
+    case 2: launch_syn_t<T, SPIN, 2>(p, g, c, msc, st); break;
+    default: launch_syn_t<T, SPIN, 4>(p, g, c, msc, st); break;
   }
 }
 template <typename T, bool SPIN>
-void launch_adj_s(Plan& p, void* g, void* c, cudaStream_t st) {
+void launch_adj_s(Plan& p, void* g, void* c, double msc, cudaStream_t st) {
   // (rings per thread, threads) covering up to 4096 rings; chosen by the planner
   switch (p.adj_rpt * 10000 + p.adj_threads) {
-    case 40128: launch_adj_t<T, SPIN, 4, 128>(p, g, c, st); break;
-    case 40256: launch_adj_t<T, SPIN, 4, 256>(p, g, c, st); break;
-    case 80128: launch_adj_t<T, SPIN, 8, 128>(p, g, c, st); break;
-    case 80256: launch_adj_t<T, SPIN, 8, 256>(p, g, c, st); break;
-    default: launch_adj_t<T, SPIN, 8, 512>(p, g, c, st); break;
+    case 40128: launch_adj_t<T, SPIN, 4, 128>(p, g, c, msc, st); break;
+    case 40256: launch_adj_t<T, SPIN, 4, 256>(p, g, c, msc, st); break;
+    case 80128: launch_adj_t<T, SPIN, 8, 128>(p, g, c, msc, st); break;
+    case 80256: launch_adj_t<T, SPIN, 8, 256>(p, g, c, msc, st); break;
+    default: launch_adj_t<T, SPIN, 8, 512>(p, g, c, msc, st); break;
   }
 }
 
 }  // namespace
 
-int rec_table_record_bytes() { return 32; }
+int rec_table_record_bytes(int prec) {
+  return prec == 64 ? (int)sizeof(TabEntry<double>) : (int)sizeof(TabEntry<float>);
+}
 
 void build_rec_table(Plan& p, cudaStream_t st) {
   const int nth = 128, nbl = (p.lmax + 1 + nth - 1) / nth;
@@ -784,25 +952,25 @@ void build_rec_table(Plan& p, cudaStream_t st) {
   PSHT_CUDA_TRY(cudaGetLastError());
 }
 
-void launch_rec_synthesis(Plan& p, const void* g, const void* c, cudaStream_t st) {
+void launch_rec_synthesis(Plan& p, const void* g, const void* c, cudaStream_t st, double msc) {
   if (p.nitems == 0) return;
   if (p.prec == 64) {
-    if (p.spin) launch_syn_s<double, true>(p, g, c, st);
-    else launch_syn_s<double, false>(p, g, c, st);
+    if (p.spin) launch_syn_s<double, true>(p, g, c, msc, st);
+    else launch_syn_s<double, false>(p, g, c, msc, st);
   } else {
-    if (p.spin) launch_syn_s<float, true>(p, g, c, st);
-    else launch_syn_s<float, false>(p, g, c, st);
+    if (p.spin) launch_syn_s<float, true>(p, g, c, msc, st);
+    else launch_syn_s<float, false>(p, g, c, msc, st);
   }
   PSHT_CUDA_TRY(cudaGetLastError());
 }
 
-void launch_rec_adjoint(Plan& p, void* g, void* c, cudaStream_t st) {
+void launch_rec_adjoint(Plan& p, void* g, void* c, cudaStream_t st, double msc) {
   if (p.prec == 64) {
-    if (p.spin) launch_adj_s<double, true>(p, g, c, st);
-    else launch_adj_s<double, false>(p, g, c, st);
+    if (p.spin) launch_adj_s<double, true>(p, g, c, msc, st);
+    else launch_adj_s<double, false>(p, g, c, msc, st);
   } else {
-    if (p.spin) launch_adj_s<float, true>(p, g, c, st);
-    else launch_adj_s<float, false>(p, g, c, st);
+    if (p.spin) launch_adj_s<float, true>(p, g, c, msc, st);
+    else launch_adj_s<float, false>(p, g, c, msc, st);
   }
   PSHT_CUDA_TRY(cudaGetLastError());
 }

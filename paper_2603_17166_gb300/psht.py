@@ -36,6 +36,31 @@ class PshtInfo(ctypes.Structure):
     ]
 
 
+class PshtRequest(ctypes.Structure):
+    _fields_ = [
+        ("op", ctypes.c_int), ("spin", ctypes.c_int), ("lmax", ctypes.c_int), ("eps", ctypes.c_double),
+        ("flags", ctypes.c_uint32), ("points_key", ctypes.c_uint64), ("theta", ctypes.c_void_p),
+        ("phi", ctypes.c_void_p), ("npts", ctypes.c_int64), ("in_a", ctypes.c_void_p), ("in_b", ctypes.c_void_p),
+        ("out_a", ctypes.c_void_p), ("out_b", ctypes.c_void_p),
+    ]
+
+
+class PshtResult(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int), ("worker", ctypes.c_int), ("plan_cached", ctypes.c_int),
+        ("precision", ctypes.c_int), ("queue_ms", ctypes.c_double), ("plan_ms", ctypes.c_double),
+        ("exec_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
+    ]
+
+
+class PshtServerStats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+        ("plans_created", ctypes.c_int64), ("cache_hits", ctypes.c_int64), ("evictions", ctypes.c_int64),
+        ("budget", ctypes.c_size_t), ("bytes_in_use", ctypes.c_size_t), ("bytes_peak", ctypes.c_size_t),
+    ]
+
+
 _lib = None
 
 
@@ -51,8 +76,9 @@ def lib():
         P, I, D, I64, U32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64, ctypes.c_uint32
         L.psht_plan_create.argtypes = [I, I, P, P, I64, D, U32, P, ctypes.POINTER(P)]
         L.psht_plan_info.argtypes = [P, ctypes.POINTER(PshtInfo)]
-        for name in ("psht_plan_synthesis", "psht_plan_adjoint", "psht_plan_synthesis_host",
-                     "psht_plan_adjoint_host", "psht_plan_ring_coeffs"):
+        for name in ("psht_plan_synthesis", "psht_plan_adjoint", "psht_plan_synthesis_packed",
+                     "psht_plan_adjoint_packed", "psht_plan_synthesis_host", "psht_plan_adjoint_host",
+                     "psht_plan_ring_coeffs"):
             getattr(L, name).argtypes = [P, P, P, P, P]
         L.psht_plan_destroy.argtypes = [P]
         L.psht_plan_rings.argtypes = [P, P, P, P]
@@ -63,6 +89,12 @@ def lib():
         L.psht_plan_stage_times.argtypes = [P, P, P]
         L.psht_ring_synthesis_noalloc.argtypes = [I, I, P, I, P, P, P, P]
         L.psht_noalloc_scratch_bytes.restype = ctypes.c_size_t
+        L.psht_plan_estimate_points.argtypes = [I, I, P, P, I64, D, U32, P, ctypes.POINTER(ctypes.c_size_t)]
+        L.psht_server_create.argtypes = [I, ctypes.c_size_t, ctypes.POINTER(P)]
+        L.psht_server_submit.argtypes = [P, ctypes.POINTER(PshtRequest), ctypes.POINTER(I64)]
+        L.psht_server_wait.argtypes = [P, I64, ctypes.POINTER(PshtResult)]
+        L.psht_server_get_stats.argtypes = [P, ctypes.POINTER(PshtServerStats)]
+        L.psht_server_destroy.argtypes = [P]
         L.psht_estimate_bytes.argtypes = [I, I, D, I64, D, U32]
         L.psht_estimate_bytes.restype = ctypes.c_size_t
         L.psht_last_error.restype = ctypes.c_char_p
@@ -130,16 +162,19 @@ class Plan:
             raise ValueError(f"a_lm must hold {nalm(self.lmax)} packed coefficients")
         return a
 
-    def synthesis(self, g, c=None, out=None, stream=None):
-        """f_p = -sum (g_lm + i c_lm) sY_lm(theta_p, phi_p) (psht_plan_synthesis)."""
+    def synthesis(self, g, c=None, out=None, stream=None, packed_grad: bool = False):
+        """f_p = -sum (g_lm + i c_lm) sY_lm(theta_p, phi_p) (psht_plan_synthesis); with packed_grad
+        the m > 0 inputs count half (psht_plan_synthesis_packed)."""
         torch = _torch()
         g, c = self._alm_in(g), self._alm_in(c)
         f = out if out is not None else torch.empty(self.npts, dtype=self.cdtype, device="cuda")
-        _check(lib().psht_plan_synthesis(self._h, _ptr(g), _ptr(c), _ptr(f), _stream(stream)))
+        fn = lib().psht_plan_synthesis_packed if packed_grad else lib().psht_plan_synthesis
+        _check(fn(self._h, _ptr(g), _ptr(c), _ptr(f), _stream(stream)))
         return f
 
-    def adjoint(self, f, g_out=None, c_out=None, want_c: bool = True, stream=None):
-        """(g~, c~) of adjoint synthesis general (psht_plan_adjoint)."""
+    def adjoint(self, f, g_out=None, c_out=None, want_c: bool = True, stream=None, packed_grad: bool = False):
+        """(g~, c~) of adjoint synthesis general (psht_plan_adjoint); with packed_grad the m > 0
+        outputs are doubled (psht_plan_adjoint_packed)."""
         torch = _torch()
         f = torch.as_tensor(f, device="cuda").to(self.cdtype).contiguous()
         if f.numel() != self.npts:
@@ -147,7 +182,8 @@ class Plan:
         n = nalm(self.lmax)
         g = g_out if g_out is not None else torch.empty(n, dtype=self.cdtype, device="cuda")
         c = (c_out if c_out is not None else torch.empty(n, dtype=self.cdtype, device="cuda")) if want_c else None
-        _check(lib().psht_plan_adjoint(self._h, _ptr(f), _ptr(g), _ptr(c), _stream(stream)))
+        fn = lib().psht_plan_adjoint_packed if packed_grad else lib().psht_plan_adjoint
+        _check(fn(self._h, _ptr(f), _ptr(g), _ptr(c), _stream(stream)))
         return g, c
 
     def synthesis_host(self, g: np.ndarray, c, f: np.ndarray, stream=None):
@@ -256,3 +292,59 @@ def ring_synthesis_noalloc(spin: int, lmax: int, theta_rings, g, c=None, out=Non
     _check(lib().psht_ring_synthesis_noalloc(int(spin), int(lmax), _ptr(th), th.numel(), _ptr(g), _ptr(c), _ptr(F),
                                              _stream(stream)))
     return F
+
+
+class Server:
+    """Request server of the library (psht_server_*): nstreams workers, a plan cache and admission
+    against a device-memory budget (bytes; 0 = 80 % of the free memory).  submit() takes device
+    tensors, which the caller keeps alive until wait() has returned for the ticket."""
+
+    SYNTHESIS, ADJOINT = 0, 1
+
+    def __init__(self, nstreams: int = 4, budget_bytes: int = 0):
+        _torch().cuda.current_device()
+        self._h = ctypes.c_void_p()
+        _check(lib().psht_server_create(int(nstreams), int(budget_bytes), ctypes.byref(self._h)))
+        self._keep = {}
+
+    def submit(self, op: int, points_key: int, spin: int, lmax: int, eps: float, theta, phi, in_a, in_b=None,
+               out_a=None, out_b=None, precision="auto") -> int:
+        r = PshtRequest(int(op), int(spin), int(lmax), float(eps), _PREC[precision], int(points_key),
+                        theta.data_ptr(), phi.data_ptr(), theta.numel(), in_a.data_ptr(),
+                        None if in_b is None else in_b.data_ptr(), out_a.data_ptr(),
+                        None if out_b is None else out_b.data_ptr())
+        t = ctypes.c_int64()
+        _check(lib().psht_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
+        self._keep[t.value] = (theta, phi, in_a, in_b, out_a, out_b)
+        return t.value
+
+    def wait(self, ticket: int) -> dict:
+        res = PshtResult()
+        _check(lib().psht_server_wait(self._h, int(ticket), ctypes.byref(res)))
+        self._keep.pop(ticket, None)
+        return {name: getattr(res, name) for name, _ in PshtResult._fields_}
+
+    def stats(self) -> dict:
+        st = PshtServerStats()
+        _check(lib().psht_server_get_stats(self._h, ctypes.byref(st)))
+        return {name: getattr(st, name) for name, _ in PshtServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().psht_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def estimate_points(spin: int, lmax: int, theta, phi, eps: float, precision="auto", stream=None) -> int:
+    """Device bytes of a plan for these points (psht_plan_estimate_points)."""
+    b = ctypes.c_size_t()
+    _check(lib().psht_plan_estimate_points(int(spin), int(lmax), _ptr(theta), _ptr(phi), theta.numel(), float(eps),
+                                           _PREC[precision], _stream(stream), ctypes.byref(b)))
+    return b.value

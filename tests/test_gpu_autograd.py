@@ -1,0 +1,110 @@
+"""torch.autograd through the C ABI's packed-gradient entry points (marked gpu).
+
+Synthesis is real-linear in (g, c), so central finite differences along any direction are exact up
+to rounding for any step; they check the packing factor (m > 0 entries stand for m and -m) and the
+zero gradients of the entries the transform ignores (Im a_l0, l < s).  The gradient itself is also
+compared with the oracle's direct adjoint summation."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _setup(prec, eps, lmax=64, s=2, n=2500, seed=11):
+    from paper_2603_17166_gb300 import Plan
+
+    rng = np.random.default_rng(seed)
+    th = np.pi - np.arccos(rng.uniform(math.cos(math.radians(10)), 1.0, n))
+    ph = rng.uniform(0, 2 * np.pi, n)
+    plan = Plan(s, lmax, torch.from_numpy(th).cuda(), torch.from_numpy(ph).cuda(), eps, precision=prec)
+    return rng, plan, th, ph
+
+
+def _cx(rng, n, dtype):
+    return torch.from_numpy(rng.standard_normal(n) + 1j * rng.standard_normal(n)).to(dtype).cuda()
+
+
+def _re_dot(a, b):
+    """torch's real inner product over stored entries: Re sum conj(a) b."""
+    return float(torch.sum(a.conj().to(torch.complex128) * b.to(torch.complex128)).real)
+
+
+@pytest.mark.parametrize("prec,eps,tol", [("fp64", 1e-10, 1e-11), ("fp32", 1e-5, 2e-5)])
+def test_synthesis_gradient_directional(prec, eps, tol):
+    from paper_2603_17166_gb300.autograd import synthesis
+
+    rng, plan, th, ph = _setup(prec, eps)
+    n = O.nalm(plan.lmax)
+    g = _cx(rng, n, plan.cdtype).requires_grad_()
+    c = _cx(rng, n, plan.cdtype).requires_grad_()
+    w = _cx(rng, plan.npts, plan.cdtype)
+    L = torch.sum(w.conj() * synthesis(plan, g, c)).real
+    L.backward()
+    dg, dc = _cx(rng, n, plan.cdtype), _cx(rng, n, plan.cdtype)
+    # L is linear: L(a + d) - L(a - d) = 2 L(d), with L(d) = Re <w, A d>
+    Ld = _re_dot(w, plan.synthesis(dg, dc))
+    pred = _re_dot(g.grad, dg) + _re_dot(c.grad, dc)
+    assert abs(pred - Ld) <= tol * (abs(Ld) + 1e-30) * 10
+    # ignored entries have zero gradient
+    lm = O.lm_of_index(plan.lmax)
+    l, m = lm
+    assert torch.all(g.grad.imag.cpu()[torch.from_numpy(m == 0)] == 0)
+    assert torch.all(g.grad.cpu()[torch.from_numpy(l < plan.spin)] == 0)
+
+
+def test_synthesis_gradient_matches_direct_adjoint():
+    """grad_g = (2 for m > 0, 1 for m = 0) x g~ of the oracle's direct adjoint of w."""
+    from paper_2603_17166_gb300.autograd import synthesis
+
+    rng, plan, th, ph = _setup("fp64", 1e-10, lmax=48, n=1500)
+    n = O.nalm(plan.lmax)
+    g = _cx(rng, n, torch.complex128).requires_grad_()
+    c = _cx(rng, n, torch.complex128).requires_grad_()
+    # band-limited point data (a synthesised field), the input the 10 eps target is stated for
+    wn = O.direct_synthesis(plan.lmax, plan.spin, O.canonical_alm(rng.standard_normal(n) + 1j * rng.standard_normal(n),
+                                                                  plan.lmax, plan.spin), None, th, ph)
+    w = torch.from_numpy(wn).cuda()
+    torch.sum(w.conj() * synthesis(plan, g, c)).real.backward()
+    gt, ct = O.direct_adjoint(plan.lmax, plan.spin, th, ph, wn)
+    _, m = O.lm_of_index(plan.lmax)
+    fac = np.where(m > 0, 2.0, 1.0)
+    assert O.rel_l2(g.grad.cpu().numpy(), fac * gt) <= 10 * 1e-10
+    assert O.rel_l2(c.grad.cpu().numpy(), fac * ct) <= 10 * 1e-10
+
+
+@pytest.mark.parametrize("prec,eps,tol", [("fp64", 1e-10, 1e-11), ("fp32", 1e-5, 2e-5)])
+def test_adjoint_gradient_directional(prec, eps, tol):
+    from paper_2603_17166_gb300.autograd import adjoint
+
+    rng, plan, th, ph = _setup(prec, eps, s=1, seed=12)
+    n = O.nalm(plan.lmax)
+    f = _cx(rng, plan.npts, plan.cdtype).requires_grad_()
+    vg, vc = _cx(rng, n, plan.cdtype), _cx(rng, n, plan.cdtype)
+    gt, ct = adjoint(plan, f)
+    L = torch.sum(vg.conj() * gt).real + torch.sum(vc.conj() * ct).real
+    L.backward()
+    df = _cx(rng, plan.npts, plan.cdtype)
+    gd, cd = plan.adjoint(df)
+    Ld = _re_dot(vg, gd) + _re_dot(vc, cd)
+    pred = _re_dot(f.grad, df)
+    assert abs(pred - Ld) <= tol * (abs(Ld) + 1e-30) * 10
+
+
+def test_gradcheck_fp64_small():
+    """torch's own finite-difference check (fast mode) on a small FP64 plan."""
+    from paper_2603_17166_gb300.autograd import adjoint, synthesis
+
+    rng, plan, th, ph = _setup("fp64", 1e-10, lmax=24, s=2, n=600, seed=13)
+    n = O.nalm(plan.lmax)
+    g = _cx(rng, n, torch.complex128).requires_grad_()
+    c = _cx(rng, n, torch.complex128).requires_grad_()
+    assert torch.autograd.gradcheck(lambda a, b: synthesis(plan, a, b), (g, c), eps=1e-6, atol=1e-7,
+                                    rtol=1e-6, fast_mode=True)
+    f = _cx(rng, plan.npts, torch.complex128).requires_grad_()
+    assert torch.autograd.gradcheck(lambda x: adjoint(plan, x), (f,), eps=1e-6, atol=1e-7, rtol=1e-6,
+                                    fast_mode=True)
