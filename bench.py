@@ -50,6 +50,11 @@ def parse():
     ap.add_argument("--forms", default="fp32,fp64", help="comma list of forms to time (fp32 is the headline)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=200, help="requests of the serving run (0: skip)")
+    ap.add_argument("--serve-fields", type=int, default=8)
+    ap.add_argument("--serve-streams", type=int, default=4)
+    ap.add_argument("--serve-loads", default="0.8", help="offered loads, fractions of single-stream capacity")
+    ap.add_argument("--serve-nmax", type=int, default=30_000_000)
     ap.add_argument("--cpu-sample-points", type=int, default=1_000_000)
     ap.add_argument("--cpu-ring-stride", type=int, default=8)
     return ap.parse_args()
@@ -128,6 +133,12 @@ def alu_peak_tflops(prec: int) -> float:
     FP64 on this part runs at 1/64 of that rate (1.26 TFLOP/s)."""
     fp32 = 152 * 128 * 2 * 2.07e9 / 1e12
     return fp32 if prec == 32 else fp32 / 64.0
+
+
+# DRAM bytes (read + write) of one k_rec_adj launch on this workload, from an ncu capture of the
+# current kernel (profiles/k_rec_fp32_spin2_lmax4096.md); None where no capture of the current
+# kernel exists.
+REC_ADJ_TRAFFIC = {"fp32": 375.727e6 + 102.386e6, "fp64": None}
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -213,12 +224,16 @@ def run_ours(args, rank, world, local_rank):
             ms = float(t.item())
         ms_step = ms / K
         value = world * npts * K / (ms * 1e-3) / 1e6
-        # dominant kernel: the recursion (synthesis and adjoint launches are the same algorithm)
-        rec_ms = stages["rec_synthesis"][0] + stages["rec_adjoint"][0]
-        rec_n = stages["rec_synthesis"][1] + stages["rec_adjoint"][1]
+        # dominant kernel: the adjoint recursion k_rec_adj (its launches per adjoint call are
+        # counted by the stage record; same algorithmic flops as the synthesis recursion)
         flops = info["recursion_triples"] * flops_per_triple(SPIN)
-        achieved = flops / (rec_ms / rec_n * 1e-3) / 1e12 if rec_n else None
         peak = alu_peak_tflops(64 if name == "fp64" else 32)
+
+        def tflops(stage):
+            t, n = stages[stage]
+            return flops / (t / n * 1e-3) / 1e12 if n else None
+
+        achieved = tflops("rec_adjoint")
         per_stage = {k: round(v[0] / max(v[1], 1), 4) for k, v in stages.items()}
         entry = dict(value=value, ms_per_step=ms_step, steps=K, warmup=W, eps=eps, plan_s=plan_s,
                      step_ms_min=min(step_ms), step_ms_max=max(step_ms),
@@ -228,9 +243,13 @@ def run_ours(args, rank, world, local_rank):
                                eps_apo=info["eps_apo"], recursion_triples=info["recursion_triples"],
                                device_gb=info["device_bytes"] / 1e9),
                      roofline=dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s",
-                                   frac=(achieved / peak if achieved else None), traffic=None,
-                                   kernel="k_rec_syn/k_rec_adj", flops_per_launch=flops,
-                                   peak_note="FMA lanes x 2 x 2.07 GHz max SM clock"))
+                                   frac=(achieved / peak if achieved else None),
+                                   traffic=REC_ADJ_TRAFFIC.get(name), kernel="k_rec_adj",
+                                   flops_per_launch=flops,
+                                   synthesis_kernel=dict(kernel="k_rec_syn", achieved=tflops("rec_synthesis"),
+                                                         frac=(tflops("rec_synthesis") or 0) / peak),
+                                   peak_note="derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"
+                                             + (" / 64 (FP64 rate)" if name == "fp64" else "")))
         # e2e through the host-buffer C-ABI entry points, pinned host memory
         if name == "fp32" and not args.no_e2e:
             hg = torch.from_numpy(wl["g"]).to(plan.cdtype).pin_memory().numpy()
@@ -279,11 +298,101 @@ def run_ours(args, rank, world, local_rank):
         "forms": {k: {kk: vv for kk, vv in v.items() if kk not in ("e2e",)} for k, v in results.items()},
         "input_generation_s": gen_s,
     }
+    if args.serve_requests > 0 and world == 1:
+        line["serving"] = run_serving(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, wl, steps=1)
     if dist is not None:
         dist.destroy_process_group()
     return line
+
+
+# ----------------------------------------------------------------------------- serving
+def run_serving(args, dev) -> dict:
+    """Mixed request stream through the library's request server (psht_server_*): a pool of
+    fields (lmax 1024-8192, spin 0/2, caps and boxes of 0.1-4 % of the sky, 1e5-3e7 points, eps
+    1e-5/1e-8/1e-10), synthesis and adjoint 50/50, Poisson arrivals at the given fractions of the
+    measured single-stream capacity.  Plans are created once (warm cache); latency = submission
+    to completion of the request's stream work."""
+    import torch
+
+    from paper_2603_17166_gb300 import Server, synthetic
+
+    t0 = time.time()
+    fields, reqs = synthetic.serving_workload(args.serve_fields, args.serve_requests, nmax=args.serve_nmax)
+    gen_s = time.time() - t0
+    dd = []
+    for f in fields:
+        cd = torch.complex64 if f["eps"] >= 1e-5 else torch.complex128
+        d = dict(theta=torch.from_numpy(f["theta"]).to(dev), phi=torch.from_numpy(f["phi"]).to(dev),
+                 g=torch.from_numpy(f["g"]).to(dev).to(cd),
+                 c=None if f["c"] is None else torch.from_numpy(f["c"]).to(dev).to(cd),
+                 f=torch.from_numpy(f["f"]).to(dev).to(cd))
+        d["fo"] = torch.empty(f["npts"], dtype=cd, device=dev)
+        d["go"] = torch.empty_like(d["g"])
+        d["co"] = torch.empty_like(d["g"]) if f["s"] else None
+        dd.append(d)
+    srv = Server(nstreams=args.serve_streams)
+
+    def submit(i, op):
+        f, d = fields[i], dd[i]
+        if op == 0:
+            return srv.submit(Server.SYNTHESIS, f["key"], f["s"], f["lmax"], f["eps"], d["theta"], d["phi"],
+                              d["g"], d["c"], d["fo"])
+        return srv.submit(Server.ADJOINT, f["key"], f["s"], f["lmax"], f["eps"], d["theta"], d["phi"],
+                          d["f"], None, d["go"], d["co"])
+
+    # warm plans, then the service time of every (field, op) alone; a field the library rejects
+    # (e.g. PSHT_ENOTSUP for an FFT longer than one CTA's shared memory) leaves the mix
+    plan_ms, alone, rejected = [], {}, {}
+    for i in range(len(fields)):
+        for op in (0, 1):
+            r = srv.wait(submit(i, op))
+            if r["status"] != 0:
+                rejected[fields[i]["key"]] = r["status"]
+                break
+            if r["plan_ms"] > 0:
+                plan_ms.append(r["plan_ms"])
+            alone[(i, op)] = min(srv.wait(submit(i, op))["exec_ms"] for _ in range(2))
+    n_all = len(reqs)
+    reqs = [r for r in reqs if (r["field"], r["op"]) in alone]
+    if not reqs:
+        return dict(error="every field was rejected", rejected=rejected)
+    mean_service = float(np.mean([alone[(r["field"], r["op"])] for r in reqs]))
+    capacity = 1000.0 / mean_service
+    runs = []
+    for load in [float(x) for x in args.serve_loads.split(",")]:
+        lam = load * capacity
+        start = time.perf_counter()
+        tickets = []
+        for r in reqs:
+            due = start + r["t"] / lam
+            while True:
+                now = time.perf_counter()
+                if now >= due:
+                    break
+                time.sleep(min(due - now, 0.002))
+            tickets.append(submit(r["field"], r["op"]))
+        res = [srv.wait(t) for t in tickets]
+        wall = time.perf_counter() - start
+        bad = sum(1 for x in res if x["status"] != 0)
+        lat = np.array([x["total_ms"] for x in res])
+        slow = np.array([x["total_ms"] / alone[(r["field"], r["op"])] for x, r in zip(res, reqs)])
+        runs.append(dict(load=load, lambda_rps=lam, p50_ms=float(np.percentile(lat, 50)),
+                         p99_ms=float(np.percentile(lat, 99)), mean_ms=float(lat.mean()), max_ms=float(lat.max()),
+                         p99_slowdown=float(np.percentile(slow, 99)), completed_rps=len(res) / wall, failed=bad))
+    st = srv.stats()
+    srv.close()
+    head = min(runs, key=lambda x: abs(x["load"] - 0.8))
+    return dict(p99_ms=head["p99_ms"], p50_ms=head["p50_ms"], load=head["load"], requests=len(reqs),
+                fields=len(fields), streams=args.serve_streams, capacity_rps=capacity,
+                mean_service_ms=mean_service, plan_ms_mean=float(np.mean(plan_ms)) if plan_ms else None,
+                runs=runs, cache_hits=st["cache_hits"], plans_created=st["plans_created"],
+                rejected_fields={str(k): v for k, v in rejected.items()}, dropped_requests=n_all - len(reqs),
+                evictions=st["evictions"], bytes_peak_gb=st["bytes_peak"] / 1e9, input_generation_s=gen_s,
+                sample=f"{len(reqs)} requests over {len(fields) - len(rejected)} fields (lmax "
+                       f"{sorted(set(f['lmax'] for f in fields))}, N {min(f['npts'] for f in fields)}.."
+                       f"{max(f['npts'] for f in fields)}), warm plan cache")
 
 
 # ----------------------------------------------------------------------------- oracle arm

@@ -225,7 +225,7 @@ void layout(Plan& p, double theta_star) {
   p.tstride = p.nalm + 64;  // one chunk of zero records after the last order
   // launch shapes of the recursion
   p.syn_rpt = (p.prec == 64) ? 1 : 4;
-  p.syn_threads = 128;
+  p.syn_threads = 32;  // one warp per synthesis item (k_rec_syn_w)
   // adjoint: all active rings of one order m in one CTA, (rings per thread, threads) from the
   // instantiated shapes, more rings per thread in FP32 to amortise the per-l warp reduction
   if (p.prec == 32) {

@@ -77,15 +77,17 @@ static_assert((kCH * sizeof(TabEntry<float>)) % 16 == 0 && (kCH * sizeof(TabEntr
               "bulk copies are whole 16-byte units");
 
 // ---------------------------------------------------------------------------------------------
-// recurrence table per packed (l, m), FP64 arithmetic, one thread per m.
+// recurrence table per packed (l, m), FP64 arithmetic: every record is a closed form in (l, m, s),
+// so one thread per record; blockIdx.x = m, threads over l = m + blockIdx.y * blockDim.x + t.
 template <typename T>
 __global__ void k_rec_table(int lmax, int s, TabEntry<T>* __restrict__ tab) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m > lmax) return;
+  const int m = blockIdx.x;
+  const int l = m + blockIdx.y * blockDim.x + threadIdx.x;
+  if (l > lmax) return;
   const int l0 = max(m, s);
   const int64_t base = alm_base(lmax, m);
   const double m2 = (double)m * m, s2 = (double)s * s;
-  for (int l = m; l <= lmax; ++l) {
+  {
     double A = 0, B = 0, C = 0, D = 0;
     if (l >= l0 && l < lmax) {
       const double lp1 = l + 1.0;
@@ -147,17 +149,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // One staged chunk of the table: records of l = lc .. lc + 63 (zero records past lmax).
-template <typename T>
+template <typename T, int CH = kCH>
 struct TabStage {
-  TabEntry<T> v[kCH];
+  TabEntry<T> v[CH];
 };
 
 // Issue the bulk copy of table records start .. start + 63 into st (one thread).  The table is
 // padded by one chunk of zero records, so the last chunk never reads past the allocation.
-template <typename T>
-__device__ __forceinline__ void issue_chunk(TabStage<T>& st, uint64_t* bar, const TabEntry<T>* __restrict__ tab,
+template <typename T, int CH = kCH>
+__device__ __forceinline__ void issue_chunk(TabStage<T, CH>& st, uint64_t* bar, const TabEntry<T>* __restrict__ tab,
                                             int64_t start) {
-  constexpr uint32_t bytes = kCH * sizeof(TabEntry<T>);
+  constexpr uint32_t bytes = CH * sizeof(TabEntry<T>);
   fence_proxy_async();  // earlier generic reads of this stage before the async-proxy writes
   mbar_expect_tx(bar, bytes);
   bulk_g2s(st.v, tab + start, bytes, bar);
@@ -168,8 +170,8 @@ struct Coef {
   double A, D, B, C;
   __device__ __forceinline__ double t(double omx) const { return fma(-A, omx, D); }
 };
-__device__ __forceinline__ Coef get_coef(const TabStage<double>& s, int i) {
-  const double2 ad = s.v[i].ad, bc = s.v[i].bc;
+__device__ __forceinline__ Coef get_coef(const TabEntry<double>* tv, int i) {
+  const double2 ad = tv[i].ad, bc = tv[i].bc;
   return Coef{ad.x, ad.y, bc.x, bc.y};
 }
 
@@ -392,7 +394,7 @@ __device__ __forceinline__ float2 summing(float2 e, int ka, int kb) {
 // One quad (4 l steps) of the synthesis for the ring slots r < nr of this thread.
 // ACC: add the current column values to the sums; SEL: per column, only where k == 0.
 template <bool SPIN, int RPT, bool ACC, bool SEL>
-__device__ __forceinline__ void syn_quad(Cols<double, RPT>& S, SynAcc<double, RPT>& A, const TabStage<double>& st,
+__device__ __forceinline__ void syn_quad(Cols<double, RPT>& S, SynAcc<double, RPT>& A, const TabEntry<double>* st,
                                          int i0, const Dbl4* sPQ, int nr) {
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
@@ -422,12 +424,12 @@ __device__ __forceinline__ void syn_quad(Cols<double, RPT>& S, SynAcc<double, RP
   }
 }
 template <bool SPIN, int RPT, bool ACC, bool SEL>
-__device__ __forceinline__ void syn_quad(Cols<float, RPT>& S, SynAcc<float, RPT>& A, const TabStage<float>& st,
+__device__ __forceinline__ void syn_quad(Cols<float, RPT>& S, SynAcc<float, RPT>& A, const TabEntry<float>* st,
                                          int i0, const PQ2* sPQ, int nr) {
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int i = i0 + u;
-    const TabEntry<float> cf = st.v[i];
+    const TabEntry<float> cf = st[i];
     const PQ2 pq = sPQ[i];
 #pragma unroll
     for (int p = 0; p < RPT / 2; ++p) {
@@ -581,7 +583,7 @@ __global__ void __launch_bounds__(NT) k_rec_syn(const RecItem* __restrict__ item
     }
     const int nq = (min(kCH, lmax - lc + 1) + 3) >> 2;
     if (nr_w > 0 && !sfail) {
-      const TabStage<T>& st = stg[sidx];
+      const TabEntry<T>* st = stg[sidx].v;
       const PQV* PQ = sPQ[sidx];
       for (int q = 0; q < nq; ++q) {
         bool fast, skip;
@@ -634,6 +636,125 @@ __global__ void __launch_bounds__(NT) k_rec_syn(const RecItem* __restrict__ item
 }
 
 // ---------------------------------------------------------------------------------------------
+// synthesis, one warp per CTA: the CTA's RecItem (order m, at most 32 RPT rings) is processed by a
+// single warp, so there is no block barrier and a warp never waits for another warp's rings.  The
+// warp stages its own table chunks of CH l (bulk copies issued by lane 0, NST stages in flight,
+// completion on mbarriers) and its own P/Q values (lane i computes l = lc + i, i < CH, from a_lm
+// loaded one chunk ahead).  Ring slots: ring = r*32 + lane; slots r >= ceil(nj/32) are empty.
+template <typename T, bool SPIN, int RPT, int CH, int NST>
+__global__ void __launch_bounds__(32) k_rec_syn_w(const RecItem* __restrict__ items, const RingDev* __restrict__ rings,
+                                                  const MSeed* __restrict__ mseed, const TabEntry<T>* __restrict__ tab,
+                                                  const typename Cx<T>::V* __restrict__ g,
+                                                  const typename Cx<T>::V* __restrict__ c, int lmax, int s, T msc,
+                                                  typename Cx<T>::V* __restrict__ F, int Lpad,
+                                                  int* __restrict__ status) {
+  static_assert(CH == 32, "one l per lane and chunk");
+  using V = typename Cx<T>::V;
+  using PQV = typename PQRec<T>::V;
+  const RecItem it = items[blockIdx.x];
+  const int m = it.m;
+  const MSeed sd = mseed[m];
+  __shared__ __align__(16) TabStage<T, CH> stg[NST];
+  __shared__ __align__(16) PQV sPQ[NST][CH];
+  __shared__ __align__(8) uint64_t bar[NST];
+  const int lane = threadIdx.x;
+  const int nr_w = (it.nj + 31) >> 5;
+  Cols<T, RPT> S;
+  SynAcc<T, RPT> A;
+  A.zero();
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) init_col<T, SPIN, RPT>(S, rings, sd, it.j0, r * 32 + lane, it.nj, r);
+  const int64_t base = alm_base(lmax, m);
+  const bool rf = it.refl != 0;
+  const bool m0 = (m == 0);
+  const int nchunk = (lmax - sd.l0 + CH) / CH;
+  const V z = mk((T)0, (T)0);
+
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NST; ++k) mbar_init(&bar[k], 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  if (lane == 0)
+    for (int k = 0; k < NST && k < nchunk; ++k) issue_chunk<T, CH>(stg[k], &bar[k], tab, base + sd.l0 + k * CH);
+  for (int k = 0; k < NST && k < nchunk; ++k) {
+    const int l = sd.l0 + k * CH + lane;
+    V P = z, Q = z;
+    if (l <= lmax) make_pq<V, T>(g[base + l], c ? c[base + l] : z, m0, rf, l + m, msc, P, Q);
+    sPQ[k][lane] = pq_rec(P, Q);
+  }
+  V pg = z, pc = z;  // a_lm of chunk NST (the next to be staged)
+  {
+    const int l = sd.l0 + NST * CH + lane;
+    if (l <= lmax) {
+      pg = g[base + l];
+      if (c) pc = c[base + l];
+    }
+  }
+  __syncwarp();
+
+  for (int ch = 0; ch < nchunk; ++ch) {
+    const int sidx = ch % NST;
+    const bool ok = mbar_wait(&bar[sidx], (uint32_t)((ch / NST) & 1));
+    if (__any_sync(0xffffffffu, !ok)) {
+      if (lane == 0) {
+        atomicExch(status, 1);
+        for (int k = ch + 1; k < nchunk && k < ch + NST; ++k)  // drain the copies still in flight
+          mbar_wait(&bar[k % NST], (uint32_t)((k / NST) & 1));
+      }
+      return;
+    }
+    const int lc = sd.l0 + ch * CH;
+    const int nq = (min(CH, lmax - lc + 1) + 3) >> 2;
+    if (nr_w > 0) {
+      const TabEntry<T>* st = stg[sidx].v;
+      const PQV* PQ = sPQ[sidx];
+      for (int q = 0; q < nq; ++q) {
+        bool fast, skip;
+        classify<T, SPIN, RPT>(S, nr_w, fast, skip);
+        if (fast) {
+          if (nr_w >= RPT) syn_quad<SPIN, RPT, true, false>(S, A, st, 4 * q, PQ, RPT);
+          else syn_quad<SPIN, RPT, true, false>(S, A, st, 4 * q, PQ, nr_w);
+        } else {
+          if (skip) syn_quad<SPIN, RPT, false, false>(S, A, st, 4 * q, PQ, nr_w);
+          else syn_quad<SPIN, RPT, true, true>(S, A, st, 4 * q, PQ, nr_w);
+          rescale_all<T, SPIN, RPT>(S, nr_w);
+        }
+      }
+    }
+    __syncwarp();  // every lane is done with stage sidx
+    if (ch + NST < nchunk) {
+      if (lane == 0) issue_chunk<T, CH>(stg[sidx], &bar[sidx], tab, base + lc + NST * CH);
+      const int l = lc + NST * CH + lane;
+      V P = z, Q = z;
+      if (l <= lmax) make_pq<V, T>(pg, pc, m0, rf, l + m, msc, P, Q);
+      sPQ[sidx][lane] = pq_rec(P, Q);
+      pg = pc = z;
+      const int l2 = l + CH;
+      if (l2 <= lmax) {
+        pg = g[base + l2];
+        if (c) pc = c[base + l2];
+      }
+    }
+    __syncwarp();
+  }
+  const T sgn_s = (s & 1) ? (T)1 : (T)-1;  // -(-1)^s
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const int jj = r * 32 + lane;
+    if (jj < it.nj) {
+      const int j = it.j0 + jj;
+      const T a0 = A.get(r, 0), a1 = A.get(r, 1), a2 = A.get(r, 2), a3 = A.get(r, 3);
+      const V fpos = rf ? mk(-a2, -a3) : mk(-a0, -a1);
+      const V fneg = rf ? mk(sgn_s * a0, sgn_s * a1) : mk(sgn_s * a2, sgn_s * a3);
+      F[(int64_t)col_of(m) * Lpad + j] = fpos;
+      if (!m0) F[(int64_t)col_of(-m) * Lpad + j] = fneg;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 // adjoint: one CTA per order m (blockIdx.x = m), the active rings of one ring part, RPT rings per
 // thread.  Per quad the 4 l values x 4 partial sums of each thread are reduced across the warp by
 // a reduce-scatter (16 values over 32 lanes: 4 halving exchanges and one final add).
@@ -654,7 +775,7 @@ __device__ __forceinline__ T reduce_scatter16(T (&v)[16], int lane) {
 
 template <bool SPIN, int RPT, bool SEL>
 __device__ __forceinline__ void adj_quad_sums(Cols<double, RPT>& S, const AdjIn<double, RPT>& f,
-                                              const TabStage<double>& st, int i0, int nr, double (&v)[16]) {
+                                              const TabEntry<double>* st, int i0, int nr, double (&v)[16]) {
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const Coef cf = get_coef(st, i0 + u);
@@ -685,10 +806,10 @@ __device__ __forceinline__ void adj_quad_sums(Cols<double, RPT>& S, const AdjIn<
 }
 template <bool SPIN, int RPT, bool SEL>
 __device__ __forceinline__ void adj_quad_sums(Cols<float, RPT>& S, const AdjIn<float, RPT>& f,
-                                              const TabStage<float>& st, int i0, int nr, float (&v)[16]) {
+                                              const TabEntry<float>* st, int i0, int nr, float (&v)[16]) {
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
-    const TabEntry<float> cf = st.v[i0 + u];
+    const TabEntry<float> cf = st[i0 + u];
     float2 p0 = make_float2(0.f, 0.f), p1 = p0, p2 = p0, p3 = p0;  // (even slot, odd slot) partial sums
 #pragma unroll
     for (int p = 0; p < RPT / 2; ++p) {
@@ -709,7 +830,7 @@ __device__ __forceinline__ void adj_quad_sums(Cols<float, RPT>& S, const AdjIn<f
   }
 }
 template <bool SPIN, int RPT>
-__device__ __forceinline__ void adj_quad_steps(Cols<double, RPT>& S, const TabStage<double>& st, int i0, int nr) {
+__device__ __forceinline__ void adj_quad_steps(Cols<double, RPT>& S, const TabEntry<double>* st, int i0, int nr) {
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const Coef cf = get_coef(st, i0 + u);
@@ -728,10 +849,10 @@ __device__ __forceinline__ void adj_quad_steps(Cols<double, RPT>& S, const TabSt
   }
 }
 template <bool SPIN, int RPT>
-__device__ __forceinline__ void adj_quad_steps(Cols<float, RPT>& S, const TabStage<float>& st, int i0, int nr) {
+__device__ __forceinline__ void adj_quad_steps(Cols<float, RPT>& S, const TabEntry<float>* st, int i0, int nr) {
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
-    const TabEntry<float> cf = st.v[i0 + u];
+    const TabEntry<float> cf = st[i0 + u];
 #pragma unroll
     for (int p = 0; p < RPT / 2; ++p)
       if (2 * p < nr) step_pair<SPIN, RPT>(S, p, cf);
@@ -814,7 +935,7 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
       atomicExch(status, 1);
       sfail = 1;
     }
-    const TabStage<T>& st = stg[sidx];
+    const TabEntry<T>* st = stg[sidx].v;
     T* redw = reinterpret_cast<T*>(red + (sidx * NW + warp) * kCH);
     for (int q = 0; q < nq; ++q) {
       T tot = (T)0;
@@ -899,6 +1020,12 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
 template <typename T, bool SPIN, int RPT>
 void launch_syn_t(Plan& p, const void* g, const void* c, double msc, cudaStream_t st) {
   using V = typename Cx<T>::V;
+  if (p.syn_threads == 32) {  // one warp per item (items of at most 32 RPT rings)
+    k_rec_syn_w<T, SPIN, RPT, 32, 4><<<p.nitems, 32, 0, st>>>(
+        p.d_items, p.d_ring, p.d_mseed, (const TabEntry<T>*)p.d_rtab, (const V*)g, (const V*)c, p.lmax, p.spin,
+        (T)msc, (V*)p.d_F, p.Lpad, p.d_status);
+    return;
+  }
   k_rec_syn<T, SPIN, RPT, 128><<<p.nitems, 128, 0, st>>>(p.d_items, p.d_ring, p.d_mseed,
                                                           (const TabEntry<T>*)p.d_rtab, (const V*)g, (const V*)c, p.lmax, p.spin, (T)msc,
                                                           (V*)p.d_F, p.Lpad, p.d_status);
@@ -946,9 +1073,10 @@ int rec_table_record_bytes(int prec) {
 }
 
 void build_rec_table(Plan& p, cudaStream_t st) {
-  const int nth = 128, nbl = (p.lmax + 1 + nth - 1) / nth;
-  if (p.prec == 64) k_rec_table<double><<<nbl, nth, 0, st>>>(p.lmax, p.spin, (TabEntry<double>*)p.d_rtab);
-  else k_rec_table<float><<<nbl, nth, 0, st>>>(p.lmax, p.spin, (TabEntry<float>*)p.d_rtab);
+  const int nth = 128;
+  const dim3 grid(p.lmax + 1, (p.lmax + 1 + nth - 1) / nth);  // blocks past lmax - m exit at once
+  if (p.prec == 64) k_rec_table<double><<<grid, nth, 0, st>>>(p.lmax, p.spin, (TabEntry<double>*)p.d_rtab);
+  else k_rec_table<float><<<grid, nth, 0, st>>>(p.lmax, p.spin, (TabEntry<float>*)p.d_rtab);
   PSHT_CUDA_TRY(cudaGetLastError());
 }
 

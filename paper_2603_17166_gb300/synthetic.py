@@ -210,3 +210,77 @@ def config3(s: int = 2, frame: str = "R", n: int = 50_000_000, realisation: int 
     c = gaussian_alm(lmax, s, rng(3, "alm", 2 * realisation + 1), "inv_l2") if s else None
     theta, phi = field_points("random1", frame, rng(3, "points"), n=n)
     return dict(lmax=lmax, s=s, g=g, c=c, theta=theta, phi=phi)
+
+
+def _rotate_from_north(v, centre):
+    """Rotation taking the north pole to `centre`, applied to v (inverse of rotate_to_north)."""
+    z = np.array([0.0, 0.0, 1.0])
+    axis = np.cross(z, centre)
+    sa = np.linalg.norm(axis)
+    ca = float(centre @ z)
+    if sa < 1e-15:
+        return v if ca > 0 else v * np.array([1.0, -1.0, -1.0])
+    k = axis / sa
+    K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+    R = np.eye(3) + sa * K + (1 - ca) * (K @ K)
+    return v @ R.T
+
+
+def patch_points(n: int, shape: str, dec_centre: float, fsky: float, gen: np.random.Generator):
+    """(theta, phi) of n points uniform in area in a patch of sky fraction fsky centred at
+    (RA 0, dec_centre): a cap, or an RA/dec box twice as wide (in RA degrees) as it is high."""
+    if shape == "cap":
+        r = math.degrees(math.acos(1.0 - 2.0 * fsky))
+        th, ph = cap_points(n, r, gen, "N")
+        st = np.sin(th)
+        v = np.stack([st * np.cos(ph), st * np.sin(ph), np.cos(th)], axis=-1)
+        return _vec_to_thetaphi(_rotate_from_north(v, _radec_to_vec(0.0, dec_centre)))
+    area = 4.0 * math.pi * fsky  # steradians = width_rad * (sin d1 - sin d0)
+    h = 1.0  # half height in degrees, grown until the box holds the area at twice its height in RA
+    for _ in range(60):
+        d0, d1 = max(-89.9, dec_centre - h), min(89.9, dec_centre + h)
+        w = area / (math.sin(math.radians(d1)) - math.sin(math.radians(d0)))
+        if math.degrees(w) <= 2.0 * (d1 - d0) or h > 40:
+            break
+        h *= 1.1
+    w = min(math.degrees(w), 360.0)
+    v = box_points_random(n, (-0.5 * w, 0.5 * w), (d0, d1), gen)
+    return _vec_to_thetaphi(v)
+
+
+SERVING_LMAX = (1024, 2048, 4096, 8192)
+SERVING_EPS = (1e-5, 1e-8, 1e-10)
+
+
+def serving_workload(n_fields: int = 8, n_requests: int = 200, nmax: int = 30_000_000, lmax_max: int = 8192):
+    """Mixed request stream: a pool of fields (patch, points, lmax, spin, eps) and a request
+    sequence over it.  Per field: lmax from {1024, 2048, 4096, 8192} (capped at lmax_max), spin 0 or
+    2, cap (centre dec U[-90, -30]) or RA/dec box 50/50, sky fraction log-uniform on [0.1 %, 4 %],
+    N log-uniform on [1e5, nmax], eps from {1e-5 (FP32 form), 1e-8, 1e-10}.  Requests: field
+    uniform over the pool, synthesis or adjoint 50/50, unit-rate Poisson arrival times (scale them
+    by 1/lambda).  a_lm and point data are drawn per field."""
+    gq = rng(4, "stream", 1)  # field parameters
+    gp = rng(4, "points")
+    ga = rng(4, "alm")
+    gs = rng(4, "stream")
+    fields = []
+    lms = [l for l in SERVING_LMAX if l <= lmax_max] or [lmax_max]
+    for i in range(n_fields):
+        lmax = int(gq.choice(lms))
+        s = int(gq.choice([0, 2]))
+        shape = "cap" if gq.uniform() < 0.5 else "box"
+        dec_c = float(gq.uniform(-90.0, -30.0))
+        fsky = float(math.exp(gq.uniform(math.log(1e-3), math.log(4e-2))))
+        n = int(math.exp(gq.uniform(math.log(1e5), math.log(nmax))))
+        eps = float(gq.choice(SERVING_EPS))
+        th, ph = patch_points(n, shape, dec_c, fsky, gp)
+        g = gaussian_alm(lmax, s, ga, "inv_l2")
+        c = gaussian_alm(lmax, s, ga, "inv_l2") if s else None
+        f = ga.standard_normal(n) + 1j * ga.standard_normal(n)
+        fields.append(dict(key=i + 1, lmax=lmax, s=s, shape=shape, dec_centre=dec_c, fsky=fsky, npts=n, eps=eps,
+                           theta=th, phi=ph, g=g, c=c, f=f))
+    which = gs.integers(0, n_fields, n_requests)
+    ops = gs.integers(0, 2, n_requests)
+    arrivals = np.cumsum(gs.exponential(1.0, n_requests))
+    requests = [dict(field=int(w), op=int(o), t=float(t)) for w, o, t in zip(which, ops, arrivals)]
+    return fields, requests

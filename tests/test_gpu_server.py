@@ -1,0 +1,131 @@
+"""The request server (psht_server_*) through the C ABI (marked gpu): results of requests run in a
+concurrent mix equal those run alone, the plan cache and the memory admission (eviction, a request
+that can never fit), and the error path of an invalid request."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _fields(n_fields=5, seed=3):
+    from paper_2603_17166_gb300 import synthetic as S
+
+    gen = np.random.default_rng(seed)
+    out = []
+    for i in range(n_fields):
+        lmax = int(gen.choice([48, 96, 160]))
+        s = int(gen.choice([0, 2]))
+        eps = float(gen.choice([1e-5, 1e-10]))
+        n = int(gen.integers(2000, 20000))
+        th, ph = S.patch_points(n, "cap" if i % 2 else "box", float(gen.uniform(-90, -30)),
+                                float(gen.uniform(0.002, 0.04)), gen)
+        cd = torch.complex64 if eps >= 1e-5 else torch.complex128
+        na = S.nalm(lmax)
+        out.append(dict(key=100 + i, lmax=lmax, s=s, eps=eps, cd=cd,
+                        theta=torch.from_numpy(th).cuda(), phi=torch.from_numpy(ph).cuda(),
+                        g=torch.from_numpy(S.gaussian_alm(lmax, s, gen, "white")).cuda().to(cd),
+                        c=torch.from_numpy(S.gaussian_alm(lmax, s, gen, "white")).cuda().to(cd) if s else None,
+                        f=torch.from_numpy(gen.standard_normal(n) + 1j * gen.standard_normal(n)).cuda().to(cd),
+                        na=na, n=n))
+    return out
+
+
+def _submit(srv, fd, op):
+    from paper_2603_17166_gb300 import Server
+
+    if op == 0:
+        out = torch.empty(fd["n"], dtype=fd["cd"], device="cuda")
+        t = srv.submit(Server.SYNTHESIS, fd["key"], fd["s"], fd["lmax"], fd["eps"], fd["theta"], fd["phi"],
+                       fd["g"], fd["c"], out)
+        return t, (out,)
+    go = torch.empty(fd["na"], dtype=fd["cd"], device="cuda")
+    co = torch.empty(fd["na"], dtype=fd["cd"], device="cuda") if fd["s"] else None
+    t = srv.submit(Server.ADJOINT, fd["key"], fd["s"], fd["lmax"], fd["eps"], fd["theta"], fd["phi"], fd["f"],
+                   None, go, co)
+    return t, (go, co)
+
+
+def _close(a, b, fd):
+    tol = 1e-12 if fd["cd"] == torch.complex128 else 1e-5
+    for x, y in zip(a, b):
+        if x is None:
+            continue
+        num = torch.linalg.vector_norm((x - y).to(torch.complex128))
+        den = torch.linalg.vector_norm(y.to(torch.complex128))
+        assert float(num) <= tol * float(den), (fd["key"], float(num / den))
+
+
+def test_mix_matches_alone():
+    """20 requests replayed alone (one worker) and then all at once on four workers."""
+    from paper_2603_17166_gb300 import Server
+
+    fields = _fields()
+    gen = np.random.default_rng(9)
+    reqs = [(int(gen.integers(len(fields))), int(gen.integers(2))) for _ in range(20)]
+    srv1 = Server(nstreams=1)
+    alone = []
+    for i, op in reqs:
+        t, out = _submit(srv1, fields[i], op)
+        r = srv1.wait(t)
+        assert r["status"] == 0
+        alone.append(out)
+    srv1.close()
+    srv4 = Server(nstreams=4)
+    pend = [_submit(srv4, fields[i], op) for i, op in reqs]
+    res = [(srv4.wait(t), out) for t, out in pend]
+    st = srv4.stats()
+    srv4.close()
+    for (i, op), (r, out), ref in zip(reqs, res, alone):
+        assert r["status"] == 0
+        if op == 0:  # synthesis has a fixed summation order: identical bits
+            assert torch.equal(out[0], ref[0])
+        else:        # the adjoint's spreading uses atomics: equal up to the summation order
+            _close(out, ref, fields[i])
+    assert st["completed"] == 20 and st["failed"] == 0
+    assert st["plans_created"] == len({i for i, _ in reqs})
+    assert st["cache_hits"] == 20 - st["plans_created"]
+    assert len({r["worker"] for r, _ in res}) > 1
+
+
+def test_budget_evicts_and_rejects():
+    from paper_2603_17166_gb300 import Server, estimate_points
+
+    fields = _fields(4, seed=4)
+    sizes = [estimate_points(fd["s"], fd["lmax"], fd["theta"], fd["phi"], fd["eps"]) for fd in fields]
+    budget = max(sizes) + min(sizes) // 2  # room for one plan at a time (plus slack)
+    srv = Server(nstreams=2, budget_bytes=budget)
+    outs = []
+    for rep in range(2):
+        for fd in fields:
+            t, out = _submit(srv, fd, 0)
+            r = srv.wait(t)
+            assert r["status"] == 0
+            outs.append(out[0].clone())
+    st = srv.stats()
+    assert st["evictions"] >= len(fields)
+    assert st["bytes_peak"] <= budget
+    for k in range(len(fields)):  # a plan rebuilt after eviction gives the same result
+        assert torch.equal(outs[k], outs[k + len(fields)])
+    srv.close()
+    tiny = Server(nstreams=1, budget_bytes=1024)
+    t, _ = _submit(tiny, fields[0], 0)
+    r = tiny.wait(t)
+    assert r["status"] == -12  # PSHT_ENOMEM: can never fit
+    tiny.close()
+
+
+def test_invalid_request_fails_alone():
+    from paper_2603_17166_gb300 import Server
+
+    fd = _fields(1, seed=5)[0]
+    bad = dict(fd)
+    bad["key"] = 999
+    bad["theta"] = fd["theta"].clone()
+    bad["theta"][0] = float("nan")
+    srv = Server(nstreams=2)
+    t_bad, _ = _submit(srv, bad, 0)
+    t_ok, _ = _submit(srv, fd, 0)
+    assert srv.wait(t_bad)["status"] == -22  # PSHT_EINVAL from the point validation
+    assert srv.wait(t_ok)["status"] == 0
+    srv.close()
