@@ -236,11 +236,11 @@ void layout(Plan& p, double theta_star) {
     p.adj_threads = p.nring <= 512 ? 128 : (p.nring <= 2048 ? 256 : 512);
   }
   PSHT_REQUIRE(p.nring <= 8 * 512, PSHT_ENOTSUP, "more than 4096 rings (lmax theta* too large for this build)");
-  const int maxlen = max_fft_len(p.prec);
-  PSHT_REQUIRE(p.nTheta <= maxlen, PSHT_ENOTSUP,
-               "Theta FFT length " + std::to_string(p.nTheta) + " above the shared-memory limit " + std::to_string(maxlen));
-  PSHT_REQUIRE(p.nphi <= maxlen, PSHT_ENOTSUP,
-               "phi FFT length " + std::to_string(p.nphi) + " above the shared-memory limit " + std::to_string(maxlen));
+  // FFTs longer than one CTA's shared memory run on global buffers (psht_fft.cu)
+  constexpr int kMaxLen = 1 << 22;
+  PSHT_REQUIRE(p.nTheta <= kMaxLen && p.nphi <= kMaxLen, PSHT_ENOTSUP,
+               "FFT length above " + std::to_string(kMaxLen) + " (Theta " + std::to_string(p.nTheta) + ", phi " +
+                   std::to_string(p.nphi) + ")");
 }
 
 size_t planned_bytes(const Plan& p) {
@@ -253,6 +253,7 @@ size_t planned_bytes(const Plan& p) {
   b += (size_t)p.npts * 8;                                     // index + cell
   b += p.prec == 64 ? (size_t)p.npts * 2 * p.W * 8 : (size_t)p.npts * 8;  // weights / fractions
   b += (size_t)(p.nTheta + 2 * p.L + p.nphi) * (cb + 4);       // twiddles + permutations
+  b += fft_scratch_elems(p) * cb;                              // long-FFT buffers
   return b;
 }
 
@@ -412,6 +413,7 @@ Plan* create(int spin, int lmax, const double* theta, const double* phi, int64_t
     p->d_F = dalloc(*p, (size_t)p->ncols * p->Lpad * cb);
     p->d_X = dalloc(*p, (size_t)p->nrows * p->ncols * cb);
     p->d_G = dalloc(*p, (size_t)p->nrows * p->gstride * cb);
+    if (const size_t fe = fft_scratch_elems(*p)) p->d_fscratch = dalloc(*p, fe * cb);
     build_rec_table(*p, st);
     // step 3 for the points: Theta_p, tiles, sorted layout (and FP64 kernel weights)
     p->d_pidx = (int32_t*)dalloc(*p, (size_t)std::max<int64_t>(npts, 1) * 4);

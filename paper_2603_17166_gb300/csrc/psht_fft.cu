@@ -10,6 +10,8 @@
 // Every transform runs in place in shared memory (psht_common.cuh), one CTA per column or row.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "psht_common.cuh"
 
 namespace psht {
@@ -25,7 +27,11 @@ struct QPer {
   static constexpr int v = ((sizeof(T) == 8 ? kMaxLenF64 : kMaxLenF32) / 2 + kFftThreads - 1) / kFftThreads;
 };
 
-template <typename T>
+// GM = false: one CTA per column, the transform in shared memory.  GM = true (lengths beyond
+// shared memory): gridDim.x CTAs loop over the columns, each with its own slice of a global
+// scratch array (4L + 2L elements: the transform, then the staged |n| <= L-1 values), which the
+// L2 cache holds while the CTA works on it.
+template <typename T, bool GM>
 __global__ void __launch_bounds__(kFftThreads) k_theta_syn(const typename Cx<T>::V* __restrict__ F, int Lpad,
                                                            const T* __restrict__ w, int nring,
                                                            const int2* __restrict__ mrange, int mstride, int s, int L,
@@ -34,15 +40,16 @@ __global__ void __launch_bounds__(kFftThreads) k_theta_syn(const typename Cx<T>:
                                                            const int* __restrict__ perm2L, FftDev f4L,
                                                            const typename Cx<T>::V* __restrict__ tw4L,
                                                            const int* __restrict__ perm4L, int r_lo, int nrows,
-                                                           typename Cx<T>::V* __restrict__ X, int ncols) {
+                                                           typename Cx<T>::V* __restrict__ X, int ncols,
+                                                           typename Cx<T>::V* __restrict__ scratch) {
   using V = typename Cx<T>::V;
   extern __shared__ __align__(16) unsigned char smraw[];
-  V* buf = reinterpret_cast<V*>(smraw);
-  const int mi = blockIdx.x;
+  const int N2 = 2 * L, N4 = 4 * L;
+  V* buf = GM ? scratch + (int64_t)blockIdx.x * (N4 + N2) : reinterpret_cast<V*>(smraw);
+  auto body = [&](const int mi) {
   const int m = col_m(mi), am = m < 0 ? -m : m;
   const T sigma = ((s + am) & 1) ? (T)-1 : (T)1;
   const int2 rr = mrange[am], rr1 = mrange[mstride + am];  // active rings: direct part, reflected part
-  const int N2 = 2 * L, N4 = 4 * L;
   const V* Fc = F + (int64_t)mi * Lpad;
   for (int k = threadIdx.x; k < N2; k += blockDim.x) {
     int j = k;
@@ -58,26 +65,41 @@ __global__ void __launch_bounds__(kFftThreads) k_theta_syn(const typename Cx<T>:
   __syncthreads();
   fft_dif<false>(buf, f2L, tw2L);
   // collect b[n] = H[n] sT(n) sP(m), |n| <= L-1, then lay them out for the inverse DIT of length 4L
-  constexpr int kQ = QPer<T>::v;
-  V hv[kQ];
   const T sp = sP[m + M];
-#pragma unroll
-  for (int q = 0; q < kQ; ++q) {
-    const int i = threadIdx.x + q * blockDim.x;
-    if (i < N2 - 1) {
+  if constexpr (GM) {
+    V* stg = buf + N4;
+    for (int i = threadIdx.x; i < N2 - 1; i += blockDim.x) {
       const int n = i - (L - 1);
-      hv[q] = cscale(buf[perm2L[n < 0 ? n + N2 : n]], sT[i] * sp);
+      stg[i] = cscale(buf[perm2L[n < 0 ? n + N2 : n]], sT[i] * sp);
     }
-  }
-  __syncthreads();
-  for (int k = threadIdx.x; k < N4; k += blockDim.x) buf[k] = mk((T)0, (T)0);
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < kQ; ++q) {
-    const int i = threadIdx.x + q * blockDim.x;
-    if (i < N2 - 1) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < N4; k += blockDim.x) buf[k] = mk((T)0, (T)0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < N2 - 1; i += blockDim.x) {
       const int n = i - (L - 1);
-      buf[perm4L[n < 0 ? n + N4 : n]] = hv[q];
+      buf[perm4L[n < 0 ? n + N4 : n]] = stg[i];
+    }
+  } else {
+    constexpr int kQ = QPer<T>::v;
+    V hv[kQ];
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+      const int i = threadIdx.x + q * blockDim.x;
+      if (i < N2 - 1) {
+        const int n = i - (L - 1);
+        hv[q] = cscale(buf[perm2L[n < 0 ? n + N2 : n]], sT[i] * sp);
+      }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < N4; k += blockDim.x) buf[k] = mk((T)0, (T)0);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+      const int i = threadIdx.x + q * blockDim.x;
+      if (i < N2 - 1) {
+        const int n = i - (L - 1);
+        buf[perm4L[n < 0 ? n + N4 : n]] = hv[q];
+      }
     }
   }
   __syncthreads();
@@ -87,18 +109,27 @@ __global__ void __launch_bounds__(kFftThreads) k_theta_syn(const typename Cx<T>:
     if (r < 0) r += N4;
     X[(int64_t)i * ncols + mi] = buf[r];
   }
+  __syncthreads();  // buf is reused by the next column
+  };
+  if constexpr (GM) {
+    for (int mi = blockIdx.x; mi < ncols; mi += gridDim.x) body(mi);
+  } else {
+    body(blockIdx.x);
+  }
 }
 
-template <typename T>
+// GM as for k_theta_syn: rows looped over gridDim.x CTAs, each with an nphi-element scratch slice
+template <typename T, bool GM>
 __global__ void __launch_bounds__(kFftThreads) k_phi_syn(const typename Cx<T>::V* __restrict__ X, int ncols,
                                                          FftDev fP, const typename Cx<T>::V* __restrict__ twP,
                                                          const int* __restrict__ permP, int padq, int gstride,
-                                                         typename Cx<T>::V* __restrict__ G) {
+                                                         typename Cx<T>::V* __restrict__ G, int nrows,
+                                                         typename Cx<T>::V* __restrict__ scratch) {
   using V = typename Cx<T>::V;
   extern __shared__ __align__(16) unsigned char smraw[];
-  V* buf = reinterpret_cast<V*>(smraw);
-  const int row = blockIdx.x;
   const int nphi = fP.n;
+  V* buf = GM ? scratch + (int64_t)blockIdx.x * nphi : reinterpret_cast<V*>(smraw);
+  auto body = [&](const int row) {
   for (int k = threadIdx.x; k < nphi; k += blockDim.x) buf[k] = mk((T)0, (T)0);
   __syncthreads();
   const V* Xr = X + (int64_t)row * ncols;
@@ -116,18 +147,26 @@ __global__ void __launch_bounds__(kFftThreads) k_phi_syn(const typename Cx<T>::V
     Gr[q] = buf[src];
   }
   for (int q = nq + threadIdx.x; q < gstride; q += blockDim.x) Gr[q] = mk((T)0, (T)0);
+  __syncthreads();  // buf is reused by the next row
+  };
+  if constexpr (GM) {
+    for (int row = blockIdx.x; row < nrows; row += gridDim.x) body(row);
+  } else {
+    body(blockIdx.x);
+  }
 }
 
-template <typename T>
+template <typename T, bool GM>
 __global__ void __launch_bounds__(kFftThreads) k_phi_adj(const typename Cx<T>::V* __restrict__ G, int gstride,
                                                          int padq, FftDev fP, const typename Cx<T>::V* __restrict__ twP,
                                                          const int* __restrict__ permP,
-                                                         typename Cx<T>::V* __restrict__ X, int ncols) {
+                                                         typename Cx<T>::V* __restrict__ X, int ncols, int nrows,
+                                                         typename Cx<T>::V* __restrict__ scratch) {
   using V = typename Cx<T>::V;
   extern __shared__ __align__(16) unsigned char smraw[];
-  V* buf = reinterpret_cast<V*>(smraw);
-  const int row = blockIdx.x;
   const int nphi = fP.n;
+  V* buf = GM ? scratch + (int64_t)blockIdx.x * nphi : reinterpret_cast<V*>(smraw);
+  auto body = [&](const int row) {
   const V* Gr = G + (int64_t)row * gstride;
   // fold every stored column qs (true column qs - padq) onto q = (qs - padq) mod nphi
   const int nq = nphi + 2 * padq;
@@ -143,9 +182,16 @@ __global__ void __launch_bounds__(kFftThreads) k_phi_adj(const typename Cx<T>::V
     const int m = col_m(mi);
     Xr[mi] = buf[permP[m < 0 ? m + nphi : m]];
   }
+  __syncthreads();  // buf is reused by the next row
+  };
+  if constexpr (GM) {
+    for (int row = blockIdx.x; row < nrows; row += gridDim.x) body(row);
+  } else {
+    body(blockIdx.x);
+  }
 }
 
-template <typename T>
+template <typename T, bool GM>
 __global__ void __launch_bounds__(kFftThreads) k_theta_adj(const typename Cx<T>::V* __restrict__ X, int ncols,
                                                            int r_lo, int nrows, const T* __restrict__ w, int nring,
                                                            int s, int L, const T* __restrict__ sT,
@@ -154,14 +200,15 @@ __global__ void __launch_bounds__(kFftThreads) k_theta_adj(const typename Cx<T>:
                                                            const int* __restrict__ perm2L, FftDev f4L,
                                                            const typename Cx<T>::V* __restrict__ tw4L,
                                                            const int* __restrict__ perm4L,
-                                                           typename Cx<T>::V* __restrict__ Ft, int Lpad) {
+                                                           typename Cx<T>::V* __restrict__ Ft, int Lpad,
+                                                           typename Cx<T>::V* __restrict__ scratch) {
   using V = typename Cx<T>::V;
   extern __shared__ __align__(16) unsigned char smraw[];
-  V* buf = reinterpret_cast<V*>(smraw);
-  const int mi = blockIdx.x;
+  const int N2 = 2 * L, N4 = 4 * L;
+  V* buf = GM ? scratch + (int64_t)blockIdx.x * (N4 + N2) : reinterpret_cast<V*>(smraw);
+  auto body = [&](const int mi) {
   const int m = col_m(mi), am = m < 0 ? -m : m;
   const T sigma = ((s + am) & 1) ? (T)-1 : (T)1;
-  const int N2 = 2 * L, N4 = 4 * L;
   // transpose of the row read-out: row r lands on r mod 4L, summing rows that coincide
   for (int k = threadIdx.x; k < N4; k += blockDim.x) {
     int i0 = (k - r_lo) % N4;  // first row index i >= 0 with r_lo + i = k (mod 4L)
@@ -172,26 +219,41 @@ __global__ void __launch_bounds__(kFftThreads) k_theta_adj(const typename Cx<T>:
   }
   __syncthreads();
   fft_dif<false>(buf, f4L, tw4L);
-  constexpr int kQ = QPer<T>::v;
-  V hv[kQ];
   const T sp = sP[m + M];
-#pragma unroll
-  for (int q = 0; q < kQ; ++q) {
-    const int i = threadIdx.x + q * blockDim.x;
-    if (i < N2 - 1) {
+  if constexpr (GM) {
+    V* stg = buf + N4;
+    for (int i = threadIdx.x; i < N2 - 1; i += blockDim.x) {
       const int n = i - (L - 1);
-      hv[q] = cscale(buf[perm4L[n < 0 ? n + N4 : n]], sT[i] * sp);
+      stg[i] = cscale(buf[perm4L[n < 0 ? n + N4 : n]], sT[i] * sp);
     }
-  }
-  __syncthreads();
-  for (int k = threadIdx.x; k < N2; k += blockDim.x) buf[k] = mk((T)0, (T)0);
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < kQ; ++q) {
-    const int i = threadIdx.x + q * blockDim.x;
-    if (i < N2 - 1) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < N2; k += blockDim.x) buf[k] = mk((T)0, (T)0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < N2 - 1; i += blockDim.x) {
       const int n = i - (L - 1);
-      buf[perm2L[n < 0 ? n + N2 : n]] = hv[q];
+      buf[perm2L[n < 0 ? n + N2 : n]] = stg[i];
+    }
+  } else {
+    constexpr int kQ = QPer<T>::v;
+    V hv[kQ];
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+      const int i = threadIdx.x + q * blockDim.x;
+      if (i < N2 - 1) {
+        const int n = i - (L - 1);
+        hv[q] = cscale(buf[perm4L[n < 0 ? n + N4 : n]], sT[i] * sp);
+      }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < N2; k += blockDim.x) buf[k] = mk((T)0, (T)0);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+      const int i = threadIdx.x + q * blockDim.x;
+      if (i < N2 - 1) {
+        const int n = i - (L - 1);
+        buf[perm2L[n < 0 ? n + N2 : n]] = hv[q];
+      }
     }
   }
   __syncthreads();
@@ -201,6 +263,13 @@ __global__ void __launch_bounds__(kFftThreads) k_theta_adj(const typename Cx<T>:
     V v = buf[j];
     if (j >= 1 && j <= L - 1) v = cadd(v, cscale(buf[N2 - j], sigma));
     Fc[j] = cscale(v, w[j]);
+  }
+  __syncthreads();  // buf is reused by the next column
+  };
+  if constexpr (GM) {
+    for (int mi = blockIdx.x; mi < ncols; mi += gridDim.x) body(mi);
+  } else {
+    body(blockIdx.x);
   }
 }
 
@@ -231,75 +300,90 @@ void set_smem(const void* fn, size_t bytes) {
 
 int max_fft_len(int prec) { return prec == 64 ? kMaxLenF64 : kMaxLenF32; }
 
+// Lengths above one CTA's shared memory run in global-buffer mode on a persistent grid.
+namespace {
+constexpr int kGmCtas = 152 * 4;
+bool theta_gm(const Plan& p) { return 4 * p.L > max_fft_len(p.prec); }
+bool phi_gm(const Plan& p) { return p.nphi > max_fft_len(p.prec); }
+}  // namespace
+
+size_t fft_scratch_elems(const Plan& p) {
+  size_t e = 0;
+  if (theta_gm(p)) e = std::max(e, (size_t)std::min(p.ncols, kGmCtas) * 6 * p.L);
+  if (phi_gm(p)) e = std::max(e, (size_t)std::min(p.nrows, kGmCtas) * p.nphi);
+  return e;
+}
+
+template <typename T>
+void theta_syn_t(Plan& p, cudaStream_t st) {
+  using V = typename Cx<T>::V;
+  const bool gm = theta_gm(p);
+  const size_t smem = gm ? 0 : (size_t)4 * p.L * sizeof(V);
+  const auto fn = gm ? k_theta_syn<T, true> : k_theta_syn<T, false>;
+  if (!gm) set_smem<T>((const void*)fn, smem);
+  fn<<<gm ? std::min(p.ncols, kGmCtas) : p.ncols, kFftThreads, smem, st>>>(
+      (const V*)p.d_F, p.Lpad, (const T*)p.d_w, p.nring, p.d_mrange, p.lmax + 1, p.spin, p.L, (const T*)p.d_sT,
+      (const T*)p.d_sP, p.M, p.f2L, (const V*)p.d_tw2L, p.d_perm2L, p.f4L, (const V*)p.d_tw4L, p.d_perm4L, p.r_lo,
+      p.nrows, (V*)p.d_X, p.ncols, (V*)p.d_fscratch);
+  PSHT_CUDA_TRY(cudaGetLastError());
+}
+template <typename T>
+void theta_adj_t(Plan& p, cudaStream_t st) {
+  using V = typename Cx<T>::V;
+  const bool gm = theta_gm(p);
+  const size_t smem = gm ? 0 : (size_t)4 * p.L * sizeof(V);
+  const auto fn = gm ? k_theta_adj<T, true> : k_theta_adj<T, false>;
+  if (!gm) set_smem<T>((const void*)fn, smem);
+  fn<<<gm ? std::min(p.ncols, kGmCtas) : p.ncols, kFftThreads, smem, st>>>(
+      (const V*)p.d_X, p.ncols, p.r_lo, p.nrows, (const T*)p.d_w, p.nring, p.spin, p.L, (const T*)p.d_sT,
+      (const T*)p.d_sP, p.M, p.f2L, (const V*)p.d_tw2L, p.d_perm2L, p.f4L, (const V*)p.d_tw4L, p.d_perm4L,
+      (V*)p.d_F, p.Lpad, (V*)p.d_fscratch);
+  PSHT_CUDA_TRY(cudaGetLastError());
+}
+template <typename T>
+void phi_syn_t(Plan& p, cudaStream_t st) {
+  using V = typename Cx<T>::V;
+  const bool gm = phi_gm(p);
+  const size_t smem = gm ? 0 : (size_t)p.nphi * sizeof(V);
+  const auto fn = gm ? k_phi_syn<T, true> : k_phi_syn<T, false>;
+  if (!gm) set_smem<T>((const void*)fn, smem);
+  fn<<<gm ? std::min(p.nrows, kGmCtas) : p.nrows, kFftThreads, smem, st>>>(
+      (const V*)p.d_X, p.ncols, p.fP, (const V*)p.d_twP, p.d_permP, p.padq, p.gstride, (V*)p.d_G, p.nrows,
+      (V*)p.d_fscratch);
+  PSHT_CUDA_TRY(cudaGetLastError());
+}
+template <typename T>
+void phi_adj_t(Plan& p, cudaStream_t st) {
+  using V = typename Cx<T>::V;
+  const bool gm = phi_gm(p);
+  const size_t smem = gm ? 0 : (size_t)p.nphi * sizeof(V);
+  const auto fn = gm ? k_phi_adj<T, true> : k_phi_adj<T, false>;
+  if (!gm) set_smem<T>((const void*)fn, smem);
+  fn<<<gm ? std::min(p.nrows, kGmCtas) : p.nrows, kFftThreads, smem, st>>>(
+      (const V*)p.d_G, p.gstride, p.padq, p.fP, (const V*)p.d_twP, p.d_permP, (V*)p.d_X, p.ncols, p.nrows,
+      (V*)p.d_fscratch);
+  PSHT_CUDA_TRY(cudaGetLastError());
+}
+
 void launch_theta_synthesis(Plan& p, cudaStream_t st) {
-  const size_t smem = (size_t)4 * p.L * (p.prec == 64 ? 16 : 8);
-  if (p.prec == 64) {
-    using V = double2;
-    set_smem<double>((const void*)k_theta_syn<double>, smem);
-    k_theta_syn<double><<<p.ncols, kFftThreads, smem, st>>>(
-        (const V*)p.d_F, p.Lpad, (const double*)p.d_w, p.nring, p.d_mrange, p.lmax + 1, p.spin, p.L, (const double*)p.d_sT,
-        (const double*)p.d_sP, p.M, p.f2L, (const V*)p.d_tw2L, p.d_perm2L, p.f4L, (const V*)p.d_tw4L, p.d_perm4L,
-        p.r_lo, p.nrows, (V*)p.d_X, p.ncols);
-  } else {
-    using V = float2;
-    set_smem<float>((const void*)k_theta_syn<float>, smem);
-    k_theta_syn<float><<<p.ncols, kFftThreads, smem, st>>>(
-        (const V*)p.d_F, p.Lpad, (const float*)p.d_w, p.nring, p.d_mrange, p.lmax + 1, p.spin, p.L, (const float*)p.d_sT,
-        (const float*)p.d_sP, p.M, p.f2L, (const V*)p.d_tw2L, p.d_perm2L, p.f4L, (const V*)p.d_tw4L, p.d_perm4L,
-        p.r_lo, p.nrows, (V*)p.d_X, p.ncols);
-  }
-  PSHT_CUDA_TRY(cudaGetLastError());
+  if (p.nrows == 0) return;
+  if (p.prec == 64) theta_syn_t<double>(p, st);
+  else theta_syn_t<float>(p, st);
 }
-
 void launch_phi_synthesis(Plan& p, cudaStream_t st) {
-  const size_t smem = (size_t)p.nphi * (p.prec == 64 ? 16 : 8);
-  if (p.prec == 64) {
-    set_smem<double>((const void*)k_phi_syn<double>, smem);
-    k_phi_syn<double><<<p.nrows, kFftThreads, smem, st>>>((const double2*)p.d_X, p.ncols, p.fP,
-                                                         (const double2*)p.d_twP, p.d_permP, p.padq, p.gstride,
-                                                         (double2*)p.d_G);
-  } else {
-    set_smem<float>((const void*)k_phi_syn<float>, smem);
-    k_phi_syn<float><<<p.nrows, kFftThreads, smem, st>>>((const float2*)p.d_X, p.ncols, p.fP,
-                                                        (const float2*)p.d_twP, p.d_permP, p.padq, p.gstride,
-                                                        (float2*)p.d_G);
-  }
-  PSHT_CUDA_TRY(cudaGetLastError());
+  if (p.nrows == 0) return;
+  if (p.prec == 64) phi_syn_t<double>(p, st);
+  else phi_syn_t<float>(p, st);
 }
-
 void launch_phi_adjoint(Plan& p, cudaStream_t st) {
-  const size_t smem = (size_t)p.nphi * (p.prec == 64 ? 16 : 8);
-  if (p.prec == 64) {
-    set_smem<double>((const void*)k_phi_adj<double>, smem);
-    k_phi_adj<double><<<p.nrows, kFftThreads, smem, st>>>((const double2*)p.d_G, p.gstride, p.padq, p.fP,
-                                                         (const double2*)p.d_twP, p.d_permP, (double2*)p.d_X,
-                                                         p.ncols);
-  } else {
-    set_smem<float>((const void*)k_phi_adj<float>, smem);
-    k_phi_adj<float><<<p.nrows, kFftThreads, smem, st>>>((const float2*)p.d_G, p.gstride, p.padq, p.fP,
-                                                        (const float2*)p.d_twP, p.d_permP, (float2*)p.d_X, p.ncols);
-  }
-  PSHT_CUDA_TRY(cudaGetLastError());
+  if (p.nrows == 0) return;
+  if (p.prec == 64) phi_adj_t<double>(p, st);
+  else phi_adj_t<float>(p, st);
 }
-
 void launch_theta_adjoint(Plan& p, cudaStream_t st) {
-  const size_t smem = (size_t)4 * p.L * (p.prec == 64 ? 16 : 8);
-  if (p.prec == 64) {
-    using V = double2;
-    set_smem<double>((const void*)k_theta_adj<double>, smem);
-    k_theta_adj<double><<<p.ncols, kFftThreads, smem, st>>>(
-        (const V*)p.d_X, p.ncols, p.r_lo, p.nrows, (const double*)p.d_w, p.nring, p.spin, p.L,
-        (const double*)p.d_sT, (const double*)p.d_sP, p.M, p.f2L, (const V*)p.d_tw2L, p.d_perm2L, p.f4L,
-        (const V*)p.d_tw4L, p.d_perm4L, (V*)p.d_F, p.Lpad);
-  } else {
-    using V = float2;
-    set_smem<float>((const void*)k_theta_adj<float>, smem);
-    k_theta_adj<float><<<p.ncols, kFftThreads, smem, st>>>(
-        (const V*)p.d_X, p.ncols, p.r_lo, p.nrows, (const float*)p.d_w, p.nring, p.spin, p.L, (const float*)p.d_sT,
-        (const float*)p.d_sP, p.M, p.f2L, (const V*)p.d_tw2L, p.d_perm2L, p.f4L, (const V*)p.d_tw4L, p.d_perm4L,
-        (V*)p.d_F, p.Lpad);
-  }
-  PSHT_CUDA_TRY(cudaGetLastError());
+  if (p.nrows == 0) return;
+  if (p.prec == 64) theta_adj_t<double>(p, st);
+  else theta_adj_t<float>(p, st);
 }
 
 void launch_ring_coeffs_export(Plan& p, void* out, cudaStream_t st) {

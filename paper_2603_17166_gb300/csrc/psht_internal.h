@@ -120,6 +120,7 @@ struct Plan {
   int* d_perm2L = nullptr;      // digit-reversed positions of each FFT length
   int* d_perm4L = nullptr;
   int* d_permP = nullptr;
+  void* d_fscratch = nullptr;   // global FFT buffers for lengths beyond shared memory (else null)
   // points (sorted by tile)
   TileItem* d_titems = nullptr;
   int ntitems = 0;
@@ -156,7 +157,8 @@ void launch_scatter(Plan& p, const void* f, cudaStream_t st);
 void launch_ring_coeffs_export(Plan& p, void* F, cudaStream_t st);
 void reduce_points(const double* theta, const double* phi, int64_t npts, double out[3], cudaStream_t st);
 void bin_points(Plan& p, const double* theta, const double* phi, cudaStream_t st);
-int max_fft_len(int prec);
+int max_fft_len(int prec);                // longest FFT held in one CTA's shared memory
+size_t fft_scratch_elems(const Plan& p);  // complex elements of the global FFT buffers (0: none)
 void ring_synthesis_noalloc(int spin, int lmax, const double* theta, int nring, const void* g, const void* c, void* F,
                             cudaStream_t st);
 size_t noalloc_scratch_bytes();
