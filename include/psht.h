@@ -50,6 +50,8 @@ extern "C" {
 #define PSHT_AUTO 0u        /* FP32 form for eps >= 1e-5, FP64 form below                       */
 #define PSHT_FP64 1u        /* FP64 everywhere                                                   */
 #define PSHT_FP32 2u        /* FP32 recursion (FP64 seeds and rescaling), FP32 FFT and kernels   */
+#define PSHT_FULL_SKY 4u    /* full-sky route whatever the points' extent (Sec. I: theta_max = pi, */
+                            /* w = 1, Lmax = lmax); the baseline of the paper's speed-ups (Table 1) */
 
 typedef struct psht_plan psht_plan; /* opaque; owned by the library, freed by psht_plan_destroy */
 

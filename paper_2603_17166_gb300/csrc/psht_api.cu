@@ -170,10 +170,12 @@ std::vector<T> cast_vec(const std::vector<double>& v) {
 
 // ---------------------------------------------------------------------------------------------
 // P1-P2 and the grid: everything that depends on (spin, lmax, eps, precision, theta*, pole)
+int64_t adj_part_elems(const Plan& p);
+
 void layout(Plan& p, double theta_star) {
   const double lneps = fabs(log(p.eps));
   p.theta_star = std::max(theta_star, 1e-9);
-  bool full = p.lmax < 1;
+  bool full = p.lmax < 1 || p.force_full;
   if (!full) {
     p.eps_apo = sqrt(2.0 * lneps / (p.theta_star * p.lmax));
     p.theta_max = p.theta_star * (1.0 + p.eps_apo);
@@ -224,23 +226,64 @@ void layout(Plan& p, double theta_star) {
   p.nalm = (int64_t)(p.lmax + 1) * (p.lmax + 2) / 2;
   p.tstride = p.nalm + 64;  // one chunk of zero records after the last order
   // launch shapes of the recursion
-  p.syn_rpt = (p.prec == 64) ? 1 : 4;
+  p.syn_rpt = (p.prec == 64) ? 1 : 2;
   p.syn_threads = 32;  // one warp per synthesis item (k_rec_syn_w)
   // adjoint: all active rings of one order m in one CTA, (rings per thread, threads) from the
   // instantiated shapes, more rings per thread in FP32 to amortise the per-l warp reduction
+  // FP32: one warp per item of 32 adj_rpt rings with per-item partial sums reduced per m
+  // (k_rec_adj_w, k_adj_reduce) while that buffer stays within 4 GB, else the block form below.
+  // Block form (FP64, large FP32 plans): one CTA per m and chunk of adj_rpt * adj_threads rings.
+  constexpr double kMaxPartBytes = 4e9;
+  p.adj_rpt = 8;
+  p.adj_threads = 128;
   if (p.prec == 32) {
-    p.adj_rpt = p.nring <= 1024 ? 4 : 8;
-    p.adj_threads = p.nring <= 2048 ? 256 : 512;
-  } else {
-    p.adj_rpt = p.nring <= 1024 ? 4 : 8;
-    p.adj_threads = p.nring <= 512 ? 128 : (p.nring <= 2048 ? 256 : 512);
+    p.adj_threads = 32;
+    p.adj_rpt = 4;
+    if (adj_part_elems(p) * 4.0 > kMaxPartBytes) p.adj_rpt = 8;
+    if (adj_part_elems(p) * 4.0 > kMaxPartBytes) {
+      p.adj_rpt = 4;
+      p.adj_threads = 256;
+    }
   }
-  PSHT_REQUIRE(p.nring <= 8 * 512, PSHT_ENOTSUP, "more than 4096 rings (lmax theta* too large for this build)");
   // FFTs longer than one CTA's shared memory run on global buffers (psht_fft.cu)
   constexpr int kMaxLen = 1 << 22;
   PSHT_REQUIRE(p.nTheta <= kMaxLen && p.nphi <= kMaxLen, PSHT_ENOTSUP,
                "FFT length above " + std::to_string(kMaxLen) + " (Theta " + std::to_string(p.nTheta) + ", phi " +
                    std::to_string(p.nphi) + ")");
+}
+
+// Walk the (m, ring part) active ranges in the order of the work items: fn(m, part, lo, hi) for
+// every non-empty range.  Ring j is active for m when M_j >= m; a ring at theta_j > pi/2 from the
+// plan's pole is in part 1 (evaluated by reflection).
+template <class Fn>
+void for_active_ranges(const Plan& p, Fn&& fn) {
+  std::vector<int> refl(p.nring);
+  for (int j = 0; j < p.nring; ++j) {
+    const double bj = p.beta_j[j];
+    refl[j] = p.pole > 0 ? (bj > 0.5 * M_PI) : (bj < 0.5 * M_PI);
+  }
+  for (int m = 0; m <= p.M; ++m) {
+    for (int part = 0; part < 2; ++part) {
+      int lo = -1, hi = -1;
+      for (int j = 0; j < p.nring; ++j)
+        if (p.Mj[j] >= m && refl[j] == part) {
+          if (lo < 0) lo = j;
+          hi = j + 1;
+        }
+      if (lo >= 0) fn(m, part, lo, hi);
+    }
+  }
+}
+
+// elements of the per-item partial sums of the one-warp adjoint (0 when it is not used)
+int64_t adj_part_elems(const Plan& p) {
+  if (p.adj_threads != 32) return 0;
+  const int cap = 32 * p.adj_rpt;
+  int64_t e = 0;
+  for_active_ranges(p, [&](int m, int, int lo, int hi) {
+    e += (int64_t)((hi - lo + cap - 1) / cap) * 4 * (p.lmax - std::max(m, p.spin) + 1);
+  });
+  return e;
 }
 
 size_t planned_bytes(const Plan& p) {
@@ -254,6 +297,7 @@ size_t planned_bytes(const Plan& p) {
   b += p.prec == 64 ? (size_t)p.npts * 2 * p.W * 8 : (size_t)p.npts * 8;  // weights / fractions
   b += (size_t)(p.nTheta + 2 * p.L + p.nphi) * (cb + 4);       // twiddles + permutations
   b += fft_scratch_elems(p) * cb;                              // long-FFT buffers
+  b += (size_t)adj_part_elems(p) * rb;                         // one-warp adjoint partial sums
   return b;
 }
 
@@ -279,6 +323,7 @@ Plan* create(int spin, int lmax, const double* theta, const double* phi, int64_t
   PSHT_REQUIRE(npts == 0 || (theta && phi), PSHT_EINVAL, "theta and phi must be device pointers");
   const uint32_t pf = flags & 3u;
   PSHT_REQUIRE(pf != 3u, PSHT_EINVAL, "PSHT_FP32 and PSHT_FP64 are exclusive");
+  PSHT_REQUIRE((flags & ~7u) == 0u, PSHT_EINVAL, "unknown flag bits");
   int prec = (pf == PSHT_FP64) ? 64 : (pf == PSHT_FP32) ? 32 : (eps >= 1e-5 ? 32 : 64);
   PSHT_REQUIRE(!(prec == 32 && eps < 1e-7), PSHT_EINVAL, "the FP32 form needs eps >= 1e-7");
 
@@ -289,6 +334,7 @@ Plan* create(int spin, int lmax, const double* theta, const double* phi, int64_t
     p->eps = eps;
     p->prec = prec;
     p->npts = npts;
+    p->force_full = (flags & PSHT_FULL_SKY) ? 1 : 0;
     // step 1: nearer pole and theta* (one device reduction, validates the points)
     double red[3];
     reduce_points(theta, phi, npts, red, st);
@@ -367,6 +413,28 @@ Plan* create(int spin, int lmax, const double* theta, const double* phi, int64_t
     p->d_mrange = (int2*)upload(*p, mr, st);
     p->nitems = (int)items.size();
     p->d_items = (RecItem*)upload(*p, items, st);
+    if (p->adj_threads == 32) {  // one-warp adjoint: items of at most 32 adj_rpt rings, per-m spans
+      const int acap = 32 * p->adj_rpt;
+      std::vector<AdjItem> ai;
+      std::vector<int2> span(lmax + 1, make_int2(0, 0));
+      int64_t off = 0;
+      for_active_ranges(*p, [&](int m, int part, int lo, int hi) {
+        const int n = hi - lo, nch = (n + acap - 1) / acap;
+        if (span[m].y == 0) span[m].x = (int)ai.size();
+        for (int c = 0; c < nch; ++c) {
+          const int a = lo + (int)((int64_t)n * c / nch), b = lo + (int)((int64_t)n * (c + 1) / nch);
+          ai.push_back(AdjItem{m, a, b - a, part, off});
+          off += 4 * (int64_t)(lmax - std::max(m, spin) + 1);
+        }
+        span[m].y += nch;
+      });
+      PSHT_REQUIRE(off == adj_part_elems(*p), PSHT_ECUDA, "internal: adjoint item layout mismatch");
+      p->naitems = (int)ai.size();
+      p->part_elems = off;
+      p->d_aitems = ai.empty() ? nullptr : (AdjItem*)upload(*p, ai, st);
+      p->d_aspan = (int2*)upload(*p, span, st);
+      p->d_part = dalloc(*p, (size_t)std::max<int64_t>(off, 1) * (prec == 64 ? 8 : 4));
+    }
     // deconvolution tables, ring weights, FFT twiddles and digit-reversal tables
     static const Quad quad;
     std::vector<double> sT(2 * p->L - 1), sP(2 * p->M + 1);
@@ -728,6 +796,7 @@ size_t psht_estimate_bytes(int spin, int lmax, double theta_star, int64_t npts, 
     const uint32_t pf = flags & 3u;
     p.prec = (pf == PSHT_FP64) ? 64 : (pf == PSHT_FP32) ? 32 : (eps >= 1e-5 ? 32 : 64);
     p.npts = npts;
+    p.force_full = (flags & PSHT_FULL_SKY) ? 1 : 0;
     p.pole = 1;
     layout(p, theta_star);
     return planned_bytes(p);
@@ -754,6 +823,7 @@ int psht_plan_estimate_points(int spin, int lmax, const double* theta, const dou
     const uint32_t pf = flags & 3u;
     p.prec = (pf == PSHT_FP64) ? 64 : (pf == PSHT_FP32) ? 32 : (eps >= 1e-5 ? 32 : 64);
     p.npts = npts;
+    p.force_full = (flags & PSHT_FULL_SKY) ? 1 : 0;
     p.pole = (red[0] <= red[1]) ? 1 : -1;
     layout(p, p.pole > 0 ? red[0] : red[1]);
     *bytes = planned_bytes(p);

@@ -65,6 +65,12 @@ struct RecItem {    // one CTA of the synthesis recursion: order m, rings [j0, j
   int refl;         // 1: the rings lie at theta > pi/2 and are evaluated at pi - theta (reflection)
 };
 
+struct AdjItem {    // one warp of the FP32 adjoint recursion: order m, rings [j0, j0 + nj)
+  int m, j0, nj;
+  int refl;
+  int64_t off;      // first element of its partial sums: 4 values per l = l0 .. lmax
+};
+
 struct TileItem {   // one CTA of the gather/scatter: a tile and a slice of its sorted points
   int tr, tq;       // tile row/column index
   int p0, np;       // first sorted point, count
@@ -81,6 +87,7 @@ struct Plan {
   int spin = 0, lmax = 0, prec = 64;
   double eps = 0;
   int pole = 1, full = 0;
+  int force_full = 0;  // PSHT_FULL_SKY
   double theta_star = 0, eps_apo = 0, theta_max = 0, dTheta = 0, alpha = 0;
   int Lmax = 0, L = 0, nring = 0, M = 0, W = 0;
   double beta_es = 0;
@@ -107,6 +114,11 @@ struct Plan {
   int* d_status = nullptr;      // device error word (bounded waits that gave up), read by psht_plan_status
   RecItem* d_items = nullptr;
   int nitems = 0;
+  AdjItem* d_aitems = nullptr;  // adjoint as one warp per item (adj_threads == 32)
+  int naitems = 0;
+  int2* d_aspan = nullptr;      // per m: first adjoint item, item count
+  void* d_part = nullptr;       // per-item partial sums, T [sum over items of 4 (lmax - l0 + 1)]
+  int64_t part_elems = 0;
   void* d_F = nullptr;          // complex T [ncols][Lpad]
   void* d_X = nullptr;          // complex T [nrows][ncols]
   void* d_G = nullptr;          // complex T [nrows][gstride]

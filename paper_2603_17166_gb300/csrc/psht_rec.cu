@@ -865,7 +865,7 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
                                                 const typename Cx<T>::V* __restrict__ Ft, int Lpad,
                                                 int lmax, int s, int M, int refl, int accumulate, T msc,
                                                 typename Cx<T>::V* __restrict__ gt, typename Cx<T>::V* __restrict__ ct,
-                                                int* __restrict__ status) {
+                                                int* __restrict__ status, int chunk) {
   using V = typename Cx<T>::V;
   const int m = blockIdx.x;
   const int64_t base = alm_base(lmax, m);
@@ -878,7 +878,14 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
     return;
   }
   const MSeed sd = mseed[m];
-  const int2 rr = mrange[m];
+  // rings of this launch: chunk `chunk` of RPT * NT rings of the part's active range
+  int2 rr = mrange[m];
+  rr.x += chunk * RPT * NT;
+  rr.y = min(rr.y, rr.x + RPT * NT);
+  if (rr.y <= rr.x) {
+    if (accumulate) return;  // nothing to add
+    rr.y = rr.x;             // first launch: write the zero projection below
+  }
   const int nact = rr.y - rr.x;
   constexpr int NW = NT / 32;
   using V4 = typename Cx4<T>::V;  // 4 partial sums of one l
@@ -1017,6 +1024,150 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// adjoint, one warp per CTA (FP32 form): the warp's item is (m, up to 32 RPT rings), with the
+// table staged as in k_rec_syn_w.  Per quad of l the warp's 16 partial sums are reduced across
+// the lanes (reduce_scatter16) and written to the item's slice of the partial-sum array, already
+// in the direct-ring convention (reflected rings: columns swapped, signed by (-1)^(l+m)); the
+// items of one m are then summed and projected by k_adj_reduce.  No block barrier, no atomics,
+// and the result does not depend on scheduling.
+template <typename T, bool SPIN, int RPT, int CH, int NST>
+__global__ void __launch_bounds__(32) k_rec_adj_w(const AdjItem* __restrict__ items, const RingDev* __restrict__ rings,
+                                                  const MSeed* __restrict__ mseed, const TabEntry<T>* __restrict__ tab,
+                                                  const typename Cx<T>::V* __restrict__ Ft, int Lpad, int lmax,
+                                                  T* __restrict__ part, int* __restrict__ status) {
+  static_assert(CH % 4 == 0, "whole quads per chunk");
+  using V = typename Cx<T>::V;
+  const AdjItem it = items[blockIdx.x];
+  const int m = it.m;
+  const MSeed sd = mseed[m];
+  __shared__ __align__(16) TabStage<T, CH> stg[NST];
+  __shared__ __align__(8) uint64_t bar[NST];
+  const int lane = threadIdx.x;
+  const int nr_w = (it.nj + 31) >> 5;
+  const bool m0 = (m == 0);
+  const bool rf = it.refl != 0;
+  const V z = mk((T)0, (T)0);
+  Cols<T, RPT> S;
+  AdjIn<T, RPT> fin;
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const int jj = r * 32 + lane;
+    init_col<T, SPIN, RPT>(S, rings, sd, it.j0, jj, it.nj, r);
+    fin.set(r, z, z);
+    if (jj < it.nj) {
+      const int j = it.j0 + jj;
+      const V fp = Ft[(int64_t)col_of(m) * Lpad + j];
+      const V fm = m0 ? z : Ft[(int64_t)col_of(-m) * Lpad + j];
+      fin.set(r, rf ? fm : fp, rf ? fp : fm);
+    }
+  }
+  const int64_t base = alm_base(lmax, m);
+  const int nl = lmax - sd.l0 + 1;
+  const int nchunk = (nl + CH - 1) / CH;
+  T* out = part + it.off;
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NST; ++k) mbar_init(&bar[k], 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  if (lane == 0)
+    for (int k = 0; k < NST && k < nchunk; ++k) issue_chunk<T, CH>(stg[k], &bar[k], tab, base + sd.l0 + k * CH);
+  __syncwarp();
+
+  for (int ch = 0; ch < nchunk; ++ch) {
+    const int sidx = ch % NST;
+    const bool ok = mbar_wait(&bar[sidx], (uint32_t)((ch / NST) & 1));
+    if (__any_sync(0xffffffffu, !ok)) {
+      if (lane == 0) {
+        atomicExch(status, 1);
+        for (int k = ch + 1; k < nchunk && k < ch + NST; ++k)  // drain the copies still in flight
+          mbar_wait(&bar[k % NST], (uint32_t)((k / NST) & 1));
+      }
+      return;
+    }
+    const int li0 = ch * CH;  // index of l = l0 + li0 in the item's slice
+    const int nq = (min(CH, nl - li0) + 3) >> 2;
+    const TabEntry<T>* st = stg[sidx].v;
+    for (int q = 0; q < nq; ++q) {
+      T tot = (T)0;
+      bool fast, skip;
+      classify<T, SPIN, RPT>(S, nr_w, fast, skip);
+      if (skip) {
+        adj_quad_steps<SPIN, RPT>(S, st, 4 * q, nr_w);
+        rescale_all<T, SPIN, RPT>(S, nr_w);
+      } else {
+        T v[16];
+        if (fast) {
+          if (nr_w >= RPT) adj_quad_sums<SPIN, RPT, false>(S, fin, st, 4 * q, RPT, v);
+          else adj_quad_sums<SPIN, RPT, false>(S, fin, st, 4 * q, nr_w, v);
+        } else {
+          adj_quad_sums<SPIN, RPT, true>(S, fin, st, 4 * q, nr_w, v);
+          rescale_all<T, SPIN, RPT>(S, nr_w);
+        }
+        tot = reduce_scatter16<T>(v, lane);  // lane < 16: sum (lane & 3) of l = 4q + (lane >> 2)
+      }
+      const int li = li0 + 4 * q + ((lane >> 2) & 3);
+      if (rf) {  // sums against d_{m,-s}(theta) and d_{m,s}(theta): swap the column pairs, sign (-1)^(l+m)
+        const T other = __shfl_xor_sync(0xffffffffu, tot, 2);
+        tot = (((sd.l0 + li + m) & 1) ? (T)-1 : (T)1) * other;
+      }
+      if (lane < 16 && li < nl) out[4 * (int64_t)li + (lane & 3)] = tot;
+    }
+    __syncwarp();  // every lane is done with stage sidx
+    if (ch + NST < nchunk && lane == 0) issue_chunk<T, CH>(stg[sidx], &bar[sidx], tab, base + sd.l0 + (ch + NST) * CH);
+    __syncwarp();
+  }
+}
+
+// Sum of the adjoint items of order m (blockIdx.x) and the projection of the adjoint synthesis
+// general formula: ut_{l,m} = -Qp, ut_{l,-m} = -(-1)^(m-s) Qm, g~ = (ut_lm + (-1)^m conj ut_{l,-m})/2,
+// c~ = (ut_lm - (-1)^m conj ut_{l,-m})/(2i); zero below l0 and for orders without active rings.
+template <typename T>
+__global__ void k_adj_reduce(const AdjItem* __restrict__ items, const int2* __restrict__ aspan,
+                             const MSeed* __restrict__ mseed, const T* __restrict__ part, int lmax, int s, T msc,
+                             typename Cx<T>::V* __restrict__ gt, typename Cx<T>::V* __restrict__ ct) {
+  using V = typename Cx<T>::V;
+  constexpr int kMaxItems = 64;
+  __shared__ int64_t off[kMaxItems];
+  const int m = blockIdx.x;
+  const int2 sp = aspan[m];
+  const int64_t base = alm_base(lmax, m);
+  const int l0 = sp.y > 0 ? mseed[m].l0 : lmax + 1;
+  for (int k = threadIdx.x; k < sp.y && k < kMaxItems; k += blockDim.x) off[k] = items[sp.x + k].off;
+  __syncthreads();
+  const bool m0 = (m == 0);
+  const T sg = (((m - s) & 1) ? (T)1 : (T)-1);  // -(-1)^(m-s)
+  const T sm = (m & 1) ? (T)-1 : (T)1;          // (-1)^m
+  for (int l = m + threadIdx.x; l <= lmax; l += blockDim.x) {
+    V gv = mk((T)0, (T)0), cv = gv;
+    if (l >= l0) {
+      T q0 = 0, q1 = 0, q2 = 0, q3 = 0;
+      const int64_t li = 4 * (int64_t)(l - l0);
+      for (int k = 0; k < sp.y; ++k) {
+        const int64_t o = (k < kMaxItems ? off[k] : items[sp.x + k].off) + li;
+        q0 += part[o];
+        q1 += part[o + 1];
+        q2 += part[o + 2];
+        q3 += part[o + 3];
+      }
+      const T ar = -q0, ai = -q1;
+      const T br = sg * q2, bi = sg * q3;
+      if (m0) {
+        gv = mk(ar, (T)0);
+        cv = mk(ai, (T)0);
+      } else {
+        const T wr = sm * br, wi = -sm * bi;  // (-1)^m conj(ut_{l,-m})
+        gv = mk(msc * (T)0.5 * (ar + wr), msc * (T)0.5 * (ai + wi));
+        cv = mk(msc * (T)0.5 * (ai - wi), msc * (T)-0.5 * (ar - wr));
+      }
+    }
+    gt[base + l] = gv;
+    if (ct) ct[base + l] = cv;
+  }
+}
+
 template <typename T, bool SPIN, int RPT>
 void launch_syn_t(Plan& p, const void* g, const void* c, double msc, cudaStream_t st) {
   using V = typename Cx<T>::V;
@@ -1031,18 +1182,32 @@ void launch_syn_t(Plan& p, const void* g, const void* c, double msc, cudaStream_
                                                           (V*)p.d_F, p.Lpad, p.d_status);
 }
 
+template <typename T, bool SPIN, int RPT>
+void launch_adj_w(Plan& p, void* g, void* c, double msc, cudaStream_t st) {
+  using V = typename Cx<T>::V;
+  if (p.naitems > 0)
+    k_rec_adj_w<T, SPIN, RPT, 32, 4><<<p.naitems, 32, 0, st>>>(p.d_aitems, p.d_ring, p.d_mseed,
+                                                                (const TabEntry<T>*)p.d_rtab, (const V*)p.d_F, p.Lpad,
+                                                                p.lmax, (T*)p.d_part, p.d_status);
+  k_adj_reduce<T><<<p.lmax + 1, 256, 0, st>>>(p.d_aitems, p.d_aspan, p.d_mseed, (const T*)p.d_part, p.lmax, p.spin,
+                                               (T)msc, (V*)g, (V*)c);
+}
+
 template <typename T, bool SPIN, int RPT, int NT>
 void launch_adj_t(Plan& p, void* g, void* c, double msc, cudaStream_t st) {
   using V = typename Cx<T>::V;
-  // one launch per ring part (rings at theta <= pi/2, then reflected rings at theta > pi/2)
+  // one launch per ring part (rings at theta <= pi/2, then reflected rings at theta > pi/2) and
+  // per chunk of RPT * NT rings of it; every launch after the first adds to the output
+  const size_t red_bytes = (size_t)2 * (NT / 32) * kCH * sizeof(typename Cx4<T>::V);
+  PSHT_CUDA_TRY(cudaFuncSetAttribute((const void*)k_rec_adj<T, SPIN, RPT, NT>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red_bytes));
+  const int nch = (p.nring + RPT * NT - 1) / (RPT * NT);
   for (int part = 0; part < 2; ++part) {
     if (part == 1 && !p.has_refl) break;
-    const size_t red_bytes = (size_t)2 * (NT / 32) * kCH * sizeof(typename Cx4<T>::V);
-    PSHT_CUDA_TRY(cudaFuncSetAttribute((const void*)k_rec_adj<T, SPIN, RPT, NT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red_bytes));
-    k_rec_adj<T, SPIN, RPT, NT><<<p.lmax + 1, NT, red_bytes, st>>>(
-        p.d_ring, p.d_mseed, p.d_mrange + part * (p.lmax + 1), (const TabEntry<T>*)p.d_rtab, (const V*)p.d_F,
-        p.Lpad, p.lmax, p.spin, p.M, part, part, (T)msc, (V*)g, (V*)c, p.d_status);
+    for (int chk = 0; chk < nch; ++chk)
+      k_rec_adj<T, SPIN, RPT, NT><<<p.lmax + 1, NT, red_bytes, st>>>(
+          p.d_ring, p.d_mseed, p.d_mrange + part * (p.lmax + 1), (const TabEntry<T>*)p.d_rtab, (const V*)p.d_F,
+          p.Lpad, p.lmax, p.spin, p.M, part, (part > 0 || chk > 0) ? 1 : 0, (T)msc, (V*)g, (V*)c, p.d_status, chk);
   }
 }
 
@@ -1056,7 +1221,15 @@ void launch_syn_s(Plan& p, const void* g, const void* c, double msc, cudaStream_
 }
 template <typename T, bool SPIN>
 void launch_adj_s(Plan& p, void* g, void* c, double msc, cudaStream_t st) {
-  // (rings per thread, threads) covering up to 4096 rings; chosen by the planner
+  if (p.adj_threads == 32) {  // one warp per item, FP32 form
+    if constexpr (sizeof(T) == 4) {
+      if (p.adj_rpt == 8) launch_adj_w<T, SPIN, 8>(p, g, c, msc, st);
+      else if (p.adj_rpt == 2) launch_adj_w<T, SPIN, 2>(p, g, c, msc, st);
+      else launch_adj_w<T, SPIN, 4>(p, g, c, msc, st);
+      return;
+    }
+  }
+  // (rings per thread, threads) of one launch chunk; chosen by the planner
   switch (p.adj_rpt * 10000 + p.adj_threads) {
     case 40128: launch_adj_t<T, SPIN, 4, 128>(p, g, c, msc, st); break;
     case 40256: launch_adj_t<T, SPIN, 4, 256>(p, g, c, msc, st); break;

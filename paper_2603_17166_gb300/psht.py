@@ -12,7 +12,7 @@ import numpy as np
 
 from . import build as _build
 
-PSHT_AUTO, PSHT_FP64, PSHT_FP32 = 0, 1, 2
+PSHT_AUTO, PSHT_FP64, PSHT_FP32, PSHT_FULL_SKY = 0, 1, 2, 4
 _PREC = {"auto": PSHT_AUTO, "fp64": PSHT_FP64, "fp32": PSHT_FP32, 64: PSHT_FP64, 32: PSHT_FP32}
 
 
@@ -132,15 +132,17 @@ def nalm(lmax: int) -> int:
 class Plan:
     """A plan for synthesis general and its adjoint at fixed points (psht_plan_create)."""
 
-    def __init__(self, spin: int, lmax: int, theta, phi, eps: float, precision="auto", stream=None):
+    def __init__(self, spin: int, lmax: int, theta, phi, eps: float, precision="auto", stream=None,
+                 full_sky: bool = False):
         torch = _torch()
         theta = torch.as_tensor(theta, dtype=torch.float64, device="cuda").contiguous()
         phi = torch.as_tensor(phi, dtype=torch.float64, device="cuda").contiguous()
         if theta.shape != phi.shape or theta.dim() != 1:
             raise ValueError("theta and phi must be 1-D tensors of equal length")
         self._h = ctypes.c_void_p()
+        flags = _PREC[precision] | (PSHT_FULL_SKY if full_sky else 0)
         _check(lib().psht_plan_create(int(spin), int(lmax), _ptr(theta), _ptr(phi), theta.numel(), float(eps),
-                                      _PREC[precision], _stream(stream), ctypes.byref(self._h)))
+                                      flags, _stream(stream), ctypes.byref(self._h)))
         self.spin, self.lmax, self.eps, self.npts = int(spin), int(lmax), float(eps), theta.numel()
         i = self.info
         self.precision = i["precision"]

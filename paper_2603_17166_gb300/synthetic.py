@@ -212,6 +212,15 @@ def config3(s: int = 2, frame: str = "R", n: int = 50_000_000, realisation: int 
     return dict(lmax=lmax, s=s, g=g, c=c, theta=theta, phi=phi)
 
 
+def config5(frame: str = "R", n: int = 100_000_000, realisation: int = 0):
+    """Spin 2 (g = E, c = B), lmax 16384, C_l ~ (l+1)^-2, 1e8 uniform random points on the ~4% field."""
+    lmax = 16384
+    g = gaussian_alm(lmax, 2, rng(5, "alm", 2 * realisation), "inv_l2")
+    c = gaussian_alm(lmax, 2, rng(5, "alm", 2 * realisation + 1), "inv_l2")
+    theta, phi = field_points("random4", frame, rng(5, "points"), n=n)
+    return dict(lmax=lmax, s=2, g=g, c=c, theta=theta, phi=phi)
+
+
 def _rotate_from_north(v, centre):
     """Rotation taking the north pole to `centre`, applied to v (inverse of rotate_to_north)."""
     z = np.array([0.0, 0.0, 1.0])
