@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--serve-streams", type=int, default=4)
     ap.add_argument("--serve-loads", default="0.8", help="offered loads, fractions of single-stream capacity")
     ap.add_argument("--serve-nmax", type=int, default=30_000_000)
+    ap.add_argument("--table1", action="store_true",
+                    help="re-measure the partial-sky / full-sky speed-ups of the paper's Table 1 instead")
     ap.add_argument("--cpu-sample-points", type=int, default=1_000_000)
     ap.add_argument("--cpu-ring-stride", type=int, default=8)
     return ap.parse_args()
@@ -135,10 +137,10 @@ def alu_peak_tflops(prec: int) -> float:
     return fp32 if prec == 32 else fp32 / 64.0
 
 
-# DRAM bytes (read + write) of one k_rec_adj launch on this workload, from an ncu capture of the
-# current kernel (profiles/k_rec_fp32_spin2_lmax4096.md); None where no capture of the current
-# kernel exists.
-REC_ADJ_TRAFFIC = {"fp32": 375.727e6 + 102.386e6, "fp64": None}
+# DRAM bytes (read + write) of one adjoint-recursion launch on this workload (k_rec_adj_w in the
+# FP32 form), from an ncu capture of the current kernel (profiles/k_rec_fp32_spin2_lmax4096.md);
+# None where no capture of the current kernel exists.
+REC_ADJ_TRAFFIC = {"fp32": 380.160e6 + 570.136e6, "fp64": None}
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -182,6 +184,7 @@ def run_ours(args, rank, world, local_rank):
     if not forms or forms[0][0] != "fp32":
         raise SystemExit("--forms must include fp32 (the headline form)")
     headline = None
+    gpu_samples = {}
     for name, eps, K in forms:
         t0 = time.time()
         plan = Plan(SPIN, LMAX, theta, phi, eps, precision=name, stream=stream)
@@ -244,9 +247,10 @@ def run_ours(args, rank, world, local_rank):
                                device_gb=info["device_bytes"] / 1e9),
                      roofline=dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s",
                                    frac=(achieved / peak if achieved else None),
-                                   traffic=REC_ADJ_TRAFFIC.get(name), kernel="k_rec_adj",
+                                   traffic=REC_ADJ_TRAFFIC.get(name),
+                                   kernel="k_rec_adj_w" if name == "fp32" else "k_rec_adj",
                                    flops_per_launch=flops,
-                                   synthesis_kernel=dict(kernel="k_rec_syn", achieved=tflops("rec_synthesis"),
+                                   synthesis_kernel=dict(kernel="k_rec_syn_w", achieved=tflops("rec_synthesis"),
                                                          frac=(tflops("rec_synthesis") or 0) / peak),
                                    peak_note="derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"
                                              + (" / 64 (FP64 rate)" if name == "fp64" else "")))
@@ -277,6 +281,11 @@ def run_ours(args, rank, world, local_rank):
             entry["e2e"] = dict(value=world * npts * K / el / 1e6, unit=UNIT,
                                 h2d_bytes_per_step=int(hg.nbytes + hc.nbytes + npts * cb),
                                 d2h_bytes_per_step=int(npts * cb + hgt.nbytes + hct.nbytes))
+        # synthesis output at a fixed sample of points, checked against the oracle in the
+        # cpu_baseline leg (the only place this script runs the oracle)
+        sel = np.random.default_rng(7).choice(npts, size=64, replace=False)
+        sel[:2] = [int(np.argmin(wl["theta"])), int(np.argmax(wl["theta"]))]
+        gpu_samples[name] = (eps, sel, f[torch.from_numpy(sel).to(dev)].cpu().numpy().astype(np.complex128))
         results[name] = entry
         if name == "fp32":
             headline = entry
@@ -301,7 +310,7 @@ def run_ours(args, rank, world, local_rank):
     if args.serve_requests > 0 and world == 1:
         line["serving"] = run_serving(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args, wl, steps=1)
+        line["cpu_baseline"] = cpu_baseline(args, wl, steps=1, gpu_samples=gpu_samples)
     if dist is not None:
         dist.destroy_process_group()
     return line
@@ -375,16 +384,19 @@ def run_serving(args, dev) -> dict:
             tickets.append(submit(r["field"], r["op"]))
         res = [srv.wait(t) for t in tickets]
         wall = time.perf_counter() - start
+        pts = sum(fields[r["field"]]["npts"] for r, x in zip(reqs, res) if x["status"] == 0)
         bad = sum(1 for x in res if x["status"] != 0)
         lat = np.array([x["total_ms"] for x in res])
         slow = np.array([x["total_ms"] / alone[(r["field"], r["op"])] for x, r in zip(res, reqs)])
         runs.append(dict(load=load, lambda_rps=lam, p50_ms=float(np.percentile(lat, 50)),
                          p99_ms=float(np.percentile(lat, 99)), mean_ms=float(lat.mean()), max_ms=float(lat.max()),
-                         p99_slowdown=float(np.percentile(slow, 99)), completed_rps=len(res) / wall, failed=bad))
+                         p99_slowdown=float(np.percentile(slow, 99)), completed_rps=len(res) / wall,
+                         aggregate_mpts=pts / wall / 1e6, failed=bad))
     st = srv.stats()
     srv.close()
     head = min(runs, key=lambda x: abs(x["load"] - 0.8))
-    return dict(p99_ms=head["p99_ms"], p50_ms=head["p50_ms"], load=head["load"], requests=len(reqs),
+    return dict(p99_ms=head["p99_ms"], p50_ms=head["p50_ms"], load=head["load"],
+                aggregate_mpts=head["aggregate_mpts"], requests=len(reqs),
                 fields=len(fields), streams=args.serve_streams, capacity_rps=capacity,
                 mean_service_ms=mean_service, plan_ms_mean=float(np.mean(plan_ms)) if plan_ms else None,
                 runs=runs, cache_hits=st["cache_hits"], plans_created=st["plans_created"],
@@ -395,13 +407,91 @@ def run_serving(args, dev) -> dict:
                        f"{max(f['npts'] for f in fields)}), warm plan cache")
 
 
+# ----------------------------------------------------------------------------- Table 1
+# rows of the paper's Table 1 (Sec. II.F): field, theta* [deg], area [deg^2], lmax, resolution
+# [arcmin], spin, and the paper's measured speed-ups (synthesis, adjoint) and prediction
+TABLE1 = [
+    ("SPT-3G main", 35, 1500, 4000, 1.7, 0, 3.5, 3.3, 4.1),
+    ("SPT-3G main", 35, 1500, 4000, 1.7, 2, 3.2, 3.1, 4.1),
+    ("SPT-3G main", 35, 1500, 5120, 1.7, 1, 3.2, 3.4, 4.2),
+    ("SPT-3G main", 35, 1500, 6000, 1.7, 0, 3.9, 3.8, 4.3),
+    ("SPT-3G main", 35, 1500, 10000, 0.43, 0, 3.5, 3.3, 4.6),
+    ("SPT-3G+/BICEP3", 20, 980, 4000, 1.7, 0, 7.7, 7.12, 11.5),
+    ("SPT-3G+/BICEP3", 20, 980, 4000, 1.7, 2, 6.4, 6.5, 11.6),
+    ("SPT-3G+/BICEP3", 20, 980, 6000, 1.7, 0, 9.0, 8.8, 12.5),
+    ("EDFS", 7, 57, 4000, 0.86, 2, 23, 21, 67),
+    ("EDFS", 7, 57, 10000, 0.43, 0, 39, 43, 85),
+]
+
+
+def run_table1(args) -> dict:
+    """Partial-sky vs full-sky (PSHT_FULL_SKY) synthesis and adjoint with the same kernels, FP64 form
+    at the paper's tolerance 1e-7, for the rows of Table 1.  Points: the row's area / resolution^2,
+    uniform in a cap of radius theta* around the north pole (the fields' footprints are not
+    available); a_lm with C_l = (l+1)^-2.  Execute time on warm plans (CUDA events; median of 3 below
+    lmax 6000, one timed call above)."""
+    import torch
+
+    from paper_2603_17166_gb300 import Plan, build, synthetic
+
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    rows = []
+    for field, ts, area, lmax, res, spin, p_syn, p_adj, pred in TABLE1:
+        n = int(round(area * 3600.0 / (res * res)))
+        gen = synthetic.rng(1, "points", 100 + len(rows))
+        th, ph = synthetic.cap_points(n, float(ts), gen, "N")
+        ga = synthetic.rng(1, "alm", 100 + len(rows))
+        g = synthetic.gaussian_alm(lmax, spin, ga, "inv_l2")
+        c = synthetic.gaussian_alm(lmax, spin, ga, "inv_l2") if spin else None
+        tt, pt = torch.from_numpy(th).to(dev), torch.from_numpy(ph).to(dev)
+        entry = dict(field=field, theta_star_deg=ts, lmax=lmax, spin=spin, npts=n, paper_synthesis=p_syn,
+                     paper_adjoint=p_adj, paper_predicted=pred)
+        for mode in ("partial", "full"):
+            plan = Plan(spin, lmax, tt, pt, 1e-7, precision="fp64", full_sky=(mode == "full"))
+            gd = torch.from_numpy(g).to(dev)
+            cd = None if c is None else torch.from_numpy(c).to(dev)
+            f = plan.synthesis(gd, cd)
+            gt, ct = plan.adjoint(f, want_c=c is not None)
+            ts_, ta_ = [], []
+            for _ in range(3 if lmax < 6000 else 1):
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                e[0].record()
+                plan.synthesis(gd, cd, out=f)
+                e[1].record()
+                plan.adjoint(f, g_out=gt, c_out=ct, want_c=c is not None)
+                e[2].record()
+                torch.cuda.synchronize(dev)
+                ts_.append(e[0].elapsed_time(e[1]))
+                ta_.append(e[1].elapsed_time(e[2]))
+            info = plan.info
+            entry[mode] = dict(synthesis_ms=float(np.median(ts_)), adjoint_ms=float(np.median(ta_)),
+                               nring=info["nring"], M=info["M"], triples=info["recursion_triples"])
+            plan.close()
+            del f, gt, ct, gd, cd
+            torch.cuda.empty_cache()
+        entry["speedup_synthesis"] = entry["full"]["synthesis_ms"] / entry["partial"]["synthesis_ms"]
+        entry["speedup_adjoint"] = entry["full"]["adjoint_ms"] / entry["partial"]["adjoint_ms"]
+        entry["triples_ratio"] = entry["full"]["triples"] / entry["partial"]["triples"]
+        print(json.dumps(entry), file=sys.stderr, flush=True)
+        rows.append(entry)
+    return {"table1": rows, "eps": 1e-7, "form": "fp64", "data": "synthetic caps of radius theta*"}
+
+
 # ----------------------------------------------------------------------------- oracle arm
-def cpu_baseline(args, wl, steps: int = 1) -> dict:
+def cpu_baseline(args, wl, steps: int = 1, gpu_samples=None) -> dict:
     """The FP64 CPU oracle pipeline (as it stands) on a bounded sample of the same workload:
     every `cpu_ring_stride`-th ring for the two recursion stages, the full FFT stages, and
     `cpu_sample_points` points for interpolation and spreading; each part's time is scaled to the
-    full workload linearly (ring count, point count)."""
+    full workload linearly (ring count, point count).  With gpu_samples ({form: (eps, indices,
+    values)}) it also reports each form's relative L2 error against the oracle's direct sum there."""
     import oracle as O
+
+    accuracy = {}
+    for form, (eps, sel, got) in (gpu_samples or {}).items():
+        ref = O.direct_synthesis(LMAX, SPIN, wl["g"], wl["c"], wl["theta"][sel], wl["phi"][sel])
+        accuracy[form] = dict(eps=eps, rel_l2=float(O.rel_l2(got, ref)), points=int(len(sel)))
 
     lmax, s = LMAX, SPIN
     th, ph = wl["theta"], wl["phi"]
@@ -444,7 +534,8 @@ def cpu_baseline(args, wl, steps: int = 1) -> dict:
             "sample": (f"FP64 oracle pipeline at eps {EPS32:g} (W={P['W']}, L={P['L']}, M={P['M']}): "
                        f"every {args.cpu_ring_stride}th ring for both recursions, full FFTs, "
                        f"{sel.size} of {N} points for interp/spread; times scaled to the full workload"),
-            "est_seconds_per_step": tot, "parts_s": {k: round(v, 3) for k, v in times[-1].items()}}
+            "est_seconds_per_step": tot, "parts_s": {k: round(v, 3) for k, v in times[-1].items()},
+            "gpu_error_vs_oracle": accuracy}
 
 
 def run_reference(args, rank, world):
@@ -472,6 +563,10 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.table1:
+        if rank == 0:
+            print(json.dumps(run_table1(args)))
+        return
     if args.impl == "reference":
         line = run_reference(args, rank, world)
     else:

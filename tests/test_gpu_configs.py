@@ -2,8 +2,9 @@
 
   * lmax 6000 on the ~1% deep field, 5e7 uniform random points: spin 2 in the patch-centred frame
     (FP32 at eps = 1e-5, FP64 at 1e-10) and spin 0 with the points as given (nearer pole, FP64);
-  * lmax 16384 on the ~4% field, 1e8 uniform random points, spin 2, patch-centred frame: FP32 at
-    eps = 1e-5 and FP64 at 1e-10 (phi FFT of ~40000 points on global buffers).
+  * lmax 16384 on the ~4% field, 1e8 uniform random points, spin 2, patch-centred frame: the eps
+    sweep 1e-4 .. 1e-12, the FP32 form at eps >= 1e-5 and the plain FP64 form at every eps (phi FFT
+    of ~40000 points on global buffers).
 
 The oracle sums a random sample of points directly (O1), <= 10 eps; the adjoint identity holds at
 any size.  The extreme points (nearest the pole, on the cap edge) are always in the sample."""
@@ -80,17 +81,33 @@ def test_lmax6000_spin0_as_given():
 def wide_lmax16384():
     from paper_2603_17166_gb300 import synthetic
 
-    return synthetic.config5(frame="R")
+    wl = synthetic.config5(frame="R")
+    sel = _sample(wl["theta"], 16, 51)
+    ref = O.direct_synthesis(wl["lmax"], wl["s"], wl["g"], wl["c"], wl["theta"][sel], wl["phi"][sel])
+    return wl, sel, ref
 
 
-@pytest.mark.parametrize("prec,eps,k", [("fp32", 1e-5, 24), ("fp64", 1e-10, 16)])
-def test_lmax16384(wide_lmax16384, prec, eps, k):
-    wl = wide_lmax16384
+# the eps sweep of the lmax 16384 workload: FP32 form for eps >= 1e-5, plain FP64 for all
+SWEEP = [("fp32", 1e-4), ("fp32", 1e-5), ("fp64", 1e-4), ("fp64", 1e-6), ("fp64", 1e-8), ("fp64", 1e-10),
+         ("fp64", 1e-12)]
+
+
+@pytest.mark.parametrize("prec,eps", SWEEP, ids=[f"{p}-{e:g}" for p, e in SWEEP])
+def test_lmax16384_eps_sweep(wide_lmax16384, prec, eps):
+    from paper_2603_17166_gb300 import Plan
+
+    wl, sel, ref = wide_lmax16384
     assert wl["theta"].size == 100_000_000
-    plan, f, g, c, err = _check_synthesis(wl, eps, prec, k, 51)
+    plan = Plan(2, 16384, torch.from_numpy(wl["theta"]).cuda(), torch.from_numpy(wl["phi"]).cuda(), eps,
+                precision=prec)
+    g = torch.from_numpy(wl["g"]).cuda().to(plan.cdtype)
+    c = torch.from_numpy(wl["c"]).cuda().to(plan.cdtype)
+    f = plan.synthesis(g, c)
+    got = f[torch.from_numpy(sel).cuda()].cpu().numpy().astype(np.complex128)
+    err = O.rel_l2(got, ref)
+    print(f"lmax 16384 {prec} eps {eps:g}: rel L2 error {err:.3e} (W {plan.info['W']}, nphi {plan.info['nphi']})")
+    assert plan.status() == 0
     assert err <= 10 * eps
-    if prec == "fp64":
-        assert plan.info["nphi"] > 14336  # global-buffer phi FFT
     plan.close()
     del f, g, c
     torch.cuda.empty_cache()

@@ -221,3 +221,53 @@ def test_full_sky_both_poles_reflection(prec, eps):
     wgt = np.tile(np.where(m == 0, 1.0, 2.0), 2)
     got = np.concatenate([gt.cpu().numpy(), ct.cpu().numpy()]).astype(np.complex128)
     assert O.rel_l2(got, np.concatenate([gt1, ct1]), wgt) <= 10 * eps
+
+
+@pytest.mark.parametrize("prec,eps", [("fp64", 1e-10), ("fp32", 1e-5)])
+def test_forced_full_sky_matches_partial(prec, eps):
+    """PSHT_FULL_SKY runs the full-sky route (theta_max = pi, w = 1, L = lmax rings + 1) on a small
+    cap; both routes approximate the same f to within the tolerance."""
+    rng = np.random.default_rng(41)
+    lmax, s = 96, 2
+    th, ph = _cap(rng, 2000, 0.4, "S")
+    g, c = _alm(rng, lmax, s), _alm(rng, lmax, s)
+    from paper_2603_17166_gb300 import Plan
+
+    pp = _plan(s, lmax, th, ph, eps, prec)
+    pf = Plan(s, lmax, torch.from_numpy(th).cuda(), torch.from_numpy(ph).cuda(), eps, precision=prec, full_sky=True)
+    assert pp.info["full_sky"] == 0 and pf.info["full_sky"] == 1
+    assert pf.info["nring"] == pf.info["L"] + 1 and pf.info["theta_max"] == pytest.approx(math.pi)
+    ref = O.direct_synthesis(lmax, s, g, c, th, ph)
+    fp = pp.synthesis(_cu(g, pp), _cu(c, pp)).cpu().numpy().astype(np.complex128)
+    ff = pf.synthesis(_cu(g, pf), _cu(c, pf)).cpu().numpy().astype(np.complex128)
+    assert O.rel_l2(fp, ref) <= 10 * eps
+    assert O.rel_l2(ff, ref) <= 10 * eps
+    gt, ct = pf.adjoint(_cu(ref, pf))
+    g1, c1 = O.direct_adjoint(lmax, s, th, ph, ref)
+    got = np.concatenate([gt.cpu().numpy(), ct.cpu().numpy()]).astype(np.complex128)
+    assert O.alm_rel_l2(got[: g1.size], g1, lmax) <= 10 * eps
+
+
+def test_block_adjoint_ring_chunks():
+    """The FP64 adjoint runs one CTA per order over chunks of 1024 rings; a full-sky plan at
+    lmax 1500 has 1501 rings (two chunks per ring part, the second adding to the first)."""
+    rng = np.random.default_rng(42)
+    lmax, s, eps = 1500, 1, 1e-8
+    th, ph = _cap(rng, 3000, 2.0, "N")
+    from paper_2603_17166_gb300 import Plan
+
+    plan = Plan(s, lmax, torch.from_numpy(th).cuda(), torch.from_numpy(ph).cuda(), eps, precision="fp64",
+                full_sky=True)
+    assert plan.info["nring"] > 1024
+    g, c = _alm(rng, lmax, s), _alm(rng, lmax, s)
+    f = plan.synthesis(_cu(g, plan), _cu(c, plan)).cpu().numpy()
+    gt, ct = plan.adjoint(_cu(f, plan))
+    ls = np.array([1, 2, 7, 30, 200, 900, 1400, 1500])
+    ms = np.array([0, 1, 5, 30, 3, 450, 1399, 1500])
+    g1, c1 = O.direct_adjoint_lm(s, th, ph, f, ls, ms)
+    idx = O.alm_index(lmax, ls, ms)
+    got = np.concatenate([gt.cpu().numpy()[idx], ct.cpu().numpy()[idx]])
+    assert O.rel_l2(got, np.concatenate([g1, c1])) <= 10 * eps
+    lhs = O.map_dot(f, f)
+    rhs = O.alm_dot(gt.cpu().numpy(), g, lmax) + O.alm_dot(ct.cpu().numpy(), c, lmax)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
