@@ -103,6 +103,40 @@ int psht_plan_synthesis(psht_plan* plan, const void* g, const void* c, void* f, 
 int psht_plan_adjoint(psht_plan* plan, const void* f, void* g, void* c, void* stream);
 
 /*
+ * Plan options beyond the paper's argument list (psht_plan_create_ex).  Zero-initialise the struct:
+ * zero fields take the defaults.
+ *   window: the bell of the apodisation window (Sec. II.D): PSHT_WINDOW_ES, the exponential of a
+ *     semicircle the paper settles on (default), or PSHT_WINDOW_KB, the Kaiser-Bessel bell
+ *     I0(|ln eps| sqrt(1 - v^2)) the paper compares it with; same support and shape parameter.
+ *   kappa: factor on the Fourier-sphere band limit, Lmax = ceil(kappa (lmax theta_star / pi)(1+eps_apo)^2)
+ *     (Sec. II.C); 0 means 1.  Below 1 the ring count shrinks and the error grows beyond eps
+ *     unless the field is smooth (psht_predict_error tells by how much).
+ */
+#define PSHT_WINDOW_ES 0
+#define PSHT_WINDOW_KB 1
+typedef struct {
+  int window;
+  double kappa;
+} psht_options;
+/* psht_plan_create with options; opt may be NULL (defaults). */
+int psht_plan_create_ex(int spin, int lmax, const double* theta, const double* phi, int64_t npts, double eps,
+                        uint32_t flags, const psht_options* opt, void* stream, psht_plan** out);
+
+/*
+ * Predicted error of the partial-sky route for a statistically isotropic field (Sec. II.E):
+ * c_m = sum_l C_l (2l+1)/2 |d^l_{m,-s}(pi/2)|^2 (eq. cm, eq. cms), the error of each wave e^{i m theta}
+ * after weighting and band limiting on the plan's rings, sigma_m^2(theta) (eq. s2m), and
+ * sigma^2(theta) = (1/2pi) sum_m c_m sigma_m^2(theta) (eq. st), returned relative to the field's
+ * variance (1/2pi) sum_m c_m as an rms ratio.  The ring set is the one psht_plan_create_ex would
+ * build for (spin, lmax, theta_star, eps, opt); the NUFFT's own error is not included.
+ *   cl: HOST double[lmax+1], C_l (spin 0) or C^E_l + C^B_l (spin > 0); beta: HOST double[n], angular
+ *   distances from the plan's pole at which to predict; rel_rms: HOST double[n] output.
+ * Runs on the current device, synchronising `stream`.  EINVAL for bad sizes or negative C_l.
+ */
+int psht_predict_error(int spin, int lmax, double theta_star, double eps, const psht_options* opt, const double* cl,
+                       const double* beta, int n, double* rel_rms, void* stream);
+
+/*
  * Packed-gradient forms, for automatic differentiation over the packed a_lm arrays.  The transpose
  * above pairs with the inner product that counts each m > 0 entry twice (it stands for m and -m,
  * eq. syn's reality condition), while a gradient over the packed storage counts every stored

@@ -264,13 +264,25 @@ def _integrate(fun, a: float, b: float, n: int = 256) -> float:
     return float(xr * np.sum(w * fun(xm + xr * x)))
 
 
-def bell_cdf(x, dTheta: float, eps: float):
-    """CDF of the ES bell b(u) ~ exp[alpha pi (sqrt(1 - (2u/dTheta)^2) - 1)] on |u| <= dTheta/2,
-    unit area, alpha = |ln eps|/pi (Sec. II.D eq. KB rescaled to support dTheta, Fig. 4 caption).
-    Integrated with u = (dTheta/2) sin(tau), which makes the integrand smooth."""
-    cexp = abs(math.log(eps))
+def bell(v, eps: float, kind: str = "es"):
+    """Unnormalised bells on |v| <= 1 (v = 2u/dTheta), shape parameter alpha pi = |ln eps|:
+    'es' the exponential of a semicircle exp[alpha pi (sqrt(1 - v^2) - 1)] (Sec. II.D eq. KB), 'kb'
+    the Kaiser-Bessel bell I0(alpha pi sqrt(1 - v^2)) whose Fourier transform Sec. II.D prints."""
+    c = abs(math.log(eps))
+    r = np.sqrt(np.clip(1.0 - np.asarray(v, dtype=np.float64) ** 2, 0.0, None))
+    if kind == "es":
+        return np.exp(c * (r - 1.0))
+    if kind == "kb":
+        return np.i0(c * r)
+    raise ValueError(kind)
+
+
+def bell_cdf(x, dTheta: float, eps: float, kind: str = "es"):
+    """CDF of the bell of support dTheta (|u| <= dTheta/2), unit area, alpha = |ln eps|/pi (Sec. II.D
+    rescaled to support dTheta, Fig. 4 caption).  Integrated with u = (dTheta/2) sin(tau), which
+    makes the integrand smooth."""
     x = np.atleast_1d(np.asarray(x, dtype=np.float64))
-    dens = lambda tau: np.exp(cexp * (np.cos(tau) - 1.0)) * np.cos(tau)
+    dens = lambda tau: bell(np.sin(tau), eps, kind) * np.cos(tau)
     total = _integrate(dens, -0.5 * math.pi, 0.5 * math.pi)
     out = np.empty_like(x)
     for i, xi in enumerate(x):
@@ -284,11 +296,11 @@ def bell_cdf(x, dTheta: float, eps: float):
     return out
 
 
-def window(Theta, dTheta: float, eps: float):
+def window(Theta, dTheta: float, eps: float, kind: str = "es"):
     """w(Theta) = (top-hat of support 2pi - dTheta) convolved with the unit-area bell of support
     dTheta, i.e. w = B(pi - dTheta/2 - |Theta|) with B the bell CDF (Sec. II.D)."""
     Theta = np.abs(np.asarray(Theta, dtype=np.float64))
-    return bell_cdf(math.pi - 0.5 * dTheta - Theta, dTheta, eps)
+    return bell_cdf(math.pi - 0.5 * dTheta - Theta, dTheta, eps, kind)
 
 
 def es_kernel(z, beta: float):
@@ -330,8 +342,9 @@ def mcut(lmax: int, s: int, eps: float, beta) -> np.ndarray:
     return out
 
 
-def plan_params(lmax: int, s: int, eps: float, theta) -> dict:
-    """P0-P2 of the partial-sky method plus the NUFFT grid (see module docstring)."""
+def plan_params(lmax: int, s: int, eps: float, theta, kappa: float = 1.0, window_kind: str = "es") -> dict:
+    """P0-P2 of the partial-sky method plus the NUFFT grid (see module docstring); kappa scales the
+    band limit Lmax (Sec. II.C), window_kind picks the bell (Sec. II.D)."""
     theta = np.asarray(theta, dtype=np.float64)
     bN = float(theta.max()) if theta.size else 0.0
     bS = float((math.pi - theta).max()) if theta.size else 0.0
@@ -345,7 +358,7 @@ def plan_params(lmax: int, s: int, eps: float, theta) -> dict:
     else:
         eps_apo = math.sqrt(2.0 * lneps / (tstar * lmax))
         tmax = tstar * (1.0 + eps_apo)
-        Lmax = math.ceil(lmax * tstar / math.pi * (1.0 + eps_apo) ** 2)
+        Lmax = math.ceil(kappa * lmax * tstar / math.pi * (1.0 + eps_apo) ** 2)
         if tmax >= math.pi or Lmax >= lmax:
             full = True
     if full:
@@ -357,7 +370,7 @@ def plan_params(lmax: int, s: int, eps: float, theta) -> dict:
     Theta_j = np.arange(nring) * (math.pi / L)
     beta_j = Theta_j * (tmax / math.pi)
     theta_j = beta_j if pole == "N" else math.pi - beta_j
-    w_j = np.ones(nring) if full else window(Theta_j, dTheta, eps)
+    w_j = np.ones(nring) if full else window(Theta_j, dTheta, eps, window_kind)
     Mj = mcut(lmax, s, eps, beta_j)
     M = int(Mj.max())
     W = es_width(eps)
@@ -528,3 +541,49 @@ def pipeline_adjoint(P: dict, f, theta, phi, exact: bool = False, return_stages:
     if return_stages:
         return (gt, ct), dict(G=G, H=Ht, F=Ft)
     return gt, ct
+
+
+# ----------------------------------------------------------------------------- error predictor
+def great_circle_spectrum(lmax: int, s: int, cl) -> np.ndarray:
+    """c_m, m = -lmax..lmax: power along a great circle through the pole of an isotropic field with
+    spectrum C_l (eq. cm for s = 0, eq. cms with C_l = C^E_l + C^B_l for s > 0):
+    c_m = sum_l C_l (2l+1)/2 |d^l_{m,-s}(pi/2)|^2."""
+    cl = np.asarray(cl, dtype=np.float64)
+    l = np.arange(lmax + 1)
+    c = np.zeros(2 * lmax + 1)
+    for m in range(-lmax, lmax + 1):
+        d = wigner_d(lmax, m, -s, 0.5 * math.pi)
+        c[m + lmax] = np.sum(cl * (2 * l + 1) / 2.0 * d * d)
+    return c
+
+
+def wave_error(P: dict, m, beta) -> np.ndarray:
+    """sigma_m^2(beta) of eq. s2m on the plan's doubled circle, written out: the wave e^{i m theta}
+    sampled at Theta_k = k pi/L, k = 0..2L-1 (Theta_k - 2pi past the pole, theta = Theta theta_max/pi),
+    weighted by w, its Fourier coefficients H_n = (2L)^-1 sum_k h_k e^{-i n Theta_k} kept for
+    |n| <= L-1, summed back at Theta = beta pi/theta_max and compared with the wave there.
+    Returns [len(m), len(beta)]."""
+    m = np.atleast_1d(np.asarray(m, dtype=np.float64))
+    beta = np.atleast_1d(np.asarray(beta, dtype=np.float64))
+    L, tmax = P["L"], P["theta_max"]
+    k = np.arange(2 * L)
+    Th_k = np.where(k > L, k - 2 * L, k) * (math.pi / L)
+    ring = np.where(k > L, 2 * L - k, k)
+    wr = np.zeros(L + 1)
+    wr[: min(P["nring"], L + 1)] = P["w_j"][: L + 1]
+    h = wr[ring][None, :] * np.exp(1j * np.outer(m, Th_k * tmax / math.pi))
+    n = np.arange(-(L - 1), L)
+    H = h @ np.exp(-1j * np.outer(Th_k, n)) / (2 * L)
+    rec = H @ np.exp(1j * np.outer(n, beta * math.pi / tmax))
+    return np.abs(rec - np.exp(1j * np.outer(m, beta))) ** 2
+
+
+def predict_error(lmax: int, s: int, eps: float, theta_star: float, cl, beta, kappa: float = 1.0,
+                  window_kind: str = "es") -> np.ndarray:
+    """Relative rms error of the partial-sky route at angles beta from the pole (Sec. II.E eq. st):
+    sqrt(sum_m c_m sigma_m^2(beta) / sum_m c_m), on the ring set of plan_params for a cap theta*."""
+    P = plan_params(lmax, s, eps, np.array([0.0, theta_star]), kappa, window_kind)
+    c = great_circle_spectrum(lmax, s, cl)
+    ms = np.arange(-lmax, lmax + 1)
+    sig = wave_error(P, ms, beta)
+    return np.sqrt(c @ sig / c.sum())

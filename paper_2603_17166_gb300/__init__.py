@@ -5,4 +5,4 @@ Fourier-sphere route of Carron & Reinecke (Wigner-d recursion onto apodised ring
 reduced oversampled grid, ES-kernel interpolation), as a C-ABI CUDA library with a thin binding.
 """
 from .psht import (Plan, PshtError, Server, adjoint_synthesis, estimate_bytes, estimate_points,  # noqa: F401
-                   lib, nalm, synthesis)
+                   lib, nalm, predict_error, synthesis)

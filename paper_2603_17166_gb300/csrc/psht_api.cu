@@ -108,14 +108,30 @@ struct Quad {
   }
 };
 
-// window w(Theta) = B(pi - dTheta/2 - |Theta|), B the CDF of the unit-area ES bell of support dTheta
-// (Sec. II.D); u = (dTheta/2) sin(tau) makes the integrand smooth.
-double window_value(double Theta, double dTheta, double cexp, const Quad& q) {
+// modified Bessel function I0(x) e^{-x} for 0 <= x <= ~50 by its power series sum (x^2/4)^k/(k!)^2
+double bessel_i0_scaled(double x) {
+  const double q = 0.25 * x * x;
+  double term = exp(-x), sum = term;
+  for (int k = 1; k < 200; ++k) {
+    term *= q / ((double)k * k);
+    sum += term;
+    if (term < 1e-17 * sum) break;
+  }
+  return sum;
+}
+
+// window w(Theta) = B(pi - dTheta/2 - |Theta|), B the CDF of the unit-area bell of support dTheta
+// (Sec. II.D): the ES bell exp[c (sqrt(1 - v^2) - 1)] or the Kaiser-Bessel bell I0(c sqrt(1 - v^2)),
+// v = 2u/dTheta, c = alpha pi = |ln eps|; u = (dTheta/2) sin(tau) makes the integrand smooth.
+double window_value(double Theta, double dTheta, double cexp, int kind, const Quad& q) {
   const double x = M_PI - 0.5 * dTheta - fabs(Theta);
   const double z = 2.0 * x / dTheta;
   if (z <= -1.0) return 0.0;
   if (z >= 1.0) return 1.0;
-  auto dens = [&](double tau) { return exp(cexp * (cos(tau) - 1.0)) * cos(tau); };
+  auto dens = [&](double tau) {
+    const double c = cos(tau);
+    return (kind == PSHT_WINDOW_KB ? bessel_i0_scaled(cexp * c) * exp(cexp * (c - 1.0)) : exp(cexp * (c - 1.0))) * c;
+  };
   return q.integrate(dens, -0.5 * M_PI, asin(z)) / q.integrate(dens, -0.5 * M_PI, 0.5 * M_PI);
 }
 
@@ -179,7 +195,7 @@ void layout(Plan& p, double theta_star) {
   if (!full) {
     p.eps_apo = sqrt(2.0 * lneps / (p.theta_star * p.lmax));
     p.theta_max = p.theta_star * (1.0 + p.eps_apo);
-    p.Lmax = (int)ceil(p.lmax * p.theta_star / M_PI * (1.0 + p.eps_apo) * (1.0 + p.eps_apo));
+    p.Lmax = (int)ceil(p.kappa * p.lmax * p.theta_star / M_PI * (1.0 + p.eps_apo) * (1.0 + p.eps_apo));
     if (p.theta_max >= M_PI || p.Lmax >= p.lmax) full = true;
   }
   p.full = full ? 1 : 0;
@@ -203,7 +219,7 @@ void layout(Plan& p, double theta_star) {
     const double Th = j * (M_PI / p.L);
     p.beta_j[j] = Th * (p.theta_max / M_PI);
     p.theta_j[j] = p.pole > 0 ? p.beta_j[j] : M_PI - p.beta_j[j];
-    p.w_j[j] = full ? 1.0 : window_value(Th, p.dTheta, lneps, quad);
+    p.w_j[j] = full ? 1.0 : window_value(Th, p.dTheta, lneps, p.window, quad);
     p.Mj[j] = mcut(p.lmax, p.spin, p.eps, p.beta_j[j]);
   }
   p.M = *std::max_element(p.Mj.begin(), p.Mj.end());
@@ -234,7 +250,7 @@ void layout(Plan& p, double theta_star) {
   // (k_rec_adj_w, k_adj_reduce) while that buffer stays within 4 GB, else the block form below.
   // Block form (FP64, large FP32 plans): one CTA per m and chunk of adj_rpt * adj_threads rings.
   constexpr double kMaxPartBytes = 4e9;
-  p.adj_rpt = 8;
+  p.adj_rpt = p.nring <= 256 ? 2 : (p.nring <= 512 ? 4 : 8);  // fewest idle ring slots per CTA
   p.adj_threads = 128;
   if (p.prec == 32) {
     p.adj_threads = 32;
@@ -313,8 +329,46 @@ void destroy(Plan* p) {
   delete p;
 }
 
+// Seeds of the recursion per order m: Wigner's closed form at l0 = max(m, s), as log2 of
+// N_l0 sqrt(C(2 l0, p1)) and the powers of the half-angle cosine and sine, for the columns
+// d_{m,-s} (e1) and d_{m,s} (e2).
+std::vector<MSeed> make_seeds(int lmax, int spin) {
+  std::vector<MSeed> ms(lmax + 1);
+  for (int m = 0; m <= lmax; ++m) {
+    MSeed d;
+    d.l0 = std::max(m, spin);
+    if (m >= spin) {
+      d.p1 = m - spin;
+      d.q1 = m + spin;
+      d.sign1 = d.sign2 = ((m + spin) & 1) ? -1 : 1;
+    } else {
+      d.p1 = spin - m;
+      d.q1 = spin + m;
+      d.sign1 = ((spin + m) & 1) ? -1 : 1;
+      d.sign2 = 1;
+    }
+    const long double l0 = d.l0;
+    const long double lb = 0.5L * (lgammal(2 * l0 + 1) - lgammal((long double)d.p1 + 1) - lgammal((long double)d.q1 + 1)) /
+                           logl(2.0L);
+    const long double ln = 0.5L * log2l((2 * l0 + 1) / (4.0L * 3.14159265358979323846264338327950288L));
+    d.lbin = (double)(lb + ln);
+    ms[m] = d;
+  }
+  return ms;
+}
+
+// options in a plan, validated
+void apply_options(Plan& p, const psht_options* opt) {
+  if (!opt) return;
+  PSHT_REQUIRE(opt->window == PSHT_WINDOW_ES || opt->window == PSHT_WINDOW_KB, PSHT_EINVAL, "unknown window");
+  PSHT_REQUIRE(opt->kappa == 0.0 || (opt->kappa >= 0.25 && opt->kappa <= 4.0), PSHT_EINVAL,
+               "kappa must be 0 (default) or lie in [0.25, 4]");
+  p.window = opt->window;
+  p.kappa = opt->kappa == 0.0 ? 1.0 : opt->kappa;
+}
+
 Plan* create(int spin, int lmax, const double* theta, const double* phi, int64_t npts, double eps, uint32_t flags,
-             cudaStream_t st) {
+             const psht_options* opt, cudaStream_t st) {
   PSHT_REQUIRE(spin >= 0, PSHT_EINVAL, "spin must be >= 0");
   PSHT_REQUIRE(lmax >= spin, PSHT_EINVAL, "lmax must be >= spin");
   PSHT_REQUIRE(lmax <= 65535, PSHT_EINVAL, "lmax above 65535");
@@ -335,6 +389,7 @@ Plan* create(int spin, int lmax, const double* theta, const double* phi, int64_t
     p->prec = prec;
     p->npts = npts;
     p->force_full = (flags & PSHT_FULL_SKY) ? 1 : 0;
+    apply_options(*p, opt);
     // step 1: nearer pole and theta* (one device reduction, validates the points)
     double red[3];
     reduce_points(theta, phi, npts, red, st);
@@ -363,27 +418,7 @@ Plan* create(int spin, int lmax, const double* theta, const double* phi, int64_t
     }
     p->d_ring = (RingDev*)upload(*p, rings, st);
     // per-m seeds
-    std::vector<MSeed> ms(lmax + 1);
-    for (int m = 0; m <= lmax; ++m) {
-      MSeed d;
-      d.l0 = std::max(m, spin);
-      if (m >= spin) {
-        d.p1 = m - spin;
-        d.q1 = m + spin;
-        d.sign1 = d.sign2 = ((m + spin) & 1) ? -1 : 1;
-      } else {
-        d.p1 = spin - m;
-        d.q1 = spin + m;
-        d.sign1 = ((spin + m) & 1) ? -1 : 1;
-        d.sign2 = 1;
-      }
-      const long double l0 = d.l0;
-      const long double lb = 0.5L * (lgammal(2 * l0 + 1) - lgammal((long double)d.p1 + 1) - lgammal((long double)d.q1 + 1)) /
-                             logl(2.0L);
-      const long double ln = 0.5L * log2l((2 * l0 + 1) / (4.0L * 3.14159265358979323846264338327950288L));
-      d.lbin = (double)(lb + ln);
-      ms[m] = d;
-    }
+    const std::vector<MSeed> ms = make_seeds(lmax, spin);
     p->d_mseed = (MSeed*)upload(*p, ms, st);
     // active ring ranges and synthesis work items
     // per order m and ring part (0: direct, 1: reflected) the active rings M_j >= m form one
@@ -582,7 +617,17 @@ int psht_plan_create(int spin, int lmax, const double* theta, const double* phi,
   return guarded([&] {
     PSHT_REQUIRE(out != nullptr, PSHT_EINVAL, "out must not be NULL");
     *out = nullptr;
-    Plan* p = create(spin, lmax, theta, phi, npts, eps, flags, (cudaStream_t)stream);
+    Plan* p = create(spin, lmax, theta, phi, npts, eps, flags, nullptr, (cudaStream_t)stream);
+    *out = new psht_plan{p};
+  });
+}
+
+int psht_plan_create_ex(int spin, int lmax, const double* theta, const double* phi, int64_t npts, double eps,
+                        uint32_t flags, const psht_options* opt, void* stream, psht_plan** out) {
+  return guarded([&] {
+    PSHT_REQUIRE(out != nullptr, PSHT_EINVAL, "out must not be NULL");
+    *out = nullptr;
+    Plan* p = create(spin, lmax, theta, phi, npts, eps, flags, opt, (cudaStream_t)stream);
     *out = new psht_plan{p};
   });
 }
@@ -758,7 +803,7 @@ int psht_plan_stage_times(psht_plan* plan, double* ms, int64_t* calls) {
 int psht_synthesis(const void* g, const void* c, int spin, int lmax, const double* theta, const double* phi,
                    int64_t npts, double eps, void* f, void* stream) {
   return guarded([&] {
-    Plan* p = create(spin, lmax, theta, phi, npts, eps, PSHT_AUTO, (cudaStream_t)stream);
+    Plan* p = create(spin, lmax, theta, phi, npts, eps, PSHT_AUTO, nullptr, (cudaStream_t)stream);
     try {
       PSHT_REQUIRE(g && (f || npts == 0), PSHT_EINVAL, "g and f must not be NULL");
       run_synthesis(*p, g, c, f, (cudaStream_t)stream);
@@ -774,7 +819,7 @@ int psht_synthesis(const void* g, const void* c, int spin, int lmax, const doubl
 int psht_adjoint_synthesis(const void* f, int spin, int lmax, const double* theta, const double* phi, int64_t npts,
                            double eps, void* g, void* c, void* stream) {
   return guarded([&] {
-    Plan* p = create(spin, lmax, theta, phi, npts, eps, PSHT_AUTO, (cudaStream_t)stream);
+    Plan* p = create(spin, lmax, theta, phi, npts, eps, PSHT_AUTO, nullptr, (cudaStream_t)stream);
     try {
       PSHT_REQUIRE(g && (f || npts == 0), PSHT_EINVAL, "f and g must not be NULL");
       run_adjoint(*p, f, g, c, (cudaStream_t)stream);
@@ -827,6 +872,27 @@ int psht_plan_estimate_points(int spin, int lmax, const double* theta, const dou
     p.pole = (red[0] <= red[1]) ? 1 : -1;
     layout(p, p.pole > 0 ? red[0] : red[1]);
     *bytes = planned_bytes(p);
+  });
+}
+
+int psht_predict_error(int spin, int lmax, double theta_star, double eps, const psht_options* opt, const double* cl,
+                       const double* beta, int n, double* rel_rms, void* stream) {
+  return guarded([&] {
+    PSHT_REQUIRE(spin >= 0 && lmax >= spin && lmax <= 65535, PSHT_EINVAL, "invalid spin or lmax");
+    PSHT_REQUIRE(eps >= 1e-14 && eps <= 1e-1, PSHT_EINVAL, "eps must lie in [1e-14, 1e-1]");
+    PSHT_REQUIRE(theta_star > 0.0 && theta_star <= M_PI, PSHT_EINVAL, "theta_star must lie in (0, pi]");
+    PSHT_REQUIRE(cl && beta && rel_rms && n >= 0, PSHT_EINVAL, "cl, beta and rel_rms must not be NULL");
+    for (int l = 0; l <= lmax; ++l) PSHT_REQUIRE(cl[l] >= 0.0, PSHT_EINVAL, "C_l must be >= 0");
+    if (n == 0) return;
+    Plan p;
+    p.spin = spin;
+    p.lmax = lmax;
+    p.eps = eps;
+    p.prec = 64;
+    p.pole = 1;
+    apply_options(p, opt);
+    layout(p, theta_star);
+    predict_error_device(p, make_seeds(lmax, spin), cl, beta, n, rel_rms, (cudaStream_t)stream);
   });
 }
 

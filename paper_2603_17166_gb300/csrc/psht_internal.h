@@ -88,6 +88,8 @@ struct Plan {
   double eps = 0;
   int pole = 1, full = 0;
   int force_full = 0;  // PSHT_FULL_SKY
+  int window = 0;      // PSHT_WINDOW_ES or PSHT_WINDOW_KB
+  double kappa = 1.0;  // ring-count factor in Lmax
   double theta_star = 0, eps_apo = 0, theta_max = 0, dTheta = 0, alpha = 0;
   int Lmax = 0, L = 0, nring = 0, M = 0, W = 0;
   double beta_es = 0;
@@ -174,5 +176,8 @@ size_t fft_scratch_elems(const Plan& p);  // complex elements of the global FFT 
 void ring_synthesis_noalloc(int spin, int lmax, const double* theta, int nring, const void* g, const void* c, void* F,
                             cudaStream_t st);
 size_t noalloc_scratch_bytes();
+// predicted relative rms error of the plan's ring set for spectrum cl at angles beta (host arrays)
+void predict_error_device(const Plan& p, const std::vector<MSeed>& seeds, const double* cl, const double* beta, int n,
+                          double* rel_rms, cudaStream_t st);
 
 }  // namespace psht

@@ -1231,6 +1231,7 @@ void launch_adj_s(Plan& p, void* g, void* c, double msc, cudaStream_t st) {
   }
   // (rings per thread, threads) of one launch chunk; chosen by the planner
   switch (p.adj_rpt * 10000 + p.adj_threads) {
+    case 20128: launch_adj_t<T, SPIN, 2, 128>(p, g, c, msc, st); break;
     case 40128: launch_adj_t<T, SPIN, 4, 128>(p, g, c, msc, st); break;
     case 40256: launch_adj_t<T, SPIN, 4, 256>(p, g, c, msc, st); break;
     case 80128: launch_adj_t<T, SPIN, 8, 128>(p, g, c, msc, st); break;

@@ -36,6 +36,13 @@ class PshtInfo(ctypes.Structure):
     ]
 
 
+class PshtOptions(ctypes.Structure):
+    _fields_ = [("window", ctypes.c_int), ("kappa", ctypes.c_double)]
+
+
+_WINDOW = {"es": 0, "kb": 1}
+
+
 class PshtRequest(ctypes.Structure):
     _fields_ = [
         ("op", ctypes.c_int), ("spin", ctypes.c_int), ("lmax", ctypes.c_int), ("eps", ctypes.c_double),
@@ -89,6 +96,8 @@ def lib():
         L.psht_plan_stage_times.argtypes = [P, P, P]
         L.psht_ring_synthesis_noalloc.argtypes = [I, I, P, I, P, P, P, P]
         L.psht_noalloc_scratch_bytes.restype = ctypes.c_size_t
+        L.psht_plan_create_ex.argtypes = [I, I, P, P, I64, D, U32, ctypes.POINTER(PshtOptions), P, ctypes.POINTER(P)]
+        L.psht_predict_error.argtypes = [I, I, D, D, ctypes.POINTER(PshtOptions), P, P, I, P, P]
         L.psht_plan_estimate_points.argtypes = [I, I, P, P, I64, D, U32, P, ctypes.POINTER(ctypes.c_size_t)]
         L.psht_server_create.argtypes = [I, ctypes.c_size_t, ctypes.POINTER(P)]
         L.psht_server_submit.argtypes = [P, ctypes.POINTER(PshtRequest), ctypes.POINTER(I64)]
@@ -133,7 +142,7 @@ class Plan:
     """A plan for synthesis general and its adjoint at fixed points (psht_plan_create)."""
 
     def __init__(self, spin: int, lmax: int, theta, phi, eps: float, precision="auto", stream=None,
-                 full_sky: bool = False):
+                 full_sky: bool = False, window: str = "es", kappa: float = 1.0):
         torch = _torch()
         theta = torch.as_tensor(theta, dtype=torch.float64, device="cuda").contiguous()
         phi = torch.as_tensor(phi, dtype=torch.float64, device="cuda").contiguous()
@@ -141,8 +150,14 @@ class Plan:
             raise ValueError("theta and phi must be 1-D tensors of equal length")
         self._h = ctypes.c_void_p()
         flags = _PREC[precision] | (PSHT_FULL_SKY if full_sky else 0)
-        _check(lib().psht_plan_create(int(spin), int(lmax), _ptr(theta), _ptr(phi), theta.numel(), float(eps),
-                                      flags, _stream(stream), ctypes.byref(self._h)))
+        if window == "es" and kappa == 1.0:
+            _check(lib().psht_plan_create(int(spin), int(lmax), _ptr(theta), _ptr(phi), theta.numel(), float(eps),
+                                          flags, _stream(stream), ctypes.byref(self._h)))
+        else:
+            opt = PshtOptions(_WINDOW[window], float(kappa))
+            _check(lib().psht_plan_create_ex(int(spin), int(lmax), _ptr(theta), _ptr(phi), theta.numel(),
+                                             float(eps), flags, ctypes.byref(opt), _stream(stream),
+                                             ctypes.byref(self._h)))
         self.spin, self.lmax, self.eps, self.npts = int(spin), int(lmax), float(eps), theta.numel()
         i = self.info
         self.precision = i["precision"]
@@ -350,3 +365,19 @@ def estimate_points(spin: int, lmax: int, theta, phi, eps: float, precision="aut
     _check(lib().psht_plan_estimate_points(int(spin), int(lmax), _ptr(theta), _ptr(phi), theta.numel(), float(eps),
                                            _PREC[precision], _stream(stream), ctypes.byref(b)))
     return b.value
+
+
+def predict_error(spin: int, lmax: int, theta_star: float, eps: float, cl, beta, window: str = "es",
+                  kappa: float = 1.0, stream=None) -> np.ndarray:
+    """Predicted relative rms error of the partial-sky route at angles beta from the pole for an
+    isotropic field with spectrum cl (psht_predict_error)."""
+    cl = np.ascontiguousarray(cl, dtype=np.float64)
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    if cl.size != lmax + 1:
+        raise ValueError("cl must hold lmax + 1 values")
+    out = np.zeros(beta.size)
+    opt = PshtOptions(_WINDOW[window], float(kappa))
+    _check(lib().psht_predict_error(int(spin), int(lmax), float(theta_star), float(eps), ctypes.byref(opt),
+                                    ctypes.c_void_p(cl.ctypes.data), ctypes.c_void_p(beta.ctypes.data), beta.size,
+                                    ctypes.c_void_p(out.ctypes.data), _stream(stream)))
+    return out

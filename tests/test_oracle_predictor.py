@@ -1,0 +1,101 @@
+"""Pins of the oracle's error predictor (Sec. II.E) and of its Kaiser-Bessel bell (Sec. II.D), CPU.
+
+  * c_m: the rows of d^l(pi/2) are unit vectors, so sum_m c_m = sum_l C_l (2l+1)/2 exactly, and at
+    high m c_m approaches the flat-sky integral (1/pi) int_m^lmax dl C_l / sqrt(1 - (m/l)^2) that
+    eq. cm prints beside the exact sum;
+  * the predicted rms error agrees with the error the oracle pipeline actually makes (exact
+    evaluation, so the NUFFT plays no part) on Gaussian realisations of the same spectrum, with a
+    band limit lowered by kappa so that the apodisation error dominates rounding;
+  * the Kaiser-Bessel bell's Fourier transform equals the closed form Sec. II.D prints.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+
+def test_cm_sum_rule_and_flat_sky_limit():
+    lmax = 160
+    rng = np.random.default_rng(3)
+    cl = rng.uniform(0.5, 2.0, lmax + 1)
+    l = np.arange(lmax + 1)
+    for s in (0, 2):
+        c = O.great_circle_spectrum(lmax, s, cl)
+        assert abs(c.sum() - np.sum(cl[s:] * (2 * l[s:] + 1) / 2.0)) <= 1e-11 * c.sum()
+    c = O.great_circle_spectrum(lmax, 0, np.ones(lmax + 1))
+    for m in (lmax // 4, lmax // 2, 3 * lmax // 4):
+        flat = math.sqrt(lmax * lmax - m * m) / math.pi
+        assert abs(c[m + lmax] / flat - 1.0) < 0.05
+
+
+def test_spin_spectrum_is_symmetric_in_m_for_e_plus_b():
+    """|d^l_{-m,-s}| = |d^l_{m,s}|: for spin s the +m and -m powers are those of the two columns,
+    and for s = 0 they coincide."""
+    lmax = 64
+    cl = 1.0 / (np.arange(lmax + 1) + 1.0) ** 2
+    c0 = O.great_circle_spectrum(lmax, 0, cl)
+    assert np.allclose(c0, c0[::-1], rtol=1e-12, atol=0)
+
+
+def test_prediction_matches_pipeline_error():
+    lmax, s, eps, kappa = 96, 0, 1e-7, 0.8
+    ts = math.radians(25.0)
+    cl = np.ones(lmax + 1)
+    beta = np.linspace(0.5 * ts, ts, 6)
+    pred = O.predict_error(lmax, s, eps, ts, cl, beta, kappa=kappa)
+    rng = np.random.default_rng(5)
+    nphi = 24
+    th = np.repeat(beta, nphi)
+    ph = np.tile(np.linspace(0.0, 2.0 * math.pi, nphi, endpoint=False), beta.size)
+    P = O.plan_params(lmax, s, eps, np.concatenate([[ts], th]), kappa=kappa)
+    err2 = np.zeros(beta.size)
+    var = np.zeros(beta.size)
+    nreal = 6
+    for _ in range(nreal):
+        n = O.nalm(lmax)
+        g = O.canonical_alm(rng.standard_normal(n) + 1j * rng.standard_normal(n), lmax, s)
+        ref = O.direct_synthesis(lmax, s, g, None, th, ph)
+        got = O.pipeline_synthesis(P, g, None, th, ph, exact=True)
+        err2 += (np.abs(got - ref) ** 2).reshape(beta.size, nphi).mean(axis=1)
+        var += (np.abs(ref) ** 2).reshape(beta.size, nphi).mean(axis=1)
+    measured = np.sqrt(err2 / var)
+    assert pred.max() > 100 * eps  # the lowered band limit dominates
+    ratio = measured / pred
+    assert np.all(ratio > 0.5) and np.all(ratio < 2.0), ratio
+
+
+@pytest.mark.parametrize("k", [0.0, 1.5, 3.0, 6.9, 7.4, 12.0])
+def test_kaiser_bessel_fourier_transform(k):
+    """b~(k) = (pi a/sinh(pi a)) sinh(pi sqrt(a^2 - k^2)) / (pi sqrt(a^2 - k^2)) for the bell
+    b(Theta) ~ I0(pi a sqrt(1 - (Theta/pi)^2)) on [-pi, pi], normalised to unit area."""
+    eps = 1e-10
+    a = abs(math.log(eps)) / math.pi
+    x, w = np.polynomial.legendre.leggauss(400)
+    tau = 0.5 * math.pi * x  # Theta = pi sin(tau)
+    wt = 0.5 * math.pi * w
+    th = math.pi * np.sin(tau)
+    b = O.bell(th / math.pi, eps, "kb") * math.pi * np.cos(tau)
+    area = np.sum(wt * b)
+    num = np.sum(wt * b * np.cos(k * th)) / area
+
+    def shc(z2):  # sinh(pi sqrt(z2)) / (pi sqrt(z2)), continued to z2 < 0
+        if z2 > 0:
+            r = math.sqrt(z2)
+            return math.sinh(math.pi * r) / (math.pi * r)
+        if z2 < 0:
+            r = math.sqrt(-z2)
+            return math.sin(math.pi * r) / (math.pi * r)
+        return 1.0
+
+    ref = shc(a * a - k * k) / shc(a * a)
+    assert abs(num - ref) <= 1e-9 * max(1.0, abs(ref)) + 1e-13
+
+
+def test_kb_window_shape():
+    eps = 1e-8
+    dT = 0.3
+    Th = np.array([0.0, math.pi - dT - 1e-6, math.pi - 0.5 * dT, math.pi])
+    w = O.window(Th, dT, eps, "kb")
+    assert w[0] == 1.0 and w[1] == 1.0 and abs(w[2] - 0.5) < 1e-12 and w[3] < 1e-15
