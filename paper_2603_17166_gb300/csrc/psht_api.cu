@@ -314,7 +314,6 @@ size_t planned_bytes(const Plan& p) {
   b += (size_t)(p.nTheta + 2 * p.L + p.nphi) * (cb + 4);       // twiddles + permutations
   b += fft_scratch_elems(p) * cb;                              // long-FFT buffers
   b += (size_t)adj_part_elems(p) * rb;                         // one-warp adjoint partial sums
-  b += ((size_t)p.ntr * p.ntq * p.TR * p.TQ + 1) * 4;          // per-cell point offsets (spreading)
   // small tables: rings, seeds, ring ranges, deconvolution, weights, work items (upper bounds)
   b += (size_t)p.nring * (sizeof(RingDev) + rb) + (size_t)(p.lmax + 1) * (sizeof(MSeed) + 4 * sizeof(int2));
   b += (size_t)(2 * p.L + 2 * p.M + 2) * rb;
@@ -592,7 +591,11 @@ void run_synthesis(Plan& p, const void* g, const void* c, void* f, cudaStream_t 
 }
 
 void run_adjoint(Plan& p, const void* f, void* g, void* c, cudaStream_t st, double msc = 1.0) {
-  staged(p, 4, st, [&] { launch_scatter(p, f, st); });  // writes every grid cell
+  const size_t cb = p.prec == 64 ? 16 : 8;
+  staged(p, 4, st, [&] {
+    PSHT_CUDA_TRY(cudaMemsetAsync(p.d_G, 0, (size_t)p.nrows * p.gstride * cb, st));
+    launch_scatter(p, f, st);
+  });
   staged(p, 5, st, [&] { launch_phi_adjoint(p, st); });
   staged(p, 6, st, [&] { launch_theta_adjoint(p, st); });
   staged(p, 7, st, [&] { launch_rec_adjoint(p, g, c, st, msc); });

@@ -138,7 +138,6 @@ struct Plan {
   // points (sorted by tile)
   TileItem* d_titems = nullptr;
   int ntitems = 0;
-  int* d_keyofs = nullptr;      // first sorted point of every (tile, base cell) key, ntiles*TR*TQ + 1
   int32_t* d_pidx = nullptr;    // original index of sorted point
   int32_t* d_pcell = nullptr;   // (r0 - tile row origin) | (q0 + padq - tile col origin) << 16
   void* d_pw = nullptr;         // FP64 form: weights [2W][npts] (psi_r[i], then psi_q[k])

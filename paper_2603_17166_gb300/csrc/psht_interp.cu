@@ -20,8 +20,6 @@ namespace {
 
 constexpr int kBinThreads = 256;
 constexpr int kInterpThreads = 256;
-constexpr int kSpreadThreads = 512;  // one thread per cell of a kTileR x kTileQ output tile
-constexpr int kTileR = 16, kTileQ = 32;
 
 __device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
 
@@ -254,124 +252,94 @@ __global__ void __launch_bounds__(kInterpThreads) k_gather(const TileItem* __res
   }
 }
 
-// Spreading (transpose of k_gather) in output-stationary form: one CTA per output tile of TR x TQ
-// grid cells, one thread per cell.  A cell (i, q) receives f_p psi_r[i - r0] psi_q[q - q0] from every
-// point whose base cell (r0, q0) lies in [i-W+1, i] x [q-W+1, q], so the CTA gathers the points of
-// the base-cell region [R0-W+1, R0+TR) x [Q0-W+1, Q0+TQ), which spans at most four point tiles,
-// into shared memory ordered region row by region row (per row: left tile's cells, then this
-// tile's), with each point's kernel weights computed once.  Each thread then reads, for each of its
-// W base rows, the contiguous run of points of the W base cells to its left.  Every grid cell is
-// written exactly once: no clearing pass, no atomics, and a fixed summation order.
-template <typename T, int W>
-__global__ void __launch_bounds__(kSpreadThreads) k_spread(const int* __restrict__ keyofs,
-                                                           const int32_t* __restrict__ pidx,
-                                                           const double* __restrict__ pw,
-                                                           const float* __restrict__ pf, int64_t npts,
-                                                           const typename Cx<T>::V* __restrict__ f,
-                                                           typename Cx<T>::V* __restrict__ G, int nrows,
-                                                           int gstride, int ntr, int ntq, T beta, int batch) {
+// Spreading (transpose of k_gather).  Each warp owns a private copy of the tile; it spreads 32
+// consecutive (cell-sorted) points at a time, one per lane.  Lanes whose points share a base cell
+// take separate rounds, so within one window offset (a, b) all lanes write distinct cells; a
+// __syncwarp after every offset orders the read-modify-writes of successive offsets.  The warp
+// copies are summed at the end and added to the grid with one global atomic per nonzero cell.
+template <typename T, int W, int NT>
+__global__ void __launch_bounds__(NT) k_scatter(const TileItem* __restrict__ items, const int32_t* __restrict__ pidx,
+                                                const int32_t* __restrict__ pcell, const double* __restrict__ pw,
+                                                const float* __restrict__ pf, int64_t npts,
+                                                const typename Cx<T>::V* __restrict__ f,
+                                                typename Cx<T>::V* __restrict__ G, int nrows, int gstride, int TR,
+                                                int TQ, T beta) {
   using V = typename Cx<T>::V;
-  constexpr int TR = kTileR, TQ = kTileQ;
-  constexpr int RR = TR + W - 1, CC = TQ + W - 1, NREG = RR * CC;
-  static_assert(NREG <= 3 * kSpreadThreads, "region scan covers three cells per thread");
-  __shared__ int cofs[NREG + 1];  // region cell -> first staged index (exclusive prefix of counts)
-  __shared__ int gofs[NREG];      // region cell -> first sorted point index
-  __shared__ int wsum[kSpreadThreads / 32];
+  constexpr int NWARP = NT / 32;
   extern __shared__ __align__(16) unsigned char smraw[];
-  V* fv = reinterpret_cast<V*>(smraw);                                   // [batch]
-  T* wts = reinterpret_cast<T*>(smraw + sizeof(V) * batch);             // [batch][2W]: psi_r, psi_q
-  unsigned char* kap = smraw + (sizeof(V) + 2 * W * sizeof(T)) * batch;  // [batch] region column
-  const int tid = threadIdx.x;
-  const int R0 = blockIdx.y * TR, Q0 = blockIdx.x * TQ;
-
-  // point counts of the region's base cells, from the per-cell offsets of the binning sort
-  int cnt[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const int c = 3 * tid + k;
-    cnt[k] = 0;
-    if (c < NREG) {
-      const int rho = c / CC, kc = c - rho * CC;
-      const int dr = R0 - (W - 1) + rho, dq = Q0 - (W - 1) + kc;
-      int g0 = 0;
-      if (dr >= 0 && dq >= 0) {
-        const int tr = dr / TR, tq = dq / TQ;
-        if (tr < ntr && tq < ntq) {
-          const int64_t key = ((int64_t)(tr * ntq + tq) * TR + (dr - tr * TR)) * TQ + (dq - tq * TQ);
-          g0 = keyofs[key];
-          cnt[k] = keyofs[key + 1] - g0;
-        }
-      }
-      gofs[c] = g0;
-    }
-  }
-  // block exclusive scan of the counts (three consecutive cells per thread)
-  const int lane = tid & 31, warp = tid >> 5;
-  const int tot = cnt[0] + cnt[1] + cnt[2];
-  int incl = tot;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (lane == 31) wsum[warp] = incl;
+  V* tiles = reinterpret_cast<V*>(smraw);
+  const TileItem it = items[blockIdx.x];
+  const int pitch = TQ + W - 1, rows = TR + W - 1, cells = rows * pitch;
+  const int row0 = it.tr * TR, col0 = it.tq * TQ;
+  for (int e = threadIdx.x; e < NWARP * cells; e += NT) tiles[e] = mk((T)0, (T)0);
   __syncthreads();
-  if (warp == 0) {
-    int w = lane < kSpreadThreads / 32 ? wsum[lane] : 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  V* tw = tiles + warp * cells;
+  const unsigned lt = (1u << lane) - 1u;
+  // warp w takes a contiguous slice of the item's points; within it lane i takes points
+  // i*ngrp .. i*ngrp + ngrp-1, so the 32 points spread at once lie in different parts of the tile and
+  // rarely share a base cell (the cell-sorted order would put equal cells side by side)
+  const int per_w = (it.np + NWARP - 1) / NWARP;
+  const int w0 = it.p0 + warp * per_w;
+  const int wn = max(0, min(per_w, it.p0 + it.np - w0));
+  const int ngrp = (wn + 31) >> 5;
+  for (int gi = 0; gi < ngrp; ++gi) {
+    const int k = lane * ngrp + gi;
+    const int pt = w0 + k;
+    const bool valid = k < wn;
+    int lr = 0, lq = 0, key = -1 - lane;
+    T wr[W], wq[W];
+    V fv = mk((T)0, (T)0);
+    if (valid) {
+      const int cell = pcell[pt];
+      lr = cell & 0xffff;
+      lq = cell >> 16;
+      key = lr * pitch + lq;
+      Weights<T, W>::get(pw, pf, npts, pt, beta, wr, wq);
+      fv = f[pidx[pt]];
+    } else {
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += y;
+      for (int a = 0; a < W; ++a) wr[a] = wq[a] = (T)0;
     }
-    if (lane < kSpreadThreads / 32) wsum[lane] = w;
-  }
-  __syncthreads();
-  int run = incl - tot + (warp > 0 ? wsum[warp - 1] : 0);
+    const unsigned same = __match_any_sync(0xffffffffu, key);
+    const unsigned rank = __popc(same & lt);
+    const unsigned rounds = __reduce_max_sync(0xffffffffu, rank) + 1u;
+    for (unsigned rd = 0; rd < rounds; ++rd) {
+      const bool on = valid && rank == rd;
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const int c = 3 * tid + k;
-    if (c < NREG) cofs[c] = run;
-    run += cnt[k];
-  }
-  if (tid == kSpreadThreads - 1) cofs[NREG] = run;
-  __syncthreads();
-  const int total = cofs[NREG];
-
-  const int a = tid / TQ, b = tid - a * TQ;
-  const bool inside = (R0 + a < nrows) && (Q0 + b < gstride);
-  T accr = 0, acci = 0;
-  for (int B0 = 0; B0 < total; B0 += batch) {
-    const int B1 = min(total, B0 + batch);
-    if (B0 > 0) __syncthreads();  // the previous batch is consumed
-    for (int c = tid; c < NREG; c += kSpreadThreads) {
-      const int s0 = cofs[c], s1 = cofs[c + 1];
-      for (int sidx = max(s0, B0); sidx < min(s1, B1); ++sidx) {
-        const int gi = gofs[c] + (sidx - s0);
-        const int slot = sidx - B0;
-        fv[slot] = f[pidx[gi]];
-        Weights<T, W>::get(pw, pf, npts, gi, beta, wts + (size_t)slot * 2 * W, wts + (size_t)slot * 2 * W + W);
-        kap[slot] = (unsigned char)(c % CC);
-      }
-    }
-    __syncthreads();
-    if (inside) {
+      for (int a = 0; a < W; ++a) {
+        const T vr = wr[a] * fv.x, vi = wr[a] * fv.y;
+        V* tp = tw + (lr + a) * pitch + lq;
 #pragma unroll
-      for (int d = 0; d < W; ++d) {  // base row i - d is region row a + W - 1 - d
-        const int c0 = (a + W - 1 - d) * CC + b;  // base columns q-W+1 .. q are region columns b .. b+W-1
-        const int lo = max(cofs[c0], B0), hi = min(cofs[c0 + W], B1);
-        for (int sidx = lo; sidx < hi; ++sidx) {
-          const int slot = sidx - B0;
-          const int e = b + W - 1 - kap[slot];
-          const T* ws = wts + (size_t)slot * 2 * W;
-          const T w = ws[d] * ws[W + e];
-          const V x = fv[slot];
-          accr = fma(w, x.x, accr);
-          acci = fma(w, x.y, acci);
+        for (int b = 0; b < W; ++b) {
+          if (on) {
+            V x = tp[b];
+            x.x = fma(wq[b], vr, x.x);
+            x.y = fma(wq[b], vi, x.y);
+            tp[b] = x;
+          }
+          __syncwarp();
         }
       }
     }
   }
-  if (inside) G[(int64_t)(R0 + a) * gstride + Q0 + b] = mk(accr, acci);
+  __syncthreads();
+  for (int e = threadIdx.x; e < cells; e += NT) {
+    T vr = 0, vi = 0;
+#pragma unroll
+    for (int w = 0; w < NWARP; ++w) {
+      vr += tiles[w * cells + e].x;
+      vi += tiles[w * cells + e].y;
+    }
+    if (vr == (T)0 && vi == (T)0) continue;
+    const int rr = e / pitch, cc = e - rr * pitch;
+    const int gr = row0 + rr, gc = col0 + cc;
+    if (gr < nrows && gc < gstride) {
+      T* gp = reinterpret_cast<T*>(G + (int64_t)gr * gstride + gc);
+      atomicAdd(gp, vr);
+      atomicAdd(gp + 1, vi);
+    }
+  }
 }
 
 template <typename T, int W>
@@ -387,16 +355,13 @@ void run_gather(Plan& p, void* f, cudaStream_t st) {
 template <typename T, int W>
 void run_scatter(Plan& p, const void* f, cudaStream_t st) {
   using V = typename Cx<T>::V;
-  // staged points per batch: within 64 KB (FP32) / 96 KB (FP64) of shared memory per CTA
-  const size_t per_pt = sizeof(V) + 2 * W * sizeof(T) + 1;
-  const int batch = (int)(((sizeof(T) == 8 ? 96 : 64) * 1024) / per_pt) / 16 * 16;
-  const size_t smem = per_pt * batch + 16;
-  PSHT_CUDA_TRY(cudaFuncSetAttribute((const void*)k_spread<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  constexpr int NT = sizeof(T) == 8 ? 128 : 256;
+  const size_t smem = (size_t)(NT / 32) * (p.TR + W - 1) * (p.TQ + W - 1) * sizeof(V);
+  PSHT_CUDA_TRY(cudaFuncSetAttribute((const void*)k_scatter<T, W, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
-  const dim3 grid((p.gstride + kTileQ - 1) / kTileQ, (p.nrows + kTileR - 1) / kTileR);
-  k_spread<T, W><<<grid, kSpreadThreads, smem, st>>>(p.d_keyofs, p.d_pidx, (const double*)p.d_pw, p.d_pfrac,
-                                                     p.npts, (const V*)f, (V*)p.d_G, p.nrows, p.gstride, p.ntr,
-                                                     p.ntq, (T)p.beta_es, batch);
+  k_scatter<T, W, NT><<<p.ntitems, NT, smem, st>>>(p.d_titems, p.d_pidx, p.d_pcell, (const double*)p.d_pw,
+                                                   p.d_pfrac, p.npts, (const V*)f, (V*)p.d_G, p.nrows, p.gstride,
+                                                   p.TR, p.TQ, (T)p.beta_es);
 }
 
 template <typename T, bool GATHER>
@@ -462,11 +427,7 @@ void bin_points(Plan& p, const double* theta, const double* phi, cudaStream_t st
   const int64_t nsb = (nkeys + 1 + kScanBlock - 1) / kScanBlock;  // blocks of the scan over nkeys + 1 entries
   int *d_key = nullptr, *d_cnt = nullptr, *d_cur = nullptr, *d_bs = nullptr, *d_toff = nullptr;
   PSHT_CUDA_TRY(cudaMallocAsync((void**)&d_key, sizeof(int) * std::max<int64_t>(n, 1), st));
-  // the per-key offsets stay with the plan (the spreading kernel reads them)
-  PSHT_CUDA_TRY(cudaMalloc((void**)&d_cnt, sizeof(int) * (nkeys + 1)));
-  p.allocs.push_back(d_cnt);
-  p.bytes += sizeof(int) * (nkeys + 1);
-  p.d_keyofs = d_cnt;
+  PSHT_CUDA_TRY(cudaMallocAsync((void**)&d_cnt, sizeof(int) * (nkeys + 1), st));
   PSHT_CUDA_TRY(cudaMallocAsync((void**)&d_cur, sizeof(int) * nkeys, st));
   PSHT_CUDA_TRY(cudaMallocAsync((void**)&d_bs, sizeof(int) * std::max<int64_t>(nsb, 1), st));
   PSHT_CUDA_TRY(cudaMallocAsync((void**)&d_toff, sizeof(int) * (ntiles + 1), st));
@@ -514,6 +475,7 @@ void bin_points(Plan& p, const double* theta, const double* phi, cudaStream_t st
                                                (double*)p.d_pw, p.d_pfrac, p.beta_es);
   PSHT_CUDA_TRY(cudaGetLastError());
   PSHT_CUDA_TRY(cudaFreeAsync(d_key, st));
+  PSHT_CUDA_TRY(cudaFreeAsync(d_cnt, st));
   PSHT_CUDA_TRY(cudaFreeAsync(d_cur, st));
   PSHT_CUDA_TRY(cudaFreeAsync(d_bs, st));
   PSHT_CUDA_TRY(cudaFreeAsync(d_toff, st));
@@ -528,7 +490,7 @@ void launch_gather(Plan& p, void* f, cudaStream_t st) {
 }
 
 void launch_scatter(Plan& p, const void* f, cudaStream_t st) {
-  PSHT_REQUIRE(p.TR == kTileR && p.TQ == kTileQ, PSHT_ECUDA, "internal: tile shape differs from the spreading kernel's");
+  if (p.ntitems == 0) return;
   if (p.prec == 64) dispatch_w<double, false>(p, const_cast<void*>(f), st);
   else dispatch_w<float, false>(p, const_cast<void*>(f), st);
   PSHT_CUDA_TRY(cudaGetLastError());
