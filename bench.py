@@ -178,7 +178,9 @@ def run_ours(args, rank, world, local_rank):
     phi = torch.from_numpy(wl["phi"]).to(dev)
     stream = torch.cuda.current_stream(dev)
     results = {}
-    launches_per_step = 8
+    # kernels of one FP32 step: recursion, Theta FFT, phi FFT, gather; scatter, phi FFT, Theta FFT,
+    # adjoint recursion and its per-order reduction (the grid clearing is a memset, not a kernel)
+    launches_per_step = 9
     want = set(args.forms.split(","))
     forms = [f for f in (("fp32", EPS32, args.steps), ("fp64", EPS64, max(1, args.steps64))) if f[0] in want]
     if not forms or forms[0][0] != "fp32":
