@@ -141,10 +141,19 @@ __global__ void __launch_bounds__(kFftThreads) k_phi_syn(const typename Cx<T>::V
   fft_dit<true>(buf, fP, twP);
   V* Gr = G + (int64_t)row * gstride;
   const int nq = nphi + 2 * padq;
-  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-    int src = (q - padq) % nphi;  // the halo may wrap more than once when nphi < padq
-    if (src < 0) src += nphi;
-    Gr[q] = buf[src];
+  if (nphi >= 2 * padq) {  // each halo wraps once
+#pragma unroll 4
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+      int src = q - padq;
+      src += src < 0 ? nphi : (src >= nphi ? -nphi : 0);
+      Gr[q] = buf[src];
+    }
+  } else {
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+      int src = (q - padq) % nphi;  // the halo may wrap more than once when nphi < padq
+      if (src < 0) src += nphi;
+      Gr[q] = buf[src];
+    }
   }
   for (int q = nq + threadIdx.x; q < gstride; q += blockDim.x) Gr[q] = mk((T)0, (T)0);
   __syncthreads();  // buf is reused by the next row
@@ -170,10 +179,20 @@ __global__ void __launch_bounds__(kFftThreads) k_phi_adj(const typename Cx<T>::V
   const V* Gr = G + (int64_t)row * gstride;
   // fold every stored column qs (true column qs - padq) onto q = (qs - padq) mod nphi
   const int nq = nphi + 2 * padq;
-  for (int q = threadIdx.x; q < nphi; q += blockDim.x) {
-    V v = mk((T)0, (T)0);
-    for (int qs = (q + padq) % nphi; qs < nq; qs += nphi) v = cadd(v, Gr[qs]);
-    buf[q] = v;
+  if (nphi >= 2 * padq) {  // each halo wraps once: a main load plus at most one halo load per q
+#pragma unroll 4
+    for (int q = threadIdx.x; q < nphi; q += blockDim.x) {
+      V v = Gr[q + padq];
+      if (q < padq) v = cadd(v, Gr[q + padq + nphi]);
+      if (q >= nphi - padq) v = cadd(v, Gr[q + padq - nphi]);
+      buf[q] = v;
+    }
+  } else {
+    for (int q = threadIdx.x; q < nphi; q += blockDim.x) {
+      V v = mk((T)0, (T)0);
+      for (int qs = (q + padq) % nphi; qs < nq; qs += nphi) v = cadd(v, Gr[qs]);
+      buf[q] = v;
+    }
   }
   __syncthreads();
   fft_dif<false>(buf, fP, twP);
