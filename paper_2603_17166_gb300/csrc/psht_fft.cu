@@ -22,17 +22,21 @@ constexpr int kFftThreads = 512;
 constexpr int kMaxLenF64 = 14336;  // complex128 elements in 224 KiB of shared memory
 constexpr int kMaxLenF32 = 28672;  // complex64
 // |n| <= L-1 values held per thread while the buffer is re-laid out (2L <= max length / 2)
+// threads of the Theta kernels per launch mode (see k_theta_syn)
+__host__ __device__ constexpr int theta_threads(int mode) { return mode == 1 ? 256 : kFftThreads; }
+
 template <typename T>
 struct QPer {
   static constexpr int v = ((sizeof(T) == 8 ? kMaxLenF64 : kMaxLenF32) / 2 + kFftThreads - 1) / kFftThreads;
 };
 
-// GM = false: one CTA per column, the transform in shared memory.  GM = true (lengths beyond
-// shared memory): gridDim.x CTAs loop over the columns, each with its own slice of a global
-// scratch array (4L + 2L elements: the transform, then the staged |n| <= L-1 values), which the
-// L2 cache holds while the CTA works on it.
-template <typename T, bool GM>
-__global__ void __launch_bounds__(kFftThreads) k_theta_syn(const typename Cx<T>::V* __restrict__ F, int Lpad,
+// MODE 1: one CTA of 256 threads per column, the transform in shared memory and the |n| <= L-1
+// values staged behind it (4L + 2L elements).  MODE 0 (when 6L elements exceed shared memory): 512
+// threads, the 4L-element transform in shared memory and those values held in registers between
+// the two transforms.  MODE 2 (lengths beyond shared memory): gridDim.x CTAs loop over the columns,
+// each with its own 6L-element slice of a global scratch array, which the L2 cache holds.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(theta_threads(MODE)) k_theta_syn(const typename Cx<T>::V* __restrict__ F, int Lpad,
                                                            const T* __restrict__ w, int nring,
                                                            const int2* __restrict__ mrange, int mstride, int s, int L,
                                                            const T* __restrict__ sT, const T* __restrict__ sP, int M,
@@ -43,6 +47,8 @@ __global__ void __launch_bounds__(kFftThreads) k_theta_syn(const typename Cx<T>:
                                                            typename Cx<T>::V* __restrict__ X, int ncols,
                                                            typename Cx<T>::V* __restrict__ scratch) {
   using V = typename Cx<T>::V;
+  constexpr bool GM = MODE == 2;   // global buffers, columns looped over a persistent grid
+  constexpr bool STG = MODE != 0;  // |n| <= L-1 values staged behind the transform, not in registers
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N2 = 2 * L, N4 = 4 * L;
   V* buf = GM ? scratch + (int64_t)blockIdx.x * (N4 + N2) : reinterpret_cast<V*>(smraw);
@@ -66,7 +72,7 @@ __global__ void __launch_bounds__(kFftThreads) k_theta_syn(const typename Cx<T>:
   fft_dif<false>(buf, f2L, tw2L);
   // collect b[n] = H[n] sT(n) sP(m), |n| <= L-1, then lay them out for the inverse DIT of length 4L
   const T sp = sP[m + M];
-  if constexpr (GM) {
+  if constexpr (STG) {
     V* stg = buf + N4;
     for (int i = threadIdx.x; i < N2 - 1; i += blockDim.x) {
       const int n = i - (L - 1);
@@ -210,8 +216,8 @@ __global__ void __launch_bounds__(kFftThreads) k_phi_adj(const typename Cx<T>::V
   }
 }
 
-template <typename T, bool GM>
-__global__ void __launch_bounds__(kFftThreads) k_theta_adj(const typename Cx<T>::V* __restrict__ X, int ncols,
+template <typename T, int MODE>
+__global__ void __launch_bounds__(theta_threads(MODE)) k_theta_adj(const typename Cx<T>::V* __restrict__ X, int ncols,
                                                            int r_lo, int nrows, const T* __restrict__ w, int nring,
                                                            int s, int L, const T* __restrict__ sT,
                                                            const T* __restrict__ sP, int M, FftDev f2L,
@@ -222,6 +228,8 @@ __global__ void __launch_bounds__(kFftThreads) k_theta_adj(const typename Cx<T>:
                                                            typename Cx<T>::V* __restrict__ Ft, int Lpad,
                                                            typename Cx<T>::V* __restrict__ scratch) {
   using V = typename Cx<T>::V;
+  constexpr bool GM = MODE == 2;   // global buffers, columns looped over a persistent grid
+  constexpr bool STG = MODE != 0;  // |n| <= L-1 values staged behind the transform, not in registers
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N2 = 2 * L, N4 = 4 * L;
   V* buf = GM ? scratch + (int64_t)blockIdx.x * (N4 + N2) : reinterpret_cast<V*>(smraw);
@@ -239,7 +247,7 @@ __global__ void __launch_bounds__(kFftThreads) k_theta_adj(const typename Cx<T>:
   __syncthreads();
   fft_dif<false>(buf, f4L, tw4L);
   const T sp = sP[m + M];
-  if constexpr (GM) {
+  if constexpr (STG) {
     V* stg = buf + N4;
     for (int i = threadIdx.x; i < N2 - 1; i += blockDim.x) {
       const int n = i - (L - 1);
@@ -322,6 +330,7 @@ int max_fft_len(int prec) { return prec == 64 ? kMaxLenF64 : kMaxLenF32; }
 // Lengths above one CTA's shared memory run in global-buffer mode on a persistent grid.
 namespace {
 constexpr int kGmCtas = 152 * 4;
+constexpr size_t kMaxSmem = 227 * 1024;  // dynamic shared memory one CTA may use
 bool theta_gm(const Plan& p) { return 4 * p.L > max_fft_len(p.prec); }
 bool phi_gm(const Plan& p) { return p.nphi > max_fft_len(p.prec); }
 }  // namespace
@@ -333,14 +342,21 @@ size_t fft_scratch_elems(const Plan& p) {
   return e;
 }
 
+// launch mode of the Theta kernels: 2 global buffers, 1 shared memory with staging, 0 registers
+template <typename T>
+int theta_mode(const Plan& p) {
+  if (theta_gm(p)) return 2;
+  return (size_t)6 * p.L * sizeof(typename Cx<T>::V) <= kMaxSmem ? 1 : 0;
+}
+
 template <typename T>
 void theta_syn_t(Plan& p, cudaStream_t st) {
   using V = typename Cx<T>::V;
-  const bool gm = theta_gm(p);
-  const size_t smem = gm ? 0 : (size_t)4 * p.L * sizeof(V);
-  const auto fn = gm ? k_theta_syn<T, true> : k_theta_syn<T, false>;
-  if (!gm) set_smem<T>((const void*)fn, smem);
-  fn<<<gm ? std::min(p.ncols, kGmCtas) : p.ncols, kFftThreads, smem, st>>>(
+  const int mode = theta_mode<T>(p);
+  const size_t smem = mode == 2 ? 0 : (size_t)(mode == 1 ? 6 : 4) * p.L * sizeof(V);
+  const auto fn = mode == 2 ? k_theta_syn<T, 2> : (mode == 1 ? k_theta_syn<T, 1> : k_theta_syn<T, 0>);
+  if (mode != 2) set_smem<T>((const void*)fn, smem);
+  fn<<<mode == 2 ? std::min(p.ncols, kGmCtas) : p.ncols, theta_threads(mode), smem, st>>>(
       (const V*)p.d_F, p.Lpad, (const T*)p.d_w, p.nring, p.d_mrange, p.lmax + 1, p.spin, p.L, (const T*)p.d_sT,
       (const T*)p.d_sP, p.M, p.f2L, (const V*)p.d_tw2L, p.d_perm2L, p.f4L, (const V*)p.d_tw4L, p.d_perm4L, p.r_lo,
       p.nrows, (V*)p.d_X, p.ncols, (V*)p.d_fscratch);
@@ -349,11 +365,11 @@ void theta_syn_t(Plan& p, cudaStream_t st) {
 template <typename T>
 void theta_adj_t(Plan& p, cudaStream_t st) {
   using V = typename Cx<T>::V;
-  const bool gm = theta_gm(p);
-  const size_t smem = gm ? 0 : (size_t)4 * p.L * sizeof(V);
-  const auto fn = gm ? k_theta_adj<T, true> : k_theta_adj<T, false>;
-  if (!gm) set_smem<T>((const void*)fn, smem);
-  fn<<<gm ? std::min(p.ncols, kGmCtas) : p.ncols, kFftThreads, smem, st>>>(
+  const int mode = theta_mode<T>(p);
+  const size_t smem = mode == 2 ? 0 : (size_t)(mode == 1 ? 6 : 4) * p.L * sizeof(V);
+  const auto fn = mode == 2 ? k_theta_adj<T, 2> : (mode == 1 ? k_theta_adj<T, 1> : k_theta_adj<T, 0>);
+  if (mode != 2) set_smem<T>((const void*)fn, smem);
+  fn<<<mode == 2 ? std::min(p.ncols, kGmCtas) : p.ncols, theta_threads(mode), smem, st>>>(
       (const V*)p.d_X, p.ncols, p.r_lo, p.nrows, (const T*)p.d_w, p.nring, p.spin, p.L, (const T*)p.d_sT,
       (const T*)p.d_sP, p.M, p.f2L, (const V*)p.d_tw2L, p.d_perm2L, p.f4L, (const V*)p.d_tw4L, p.d_perm4L,
       (V*)p.d_F, p.Lpad, (V*)p.d_fscratch);
