@@ -20,7 +20,6 @@ namespace {
 
 constexpr int kBinThreads = 256;
 constexpr int kInterpThreads = 256;
-constexpr bool kScatterAtomic = false;  // true: shared-memory atomic adds into one tile per CTA
 
 __device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
 
@@ -253,14 +252,12 @@ __global__ void __launch_bounds__(kInterpThreads) k_gather(const TileItem* __res
   }
 }
 
-// Spreading (transpose of k_gather).  Each warp spreads 32 of the item's points at a time, one per
-// lane, taken strided through the warp's slice of the cell-sorted points so that they lie in
-// different parts of the tile.  ATOM: all warps add into one shared tile with shared-memory atomic
-// adds.  Otherwise each warp owns a private copy of the tile; lanes whose points share a base cell
-// take separate rounds, so within one window offset (a, b) all lanes write distinct cells, and a
-// __syncwarp after every offset orders the read-modify-writes of successive offsets.  The tile
+// Spreading (transpose of k_gather).  Each warp owns a private copy of the tile; it spreads 32
+// consecutive (cell-sorted) points at a time, one per lane.  Lanes whose points share a base cell
+// take separate rounds, so within one window offset (a, b) all lanes write distinct cells; a
+// __syncwarp after every offset orders the read-modify-writes of successive offsets.  The warp
 // copies are summed at the end and added to the grid with one global atomic per nonzero cell.
-template <typename T, int W, int NT, bool ATOM>
+template <typename T, int W, int NT>
 __global__ void __launch_bounds__(NT) k_scatter(const TileItem* __restrict__ items, const int32_t* __restrict__ pidx,
                                                 const int32_t* __restrict__ pcell, const double* __restrict__ pw,
                                                 const float* __restrict__ pf, int64_t npts,
@@ -269,16 +266,15 @@ __global__ void __launch_bounds__(NT) k_scatter(const TileItem* __restrict__ ite
                                                 int TQ, T beta) {
   using V = typename Cx<T>::V;
   constexpr int NWARP = NT / 32;
-  constexpr int NTILE = ATOM ? 1 : NWARP;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* tiles = reinterpret_cast<V*>(smraw);
   const TileItem it = items[blockIdx.x];
   const int pitch = TQ + W - 1, rows = TR + W - 1, cells = rows * pitch;
   const int row0 = it.tr * TR, col0 = it.tq * TQ;
-  for (int e = threadIdx.x; e < NTILE * cells; e += NT) tiles[e] = mk((T)0, (T)0);
+  for (int e = threadIdx.x; e < NWARP * cells; e += NT) tiles[e] = mk((T)0, (T)0);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  V* tw = tiles + (ATOM ? 0 : warp) * cells;
+  V* tw = tiles + warp * cells;
   const unsigned lt = (1u << lane) - 1u;
   // warp w takes a contiguous slice of the item's points; within it lane i takes points
   // i*ngrp .. i*ngrp + ngrp-1, so the 32 points spread at once lie in different parts of the tile and
@@ -304,21 +300,6 @@ __global__ void __launch_bounds__(NT) k_scatter(const TileItem* __restrict__ ite
     } else {
 #pragma unroll
       for (int a = 0; a < W; ++a) wr[a] = wq[a] = (T)0;
-    }
-    if (ATOM) {
-      if (valid) {
-#pragma unroll
-        for (int a = 0; a < W; ++a) {
-          const T vr = wr[a] * fv.x, vi = wr[a] * fv.y;
-          T* tp = reinterpret_cast<T*>(tw + (lr + a) * pitch + lq);
-#pragma unroll
-          for (int b = 0; b < W; ++b) {
-            atomicAdd(tp + 2 * b, wq[b] * vr);
-            atomicAdd(tp + 2 * b + 1, wq[b] * vi);
-          }
-        }
-      }
-      continue;
     }
     const unsigned same = __match_any_sync(0xffffffffu, key);
     const unsigned rank = __popc(same & lt);
@@ -346,7 +327,7 @@ __global__ void __launch_bounds__(NT) k_scatter(const TileItem* __restrict__ ite
   for (int e = threadIdx.x; e < cells; e += NT) {
     T vr = 0, vi = 0;
 #pragma unroll
-    for (int w = 0; w < NTILE; ++w) {
+    for (int w = 0; w < NWARP; ++w) {
       vr += tiles[w * cells + e].x;
       vi += tiles[w * cells + e].y;
     }
@@ -375,13 +356,12 @@ template <typename T, int W>
 void run_scatter(Plan& p, const void* f, cudaStream_t st) {
   using V = typename Cx<T>::V;
   constexpr int NT = sizeof(T) == 8 ? 128 : 256;
-  constexpr bool ATOM = kScatterAtomic;
-  const size_t smem = (size_t)(ATOM ? 1 : NT / 32) * (p.TR + W - 1) * (p.TQ + W - 1) * sizeof(V);
-  PSHT_CUDA_TRY(cudaFuncSetAttribute((const void*)k_scatter<T, W, NT, ATOM>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_scatter<T, W, NT, ATOM><<<p.ntitems, NT, smem, st>>>(p.d_titems, p.d_pidx, p.d_pcell, (const double*)p.d_pw,
-                                                         p.d_pfrac, p.npts, (const V*)f, (V*)p.d_G, p.nrows,
-                                                         p.gstride, p.TR, p.TQ, (T)p.beta_es);
+  const size_t smem = (size_t)(NT / 32) * (p.TR + W - 1) * (p.TQ + W - 1) * sizeof(V);
+  PSHT_CUDA_TRY(cudaFuncSetAttribute((const void*)k_scatter<T, W, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+  k_scatter<T, W, NT><<<p.ntitems, NT, smem, st>>>(p.d_titems, p.d_pidx, p.d_pcell, (const double*)p.d_pw,
+                                                   p.d_pfrac, p.npts, (const V*)f, (V*)p.d_G, p.nrows, p.gstride,
+                                                   p.TR, p.TQ, (T)p.beta_es);
 }
 
 template <typename T, bool GATHER>
