@@ -236,6 +236,42 @@ __device__ __forceinline__ int fft_pos(const FftDev& f, int k) {
   return p;
 }
 
+// ---------------------------------------------------------------------------------------------
+// mbarrier + bulk copy helpers (inline PTX): a single thread arms the barrier with the expected
+// byte count and issues cp.async.bulk; consumers wait on the barrier's phase parity, for at most
+// kSpinLimit polls, after which the caller records a status and leaves instead of hanging.
+constexpr int kSpinLimit = 1 << 26;
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: false after kSpinLimit polls (the caller reports it and leaves)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (int i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
 // m of column index mi: 0 -> 0, 2m -> +m, 2m-1 -> -m
 __device__ __forceinline__ int col_m(int mi) { return (mi == 0) ? 0 : ((mi & 1) ? -((mi + 1) >> 1) : (mi >> 1)); }
 __device__ __forceinline__ int col_of(int m) { return m >= 0 ? 2 * m : -2 * m - 1; }
