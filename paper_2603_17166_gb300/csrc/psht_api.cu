@@ -332,6 +332,8 @@ void destroy(Plan* p) {
     cudaEventDestroy(r.b);
   }
   for (cudaEvent_t e : p->evpool) cudaEventDestroy(e);
+  for (cudaEvent_t e : p->chunk_ev) cudaEventDestroy(e);
+  if (p->copy_st) cudaStreamDestroy(p->copy_st);
   delete p;
 }
 
@@ -475,6 +477,28 @@ Plan* create(int spin, int lmax, const double* theta, const double* phi, int64_t
       p->d_aitems = ai.empty() ? nullptr : (AdjItem*)upload(*p, ai, st);
       p->d_aspan = (int2*)upload(*p, span, st);
       p->d_part = dalloc(*p, (size_t)std::max<int64_t>(off, 1) * (prec == 64 ? 8 : 4));
+      // order chunks for the host-buffer entry points: kChunks ranges of m with about equal
+      // recursion work (ring count x l range of the synthesis items), split at order boundaries
+      constexpr int kChunks = 8;
+      std::vector<double> cum(items.size() + 1, 0.0);
+      for (size_t i = 0; i < items.size(); ++i)
+        cum[i + 1] = cum[i] + (double)items[i].nj * (lmax - std::max(items[i].m, spin) + 1);
+      p->chunk_m.assign(1, 0);
+      for (int k = 1; k < kChunks; ++k) {
+        const double target = cum.back() * k / kChunks;
+        size_t i = std::lower_bound(cum.begin(), cum.end(), target) - cum.begin();
+        if (i >= items.size()) break;
+        const int mb = items[i].m;
+        if (mb > p->chunk_m.back()) p->chunk_m.push_back(mb);
+      }
+      p->chunk_m.push_back(p->M + 1);
+      for (int mb : p->chunk_m) {
+        int it = 0, ia = 0;
+        while (it < (int)items.size() && items[it].m < mb) ++it;
+        while (ia < (int)ai.size() && ai[ia].m < mb) ++ia;
+        p->chunk_item.push_back(it);
+        p->chunk_aitem.push_back(ia);
+      }
     }
     // deconvolution tables, ring weights, FFT twiddles and digit-reversal tables
     static const Quad quad;
@@ -605,6 +629,80 @@ void ensure_io(Plan& p) {
   const size_t cb = p.prec == 64 ? 16 : 8;
   if (!p.d_io_a) p.d_io_a = dalloc(p, 2 * (size_t)p.nalm * cb);
   if (!p.d_io_f) p.d_io_f = dalloc(p, (size_t)std::max<int64_t>(p.npts, 1) * cb);
+  if (!p.chunk_m.empty() && !p.copy_st) {
+    PSHT_CUDA_TRY(cudaStreamCreateWithFlags(&p.copy_st, cudaStreamNonBlocking));
+    p.chunk_ev.resize(p.chunk_m.size() + 1);
+    for (auto& e : p.chunk_ev) PSHT_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+}
+
+// first packed index of order m (orders m' < m hold lmax - m' + 1 entries each); nalm at m = lmax + 1
+int64_t alm_off(int lmax, int m) { return (int64_t)m * (2 * lmax + 3 - m) / 2; }
+
+// Host-buffer synthesis with the a_lm upload overlapping the recursion: the orders of chunk k are
+// copied on the copy stream and the recursion items of those orders start as soon as they landed.
+void synthesis_host_chunked(Plan& p, const void* g, const void* c, void* f, cudaStream_t st) {
+  const size_t cb = p.prec == 64 ? 16 : 8, na = (size_t)p.nalm * cb;
+  char* da = (char*)p.d_io_a;
+  const int K = (int)p.chunk_m.size() - 1;
+  cudaEvent_t start = p.chunk_ev[K];
+  PSHT_CUDA_TRY(cudaEventRecord(start, st));  // earlier work on st may still read the staging
+  PSHT_CUDA_TRY(cudaStreamWaitEvent(p.copy_st, start, 0));
+  for (int k = 0; k < K; ++k) {
+    const size_t b0 = alm_off(p.lmax, p.chunk_m[k]) * cb, b1 = alm_off(p.lmax, p.chunk_m[k + 1]) * cb;
+    PSHT_CUDA_TRY(cudaMemcpyAsync(da + b0, (const char*)g + b0, b1 - b0, cudaMemcpyHostToDevice, p.copy_st));
+    if (c) PSHT_CUDA_TRY(cudaMemcpyAsync(da + na + b0, (const char*)c + b0, b1 - b0, cudaMemcpyHostToDevice, p.copy_st));
+    PSHT_CUDA_TRY(cudaEventRecord(p.chunk_ev[k], p.copy_st));
+  }
+  staged(p, 0, st, [&] {
+    for (int k = 0; k < K; ++k) {
+      PSHT_CUDA_TRY(cudaStreamWaitEvent(st, p.chunk_ev[k], 0));
+      p.r_item0 = p.chunk_item[k];
+      p.r_item1 = p.chunk_item[k + 1];
+      launch_rec_synthesis(p, da, c ? da + na : nullptr, st);
+    }
+    p.r_item0 = 0;
+    p.r_item1 = -1;
+  });
+  staged(p, 1, st, [&] { launch_theta_synthesis(p, st); });
+  staged(p, 2, st, [&] { launch_phi_synthesis(p, st); });
+  staged(p, 3, st, [&] { launch_gather(p, p.d_io_f, st); });
+  PSHT_CUDA_TRY(cudaMemcpyAsync(f, p.d_io_f, (size_t)p.npts * cb, cudaMemcpyDeviceToHost, st));
+}
+
+// Host-buffer adjoint with the download overlapping the recursion: after the recursion items and
+// the reduction of the orders of chunk k, their g~ and c~ go to the host on the copy stream.
+void adjoint_host_chunked(Plan& p, const void* f, void* g, void* c, cudaStream_t st) {
+  const size_t cb = p.prec == 64 ? 16 : 8, na = (size_t)p.nalm * cb;
+  char* da = (char*)p.d_io_a;
+  const int K = (int)p.chunk_m.size() - 1;
+  PSHT_CUDA_TRY(cudaMemcpyAsync(p.d_io_f, f, (size_t)p.npts * cb, cudaMemcpyHostToDevice, st));
+  staged(p, 4, st, [&] {
+    PSHT_CUDA_TRY(cudaMemsetAsync(p.d_G, 0, (size_t)p.nrows * p.gstride * cb, st));
+    launch_scatter(p, p.d_io_f, st);
+  });
+  staged(p, 5, st, [&] { launch_phi_adjoint(p, st); });
+  staged(p, 6, st, [&] { launch_theta_adjoint(p, st); });
+  staged(p, 7, st, [&] {
+    for (int k = 0; k < K; ++k) {
+      p.r_aitem0 = p.chunk_aitem[k];
+      p.r_aitem1 = p.chunk_aitem[k + 1];
+      p.r_m0 = p.chunk_m[k];
+      p.r_m1 = k + 1 < K ? p.chunk_m[k + 1] : p.lmax + 1;  // the last chunk also writes the zero orders
+      launch_rec_adjoint(p, da, c ? da + na : nullptr, st);
+      PSHT_CUDA_TRY(cudaEventRecord(p.chunk_ev[k], st));
+      PSHT_CUDA_TRY(cudaStreamWaitEvent(p.copy_st, p.chunk_ev[k], 0));
+      const size_t b0 = alm_off(p.lmax, p.r_m0) * cb, b1 = alm_off(p.lmax, p.r_m1) * cb;
+      PSHT_CUDA_TRY(cudaMemcpyAsync((char*)g + b0, da + b0, b1 - b0, cudaMemcpyDeviceToHost, p.copy_st));
+      if (c) PSHT_CUDA_TRY(cudaMemcpyAsync((char*)c + b0, da + na + b0, b1 - b0, cudaMemcpyDeviceToHost, p.copy_st));
+    }
+    p.r_aitem0 = 0;
+    p.r_aitem1 = -1;
+    p.r_m0 = 0;
+    p.r_m1 = -1;
+  });
+  PSHT_CUDA_TRY(cudaEventRecord(p.chunk_ev[K], p.copy_st));
+  PSHT_CUDA_TRY(cudaStreamWaitEvent(st, p.chunk_ev[K], 0));
 }
 
 }  // namespace
@@ -713,10 +811,14 @@ int psht_plan_synthesis_host(psht_plan* plan, const void* g, const void* c, void
     ensure_io(p);
     const size_t cb = p.prec == 64 ? 16 : 8, na = (size_t)p.nalm * cb;
     char* da = (char*)p.d_io_a;
-    PSHT_CUDA_TRY(cudaMemcpyAsync(da, g, na, cudaMemcpyHostToDevice, st));
-    if (c) PSHT_CUDA_TRY(cudaMemcpyAsync(da + na, c, na, cudaMemcpyHostToDevice, st));
-    run_synthesis(p, da, c ? da + na : nullptr, p.d_io_f, st);
-    PSHT_CUDA_TRY(cudaMemcpyAsync(f, p.d_io_f, (size_t)p.npts * cb, cudaMemcpyDeviceToHost, st));
+    if (!p.chunk_m.empty()) {
+      synthesis_host_chunked(p, g, c, f, st);
+    } else {
+      PSHT_CUDA_TRY(cudaMemcpyAsync(da, g, na, cudaMemcpyHostToDevice, st));
+      if (c) PSHT_CUDA_TRY(cudaMemcpyAsync(da + na, c, na, cudaMemcpyHostToDevice, st));
+      run_synthesis(p, da, c ? da + na : nullptr, p.d_io_f, st);
+      PSHT_CUDA_TRY(cudaMemcpyAsync(f, p.d_io_f, (size_t)p.npts * cb, cudaMemcpyDeviceToHost, st));
+    }
     PSHT_CUDA_TRY(cudaStreamSynchronize(st));
   });
 }
@@ -729,10 +831,14 @@ int psht_plan_adjoint_host(psht_plan* plan, const void* f, void* g, void* c, voi
     ensure_io(p);
     const size_t cb = p.prec == 64 ? 16 : 8, na = (size_t)p.nalm * cb;
     char* da = (char*)p.d_io_a;
-    PSHT_CUDA_TRY(cudaMemcpyAsync(p.d_io_f, f, (size_t)p.npts * cb, cudaMemcpyHostToDevice, st));
-    run_adjoint(p, p.d_io_f, da, c ? da + na : nullptr, st);
-    PSHT_CUDA_TRY(cudaMemcpyAsync(g, da, na, cudaMemcpyDeviceToHost, st));
-    if (c) PSHT_CUDA_TRY(cudaMemcpyAsync(c, da + na, na, cudaMemcpyDeviceToHost, st));
+    if (!p.chunk_m.empty()) {
+      adjoint_host_chunked(p, f, g, c, st);
+    } else {
+      PSHT_CUDA_TRY(cudaMemcpyAsync(p.d_io_f, f, (size_t)p.npts * cb, cudaMemcpyHostToDevice, st));
+      run_adjoint(p, p.d_io_f, da, c ? da + na : nullptr, st);
+      PSHT_CUDA_TRY(cudaMemcpyAsync(g, da, na, cudaMemcpyDeviceToHost, st));
+      if (c) PSHT_CUDA_TRY(cudaMemcpyAsync(c, da + na, na, cudaMemcpyDeviceToHost, st));
+    }
     PSHT_CUDA_TRY(cudaStreamSynchronize(st));
   });
 }

@@ -144,6 +144,13 @@ struct Plan {
   float* d_pfrac = nullptr;     // FP32 form: [2][npts] t - r0, u - q0
   void* d_io_a = nullptr;       // device staging for the host-buffer entry points (lazy)
   void* d_io_f = nullptr;
+  // host-buffer entry points: the recursions run in chunks of orders m so that the a_lm copies
+  // overlap them (FP32 form); chunk k covers m in [chunk_m[k], chunk_m[k+1])
+  std::vector<int> chunk_m, chunk_item, chunk_aitem;
+  cudaStream_t copy_st = nullptr;
+  std::vector<cudaEvent_t> chunk_ev;
+  // item and order ranges of the next recursion launch (-1: all); set only around chunked launches
+  int r_item0 = 0, r_item1 = -1, r_aitem0 = 0, r_aitem1 = -1, r_m0 = 0, r_m1 = -1;
   size_t bytes = 0;
   std::vector<void*> allocs;
   // stage timing (psht_plan_profile)

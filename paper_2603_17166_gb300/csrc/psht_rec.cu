@@ -1088,17 +1088,17 @@ __global__ void __launch_bounds__(32) k_rec_adj_w(const AdjItem* __restrict__ it
   }
 }
 
-// Sum of the adjoint items of order m (blockIdx.x) and the projection of the adjoint synthesis
+// Sum of the adjoint items of order m (m_first + blockIdx.x) and the projection of the adjoint synthesis
 // general formula: ut_{l,m} = -Qp, ut_{l,-m} = -(-1)^(m-s) Qm, g~ = (ut_lm + (-1)^m conj ut_{l,-m})/2,
 // c~ = (ut_lm - (-1)^m conj ut_{l,-m})/(2i); zero below l0 and for orders without active rings.
 template <typename T>
 __global__ void k_adj_reduce(const AdjItem* __restrict__ items, const int2* __restrict__ aspan,
                              const MSeed* __restrict__ mseed, const T* __restrict__ part, int lmax, int s, T msc,
-                             typename Cx<T>::V* __restrict__ gt, typename Cx<T>::V* __restrict__ ct) {
+                             int m_first, typename Cx<T>::V* __restrict__ gt, typename Cx<T>::V* __restrict__ ct) {
   using V = typename Cx<T>::V;
   constexpr int kMaxItems = 64;
   __shared__ int64_t off[kMaxItems];
-  const int m = blockIdx.x;
+  const int m = m_first + blockIdx.x;
   const int2 sp = aspan[m];
   const int64_t base = alm_base(lmax, m);
   const int l0 = sp.y > 0 ? mseed[m].l0 : lmax + 1;
@@ -1139,9 +1139,11 @@ template <typename T, bool SPIN, int RPT>
 void launch_syn_t(Plan& p, const void* g, const void* c, double msc, cudaStream_t st) {
   using V = typename Cx<T>::V;
   if (p.syn_threads == 32) {  // one warp per item (items of at most 32 RPT rings)
-    k_rec_syn_w<T, SPIN, RPT, 32, 4><<<p.nitems, 32, 0, st>>>(
-        p.d_items, p.d_ring, p.d_mseed, (const TabEntry<T>*)p.d_rtab, (const V*)g, (const V*)c, p.lmax, p.spin,
-        (T)msc, (V*)p.d_F, p.Lpad, p.d_status);
+    const int i0 = p.r_item0, i1 = p.r_item1 < 0 ? p.nitems : p.r_item1;
+    if (i1 > i0)
+      k_rec_syn_w<T, SPIN, RPT, 32, 4><<<i1 - i0, 32, 0, st>>>(
+          p.d_items + i0, p.d_ring, p.d_mseed, (const TabEntry<T>*)p.d_rtab, (const V*)g, (const V*)c, p.lmax,
+          p.spin, (T)msc, (V*)p.d_F, p.Lpad, p.d_status);
     return;
   }
   k_rec_syn<T, SPIN, RPT, 128><<<p.nitems, 128, 0, st>>>(p.d_items, p.d_ring, p.d_mseed,
@@ -1152,12 +1154,15 @@ void launch_syn_t(Plan& p, const void* g, const void* c, double msc, cudaStream_
 template <typename T, bool SPIN, int RPT>
 void launch_adj_w(Plan& p, void* g, void* c, double msc, cudaStream_t st) {
   using V = typename Cx<T>::V;
-  if (p.naitems > 0)
-    k_rec_adj_w<T, SPIN, RPT, 32, 4><<<p.naitems, 32, 0, st>>>(p.d_aitems, p.d_ring, p.d_mseed,
-                                                                (const TabEntry<T>*)p.d_rtab, (const V*)p.d_F, p.Lpad,
-                                                                p.lmax, (T*)p.d_part, p.d_status);
-  k_adj_reduce<T><<<p.lmax + 1, 256, 0, st>>>(p.d_aitems, p.d_aspan, p.d_mseed, (const T*)p.d_part, p.lmax, p.spin,
-                                               (T)msc, (V*)g, (V*)c);
+  const int i0 = p.r_aitem0, i1 = p.r_aitem1 < 0 ? p.naitems : p.r_aitem1;
+  const int m0 = p.r_m0, m1 = p.r_m1 < 0 ? p.lmax + 1 : p.r_m1;
+  if (i1 > i0)
+    k_rec_adj_w<T, SPIN, RPT, 32, 4><<<i1 - i0, 32, 0, st>>>(p.d_aitems + i0, p.d_ring, p.d_mseed,
+                                                              (const TabEntry<T>*)p.d_rtab, (const V*)p.d_F, p.Lpad,
+                                                              p.lmax, (T*)p.d_part, p.d_status);
+  if (m1 > m0)
+    k_adj_reduce<T><<<m1 - m0, 256, 0, st>>>(p.d_aitems, p.d_aspan, p.d_mseed, (const T*)p.d_part, p.lmax, p.spin,
+                                             (T)msc, m0, (V*)g, (V*)c);
 }
 
 template <typename T, bool SPIN, int RPT, int NT>

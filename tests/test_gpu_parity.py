@@ -271,3 +271,31 @@ def test_block_adjoint_ring_chunks():
     lhs = O.map_dot(f, f)
     rhs = O.alm_dot(gt.cpu().numpy(), g, lmax) + O.alm_dot(ct.cpu().numpy(), c, lmax)
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+@pytest.mark.parametrize("prec,eps,s", [("fp32", 1e-5, 2), ("fp64", 1e-10, 2), ("fp32", 1e-5, 0)])
+def test_host_buffer_entry_points_match_device_ones(prec, eps, s):
+    """psht_plan_synthesis_host / _adjoint_host (host arrays in and out; the FP32 form runs the
+    recursions in chunks of orders so that the copies overlap them) give the device entry points'
+    results: synthesis bit for bit, the adjoint up to the scatter's atomic summation order."""
+    rng = np.random.default_rng(43)
+    lmax = 300
+    th, ph = _cap(rng, 20000, 0.5, "N")
+    g, c = _alm(rng, lmax, s), _alm(rng, lmax, s)
+    plan = _plan(s, lmax, th, ph, eps, prec)
+    cd = plan.np_cdtype
+    gh = np.ascontiguousarray(g.astype(cd))
+    ch = np.ascontiguousarray(c.astype(cd))
+    for rep in range(2):
+        fh = np.zeros(th.size, dtype=cd)
+        plan.synthesis_host(gh, ch, fh)
+        fd = plan.synthesis(_cu(g, plan), _cu(c, plan)).cpu().numpy()
+        assert np.array_equal(fh, fd)
+        gt_h = np.zeros(O.nalm(lmax), dtype=cd)
+        ct_h = np.zeros(O.nalm(lmax), dtype=cd)
+        plan.adjoint_host(fh, gt_h, ct_h)
+        gt_d, ct_d = plan.adjoint(torch.from_numpy(fh).cuda())
+        tol = 1e-12 if prec == "fp64" else 1e-5
+        for a, b in ((gt_h, gt_d), (ct_h, ct_d)):
+            b = b.cpu().numpy().astype(np.complex128)
+            assert O.alm_rel_l2(a.astype(np.complex128), b, lmax) <= tol
