@@ -636,6 +636,15 @@ void ensure_io(Plan& p) {
   }
 }
 
+// resets the plan's launch ranges on scope exit, also when a launch throws
+struct RangeReset {
+  Plan& p;
+  ~RangeReset() {
+    p.r_item0 = p.r_aitem0 = p.r_m0 = 0;
+    p.r_item1 = p.r_aitem1 = p.r_m1 = -1;
+  }
+};
+
 // first packed index of order m (orders m' < m hold lmax - m' + 1 entries each); nalm at m = lmax + 1
 int64_t alm_off(int lmax, int m) { return (int64_t)m * (2 * lmax + 3 - m) / 2; }
 
@@ -654,6 +663,7 @@ void synthesis_host_chunked(Plan& p, const void* g, const void* c, void* f, cuda
     if (c) PSHT_CUDA_TRY(cudaMemcpyAsync(da + na + b0, (const char*)c + b0, b1 - b0, cudaMemcpyHostToDevice, p.copy_st));
     PSHT_CUDA_TRY(cudaEventRecord(p.chunk_ev[k], p.copy_st));
   }
+  RangeReset reset{p};
   staged(p, 0, st, [&] {
     for (int k = 0; k < K; ++k) {
       PSHT_CUDA_TRY(cudaStreamWaitEvent(st, p.chunk_ev[k], 0));
@@ -683,6 +693,7 @@ void adjoint_host_chunked(Plan& p, const void* f, void* g, void* c, cudaStream_t
   });
   staged(p, 5, st, [&] { launch_phi_adjoint(p, st); });
   staged(p, 6, st, [&] { launch_theta_adjoint(p, st); });
+  RangeReset reset{p};
   staged(p, 7, st, [&] {
     for (int k = 0; k < K; ++k) {
       p.r_aitem0 = p.chunk_aitem[k];
