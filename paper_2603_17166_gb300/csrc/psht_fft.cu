@@ -216,73 +216,6 @@ __global__ void __launch_bounds__(kFftThreads) k_phi_adj(const typename Cx<T>::V
   }
 }
 
-// phi adjoint, FP32 rows streamed by bulk copies: one persistent CTA per SM with two row buffers, so
-// that while one row is folded, transformed and written out the next row's copy lands in the other
-// buffer.  The row is transformed in place at offset padq of its buffer after the two halos (which
-// lie outside that range) have been added onto the columns they wrap to.  Needs nphi >= 2 padq.
-__global__ void __launch_bounds__(kFftThreads) k_phi_adj_pipe(const float2* __restrict__ G, int gstride, int padq,
-                                                              FftDev fP, const float2* __restrict__ twP,
-                                                              const int* __restrict__ permP, float2* __restrict__ X,
-                                                              int ncols, int nrows, int nq_pad,
-                                                              int* __restrict__ status) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  float2* const row0 = reinterpret_cast<float2*>(smraw);
-  float2* const row1 = row0 + nq_pad;
-  __shared__ __align__(8) uint64_t bar[2];
-  __shared__ int sfail;
-  const int nphi = fP.n, nq = nphi + 2 * padq;
-  const uint32_t bytes = (uint32_t)nq * sizeof(float2);
-  if (threadIdx.x == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    fence_mbar_init();
-    sfail = 0;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0)
-    for (int k = 0; k < 2; ++k) {
-      const int r = blockIdx.x + k * gridDim.x;
-      if (r < nrows) {
-        mbar_expect_tx(&bar[k], bytes);
-        bulk_g2s(k ? row1 : row0, G + (int64_t)r * gstride, bytes, &bar[k]);
-      }
-    }
-  int k = 0;
-  for (int row = blockIdx.x; row < nrows; row += gridDim.x, ++k) {
-    const int sidx = k & 1;
-    float2* in = sidx ? row1 : row0;
-    if (!mbar_wait(&bar[sidx], (uint32_t)((k >> 1) & 1))) {
-      atomicExch(status, 1);
-      sfail = 1;
-    }
-    __syncthreads();
-    if (sfail) {
-      if (threadIdx.x == 0 && row + gridDim.x < nrows)  // drain the other buffer's copy
-        mbar_wait(&bar[sidx ^ 1], (uint32_t)(((k + 1) >> 1) & 1));
-      return;
-    }
-    float2* buf = in + padq;
-    for (int q = threadIdx.x; q < padq; q += blockDim.x) {
-      buf[q] = cadd(buf[q], in[q + padq + nphi]);                // right halo: true columns nphi + q
-      buf[nphi - padq + q] = cadd(buf[nphi - padq + q], in[q]);  // left halo: true columns q - padq
-    }
-    __syncthreads();
-    fft_dif<false>(buf, fP, twP);
-    float2* Xr = X + (int64_t)row * ncols;
-    for (int mi = threadIdx.x; mi < ncols; mi += blockDim.x) {
-      const int m = col_m(mi);
-      Xr[mi] = buf[permP[m < 0 ? m + nphi : m]];
-    }
-    __syncthreads();  // this buffer is free again
-    const int rn = row + 2 * gridDim.x;
-    if (threadIdx.x == 0 && rn < nrows) {
-      fence_proxy_async();
-      mbar_expect_tx(&bar[sidx], bytes);
-      bulk_g2s(in, G + (int64_t)rn * gstride, bytes, &bar[sidx]);
-    }
-  }
-}
-
 template <typename T, int MODE>
 __global__ void __launch_bounds__(theta_threads(MODE)) k_theta_adj(const typename Cx<T>::V* __restrict__ X, int ncols,
                                                            int r_lo, int nrows, const T* __restrict__ w, int nring,
@@ -397,7 +330,6 @@ int max_fft_len(int prec) { return prec == 64 ? kMaxLenF64 : kMaxLenF32; }
 // Lengths above one CTA's shared memory run in global-buffer mode on a persistent grid.
 namespace {
 constexpr int kGmCtas = 152 * 4;
-constexpr int kSms = 152;
 constexpr size_t kMaxSmem = 227 * 1024;  // dynamic shared memory one CTA may use
 bool theta_gm(const Plan& p) { return 4 * p.L > max_fft_len(p.prec); }
 bool phi_gm(const Plan& p) { return p.nphi > max_fft_len(p.prec); }
@@ -458,18 +390,6 @@ void phi_syn_t(Plan& p, cudaStream_t st) {
 template <typename T>
 void phi_adj_t(Plan& p, cudaStream_t st) {
   using V = typename Cx<T>::V;
-  if constexpr (sizeof(T) == 4) {
-    const int nq = p.nphi + 2 * p.padq, nq_pad = (nq + 1) & ~1;
-    const size_t smem = (size_t)2 * nq_pad * sizeof(V);
-    if (p.nphi >= 2 * p.padq && smem <= kMaxSmem) {
-      set_smem<T>((const void*)k_phi_adj_pipe, smem);
-      k_phi_adj_pipe<<<std::min(p.nrows, kSms), kFftThreads, smem, st>>>(
-          (const float2*)p.d_G, p.gstride, p.padq, p.fP, (const float2*)p.d_twP, p.d_permP, (float2*)p.d_X, p.ncols,
-          p.nrows, nq_pad, p.d_status);
-      PSHT_CUDA_TRY(cudaGetLastError());
-      return;
-    }
-  }
   const bool gm = phi_gm(p);
   const size_t smem = gm ? 0 : (size_t)p.nphi * sizeof(V);
   const auto fn = gm ? k_phi_adj<T, true> : k_phi_adj<T, false>;
