@@ -143,6 +143,24 @@ def alu_peak_tflops(prec: int) -> float:
 REC_ADJ_TRAFFIC = {"fp32": 380.160e6 + 570.136e6, "fp64": None}
 
 
+# ----------------------------------------------------------------------------- replicas
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The largest of every rank's x (the slowest replica's time); x itself on one rank."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(npts_per_rank: int, world: int, steps: int, ms_slowest: float) -> float:
+    """Whole-job Mpoints/s of `world` replicas, each doing `steps` steps over its own points, timed by
+    the slowest rank (weak scaling: the per-GPU work is fixed)."""
+    return world * npts_per_rank * steps / (ms_slowest * 1e-3) / 1e6
+
+
 # ----------------------------------------------------------------------------- our arm
 def flops_per_triple(spin: int) -> int:
     """Algorithmic FLOPs of one (ring, m, l) step: a three-term recurrence step for each of the
@@ -223,12 +241,9 @@ def run_ours(args, rank, world, local_rank):
         clocks = clk.stop()
         ms = e0.elapsed_time(e1)
         stages = plan.stage_times()
-        if dist is not None:
-            t = torch.tensor([ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dist, dev)
         ms_step = ms / K
-        value = world * npts * K / (ms * 1e-3) / 1e6
+        value = replica_throughput(npts, world, K, ms)
         # dominant kernel: the adjoint recursion k_rec_adj (its launches per adjoint call are
         # counted by the stage record; same algorithmic flops as the synthesis recursion)
         flops = info["recursion_triples"] * flops_per_triple(SPIN)
@@ -275,12 +290,9 @@ def run_ours(args, rank, world, local_rank):
             torch.cuda.synchronize(dev)
             el = time.perf_counter() - t0
             barrier()
-            if dist is not None:
-                t = torch.tensor([el], device=dev, dtype=torch.float64)
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                el = float(t.item())
+            el = max_over_ranks(el, dist, dev)
             cb = hf.itemsize
-            entry["e2e"] = dict(value=world * npts * K / el / 1e6, unit=UNIT,
+            entry["e2e"] = dict(value=replica_throughput(npts, world, K, el * 1e3), unit=UNIT,
                                 h2d_bytes_per_step=int(hg.nbytes + hc.nbytes + npts * cb),
                                 d2h_bytes_per_step=int(npts * cb + hgt.nbytes + hct.nbytes))
         # synthesis output at a fixed sample of points, checked against the oracle in the
