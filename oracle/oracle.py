@@ -79,6 +79,7 @@ def _lib():
         lib.orc_interp.argtypes = [L, P, P, I, D, L, L, L, P, P]
         lib.orc_spread.argtypes = [L, P, P, P, I, D, L, L, L, P, P]
         lib.orc_direct_adjoint_lm.argtypes = [I, L, P, P, P, I, P, P, P, P]
+        lib.orc_rotate_alm.argtypes = [I, D, D, D, P, I, P, P, P]
         lib.orc_num_threads.restype = I
         _lib_handle = lib
     return _lib_handle
@@ -212,6 +213,87 @@ def direct_adjoint_lm(s: int, theta, phi, f, ls, ms):
     _lib().orc_direct_adjoint_lm(s, theta.size, _ptr(theta), _ptr(phi), _ptr(f), ls.size, _ptr(ls), _ptr(ms),
                                  _ptr(gt), _ptr(ct))
     return gt, ct
+
+
+# ----------------------------------------------------------------------------- rotations
+# The paper centres the patch at the north pole (Sec. II, step 1) without saying how a caller's
+# a_lm get there.  These are the plain definitions of that change of frame: the Wigner-D
+# rotation of a coefficient set, the rotation of points, and the angle between the two frames'
+# local bases at each point, which a spin-s field picks up as a phase.
+def rotation_matrix(alpha: float, beta: float, gamma: float) -> np.ndarray:
+    """R = R_z(alpha) R_y(beta) R_z(gamma), active rotations of vectors (zyz Euler angles)."""
+    def rz(a):
+        return np.array([[math.cos(a), -math.sin(a), 0.0], [math.sin(a), math.cos(a), 0.0], [0.0, 0.0, 1.0]])
+
+    def ry(b):
+        return np.array([[math.cos(b), 0.0, math.sin(b)], [0.0, 1.0, 0.0], [-math.sin(b), 0.0, math.cos(b)]])
+
+    return rz(alpha) @ ry(beta) @ rz(gamma)
+
+
+def rotate_alm(lmax: int, a, alpha: float, beta: float, gamma: float) -> np.ndarray:
+    """a'_lm = sum_m' e^{-i m alpha} d^l_{m m'}(beta) e^{-i m' gamma} a_lm' for one real field's
+    packed set (m >= 0, a_{l,-m} = (-1)^m a*_lm): the field carried along by R(alpha, beta, gamma).
+    For a spin-s field synthesised from rotated g and c, f'(R p) = e^{-i s psi_p} f(p), psi_p from
+    ``rotate_points``."""
+    a = _c128(a)
+    out = np.zeros(nalm(lmax), dtype=np.complex128)
+    _lib().orc_rotate_alm(lmax, alpha, beta, gamma, _ptr(a), -1, None, None, _ptr(out))
+    return out
+
+
+def rotate_alm_lm(lmax: int, a, alpha: float, beta: float, gamma: float, ls, ms) -> np.ndarray:
+    """``rotate_alm`` at selected (l, m >= 0) only (O(l^2) each)."""
+    a = _c128(a)
+    ls = np.ascontiguousarray(ls, dtype=np.int32)
+    ms = np.ascontiguousarray(ms, dtype=np.int32)
+    out = np.zeros(ls.size, dtype=np.complex128)
+    _lib().orc_rotate_alm(lmax, alpha, beta, gamma, _ptr(a), int(ls.size), _ptr(ls), _ptr(ms), _ptr(out))
+    return out
+
+
+def _unit(theta, phi):
+    return np.stack([np.sin(theta) * np.cos(phi), np.sin(theta) * np.sin(phi), np.cos(theta)], axis=-1)
+
+
+def rotate_points(alpha: float, beta: float, gamma: float, theta, phi):
+    """n_p = R p for points p = (theta, phi): returns (theta', phi' in [0, 2pi), psi), where psi is
+    the angle from e_theta(p) towards e_phi(p) of the rotated frame's e_theta at n_p carried back by
+    R^-1, so that a spin-s field in the two frames' local bases satisfies f(p) = e^{i s psi} f'(n_p)."""
+    theta = np.asarray(theta, dtype=np.float64)
+    phi = np.asarray(phi, dtype=np.float64)
+    R = rotation_matrix(alpha, beta, gamma)
+    n = _unit(theta, phi) @ R.T
+    th2 = np.arctan2(np.hypot(n[..., 0], n[..., 1]), n[..., 2])
+    ph2 = np.mod(np.arctan2(n[..., 1], n[..., 0]), 2.0 * math.pi)
+    et2 = np.stack([np.cos(th2) * np.cos(ph2), np.cos(th2) * np.sin(ph2), -np.sin(th2)], axis=-1)
+    back = et2 @ R  # R^-1 e_theta'(n), rows
+    et = np.stack([np.cos(theta) * np.cos(phi), np.cos(theta) * np.sin(phi), -np.sin(theta)], axis=-1)
+    ep = np.stack([-np.sin(phi), np.cos(phi), np.zeros_like(phi)], axis=-1)
+    psi = np.arctan2(np.sum(back * ep, axis=-1), np.sum(back * et, axis=-1))
+    return th2, ph2, psi
+
+
+def min_enclosing_cap(theta, phi):
+    """Smallest spherical cap holding every point: the centre c maximises min_p <p, c>, and by
+    duality c is the direction of the minimum-norm point of the points' convex hull, with
+    cos(radius) = its norm (valid while the points lie in an open hemisphere).  Solved here as the
+    small quadratic programme min |sum_p lambda_p p|^2, lambda >= 0, sum lambda = 1 (SLSQP), for a
+    few hundred points at most.  Returns (theta_c, phi_c, radius)."""
+    from scipy.optimize import minimize
+
+    P = _unit(np.asarray(theta, dtype=np.float64), np.asarray(phi, dtype=np.float64))
+    n = P.shape[0]
+    G = P @ P.T
+    x0 = np.full(n, 1.0 / n)
+    res = minimize(lambda lam: lam @ G @ lam, x0, jac=lambda lam: 2.0 * G @ lam, method="SLSQP",
+                   bounds=[(0.0, None)] * n, constraints=[{"type": "eq", "fun": lambda lam: lam.sum() - 1.0,
+                                                          "jac": lambda lam: np.ones_like(lam)}],
+                   options={"ftol": 1e-16, "maxiter": 2000})
+    x = res.x @ P
+    c = x / np.linalg.norm(x)
+    radius = math.acos(min(1.0, float(np.min(P @ c))))
+    return math.atan2(math.hypot(c[0], c[1]), c[2]), math.atan2(c[1], c[0]) % (2.0 * math.pi), radius
 
 
 # ----------------------------------------------------------------------------- O2 building blocks

@@ -386,3 +386,74 @@ void orc_direct_adjoint_lm(int s, int64_t npts, const double* theta, const doubl
     }
   }
 }
+
+/*
+ * Rotation of one harmonic coefficient set (a real field's g or c) by the Euler angles
+ * (alpha, beta, gamma) of R = R_z(alpha) R_y(beta) R_z(gamma), plain definition:
+ *   a'_{l,m} = sum_{m'=-l}^{l} e^{-i m alpha} d^l_{m,m'}(beta) e^{-i m' gamma} a_{l,m'},   m >= 0,
+ * with a_{l,-m'} = (-1)^{m'} a*_{l,m'}; Im(a_l0) is ignored.  The rotated field is the original
+ * one carried along by R (scalar case: f'(n) = f(R^-1 n)); the appendix's Wigner small-d is the
+ * one used everywhere in this file.  nsel < 0 computes every (l, m); otherwise only the nsel
+ * pairs (ls[k], ms[k]), written to out[k] (each costs O(l^2), so single coefficients of a large
+ * band limit stay cheap).  Cost of the full form O(lmax^3).
+ */
+static void rot_one_m(int lmax, int m, int lsel, double alpha, double gamma, double cb, double ch, double sh,
+                      const double* a, double* acc /* 2*(lmax+1) */, double* d) {
+  const int lhi = lsel >= 0 ? lsel : lmax;
+  for (int l = 0; l <= lhi; ++l) acc[2 * l] = acc[2 * l + 1] = 0.0;
+  for (int mp = -lhi; mp <= lhi; ++mp) {
+    const int amp = mp < 0 ? -mp : mp;
+    orc_wigner_d_column(lhi, m, mp, cb, ch, sh, d);
+    /* e^{-i m alpha} e^{-i mp gamma} */
+    const double ph = -(double)m * alpha - (double)mp * gamma;
+    const double er = cos(ph), ei = sin(ph);
+    const int l0 = m > amp ? m : amp;
+    for (int l = (lsel >= 0 ? lsel : l0); l <= lhi; ++l) {
+      if (l < l0) continue;
+      const int64_t k = alm_idx(lmax, l, amp);
+      double ar = a[2 * k], ai = (amp == 0) ? 0.0 : a[2 * k + 1];
+      if (mp < 0) { /* a_{l,-|mp|} = (-1)^|mp| conj(a_{l,|mp|}) */
+        const double sg = (amp & 1) ? -1.0 : 1.0;
+        ar = sg * ar; ai = -sg * ai;
+      }
+      const double tr = er * ar - ei * ai, ti = er * ai + ei * ar;
+      acc[2 * l] += d[l] * tr;
+      acc[2 * l + 1] += d[l] * ti;
+    }
+  }
+}
+
+void orc_rotate_alm(int lmax, double alpha, double beta, double gamma, const double* a, int nsel, const int* ls,
+                    const int* ms, double* out) {
+  double cb, ch, sh; half_angles(beta, &cb, &ch, &sh);
+  if (nsel < 0) {
+#pragma omp parallel
+    {
+      double* acc = (double*)malloc(sizeof(double) * 2 * (lmax + 1));
+      double* d = (double*)malloc(sizeof(double) * (lmax + 1));
+#pragma omp for schedule(dynamic, 1)
+      for (int m = 0; m <= lmax; ++m) {
+        rot_one_m(lmax, m, -1, alpha, gamma, cb, ch, sh, a, acc, d);
+        for (int l = m; l <= lmax; ++l) {
+          const int64_t k = alm_idx(lmax, l, m);
+          out[2 * k] = acc[2 * l];
+          out[2 * k + 1] = (m == 0) ? 0.0 : acc[2 * l + 1];
+        }
+      }
+      free(acc); free(d);
+    }
+    return;
+  }
+#pragma omp parallel
+  {
+    double* acc = (double*)malloc(sizeof(double) * 2 * (lmax + 1));
+    double* d = (double*)malloc(sizeof(double) * (lmax + 1));
+#pragma omp for schedule(dynamic, 1)
+    for (int k = 0; k < nsel; ++k) {
+      rot_one_m(lmax, ms[k], ls[k], alpha, gamma, cb, ch, sh, a, acc, d);
+      out[2 * k] = acc[2 * ls[k]];
+      out[2 * k + 1] = (ms[k] == 0) ? 0.0 : acc[2 * ls[k] + 1];
+    }
+    free(acc); free(d);
+  }
+}
