@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--serve-streams", type=int, default=4)
     ap.add_argument("--serve-loads", default="0.8", help="offered loads, fractions of single-stream capacity")
     ap.add_argument("--serve-nmax", type=int, default=30_000_000)
+    ap.add_argument("--no-frames", action="store_true",
+                    help="skip the frame comparison (points as given about the nearer pole vs the patch frame)")
     ap.add_argument("--table1", action="store_true",
                     help="re-measure the partial-sky / full-sky speed-ups of the paper's Table 1 instead")
     ap.add_argument("--cpu-sample-points", type=int, default=1_000_000)
@@ -321,6 +323,8 @@ def run_ours(args, rank, world, local_rank):
         "forms": {k: {kk: vv for kk, vv in v.items() if kk not in ("e2e",)} for k, v in results.items()},
         "input_generation_s": gen_s,
     }
+    if not args.no_frames and world == 1:
+        line["frames"] = run_frames(args, dev)
     if args.serve_requests > 0 and world == 1:
         line["serving"] = run_serving(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -328,6 +332,65 @@ def run_ours(args, rank, world, local_rank):
     if dist is not None:
         dist.destroy_process_group()
     return line
+
+
+# ----------------------------------------------------------------------------- frames
+def run_frames(args, dev, K: int = 5) -> dict:
+    """The same field's points as given (the box near the south pole): a plan about the nearer pole
+    (theta* ~ 48 deg) against a patch-frame plan (theta* ~ 34.7 deg, a_lm rotated in and out on
+    every call), FP32 form; step = synthesis + adjoint, CUDA events, K steps after 2 warm-up steps."""
+    import torch
+    from paper_2603_17166_gb300 import Plan, Rotator, synthetic
+
+    wl = synthetic.config2(frame="S", step_arcmin=args.step_arcmin)
+    theta = torch.from_numpy(wl["theta"]).to(dev)
+    phi = torch.from_numpy(wl["phi"]).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    out = {"points": int(theta.numel()), "eps": EPS32, "form": "fp32", "steps": K}
+    for key, patch in (("nearest_pole", False), ("patch_frame", True)):
+        t0 = time.time()
+        plan = Plan(SPIN, LMAX, theta, phi, EPS32, precision="fp32", stream=stream, patch_frame=patch)
+        torch.cuda.synchronize(dev)
+        plan_s = time.time() - t0
+        g = torch.from_numpy(wl["g"]).to(dev).to(plan.cdtype)
+        c = torch.from_numpy(wl["c"]).to(dev).to(plan.cdtype)
+        f = torch.empty(theta.numel(), dtype=plan.cdtype, device=dev)
+        gt, ct = torch.empty_like(g), torch.empty_like(c)
+        for _ in range(2):
+            plan.synthesis(g, c, out=f, stream=stream)
+            plan.adjoint(f, g_out=gt, c_out=ct, stream=stream)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            plan.synthesis(g, c, out=f, stream=stream)
+            plan.adjoint(f, g_out=gt, c_out=ct, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / K
+        info = plan.info
+        out[key] = dict(ms_per_step=ms, mpoints_per_s=theta.numel() / ms / 1e3, plan_s=plan_s,
+                        theta_star_deg=math.degrees(info["theta_star"]), L=info["L"], M=info["M"],
+                        recursion_triples=info["recursion_triples"])
+        plan.close()
+        del g, c, f, gt, ct
+    # the rotation alone: one rotation of (g, c) (a patch-frame step does two)
+    rot = Rotator(LMAX, precision="fp32")
+    g = torch.from_numpy(wl["g"]).to(dev).to(rot.cdtype)
+    c = torch.from_numpy(wl["c"]).to(dev).to(rot.cdtype)
+    go, co = torch.empty_like(g), torch.empty_like(c)
+    for _ in range(2):
+        rot.apply(g, c, 0.1, 0.6, -0.4, g_out=go, c_out=co, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        rot.apply(g, c, 0.1, 0.6, -0.4, g_out=go, c_out=co, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    out["rotation_ms"] = e0.elapsed_time(e1) / K
+    rot.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 # ----------------------------------------------------------------------------- serving

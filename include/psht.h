@@ -52,6 +52,11 @@ extern "C" {
 #define PSHT_FP32 2u        /* FP32 recursion (FP64 seeds and rescaling), FP32 FFT and kernels   */
 #define PSHT_FULL_SKY 4u    /* full-sky route whatever the points' extent (Sec. I: theta_max = pi, */
                             /* w = 1, Lmax = lmax); the baseline of the paper's speed-ups (Table 1) */
+#define PSHT_PATCH_FRAME 8u /* run in the patch-centred frame (Sec. II step 1): the plan rotates the */
+                            /* points so that the centre of their smallest cap is the north pole    */
+                            /* (psht_patch_rotation), rotates a_lm in (and the adjoint's a_lm back)  */
+                            /* with psht_rotator_apply, and applies each point's basis angle to     */
+                            /* spin-s values; inputs and outputs stay in the caller's frame         */
 
 typedef struct psht_plan psht_plan; /* opaque; owned by the library, freed by psht_plan_destroy */
 
@@ -71,6 +76,8 @@ typedef struct psht_info {
   int64_t ring_mode_pairs;       /* (ring, m) pairs the recursion computes                    */
   int64_t recursion_triples;     /* (ring, m, l) steps of the recursion                       */
   size_t device_bytes;           /* device memory held by the plan                             */
+  int patch_frame;               /* 1: PSHT_PATCH_FRAME (theta_star etc. refer to that frame)  */
+  double euler[3];               /* its rotation (alpha, beta, gamma), as psht_patch_rotation  */
 } psht_info;
 
 /*
@@ -227,6 +234,62 @@ int psht_adjoint_synthesis(const void* f, int spin, int lmax, const double* thet
 int psht_ring_synthesis_noalloc(int spin, int lmax, const double* theta, int nring, const void* g, const void* c,
                                 void* F, void* stream);
 size_t psht_noalloc_scratch_bytes(void);
+
+/*
+ * Change of frame.  The paper evaluates its rings about a pole placed at the centre of the patch
+ * (Sec. II, step 1) and leaves the rotation of a caller's coefficients to them.  These entry points
+ * rotate a_lm sets, points and the spin basis between frames.
+ *
+ * A rotation is given by zyz Euler angles, R = R_z(alpha) R_y(beta) R_z(gamma) acting on vectors.
+ * Rotating one real field's coefficient set (g or c, packed m-major as everywhere in this header):
+ *   a'_lm = sum_{m'=-l..l} e^{-i m alpha} d^l_{m m'}(beta) e^{-i m' gamma} a_lm',  m >= 0,
+ * with a_{l,-m'} = (-1)^m' a*_lm' and d^l the appendix's Wigner small-d (eq. Ylm).  A spin-s map
+ * synthesised from the rotated (g', c') at the rotated point n = R p equals the original map at p up
+ * to the change of local basis: f(p) = e^{i s psi_p} f'(R p), psi_p from psht_rotate_points.  The
+ * inverse rotation is (-gamma, -beta, -alpha); it is also the adjoint, since D^l is unitary for the
+ * inner product of the adjoint synthesis (sum over all m of Re(a* a')).
+ *
+ * The library evaluates d^l(beta) through d^l(pi/2) by the appendix's Fourier identity
+ * d^l_{m m'}(beta) = sum_k i^m d^l_{km}(pi/2) e^{-i k beta} d^l_{km'}(pi/2) (-i)^m', with
+ * d^l(pi/2) generated on the fly by a recurrence, in O(lmax^3) work and no O(lmax^2) table beyond
+ * one coefficient per (l, m').  Precision PSHT_FP64 (complex128 sets) or PSHT_FP32 (complex64 sets;
+ * relative error a few 1e-6 at lmax 4096, growing slowly with lmax); PSHT_AUTO means PSHT_FP64.
+ *
+ * psht_rotator_create: the per-band-limit tables and scratch (psht_rotator_bytes); asynchronous on
+ *   `stream`.  psht_rotator_apply: rotates g (and c, if not NULL) into g_out (c_out); all DEVICE
+ *   pointers of nalm = (lmax+1)(lmax+2)/2 complex elements; the output may alias the input; c and
+ *   c_out are both NULL or both set.  Asynchronous on `stream`; calls on one rotator share its
+ *   scratch and must be ordered.  Im of the m = 0 inputs is ignored and written as 0.
+ * psht_rotate_alm: create, apply, destroy (synchronises `stream`).
+ */
+typedef struct psht_rotator psht_rotator;
+int psht_rotator_create(int lmax, uint32_t flags, void* stream, psht_rotator** out);
+int psht_rotator_apply(psht_rotator* rot, double alpha, double beta, double gamma, const void* g, const void* c,
+                       void* g_out, void* c_out, void* stream);
+int psht_rotator_destroy(psht_rotator* rot);
+size_t psht_rotator_bytes(int lmax, uint32_t flags);
+int psht_rotate_alm(int lmax, double alpha, double beta, double gamma, const void* g, const void* c, void* g_out,
+                    void* c_out, uint32_t flags, void* stream);
+
+/*
+ * Rotated points n_p = R p: theta_out in [0, pi], phi_out in [0, 2 pi), and (if psi_out is not NULL)
+ * psi_p, the angle from e_theta(p) towards e_phi(p) of the rotated frame's e_theta at n_p carried
+ * back by R^-1, so that f(p) = e^{i s psi_p} f'(n_p) for a spin-s map in the two frames.
+ * All arrays DEVICE float64[npts]; outputs may alias inputs.  Asynchronous on `stream`.
+ */
+int psht_rotate_points(double alpha, double beta, double gamma, const double* theta, const double* phi, int64_t npts,
+                       double* theta_out, double* phi_out, double* psi_out, void* stream);
+
+/*
+ * Patch-centred frame (Sec. II, step 1, "centre of the patch at the north pole"): the centre c of
+ * the smallest spherical cap holding the points (the direction of the minimum-norm point of their
+ * convex hull, by Wolfe's iteration with the linear minimisations on the device), returned as the
+ * Euler angles euler[3] = (0, theta_c, pi - phi_c) of a rotation taking c to the north pole, and
+ * (if theta_star is not NULL) the cap radius.  theta, phi: DEVICE float64[npts]; euler, theta_star:
+ * HOST.  Synchronises `stream`.  EINVAL if the points do not lie in an open hemisphere.
+ */
+int psht_patch_rotation(const double* theta, const double* phi, int64_t npts, double* euler, double* theta_star,
+                        void* stream);
 
 /* Device bytes a plan for these arguments would hold (theta_star = max distance to the pole). */
 size_t psht_estimate_bytes(int spin, int lmax, double theta_star, int64_t npts, double eps, uint32_t flags);

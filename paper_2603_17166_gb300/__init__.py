@@ -4,5 +4,5 @@ Synthesis general and its adjoint at arbitrary points inside one sky patch, by t
 Fourier-sphere route of Carron & Reinecke (Wigner-d recursion onto apodised rings, FFTs onto a
 reduced oversampled grid, ES-kernel interpolation), as a C-ABI CUDA library with a thin binding.
 """
-from .psht import (Plan, PshtError, Server, adjoint_synthesis, estimate_bytes, estimate_points,  # noqa: F401
-                   lib, nalm, predict_error, synthesis)
+from .psht import (Plan, PshtError, Rotator, Server, adjoint_synthesis, estimate_bytes, estimate_points,  # noqa: F401
+                   lib, nalm, patch_rotation, predict_error, rotate_alm, rotate_points, synthesis)

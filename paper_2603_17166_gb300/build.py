@@ -16,7 +16,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpsht.so")
 SOURCES = ["psht_api.cu", "psht_rec.cu", "psht_fft.cu", "psht_interp.cu", "psht_noalloc.cu", "psht_server.cu",
-           "psht_predict.cu"]
+           "psht_predict.cu", "psht_rotate.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC,-O2",
          "-Xptxas", "-warn-spills"]

@@ -320,6 +320,10 @@ size_t planned_bytes(const Plan& p) {
   const size_t items = (size_t)(p.M + 1) * (2 + (size_t)p.nring / 32);  // items hold >= 32 rings, one per part
   b += items * (sizeof(RecItem) + sizeof(AdjItem));
   b += ((size_t)p.ntr * p.ntq + (size_t)p.npts / 2048 + 1) * sizeof(TileItem);
+  if (p.patch) {  // rotator, rotated a_lm, spin phases and the adjoint's rotated input
+    b += rotator_bytes(p.lmax, p.prec) + 2 * (size_t)p.nalm * cb;
+    if (p.spin > 0) b += 2 * (size_t)p.npts * cb;
+  }
   return b;
 }
 
@@ -327,6 +331,7 @@ void destroy(Plan* p) {
   if (!p) return;
   cudaDeviceSynchronize();
   for (void* a : p->allocs) cudaFree(a);
+  rotator_destroy(p->rot);
   for (auto& r : p->recs) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -375,6 +380,14 @@ void apply_options(Plan& p, const psht_options* opt) {
   p.kappa = opt->kappa == 0.0 ? 1.0 : opt->kappa;
 }
 
+// device scratch freed on scope exit (after the stream work that uses it: cudaFree waits for the device)
+struct DevTmp {
+  void* p = nullptr;
+  ~DevTmp() {
+    if (p) cudaFree(p);
+  }
+};
+
 Plan* create(int spin, int lmax, const double* theta, const double* phi, int64_t npts, double eps, uint32_t flags,
              const psht_options* opt, cudaStream_t st) {
   PSHT_REQUIRE(spin >= 0, PSHT_EINVAL, "spin must be >= 0");
@@ -385,7 +398,7 @@ Plan* create(int spin, int lmax, const double* theta, const double* phi, int64_t
   PSHT_REQUIRE(npts == 0 || (theta && phi), PSHT_EINVAL, "theta and phi must be device pointers");
   const uint32_t pf = flags & 3u;
   PSHT_REQUIRE(pf != 3u, PSHT_EINVAL, "PSHT_FP32 and PSHT_FP64 are exclusive");
-  PSHT_REQUIRE((flags & ~7u) == 0u, PSHT_EINVAL, "unknown flag bits");
+  PSHT_REQUIRE((flags & ~15u) == 0u, PSHT_EINVAL, "unknown flag bits");
   int prec = (pf == PSHT_FP64) ? 64 : (pf == PSHT_FP32) ? 32 : (eps >= 1e-5 ? 32 : 64);
   PSHT_REQUIRE(!(prec == 32 && eps < 1e-7), PSHT_EINVAL, "the FP32 form needs eps >= 1e-7");
 
@@ -398,6 +411,24 @@ Plan* create(int spin, int lmax, const double* theta, const double* phi, int64_t
     p->npts = npts;
     p->force_full = (flags & PSHT_FULL_SKY) ? 1 : 0;
     apply_options(*p, opt);
+    // patch-centred frame: validate the caller's points, then rotate them (and keep each one's
+    // spin-basis angle)
+    DevTmp rpts;
+    if (flags & PSHT_PATCH_FRAME) {
+      p->patch = 1;
+      if (npts > 0) {
+        double red0[3];
+        reduce_points(theta, phi, npts, red0, st);
+        PSHT_REQUIRE(red0[2] == 0.0, PSHT_EINVAL, "theta outside [0, pi], NaN, or non-finite phi in the points");
+        patch_rotation_device(theta, phi, npts, p->euler, nullptr, st);
+        PSHT_CUDA_TRY(cudaMalloc(&rpts.p, (size_t)npts * 3 * sizeof(double)));
+        double* t2 = (double*)rpts.p;
+        rotate_points_device(p->euler[0], p->euler[1], p->euler[2], theta, phi, npts, t2, t2 + npts,
+                             spin > 0 ? t2 + 2 * npts : nullptr, st);
+        theta = t2;
+        phi = t2 + npts;
+      }
+    }
     // step 1: nearer pole and theta* (one device reduction, validates the points)
     double red[3];
     reduce_points(theta, phi, npts, red, st);
@@ -554,6 +585,16 @@ Plan* create(int spin, int lmax, const double* theta, const double* phi, int64_t
     if (prec == 64) p->d_pw = dalloc(*p, (size_t)std::max<int64_t>(npts, 1) * 2 * p->W * 8);
     else p->d_pfrac = (float*)dalloc(*p, (size_t)std::max<int64_t>(npts, 1) * 2 * 4);
     bin_points(*p, theta, phi, st);
+    if (p->patch) {
+      p->rot = rotator_create(lmax, prec, st);
+      p->bytes += rotator_bytes(lmax, prec);
+      p->d_ra = dalloc(*p, 2 * (size_t)p->nalm * cb);
+      if (spin > 0 && npts > 0) {
+        p->d_sph = dalloc(*p, (size_t)npts * cb);
+        p->d_fr = dalloc(*p, (size_t)npts * cb);
+        spin_phase_device(prec, (const double*)rpts.p + 2 * npts, spin, npts, p->d_sph, st);
+      }
+    }
     PSHT_CUDA_TRY(cudaStreamSynchronize(st));
     return p;
   } catch (...) {
@@ -623,6 +664,38 @@ void run_adjoint(Plan& p, const void* f, void* g, void* c, cudaStream_t st, doub
   staged(p, 5, st, [&] { launch_phi_adjoint(p, st); });
   staged(p, 6, st, [&] { launch_theta_adjoint(p, st); });
   staged(p, 7, st, [&] { launch_rec_adjoint(p, g, c, st, msc); });
+}
+
+// Synthesis and adjoint as the entry points see them: in a patch-frame plan the a_lm are rotated
+// into the plan's frame first (the synthesis weight msc applies to the caller's m > 0 entries), and
+// the spin-s values carry each point's basis angle, f(p) = e^{i s psi_p} f'(R p); the adjoint is
+// the exact transpose: conjugate phase, adjoint in the plan's frame, inverse rotation.
+void exec_synthesis(Plan& p, const void* g, const void* c, void* f, cudaStream_t st, double msc = 1.0) {
+  if (!p.patch) {
+    run_synthesis(p, g, c, f, st, msc);
+    return;
+  }
+  const size_t na = (size_t)p.nalm * (p.prec == 64 ? 16 : 8);
+  char* ra = (char*)p.d_ra;
+  rotator_apply(*p.rot, p.euler[0], p.euler[1], p.euler[2], g, c, ra, c ? ra + na : nullptr, st, msc, 1.0);
+  run_synthesis(p, ra, c ? ra + na : nullptr, f, st);
+  if (p.d_sph) mul_phase_device(p.prec, f, p.d_sph, p.npts, false, f, st);
+}
+
+void exec_adjoint(Plan& p, const void* f, void* g, void* c, cudaStream_t st, double msc = 1.0) {
+  if (!p.patch) {
+    run_adjoint(p, f, g, c, st, msc);
+    return;
+  }
+  const size_t na = (size_t)p.nalm * (p.prec == 64 ? 16 : 8);
+  char* ra = (char*)p.d_ra;
+  const void* fr = f;
+  if (p.d_sph) {
+    mul_phase_device(p.prec, f, p.d_sph, p.npts, true, p.d_fr, st);
+    fr = p.d_fr;
+  }
+  run_adjoint(p, fr, ra, c ? ra + na : nullptr, st);
+  rotator_apply(*p.rot, -p.euler[2], -p.euler[1], -p.euler[0], ra, c ? ra + na : nullptr, g, c, st, 1.0, msc);
 }
 
 void ensure_io(Plan& p) {
@@ -778,6 +851,8 @@ int psht_plan_info(const psht_plan* plan, psht_info* info) {
     i.ring_mode_pairs = p.pairs;
     i.recursion_triples = p.triples;
     i.device_bytes = p.bytes;
+    i.patch_frame = p.patch;
+    for (int k = 0; k < 3; ++k) i.euler[k] = p.euler[k];
     *info = i;
   });
 }
@@ -786,7 +861,7 @@ int psht_plan_synthesis(psht_plan* plan, const void* g, const void* c, void* f, 
   return guarded([&] {
     PSHT_REQUIRE(plan && g, PSHT_EINVAL, "plan and g must not be NULL");
     PSHT_REQUIRE(f || plan->p->npts == 0, PSHT_EINVAL, "f must not be NULL");
-    run_synthesis(*plan->p, g, c, f, (cudaStream_t)stream);
+    exec_synthesis(*plan->p, g, c, f, (cudaStream_t)stream);
   });
 }
 
@@ -794,7 +869,7 @@ int psht_plan_adjoint(psht_plan* plan, const void* f, void* g, void* c, void* st
   return guarded([&] {
     PSHT_REQUIRE(plan && g, PSHT_EINVAL, "plan and g must not be NULL");
     PSHT_REQUIRE(f || plan->p->npts == 0, PSHT_EINVAL, "f must not be NULL");
-    run_adjoint(*plan->p, f, g, c, (cudaStream_t)stream);
+    exec_adjoint(*plan->p, f, g, c, (cudaStream_t)stream);
   });
 }
 
@@ -802,7 +877,7 @@ int psht_plan_synthesis_packed(psht_plan* plan, const void* g, const void* c, vo
   return guarded([&] {
     PSHT_REQUIRE(plan && g, PSHT_EINVAL, "plan and g must not be NULL");
     PSHT_REQUIRE(f || plan->p->npts == 0, PSHT_EINVAL, "f must not be NULL");
-    run_synthesis(*plan->p, g, c, f, (cudaStream_t)stream, 0.5);
+    exec_synthesis(*plan->p, g, c, f, (cudaStream_t)stream, 0.5);
   });
 }
 
@@ -810,7 +885,7 @@ int psht_plan_adjoint_packed(psht_plan* plan, const void* f, void* g, void* c, v
   return guarded([&] {
     PSHT_REQUIRE(plan && g, PSHT_EINVAL, "plan and g must not be NULL");
     PSHT_REQUIRE(f || plan->p->npts == 0, PSHT_EINVAL, "f must not be NULL");
-    run_adjoint(*plan->p, f, g, c, (cudaStream_t)stream, 2.0);
+    exec_adjoint(*plan->p, f, g, c, (cudaStream_t)stream, 2.0);
   });
 }
 
@@ -822,12 +897,12 @@ int psht_plan_synthesis_host(psht_plan* plan, const void* g, const void* c, void
     ensure_io(p);
     const size_t cb = p.prec == 64 ? 16 : 8, na = (size_t)p.nalm * cb;
     char* da = (char*)p.d_io_a;
-    if (!p.chunk_m.empty()) {
+    if (!p.chunk_m.empty() && !p.patch) {
       synthesis_host_chunked(p, g, c, f, st);
     } else {
       PSHT_CUDA_TRY(cudaMemcpyAsync(da, g, na, cudaMemcpyHostToDevice, st));
       if (c) PSHT_CUDA_TRY(cudaMemcpyAsync(da + na, c, na, cudaMemcpyHostToDevice, st));
-      run_synthesis(p, da, c ? da + na : nullptr, p.d_io_f, st);
+      exec_synthesis(p, da, c ? da + na : nullptr, p.d_io_f, st);
       PSHT_CUDA_TRY(cudaMemcpyAsync(f, p.d_io_f, (size_t)p.npts * cb, cudaMemcpyDeviceToHost, st));
     }
     PSHT_CUDA_TRY(cudaStreamSynchronize(st));
@@ -842,11 +917,11 @@ int psht_plan_adjoint_host(psht_plan* plan, const void* f, void* g, void* c, voi
     ensure_io(p);
     const size_t cb = p.prec == 64 ? 16 : 8, na = (size_t)p.nalm * cb;
     char* da = (char*)p.d_io_a;
-    if (!p.chunk_m.empty()) {
+    if (!p.chunk_m.empty() && !p.patch) {
       adjoint_host_chunked(p, f, g, c, st);
     } else {
       PSHT_CUDA_TRY(cudaMemcpyAsync(p.d_io_f, f, (size_t)p.npts * cb, cudaMemcpyHostToDevice, st));
-      run_adjoint(p, p.d_io_f, da, c ? da + na : nullptr, st);
+      exec_adjoint(p, p.d_io_f, da, c ? da + na : nullptr, st);
       PSHT_CUDA_TRY(cudaMemcpyAsync(g, da, na, cudaMemcpyDeviceToHost, st));
       if (c) PSHT_CUDA_TRY(cudaMemcpyAsync(c, da + na, na, cudaMemcpyDeviceToHost, st));
     }
@@ -876,6 +951,15 @@ int psht_plan_rings(const psht_plan* plan, double* theta_j, double* w_j, int32_t
 int psht_plan_ring_coeffs(psht_plan* plan, const void* g, const void* c, void* F, void* stream) {
   return guarded([&] {
     PSHT_REQUIRE(plan && g && F, PSHT_EINVAL, "plan, g and F must not be NULL");
+    Plan& p = *plan->p;
+    if (p.patch) {  // the rings live in the plan's frame
+      const size_t na = (size_t)p.nalm * (p.prec == 64 ? 16 : 8);
+      char* ra = (char*)p.d_ra;
+      rotator_apply(*p.rot, p.euler[0], p.euler[1], p.euler[2], g, c, ra, c ? ra + na : nullptr,
+                    (cudaStream_t)stream);
+      g = ra;
+      c = c ? ra + na : nullptr;
+    }
     launch_rec_synthesis(*plan->p, g, c, (cudaStream_t)stream);
     launch_ring_coeffs_export(*plan->p, F, (cudaStream_t)stream);
   });
@@ -965,6 +1049,7 @@ size_t psht_estimate_bytes(int spin, int lmax, double theta_star, int64_t npts, 
     p.prec = (pf == PSHT_FP64) ? 64 : (pf == PSHT_FP32) ? 32 : (eps >= 1e-5 ? 32 : 64);
     p.npts = npts;
     p.force_full = (flags & PSHT_FULL_SKY) ? 1 : 0;
+    p.patch = (flags & PSHT_PATCH_FRAME) ? 1 : 0;
     p.pole = 1;
     layout(p, theta_star);
     return planned_bytes(p);
@@ -984,6 +1069,12 @@ int psht_plan_estimate_points(int spin, int lmax, const double* theta, const dou
     double red[3];
     reduce_points(theta, phi, npts, red, (cudaStream_t)stream);
     PSHT_REQUIRE(red[2] == 0.0, PSHT_EINVAL, "theta outside [0, pi], NaN, or non-finite phi in the points");
+    if ((flags & PSHT_PATCH_FRAME) && npts > 0) {  // theta* in the patch-centred frame
+      double eul[3], ts = 0.0;
+      patch_rotation_device(theta, phi, npts, eul, &ts, (cudaStream_t)stream);
+      red[0] = ts;
+      red[1] = M_PI;
+    }
     Plan p;
     p.spin = spin;
     p.lmax = lmax;
@@ -992,6 +1083,7 @@ int psht_plan_estimate_points(int spin, int lmax, const double* theta, const dou
     p.prec = (pf == PSHT_FP64) ? 64 : (pf == PSHT_FP32) ? 32 : (eps >= 1e-5 ? 32 : 64);
     p.npts = npts;
     p.force_full = (flags & PSHT_FULL_SKY) ? 1 : 0;
+    p.patch = (flags & PSHT_PATCH_FRAME) ? 1 : 0;
     p.pole = (red[0] <= red[1]) ? 1 : -1;
     layout(p, p.pole > 0 ? red[0] : red[1]);
     *bytes = planned_bytes(p);
@@ -1017,6 +1109,60 @@ int psht_predict_error(int spin, int lmax, double theta_star, double eps, const 
     layout(p, theta_star);
     predict_error_device(p, make_seeds(lmax, spin), cl, beta, n, rel_rms, (cudaStream_t)stream);
   });
+}
+
+static int rot_prec(uint32_t flags) { return (flags & 3u) == PSHT_FP32 ? 32 : 64; }
+
+int psht_rotator_create(int lmax, uint32_t flags, void* stream, psht_rotator** out) {
+  return guarded([&] {
+    PSHT_REQUIRE(out, PSHT_EINVAL, "out must not be NULL");
+    *out = reinterpret_cast<psht_rotator*>(rotator_create(lmax, rot_prec(flags), (cudaStream_t)stream));
+  });
+}
+
+int psht_rotator_apply(psht_rotator* rot, double alpha, double beta, double gamma, const void* g, const void* c,
+                       void* g_out, void* c_out, void* stream) {
+  return guarded([&] {
+    PSHT_REQUIRE(rot, PSHT_EINVAL, "rotator must not be NULL");
+    rotator_apply(*reinterpret_cast<Rotator*>(rot), alpha, beta, gamma, g, c, g_out, c_out, (cudaStream_t)stream);
+  });
+}
+
+int psht_rotator_destroy(psht_rotator* rot) {
+  rotator_destroy(reinterpret_cast<Rotator*>(rot));
+  return PSHT_OK;
+}
+
+size_t psht_rotator_bytes(int lmax, uint32_t flags) {
+  return lmax < 0 ? 0 : rotator_bytes(lmax, rot_prec(flags));
+}
+
+int psht_rotate_alm(int lmax, double alpha, double beta, double gamma, const void* g, const void* c, void* g_out,
+                    void* c_out, uint32_t flags, void* stream) {
+  return guarded([&] {
+    cudaStream_t st = (cudaStream_t)stream;
+    Rotator* r = rotator_create(lmax, rot_prec(flags), st);
+    try {
+      rotator_apply(*r, alpha, beta, gamma, g, c, g_out, c_out, st);
+      PSHT_CUDA_TRY(cudaStreamSynchronize(st));
+    } catch (...) {
+      rotator_destroy(r);
+      throw;
+    }
+    rotator_destroy(r);
+  });
+}
+
+int psht_rotate_points(double alpha, double beta, double gamma, const double* theta, const double* phi, int64_t npts,
+                       double* theta_out, double* phi_out, double* psi_out, void* stream) {
+  return guarded([&] {
+    rotate_points_device(alpha, beta, gamma, theta, phi, npts, theta_out, phi_out, psi_out, (cudaStream_t)stream);
+  });
+}
+
+int psht_patch_rotation(const double* theta, const double* phi, int64_t npts, double* euler, double* theta_star,
+                        void* stream) {
+  return guarded([&] { patch_rotation_device(theta, phi, npts, euler, theta_star, (cudaStream_t)stream); });
 }
 
 const char* psht_last_error(void) { return g_err.c_str(); }

@@ -82,6 +82,8 @@ struct FftDev {     // radix schedule of one FFT length (at most 32 stages)
 };
 
 // ---------------------------------------------------------------------------------------------
+struct Rotator;  // Wigner-D rotation of a_lm sets (psht_rotate.cu)
+
 struct Plan {
   // parameters (names as in the paper)
   int spin = 0, lmax = 0, prec = 64;
@@ -151,6 +153,15 @@ struct Plan {
   std::vector<cudaEvent_t> chunk_ev;
   // item and order ranges of the next recursion launch (-1: all); set only around chunked launches
   int r_item0 = 0, r_item1 = -1, r_aitem0 = 0, r_aitem1 = -1, r_m0 = 0, r_m1 = -1;
+  // patch-centred frame (PSHT_PATCH_FRAME): the plan's rings, grid and points live in the frame
+  // rotated by euler; a_lm are rotated on the way in and back on the way out, and a spin-s map
+  // picks up the basis angle of each point
+  int patch = 0;
+  double euler[3] = {0.0, 0.0, 0.0};
+  Rotator* rot = nullptr;
+  void* d_ra = nullptr;   // complex T [2][nalm], rotated a_lm
+  void* d_sph = nullptr;  // complex T [npts], e^{i s psi_p} (spin > 0)
+  void* d_fr = nullptr;   // complex T [npts], adjoint input in the rotated basis (spin > 0)
   size_t bytes = 0;
   std::vector<void*> allocs;
   // stage timing (psht_plan_profile)
@@ -186,5 +197,22 @@ size_t noalloc_scratch_bytes();
 // predicted relative rms error of the plan's ring set for spectrum cl at angles beta (host arrays)
 void predict_error_device(const Plan& p, const std::vector<MSeed>& seeds, const double* cl, const double* beta, int n,
                           double* rel_rms, cudaStream_t st);
+
+// change of frame (psht_rotate.cu): Wigner-D rotation of a_lm sets through d(pi/2), rotation of
+// points with the spin-basis angle, and the rotation that centres the points' smallest cap on the pole
+Rotator* rotator_create(int lmax, int prec, cudaStream_t st);
+void rotator_destroy(Rotator* r);
+// in_msc weighs the m > 0 inputs, out_msc the m > 0 outputs
+void rotator_apply(Rotator& r, double alpha, double beta, double gamma, const void* g, const void* c, void* go,
+                   void* co, cudaStream_t st, double in_msc = 1.0, double out_msc = 1.0);
+int rotator_lmax(const Rotator* r);
+int rotator_prec(const Rotator* r);
+size_t rotator_bytes(int lmax, int prec);
+void rotate_points_device(double alpha, double beta, double gamma, const double* theta, const double* phi,
+                          int64_t n, double* theta2, double* phi2, double* psi, cudaStream_t st);
+void patch_rotation_device(const double* theta, const double* phi, int64_t n, double euler[3], double* theta_star,
+                           cudaStream_t st);
+void spin_phase_device(int prec, const double* psi, int s, int64_t n, void* ph, cudaStream_t st);
+void mul_phase_device(int prec, const void* in, const void* ph, int64_t n, bool conj, void* out, cudaStream_t st);
 
 }  // namespace psht

@@ -12,7 +12,7 @@ import numpy as np
 
 from . import build as _build
 
-PSHT_AUTO, PSHT_FP64, PSHT_FP32, PSHT_FULL_SKY = 0, 1, 2, 4
+PSHT_AUTO, PSHT_FP64, PSHT_FP32, PSHT_FULL_SKY, PSHT_PATCH_FRAME = 0, 1, 2, 4, 8
 _PREC = {"auto": PSHT_AUTO, "fp64": PSHT_FP64, "fp32": PSHT_FP32, 64: PSHT_FP64, 32: PSHT_FP32}
 
 
@@ -32,7 +32,7 @@ class PshtInfo(ctypes.Structure):
         ("M", ctypes.c_int), ("W", ctypes.c_int), ("beta_es", ctypes.c_double),
         ("nTheta", ctypes.c_int), ("nphi", ctypes.c_int), ("r_lo", ctypes.c_int), ("nrows", ctypes.c_int),
         ("npts", ctypes.c_int64), ("ring_mode_pairs", ctypes.c_int64), ("recursion_triples", ctypes.c_int64),
-        ("device_bytes", ctypes.c_size_t),
+        ("device_bytes", ctypes.c_size_t), ("patch_frame", ctypes.c_int), ("euler", ctypes.c_double * 3),
     ]
 
 
@@ -105,6 +105,14 @@ def lib():
         L.psht_server_get_stats.argtypes = [P, ctypes.POINTER(PshtServerStats)]
         L.psht_server_destroy.argtypes = [P]
         L.psht_estimate_bytes.argtypes = [I, I, D, I64, D, U32]
+        L.psht_rotator_create.argtypes = [I, U32, P, ctypes.POINTER(P)]
+        L.psht_rotator_apply.argtypes = [P, D, D, D, P, P, P, P, P]
+        L.psht_rotator_destroy.argtypes = [P]
+        L.psht_rotator_bytes.argtypes = [I, U32]
+        L.psht_rotator_bytes.restype = ctypes.c_size_t
+        L.psht_rotate_alm.argtypes = [I, D, D, D, P, P, P, P, U32, P]
+        L.psht_rotate_points.argtypes = [D, D, D, P, P, I64, P, P, P, P]
+        L.psht_patch_rotation.argtypes = [P, P, I64, P, P, P]
         L.psht_estimate_bytes.restype = ctypes.c_size_t
         L.psht_last_error.restype = ctypes.c_char_p
         L.psht_version.restype = ctypes.c_char_p
@@ -142,14 +150,14 @@ class Plan:
     """A plan for synthesis general and its adjoint at fixed points (psht_plan_create)."""
 
     def __init__(self, spin: int, lmax: int, theta, phi, eps: float, precision="auto", stream=None,
-                 full_sky: bool = False, window: str = "es", kappa: float = 1.0):
+                 full_sky: bool = False, window: str = "es", kappa: float = 1.0, patch_frame: bool = False):
         torch = _torch()
         theta = torch.as_tensor(theta, dtype=torch.float64, device="cuda").contiguous()
         phi = torch.as_tensor(phi, dtype=torch.float64, device="cuda").contiguous()
         if theta.shape != phi.shape or theta.dim() != 1:
             raise ValueError("theta and phi must be 1-D tensors of equal length")
         self._h = ctypes.c_void_p()
-        flags = _PREC[precision] | (PSHT_FULL_SKY if full_sky else 0)
+        flags = _PREC[precision] | (PSHT_FULL_SKY if full_sky else 0) | (PSHT_PATCH_FRAME if patch_frame else 0)
         if window == "es" and kappa == 1.0:
             _check(lib().psht_plan_create(int(spin), int(lmax), _ptr(theta), _ptr(phi), theta.numel(), float(eps),
                                           flags, _stream(stream), ctypes.byref(self._h)))
@@ -168,7 +176,9 @@ class Plan:
     def info(self) -> dict:
         inf = PshtInfo()
         _check(lib().psht_plan_info(self._h, ctypes.byref(inf)))
-        return {name: getattr(inf, name) for name, _ in PshtInfo._fields_}
+        d = {name: getattr(inf, name) for name, _ in PshtInfo._fields_}
+        d["euler"] = tuple(d["euler"])
+        return d
 
     def _alm_in(self, a):
         torch = _torch()
@@ -381,3 +391,91 @@ def predict_error(spin: int, lmax: int, theta_star: float, eps: float, cl, beta,
                                     ctypes.c_void_p(cl.ctypes.data), ctypes.c_void_p(beta.ctypes.data), beta.size,
                                     ctypes.c_void_p(out.ctypes.data), _stream(stream)))
     return out
+
+
+class Rotator:
+    """Wigner-D rotation of a_lm sets at one band limit (psht_rotator_create / _apply)."""
+
+    def __init__(self, lmax: int, precision="fp64", stream=None):
+        self.lmax = int(lmax)
+        self.precision = 32 if _PREC[precision] == PSHT_FP32 else 64
+        self._h = ctypes.c_void_p()
+        _check(lib().psht_rotator_create(self.lmax, _PREC[precision], _stream(stream), ctypes.byref(self._h)))
+        torch = _torch()
+        self.cdtype = torch.complex128 if self.precision == 64 else torch.complex64
+
+    def _in(self, a):
+        torch = _torch()
+        if a is None:
+            return None
+        a = torch.as_tensor(a, device="cuda").to(self.cdtype).contiguous()
+        if a.numel() != nalm(self.lmax):
+            raise ValueError(f"a_lm must hold {nalm(self.lmax)} packed coefficients")
+        return a
+
+    def apply(self, g, c=None, alpha: float = 0.0, beta: float = 0.0, gamma: float = 0.0, g_out=None, c_out=None,
+              stream=None):
+        """Rotated (g', c') = D(alpha, beta, gamma) (g, c); c may be None."""
+        torch = _torch()
+        g, c = self._in(g), self._in(c)
+        go = g_out if g_out is not None else torch.empty_like(g)
+        co = None if c is None else (c_out if c_out is not None else torch.empty_like(c))
+        _check(lib().psht_rotator_apply(self._h, float(alpha), float(beta), float(gamma), _ptr(g), _ptr(c), _ptr(go),
+                                        _ptr(co), _stream(stream)))
+        return go, co
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().psht_rotator_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rotate_alm(g, c=None, alpha: float = 0.0, beta: float = 0.0, gamma: float = 0.0, lmax: int = None,
+               precision=None, stream=None):
+    """One-shot rotation of packed a_lm (psht_rotate_alm); precision follows g's dtype by default."""
+    torch = _torch()
+    g = torch.as_tensor(g, device="cuda")
+    if precision is None:
+        precision = "fp32" if g.dtype == torch.complex64 else "fp64"
+    cd = torch.complex64 if _PREC[precision] == PSHT_FP32 else torch.complex128
+    g = g.to(cd).contiguous()
+    c = None if c is None else torch.as_tensor(c, device="cuda").to(cd).contiguous()
+    if lmax is None:
+        lmax = int(round((np.sqrt(8 * g.numel() + 1) - 3) / 2))
+    if g.numel() != nalm(lmax) or (c is not None and c.numel() != nalm(lmax)):
+        raise ValueError(f"a_lm must hold {nalm(lmax)} packed coefficients")
+    go = torch.empty_like(g)
+    co = None if c is None else torch.empty_like(c)
+    _check(lib().psht_rotate_alm(int(lmax), float(alpha), float(beta), float(gamma), _ptr(g), _ptr(c), _ptr(go),
+                                 _ptr(co), _PREC[precision], _stream(stream)))
+    return go, co
+
+
+def rotate_points(theta, phi, alpha: float, beta: float, gamma: float, want_psi: bool = True, stream=None):
+    """Rotated points (theta', phi') and the spin-basis angle psi (psht_rotate_points)."""
+    torch = _torch()
+    theta = torch.as_tensor(theta, dtype=torch.float64, device="cuda").contiguous()
+    phi = torch.as_tensor(phi, dtype=torch.float64, device="cuda").contiguous()
+    t2, p2 = torch.empty_like(theta), torch.empty_like(phi)
+    psi = torch.empty_like(theta) if want_psi else None
+    _check(lib().psht_rotate_points(float(alpha), float(beta), float(gamma), _ptr(theta), _ptr(phi), theta.numel(),
+                                    _ptr(t2), _ptr(p2), _ptr(psi), _stream(stream)))
+    return t2, p2, psi
+
+
+def patch_rotation(theta, phi, stream=None):
+    """Euler angles of the rotation taking the centre of the points' smallest cap to the north pole,
+    and the cap radius (psht_patch_rotation)."""
+    torch = _torch()
+    theta = torch.as_tensor(theta, dtype=torch.float64, device="cuda").contiguous()
+    phi = torch.as_tensor(phi, dtype=torch.float64, device="cuda").contiguous()
+    eul = (ctypes.c_double * 3)()
+    ts = ctypes.c_double()
+    _check(lib().psht_patch_rotation(_ptr(theta), _ptr(phi), theta.numel(), eul, ctypes.byref(ts), _stream(stream)))
+    return (eul[0], eul[1], eul[2]), ts.value
