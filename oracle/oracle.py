@@ -424,9 +424,45 @@ def mcut(lmax: int, s: int, eps: float, beta) -> np.ndarray:
     return out
 
 
-def plan_params(lmax: int, s: int, eps: float, theta, kappa: float = 1.0, window_kind: str = "es") -> dict:
+def legendre_cost(lmax: int, s: int, Mj) -> int:
+    """(ring, m, l) steps of the recursion: sum over rings j and 0 <= m <= M_j of lmax - max(m, s) + 1."""
+    tot = 0
+    for M in np.asarray(Mj, dtype=np.int64):
+        m = np.arange(int(M) + 1)
+        tot += int(np.sum(lmax - np.maximum(m, s) + 1))
+    return tot
+
+
+def cost_optimal_eps_apo(lmax: int, s: int, eps: float, tstar: float, kappa: float = 1.0):
+    """The apodisation length that minimises the Legendre cost inclusive of polar optimisation, the
+    alternative to eq. Lmax2 the paper mentions beside it (Sec. II.C).  For a relative apodisation
+    length e = Delta theta / theta*, the window adds Delta Lmax = Delta l pi / Delta theta modes
+    (Delta l = 2 alpha), so Lmax(e) = (lmax + Delta l pi / (e theta*)) theta* (1 + e) / pi; eq. Lmax2
+    is its minimum over e.  Candidates e = e0 r, r = (20 + k)/40, k = 0..80 (e0 the paper's value);
+    returns (e, Lmax) of the cheapest (the first on ties), or None if every candidate needs the full
+    sky."""
+    lneps = abs(math.log(eps))
+    e0 = math.sqrt(2.0 * lneps / (tstar * lmax))
+    best = None
+    for k in range(81):
+        e = e0 * ((20 + k) / 40.0)
+        tmax = tstar * (1.0 + e)
+        Lmax = math.ceil(kappa * lmax * tstar / math.pi * (1.0 + e) * (1.0 + e0 * e0 / e))
+        if tmax >= math.pi or Lmax >= lmax:
+            continue
+        L = fft_friendly(Lmax + 1)
+        beta_j = np.arange(L) * (math.pi / L) * (tmax / math.pi)
+        cost = legendre_cost(lmax, s, mcut(lmax, s, eps, beta_j))
+        if best is None or cost < best[0]:
+            best = (cost, e, Lmax)
+    return None if best is None else (best[1], best[2])
+
+
+def plan_params(lmax: int, s: int, eps: float, theta, kappa: float = 1.0, window_kind: str = "es",
+                eps_apo_choice: str = "paper") -> dict:
     """P0-P2 of the partial-sky method plus the NUFFT grid (see module docstring); kappa scales the
-    band limit Lmax (Sec. II.C), window_kind picks the bell (Sec. II.D)."""
+    band limit Lmax (Sec. II.C), window_kind picks the bell (Sec. II.D), eps_apo_choice "cost" takes
+    the apodisation length from ``cost_optimal_eps_apo`` instead of eq. Lmax2."""
     theta = np.asarray(theta, dtype=np.float64)
     bN = float(theta.max()) if theta.size else 0.0
     bS = float((math.pi - theta).max()) if theta.size else 0.0
@@ -443,6 +479,12 @@ def plan_params(lmax: int, s: int, eps: float, theta, kappa: float = 1.0, window
         Lmax = math.ceil(kappa * lmax * tstar / math.pi * (1.0 + eps_apo) ** 2)
         if tmax >= math.pi or Lmax >= lmax:
             full = True
+        if eps_apo_choice == "cost":
+            opt = cost_optimal_eps_apo(lmax, s, eps, tstar, kappa)
+            full = opt is None
+            if opt is not None:
+                eps_apo, Lmax = opt
+                tmax = tstar * (1.0 + eps_apo)
     if full:
         eps_apo, tmax, Lmax, dTheta = 0.0, math.pi, lmax, 0.0
     else:
