@@ -121,9 +121,17 @@ int psht_plan_adjoint(psht_plan* plan, const void* f, void* g, void* c, void* st
  */
 #define PSHT_WINDOW_ES 0
 #define PSHT_WINDOW_KB 1
+#define PSHT_APO_PAPER 0    /* eps_apo = sqrt(2 |ln eps| / (theta_star lmax)), minimising Lmax (eq. Lmax2)  */
+#define PSHT_APO_COST 1     /* eps_apo minimising the recursion's (ring, m, l) count with polar          */
+                            /* optimisation, the alternative the paper mentions beside eq. Lmax2        */
 typedef struct {
   int window;
   double kappa;
+  /* apodisation: PSHT_APO_PAPER (default) or PSHT_APO_COST.  With PSHT_APO_COST the planner tries
+   * eps_apo = e0 (20 + k)/40, k = 0..80 (e0 the paper's value), with the band limit the window needs
+   * for that apodisation length, Lmax = ceil(kappa (lmax theta_star / pi)(1 + eps_apo)(1 + e0^2/eps_apo))
+   * (the paper's Lmax before minimisation over eps_apo), and keeps the cheapest. */
+  int apodisation;
 } psht_options;
 /* psht_plan_create with options; opt may be NULL (defaults). */
 int psht_plan_create_ex(int spin, int lmax, const double* theta, const double* phi, int64_t npts, double eps,

@@ -188,6 +188,41 @@ std::vector<T> cast_vec(const std::vector<double>& v) {
 // P1-P2 and the grid: everything that depends on (spin, lmax, eps, precision, theta*, pole)
 int64_t adj_part_elems(const Plan& p);
 
+// (ring, m, l) steps of the recursion on one ring with cutoff M: sum_{m=0}^{M} (lmax + 1 - max(m, s))
+int64_t ring_cost(int lmax, int s, int M) {
+  const int64_t n = (int64_t)(M + 1) * (lmax + 1);
+  const int64_t sm = M < s ? (int64_t)(M + 1) * s : (int64_t)s * s + ((int64_t)M * (M + 1) - (int64_t)(s - 1) * s) / 2;
+  return n - sm;
+}
+
+// The apodisation length minimising the recursion's step count with polar optimisation: for
+// eps_apo = e the window adds Delta l pi / (e theta*) modes, Lmax(e) = kappa (lmax theta*/pi)(1 + e)
+// (1 + e0^2/e), minimal at the paper's e0 (eq. Lmax2); candidates e = e0 (20 + k)/40, k = 0..80.
+// False if every candidate needs the full sky.
+bool cost_optimal_apo(const Plan& p, double e0, double& e_best, int& Lmax_best) {
+  bool found = false;
+  int64_t best = 0;
+  for (int k = 0; k <= 80; ++k) {
+    const double e = e0 * ((20 + k) / 40.0);
+    const double tmax = p.theta_star * (1.0 + e);
+    const int Lmax = (int)ceil(p.kappa * p.lmax * p.theta_star / M_PI * (1.0 + e) * (1.0 + e0 * e0 / e));
+    if (tmax >= M_PI || Lmax >= p.lmax) continue;
+    const int L = fft_friendly(Lmax + 1);
+    int64_t cost = 0;
+    for (int j = 0; j < L; ++j) {
+      const double Th = j * (M_PI / L);
+      cost += ring_cost(p.lmax, p.spin, mcut(p.lmax, p.spin, p.eps, Th * (tmax / M_PI)));
+    }
+    if (!found || cost < best) {
+      found = true;
+      best = cost;
+      e_best = e;
+      Lmax_best = Lmax;
+    }
+  }
+  return found;
+}
+
 void layout(Plan& p, double theta_star) {
   const double lneps = fabs(log(p.eps));
   p.theta_star = std::max(theta_star, 1e-9);
@@ -197,6 +232,16 @@ void layout(Plan& p, double theta_star) {
     p.theta_max = p.theta_star * (1.0 + p.eps_apo);
     p.Lmax = (int)ceil(p.kappa * p.lmax * p.theta_star / M_PI * (1.0 + p.eps_apo) * (1.0 + p.eps_apo));
     if (p.theta_max >= M_PI || p.Lmax >= p.lmax) full = true;
+    if (p.apo_cost) {
+      double e = 0.0;
+      int Lm = 0;
+      full = !cost_optimal_apo(p, p.eps_apo, e, Lm);
+      if (!full) {
+        p.eps_apo = e;
+        p.theta_max = p.theta_star * (1.0 + e);
+        p.Lmax = Lm;
+      }
+    }
   }
   p.full = full ? 1 : 0;
   if (full) {
@@ -376,8 +421,11 @@ void apply_options(Plan& p, const psht_options* opt) {
   PSHT_REQUIRE(opt->window == PSHT_WINDOW_ES || opt->window == PSHT_WINDOW_KB, PSHT_EINVAL, "unknown window");
   PSHT_REQUIRE(opt->kappa == 0.0 || (opt->kappa >= 0.25 && opt->kappa <= 4.0), PSHT_EINVAL,
                "kappa must be 0 (default) or lie in [0.25, 4]");
+  PSHT_REQUIRE(opt->apodisation == PSHT_APO_PAPER || opt->apodisation == PSHT_APO_COST, PSHT_EINVAL,
+               "unknown apodisation choice");
   p.window = opt->window;
   p.kappa = opt->kappa == 0.0 ? 1.0 : opt->kappa;
+  p.apo_cost = opt->apodisation == PSHT_APO_COST ? 1 : 0;
 }
 
 // device scratch freed on scope exit (after the stream work that uses it: cudaFree waits for the device)

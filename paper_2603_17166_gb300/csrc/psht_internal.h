@@ -92,6 +92,7 @@ struct Plan {
   int force_full = 0;  // PSHT_FULL_SKY
   int window = 0;      // PSHT_WINDOW_ES or PSHT_WINDOW_KB
   double kappa = 1.0;  // ring-count factor in Lmax
+  int apo_cost = 0;    // PSHT_APO_COST: eps_apo minimising the recursion's step count
   double theta_star = 0, eps_apo = 0, theta_max = 0, dTheta = 0, alpha = 0;
   int Lmax = 0, L = 0, nring = 0, M = 0, W = 0;
   double beta_es = 0;

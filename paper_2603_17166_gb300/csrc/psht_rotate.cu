@@ -25,8 +25,10 @@
 //
 // One CTA per (degree l, block of 512 outputs j): 128 threads with four outputs each walk i = l..0
 // in lockstep, reading the staged inputs and recurrence coefficients of each chunk of 512 i from
-// shared memory by broadcast; the sums stay in registers.  Work per stage: (l+1)^2 recurrence steps
-// per degree, each a multiply, a multiply-add and one multiply-add per coefficient set.
+// shared memory by broadcast; the sums stay in registers.  (Staging per warp instead, to spare the
+// warps the per-chunk barrier, measured 7 % slower: four times the staging work, fewer warps.)  Work per stage: (l+1)^2 recurrence steps
+// per degree, each a multiply and a multiply-add (normalised form, see k_rot_coef) and one
+// multiply-add per coefficient set, on pairs of outputs (FP32x2 instructions in the FP32 form).
 #include <math.h>
 
 #include <algorithm>
@@ -41,7 +43,8 @@ namespace psht {
 namespace {
 
 constexpr int kRotNT = 128;              // threads per CTA
-constexpr int kRotKPT = 4;               // outputs j per thread
+constexpr int kRotNPAIR = 2;             // output pairs per thread (even)
+constexpr int kRotKPT = 2 * kRotNPAIR;   // outputs j per thread
 constexpr int kRotJB = kRotNT * kRotKPT; // outputs per CTA
 constexpr int kRotCH = 512;              // i values staged per chunk
 
@@ -77,23 +80,33 @@ struct Vec4<double> {
 __host__ __device__ inline int64_t tri_off(int l) { return (int64_t)l * (l + 1) / 2; }
 __host__ __device__ inline int64_t alm_base(int lmax, int m) { return (int64_t)m * (2 * lmax + 1 - m) / 2; }
 
-// coefficients of the recurrence in the second index, per (l, i), degree-major triangle:
-// c.x = -2 / sqrt((l+i)(l-i+1)), c.y = sqrt((l-i)(l+i+1)) / sqrt((l+i)(l-i+1)), zero at i = 0
+// Coefficients of the recurrence in the second index, per (l, i), degree-major triangle, in the
+// normalised form used by the kernels.  With p_i = -2 / sqrt((l+i)(l-i+1)) and
+// q_i = sqrt((l-i)(l+i+1)) / sqrt((l+i)(l-i+1)) the recurrence reads
+//   Delta_{i-1} = j p_i Delta_i - q_i Delta_{i+1}.
+// Writing Delta_i = s_i sigma_i u_i with sigma_l = sigma_{l-1} = 1, sigma_{i-1} = q_i sigma_{i+1}
+// (so sigma lies in (0, 1]: about 0.13 at l = 4096) and s_i = (-1)^floor((l-i)/2) turns it into
+//   u_{i-1} = j c.x_i u_i + u_{i+1},   c.x_i = p_i (sigma_i / sigma_{i-1}) (s_{i-1} / s_i),
+// one multiply and one multiply-add per step, and the products Delta_i W_i into u_i (c.y_i W_i),
+// c.y_i = s_i sigma_i, folded into the staged inputs.  One thread per degree (the sigma chain is
+// sequential), FP64.
 template <typename T>
 __global__ void k_rot_coef(int lmax, typename Cx<T>::V* __restrict__ coef) {
-  const int64_t n = tri_off(lmax + 1);
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-    int l = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-    while (tri_off(l) > t) --l;
-    while (tri_off(l + 1) <= t) ++l;
-    const int i = (int)(t - tri_off(l));
-    double p = 0.0, q = 0.0;
-    if (i > 0) {
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l <= lmax; l += gridDim.x * blockDim.x) {
+    typename Cx<T>::V* cf = coef + tri_off(l);
+    double sig_up = 1.0, sig = 1.0;  // sigma_{i+1}, sigma_i
+    for (int i = l; i >= 1; --i) {
       const double den = 1.0 / sqrt((double)(l + i) * (double)(l - i + 1));
-      p = -2.0 * den;
-      q = sqrt((double)(l - i) * (double)(l + i + 1)) * den;
+      const double p = -2.0 * den;
+      const double q = sqrt((double)(l - i) * (double)(l + i + 1)) * den;
+      const double sig_dn = (i == l) ? 1.0 : q * sig_up;  // sigma_{i-1}
+      const double si = (((l - i) >> 1) & 1) ? -1.0 : 1.0, sd = (((l - i + 1) >> 1) & 1) ? -1.0 : 1.0;
+      cf[i] = mk((T)(p * (sig / sig_dn) * (sd * si)), (T)(si * sig));
+      sig_up = sig;
+      sig = sig_dn;
     }
-    coef[t] = mk((T)p, (T)q);
+    const double s0 = ((l >> 1) & 1) ? -1.0 : 1.0;
+    cf[0] = mk((T)0, (T)(s0 * sig));
   }
 }
 
@@ -124,10 +137,21 @@ __global__ void k_rot_phases(int lmax, double alpha, double beta, double gamma, 
   }
 }
 
+// packed pair arithmetic: two outputs per register pair (FP32x2 instructions for float)
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 fma2(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double2 mul2(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+
 // One contraction stage.  STAGE 1 reads the packed m-major input a[alm_base(i) + l] and writes
 // z[tri_off(l) + j]; STAGE 2 reads z[tri_off(l) + i] and writes a'[alm_base(j) + l].
 // pre[i] multiplies the input, post[j] the output (STAGE 2 only).  msc weighs the inputs i > 0
 // (STAGE 1) or the outputs j > 0 (STAGE 2): the packed-gradient conventions of the plan entry points.
+// Thread t owns outputs j0 + r, j0 = jfirst + 2 P t, r = 0..2P-1 (P = kRotNPAIR, even), held as P
+// pairs: pair k = (r = k, r = k + P), so both members of a pair have the parity of k and read the
+// same staged input.
 template <typename T, int STAGE, int NSET>
 __global__ void __launch_bounds__(kRotNT) k_rot_stage(int lmax, const typename Cx<T>::V* __restrict__ in0,
                                                        const typename Cx<T>::V* __restrict__ in1,
@@ -142,38 +166,62 @@ __global__ void __launch_bounds__(kRotNT) k_rot_stage(int lmax, const typename C
   const int l = lmax - (int)blockIdx.y;
   const int jfirst = (int)blockIdx.x * kRotJB;
   if (jfirst > l) return;
-  __shared__ V4 sW[kRotCH];  // per i: (W0 set 0, W1 set 0, W0 set 1, W1 set 1)
-  __shared__ V sC[kRotCH];   // per i: recurrence coefficients
+  __shared__ V4 sW[kRotCH];  // per i: (W0 set 0, W1 set 0, W0 set 1, W1 set 1), times c.y_i
+  __shared__ T sC[kRotCH];   // per i: recurrence coefficient c.x_i
   const int tid = threadIdx.x;
   const int j0 = jfirst + kRotKPT * tid;
 
-  T d[kRotKPT], dn[kRotKPT], mj[kRotKPT];
-  int ex[kRotKPT];
-  T acc[kRotKPT][2][NSET];  // [output][parity of l+i][set]
+  constexpr int NP = kRotNPAIR;
+  V u[NP], un[NP], mj[NP], acc[NP][2][NSET];  // [pair][parity of l+i][set]
+  int ex[NP][2];                               // scale exponent of each pair member
 #pragma unroll
-  for (int r = 0; r < kRotKPT; ++r) {
-    const int j = j0 + r;
-    dn[r] = (T)0;
-    mj[r] = (T)j;
-    ex[r] = 0;
-    d[r] = (T)0;
-    if (j <= l) {
-      // log2 Delta_{j,l} = log2 sqrt(C(2l, l+j)) - l
-      double x = 0.5 * (lf[2 * l] - lf[l + j] - lf[l - j]) - (double)l;
-      constexpr double low = RotScale<T>::LOG_BIG - RotScale<T>::LOG_STEP;
-      if (x < low) {  // bring the mantissa into [2^low, 2^B)
-        const double nres = ceil((low - x) / RotScale<T>::LOG_STEP);
-        x += nres * RotScale<T>::LOG_STEP;
-        ex[r] = -(int)nres;
+  for (int k = 0; k < NP; ++k) {
+    T uu[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = j0 + k + NP * h;
+      ex[k][h] = 0;
+      uu[h] = (T)0;
+      if (j <= l) {
+        // log2 Delta_{j,l} = log2 sqrt(C(2l, l+j)) - l  (u_l = Delta_{j,l}: s_l = sigma_l = 1)
+        double x = 0.5 * (lf[2 * l] - lf[l + j] - lf[l - j]) - (double)l;
+        constexpr double low = RotScale<T>::LOG_BIG - RotScale<T>::LOG_STEP;
+        if (x < low) {  // bring the mantissa into [2^low, 2^B)
+          const double nres = ceil((low - x) / RotScale<T>::LOG_STEP);
+          x += nres * RotScale<T>::LOG_STEP;
+          ex[k][h] = -(int)nres;
+        }
+        uu[h] = (T)exp2(x);
       }
-      d[r] = (T)exp2(x);
     }
+    u[k] = mk(uu[0], uu[1]);
+    un[k] = mk((T)0, (T)0);
+    mj[k] = mk((T)(j0 + k), (T)(j0 + k + NP));
 #pragma unroll
     for (int p = 0; p < 2; ++p)
 #pragma unroll
-      for (int s = 0; s < NSET; ++s) acc[r][p][s] = (T)0;
+      for (int s = 0; s < NSET; ++s) acc[k][p][s] = mk((T)0, (T)0);
   }
   bool fast = false;  // every output of this warp is at scale 0: no gate, no rescale test
+
+  auto rescale = [&]() {
+    bool all0 = true;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      if (fabs(u[k].x) > RotScale<T>::big()) {
+        u[k].x *= RotScale<T>::step();
+        un[k].x *= RotScale<T>::step();
+        ex[k][0] += 1;
+      }
+      if (fabs(u[k].y) > RotScale<T>::big()) {
+        u[k].y *= RotScale<T>::step();
+        un[k].y *= RotScale<T>::step();
+        ex[k][1] += 1;
+      }
+      all0 = all0 && ex[k][0] == 0 && ex[k][1] == 0;
+    }
+    return all0;
+  };
 
   for (int ihi = l; ihi >= 0; ihi -= kRotCH) {
     const int ilo = max(0, ihi - kRotCH + 1);
@@ -190,9 +238,10 @@ __global__ void __launch_bounds__(kRotNT) k_rot_stage(int lmax, const typename C
         if (NSET == 2) x1 = in1[k];
       }
       const V ph = pre[i];
+      const V c = coef[tri_off(l) + i];
       x0 = cmul(x0, ph);
       x1 = cmul(x1, ph);
-      const T two = i == 0 ? (T)1 : (STAGE == 1 ? (T)2 * msc : (T)2);
+      const T two = (i == 0 ? (T)1 : (STAGE == 1 ? (T)2 * msc : (T)2)) * c.y;
       const T R0 = two * x0.x, I0 = i == 0 ? (T)0 : two * x0.y;
       const T R1 = two * x1.x, I1 = i == 0 ? (T)0 : two * x1.y;
       const bool odd = ((l + i) & 1) != 0;
@@ -202,7 +251,7 @@ __global__ void __launch_bounds__(kRotNT) k_rot_stage(int lmax, const typename C
       w.z = odd ? I1 : R1;
       w.w = odd ? R1 : I1;
       sW[i - ilo] = w;
-      sC[i - ilo] = coef[tri_off(l) + i];
+      sC[i - ilo] = c.x;
     }
     __syncthreads();
 
@@ -210,22 +259,24 @@ __global__ void __launch_bounds__(kRotNT) k_rot_stage(int lmax, const typename C
     // for ihi = l - 512 c)
     auto step = [&](int i, int P, bool gated) {
       const V4 w = sW[i - ilo];
-      const V c = sC[i - ilo];
+      const T cx = sC[i - ilo];
+      const V cx2 = mk(cx, cx);
 #pragma unroll
-      for (int r = 0; r < kRotKPT; ++r) {
-        const T dv = (gated && ex[r] != 0) ? (T)0 : d[r];
-        const T wa = (r & 1) ? w.y : w.x;
-        if (P == 0) acc[r][0][0] = fma(dv, wa, acc[r][0][0]);
-        else acc[r][1][0] = fma(dv, wa, acc[r][1][0]);
-        if (NSET == 2) {
-          const T wb = (r & 1) ? w.w : w.z;
-          if (P == 0) acc[r][0][NSET - 1] = fma(dv, wb, acc[r][0][NSET - 1]);
-          else acc[r][1][NSET - 1] = fma(dv, wb, acc[r][1][NSET - 1]);
+      for (int k = 0; k < NP; ++k) {
+        V dv = u[k];
+        if (gated) {
+          if (ex[k][0] != 0) dv.x = (T)0;
+          if (ex[k][1] != 0) dv.y = (T)0;
         }
-        const T jp = mj[r] * c.x;
-        const T nd = fma(jp, d[r], -(c.y * dn[r]));
-        dn[r] = d[r];
-        d[r] = nd;
+        const T wa = (k & 1) ? w.y : w.x;
+        acc[k][P][0] = fma2(dv, mk(wa, wa), acc[k][P][0]);
+        if (NSET == 2) {
+          const T wb = (k & 1) ? w.w : w.z;
+          acc[k][P][NSET - 1] = fma2(dv, mk(wb, wb), acc[k][P][NSET - 1]);
+        }
+        const V nu = fma2(mul2(mj[k], cx2), u[k], un[k]);
+        un[k] = u[k];
+        u[k] = nu;
       }
     };
     int i = ihi;
@@ -236,17 +287,7 @@ __global__ void __launch_bounds__(kRotNT) k_rot_stage(int lmax, const typename C
       step(i - 2, 0, true);
       step(i - 3, 1, true);
       i -= 4;
-      bool all0 = true;
-#pragma unroll
-      for (int r = 0; r < kRotKPT; ++r) {
-        if (fabs(d[r]) > RotScale<T>::big()) {
-          d[r] *= RotScale<T>::step();
-          dn[r] *= RotScale<T>::step();
-          ex[r] += 1;
-        }
-        all0 = all0 && ex[r] == 0;
-      }
-      fast = __all_sync(0xffffffffu, all0);
+      fast = __all_sync(0xffffffffu, rescale());
     }
     if (fast) {
       for (; i >= ilo + 1; i -= 2) {
@@ -259,13 +300,7 @@ __global__ void __launch_bounds__(kRotNT) k_rot_stage(int lmax, const typename C
         step(i, 0, true);
         step(i - 1, 1, true);
       }
-#pragma unroll
-      for (int r = 0; r < kRotKPT; ++r)
-        if (fabs(d[r]) > RotScale<T>::big()) {
-          d[r] *= RotScale<T>::step();
-          dn[r] *= RotScale<T>::step();
-          ex[r] += 1;
-        }
+      rescale();
     }
     if (i == ilo) step(i, 0, !fast);
     __syncthreads();
@@ -273,22 +308,26 @@ __global__ void __launch_bounds__(kRotNT) k_rot_stage(int lmax, const typename C
 
   // outputs: for even j, S_e = acc[.][0], S_o = acc[.][1]; for odd j the other way round
 #pragma unroll
-  for (int r = 0; r < kRotKPT; ++r) {
-    const int j = j0 + r;
-    if (j > l) continue;
+  for (int k = 0; k < NP; ++k) {
 #pragma unroll
-    for (int s = 0; s < NSET; ++s) {
-      const T Se = (r & 1) ? acc[r][1][s] : acc[r][0][s];
-      const T So = (r & 1) ? acc[r][0][s] : acc[r][1][s];
-      V* out = s == 0 ? out0 : out1;
-      if (STAGE == 1) {
-        out[tri_off(l) + j] = mk(Se, So);
-      } else {
-        const T sg = (l & 1) ? (T)-1 : (T)1;
-        V v = cmul(mk(sg * Se, -sg * So), post[j]);
-        if (j == 0) v.y = (T)0;
-        else v = cscale(v, msc);
-        out[alm_base(lmax, j) + l] = v;
+    for (int h = 0; h < 2; ++h) {
+      const int j = j0 + k + NP * h;
+      if (j > l) continue;
+#pragma unroll
+      for (int s = 0; s < NSET; ++s) {
+        const V ae = (k & 1) ? acc[k][1][s] : acc[k][0][s];
+        const V ao = (k & 1) ? acc[k][0][s] : acc[k][1][s];
+        const T Se = h ? ae.y : ae.x, So = h ? ao.y : ao.x;
+        V* out = s == 0 ? out0 : out1;
+        if (STAGE == 1) {
+          out[tri_off(l) + j] = mk(Se, So);
+        } else {
+          const T sg = (l & 1) ? (T)-1 : (T)1;
+          V v = cmul(mk(sg * Se, -sg * So), post[j]);
+          if (j == 0) v.y = (T)0;
+          else v = cscale(v, msc);
+          out[alm_base(lmax, j) + l] = v;
+        }
       }
     }
   }
@@ -504,9 +543,9 @@ Rotator* rotator_create(int lmax, int prec, cudaStream_t st) {
   if ((e = cudaMalloc(&r->d_ph, (size_t)3 * (lmax + 1) * cb)) != cudaSuccess) fail(e);
   if ((e = cudaMalloc(&r->d_z, (size_t)2 * r->nalm * cb)) != cudaSuccess) fail(e);
   r->bytes = rotator_bytes(lmax, prec);
-  const int nb = (int)std::min<int64_t>((r->nalm + 255) / 256, 152 * 16);
-  if (prec == 64) k_rot_coef<double><<<nb, 256, 0, st>>>(lmax, (double2*)r->d_coef);
-  else k_rot_coef<float><<<nb, 256, 0, st>>>(lmax, (float2*)r->d_coef);
+  const int nb = (lmax + 64) / 64;
+  if (prec == 64) k_rot_coef<double><<<nb, 64, 0, st>>>(lmax, (double2*)r->d_coef);
+  else k_rot_coef<float><<<nb, 64, 0, st>>>(lmax, (float2*)r->d_coef);
   k_rot_logfact<<<(2 * lmax + 2 + 255) / 256, 256, 0, st>>>(2 * lmax + 1, r->d_lf);
   if ((e = cudaGetLastError()) != cudaSuccess) fail(e);
   return r;

@@ -37,10 +37,11 @@ class PshtInfo(ctypes.Structure):
 
 
 class PshtOptions(ctypes.Structure):
-    _fields_ = [("window", ctypes.c_int), ("kappa", ctypes.c_double)]
+    _fields_ = [("window", ctypes.c_int), ("kappa", ctypes.c_double), ("apodisation", ctypes.c_int)]
 
 
 _WINDOW = {"es": 0, "kb": 1}
+_APO = {"paper": 0, "cost": 1}
 
 
 class PshtRequest(ctypes.Structure):
@@ -150,7 +151,8 @@ class Plan:
     """A plan for synthesis general and its adjoint at fixed points (psht_plan_create)."""
 
     def __init__(self, spin: int, lmax: int, theta, phi, eps: float, precision="auto", stream=None,
-                 full_sky: bool = False, window: str = "es", kappa: float = 1.0, patch_frame: bool = False):
+                 full_sky: bool = False, window: str = "es", kappa: float = 1.0, patch_frame: bool = False,
+                 apodisation: str = "paper"):
         torch = _torch()
         theta = torch.as_tensor(theta, dtype=torch.float64, device="cuda").contiguous()
         phi = torch.as_tensor(phi, dtype=torch.float64, device="cuda").contiguous()
@@ -158,11 +160,11 @@ class Plan:
             raise ValueError("theta and phi must be 1-D tensors of equal length")
         self._h = ctypes.c_void_p()
         flags = _PREC[precision] | (PSHT_FULL_SKY if full_sky else 0) | (PSHT_PATCH_FRAME if patch_frame else 0)
-        if window == "es" and kappa == 1.0:
+        if window == "es" and kappa == 1.0 and apodisation == "paper":
             _check(lib().psht_plan_create(int(spin), int(lmax), _ptr(theta), _ptr(phi), theta.numel(), float(eps),
                                           flags, _stream(stream), ctypes.byref(self._h)))
         else:
-            opt = PshtOptions(_WINDOW[window], float(kappa))
+            opt = PshtOptions(_WINDOW[window], float(kappa), _APO[apodisation])
             _check(lib().psht_plan_create_ex(int(spin), int(lmax), _ptr(theta), _ptr(phi), theta.numel(),
                                              float(eps), flags, ctypes.byref(opt), _stream(stream),
                                              ctypes.byref(self._h)))
@@ -386,7 +388,7 @@ def predict_error(spin: int, lmax: int, theta_star: float, eps: float, cl, beta,
     if cl.size != lmax + 1:
         raise ValueError("cl must hold lmax + 1 values")
     out = np.zeros(beta.size)
-    opt = PshtOptions(_WINDOW[window], float(kappa))
+    opt = PshtOptions(_WINDOW[window], float(kappa), 0)
     _check(lib().psht_predict_error(int(spin), int(lmax), float(theta_star), float(eps), ctypes.byref(opt),
                                     ctypes.c_void_p(cl.ctypes.data), ctypes.c_void_p(beta.ctypes.data), beta.size,
                                     ctypes.c_void_p(out.ctypes.data), _stream(stream)))

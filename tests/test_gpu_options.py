@@ -88,3 +88,27 @@ def test_predictor_bounds_lowered_band_limit():
     assert measured.max() > 100 * eps
     ratio = measured / pred
     assert np.all(ratio > 0.5) and np.all(ratio < 2.0), ratio
+
+
+@pytest.mark.parametrize("s,deg,prec,eps", [(2, 25.0, "fp64", 1e-10), (0, 7.0, "fp64", 1e-8), (2, 20.0, "fp32", 1e-5)])
+def test_cost_optimal_apodisation(s, deg, prec, eps):
+    """PSHT_APO_COST: the planner's apodisation length and ring set equal the oracle's search, the
+    recursion takes no more steps than with eq. Lmax2, and the result stays within 10 eps."""
+    from paper_2603_17166_gb300 import Plan
+
+    rng = np.random.default_rng(63)
+    lmax = 256
+    th, ph = _cap(rng, 2500, math.radians(deg))
+    P = O.plan_params(lmax, s, eps, th, eps_apo_choice="cost")
+    plan = Plan(s, lmax, torch.from_numpy(th).cuda(), torch.from_numpy(ph).cuda(), eps, precision=prec,
+                apodisation="cost")
+    ref_plan = Plan(s, lmax, torch.from_numpy(th).cuda(), torch.from_numpy(ph).cuda(), eps, precision=prec)
+    i = plan.info
+    assert (i["Lmax"], i["L"], i["nring"], i["M"]) == (P["Lmax"], P["L"], P["nring"], P["M"])
+    assert i["eps_apo"] == pytest.approx(P["eps_apo"], rel=1e-15)
+    assert i["recursion_triples"] <= ref_plan.info["recursion_triples"]
+    _, w, _ = plan.rings()
+    assert np.allclose(w, P["w_j"], rtol=0, atol=1e-12)
+    g = _alm(rng, lmax, s)
+    f = plan.synthesis(torch.from_numpy(g).cuda().to(plan.cdtype)).cpu().numpy().astype(np.complex128)
+    assert O.rel_l2(f, O.direct_synthesis(lmax, s, g, None, th, ph)) <= 10 * eps
