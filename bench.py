@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--serve-nmax", type=int, default=30_000_000)
     ap.add_argument("--no-frames", action="store_true",
                     help="skip the frame comparison (points as given about the nearer pole vs the patch frame)")
+    ap.add_argument("--rotation", action="store_true",
+                    help="time only the rotation of (g, c) at lmax 4096 (FP32 and FP64 forms) and print its line")
     ap.add_argument("--table1", action="store_true",
                     help="re-measure the partial-sky / full-sky speed-ups of the paper's Table 1 instead")
     ap.add_argument("--cpu-sample-points", type=int, default=1_000_000)
@@ -393,6 +395,51 @@ def run_frames(args, dev, K: int = 5) -> dict:
     return out
 
 
+# ----------------------------------------------------------------------------- rotation alone
+def run_rotation(args) -> dict:
+    """One rotation of the ~4% field's (g, c) at lmax 4096, spin 2 spectra, per form: K timed calls
+    after W warm-up calls, CUDA events.  Roofline of its contraction kernel k_rot_stage (two
+    launches per rotation): 7 flops per (degree, output, step) -- the recurrence's multiply and
+    multiply-add (3) and one multiply-add per set (2 x 2) -- over sum_l (l+1)^2 steps per launch."""
+    import torch
+    from paper_2603_17166_gb300 import Rotator, synthetic
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    gen = synthetic.rng(2, "alm")
+    g0 = synthetic.gaussian_alm(LMAX, SPIN, gen, "inv_l2")
+    c0 = synthetic.gaussian_alm(LMAX, SPIN, gen, "inv_l2")
+    steps = sum((l + 1) ** 2 for l in range(LMAX + 1))
+    out = {"metric": "rotation of (g, c), lmax 4096", "unit": "ms", "higher_is_better": False,
+           "config": {"workload": "Wigner-D rotation of two packed a_lm sets, lmax 4096, (alpha, beta, gamma) "
+                                  "= (0, 0.61, 2.2)", "lmax": LMAX}, "forms": {}}
+    for name, K in (("fp32", args.steps), ("fp64", max(1, min(args.steps, 2)))):
+        rot = Rotator(LMAX, precision=name, stream=stream)
+        g = torch.from_numpy(g0).to(dev).to(rot.cdtype)
+        c = torch.from_numpy(c0).to(dev).to(rot.cdtype)
+        go, co = torch.empty_like(g), torch.empty_like(c)
+        for _ in range(max(1, args.warmup if name == "fp32" else 1)):
+            rot.apply(g, c, 0.0, 0.61, 2.2, g_out=go, c_out=co, stream=stream)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            rot.apply(g, c, 0.0, 0.61, 2.2, g_out=go, c_out=co, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / K
+        flops = 7.0 * steps
+        peak = alu_peak_tflops(64 if name == "fp64" else 32)
+        achieved = flops / (0.5 * ms * 1e-3) / 1e12  # two stage launches of equal work per rotation
+        out["forms"][name] = dict(ms=ms, steps=K, roofline=dict(
+            bound="alu", kernel="k_rot_stage", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
+            flops_per_launch=flops))
+        rot.close()
+        del g, c, go, co
+    out["value"] = out["forms"]["fp32"]["ms"]
+    return out
+
+
 # ----------------------------------------------------------------------------- serving
 def run_serving(args, dev) -> dict:
     """Mixed request stream through the library's request server (psht_server_*): a pool of
@@ -643,6 +690,10 @@ def main():
     if args.table1:
         if rank == 0:
             print(json.dumps(run_table1(args)))
+        return
+    if args.rotation:
+        if rank == 0:
+            print(json.dumps(run_rotation(args)))
         return
     if args.impl == "reference":
         line = run_reference(args, rank, world)
