@@ -101,3 +101,44 @@ def test_ring_coefficients_sampled_rings(planned, workload):
     js = np.unique(np.linspace(0, i["nring"] - 1, 24).astype(int))
     Fo = O.ring_synthesis(4096, 2, i["M"], workload["g"], workload["c"], th_j[js])
     assert O.rel_l2(F[js], Fo) <= (1e-11 if plan.precision == 64 else 10 * eps)
+
+
+@pytest.mark.parametrize("prec,eps", [("fp32", 1e-5), ("fp64", 1e-10)])
+def test_patch_frame_full_size(prec, eps):
+    """The same field's points as given (centre near dec -55 deg, theta* 48 deg about the south pole)
+    through a patch-frame plan: theta* drops to the smallest cap's 34.7 deg; sampled points against
+    the direct sum in the caller's frame, selected adjoint coefficients summed over all points, and
+    the adjoint identity."""
+    from paper_2603_17166_gb300 import Plan, synthetic
+
+    wl = synthetic.config2(frame="S")
+    th = torch.from_numpy(wl["theta"]).cuda()
+    ph = torch.from_numpy(wl["phi"]).cuda()
+    plan = Plan(2, 4096, th, ph, eps, precision=prec, patch_frame=True)
+    assert 34.0 < np.degrees(plan.info["theta_star"]) < 35.0
+    g = torch.from_numpy(wl["g"]).cuda().to(plan.cdtype)
+    c = torch.from_numpy(wl["c"]).cuda().to(plan.cdtype)
+    f = plan.synthesis(g, c)
+    assert plan.status() == 0
+    sel = np.random.default_rng(13).choice(wl["theta"].size, size=96, replace=False)
+    ref = O.direct_synthesis(4096, 2, wl["g"], wl["c"], wl["theta"][sel], wl["phi"][sel])
+    got = f[torch.from_numpy(sel).cuda()].cpu().numpy().astype(np.complex128)
+    assert O.rel_l2(got, ref) <= 10 * eps
+    gt, ct = plan.adjoint(f)
+    ls = np.array([2, 3, 12, 40, 300, 1200])
+    ms = np.array([0, 1, 0, 40, 297, 1198])
+    g1, c1 = O.direct_adjoint_lm(2, wl["theta"], wl["phi"], f.cpu().numpy().astype(np.complex128), ls, ms)
+    idx = torch.from_numpy(O.alm_index(4096, ls, ms)).cuda()
+    got = np.concatenate([gt[idx].cpu().numpy(), ct[idx].cpu().numpy()]).astype(np.complex128)
+    assert O.rel_l2(got, np.concatenate([g1, c1])) <= 10 * eps
+    rng = np.random.default_rng(14)
+    n = wl["theta"].size
+    fr = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(plan.np_cdtype)
+    Aa = f.cpu().numpy().astype(np.complex128)
+    gt, ct = plan.adjoint(torch.from_numpy(fr).cuda())
+    lhs = O.map_dot(fr.astype(np.complex128), Aa)
+    rhs = O.alm_dot(gt.cpu().numpy().astype(np.complex128), wl["g"], 4096) + \
+        O.alm_dot(ct.cpu().numpy().astype(np.complex128), wl["c"], 4096)
+    assert abs(lhs - rhs) <= (1e-11 if prec == "fp64" else 1e-4) * abs(lhs)
+    plan.close()
+    torch.cuda.empty_cache()
