@@ -340,7 +340,8 @@ def run_ours(args, rank, world, local_rank):
 def run_frames(args, dev, K: int = 5) -> dict:
     """The same field's points as given (the box near the south pole): a plan about the nearer pole
     (theta* ~ 48 deg) against a patch-frame plan (theta* ~ 34.7 deg, a_lm rotated in and out on
-    every call), FP32 form; step = synthesis + adjoint, CUDA events, K steps after 2 warm-up steps."""
+    every call, and with the a_lm kept in the plan's frame), FP32 form; step = synthesis + adjoint,
+    CUDA events, K steps after 2 warm-up steps."""
     import torch
     from paper_2603_17166_gb300 import Plan, Rotator, synthetic
 
@@ -374,6 +375,15 @@ def run_frames(args, dev, K: int = 5) -> dict:
         out[key] = dict(ms_per_step=ms, mpoints_per_s=theta.numel() / ms / 1e3, plan_s=plan_s,
                         theta_star_deg=math.degrees(info["theta_star"]), L=info["L"], M=info["M"],
                         recursion_triples=info["recursion_triples"])
+        if patch:  # a_lm already in the plan's frame (an iterative solver after one rotation)
+            e0.record(stream)
+            for _ in range(K):
+                plan.synthesis(g, c, out=f, stream=stream, in_frame=True)
+                plan.adjoint(f, g_out=gt, c_out=ct, stream=stream, in_frame=True)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms2 = e0.elapsed_time(e1) / K
+            out["patch_frame_in_frame"] = dict(ms_per_step=ms2, mpoints_per_s=theta.numel() / ms2 / 1e3)
         plan.close()
         del g, c, f, gt, ct
     # the rotation alone: one rotation of (g, c) (a patch-frame step does two)

@@ -280,6 +280,17 @@ int psht_rotate_alm(int lmax, double alpha, double beta, double gamma, const voi
                     void* c_out, uint32_t flags, void* stream);
 
 /*
+ * Synthesis and adjoint of a PSHT_PATCH_FRAME plan with the a_lm in the plan's own frame (rotated
+ * by psht_plan_info's euler): no rotation on the way in or out, the points' spin-basis angle still
+ * applied, so f stays in the caller's frame and basis.  An iterative solver rotates its a_lm once
+ * (psht_rotator_apply with euler), iterates with these, and rotates the result back with
+ * (-gamma, -beta, -alpha).  Same arguments and rules as psht_plan_synthesis / psht_plan_adjoint;
+ * EINVAL for a plan without PSHT_PATCH_FRAME.
+ */
+int psht_plan_synthesis_inframe(psht_plan* plan, const void* g, const void* c, void* f, void* stream);
+int psht_plan_adjoint_inframe(psht_plan* plan, const void* f, void* g, void* c, void* stream);
+
+/*
  * Rotated points n_p = R p: theta_out in [0, pi], phi_out in [0, 2 pi), and (if psi_out is not NULL)
  * psi_p, the angle from e_theta(p) towards e_phi(p) of the rotated frame's e_theta at n_p carried
  * back by R^-1, so that f(p) = e^{i s psi_p} f'(n_p) for a spin-s map in the two frames.

@@ -718,9 +718,16 @@ void run_adjoint(Plan& p, const void* f, void* g, void* c, cudaStream_t st, doub
 // into the plan's frame first (the synthesis weight msc applies to the caller's m > 0 entries), and
 // the spin-s values carry each point's basis angle, f(p) = e^{i s psi_p} f'(R p); the adjoint is
 // the exact transpose: conjugate phase, adjoint in the plan's frame, inverse rotation.
-void exec_synthesis(Plan& p, const void* g, const void* c, void* f, cudaStream_t st, double msc = 1.0) {
+// rotate = false: the a_lm are already in the plan's frame (PSHT_PATCH_FRAME plans only)
+void exec_synthesis(Plan& p, const void* g, const void* c, void* f, cudaStream_t st, double msc = 1.0,
+                    bool rotate = true) {
   if (!p.patch) {
     run_synthesis(p, g, c, f, st, msc);
+    return;
+  }
+  if (!rotate) {
+    run_synthesis(p, g, c, f, st, msc);
+    if (p.d_sph) mul_phase_device(p.prec, f, p.d_sph, p.npts, false, f, st);
     return;
   }
   const size_t na = (size_t)p.nalm * (p.prec == 64 ? 16 : 8);
@@ -730,7 +737,7 @@ void exec_synthesis(Plan& p, const void* g, const void* c, void* f, cudaStream_t
   if (p.d_sph) mul_phase_device(p.prec, f, p.d_sph, p.npts, false, f, st);
 }
 
-void exec_adjoint(Plan& p, const void* f, void* g, void* c, cudaStream_t st, double msc = 1.0) {
+void exec_adjoint(Plan& p, const void* f, void* g, void* c, cudaStream_t st, double msc = 1.0, bool rotate = true) {
   if (!p.patch) {
     run_adjoint(p, f, g, c, st, msc);
     return;
@@ -741,6 +748,10 @@ void exec_adjoint(Plan& p, const void* f, void* g, void* c, cudaStream_t st, dou
   if (p.d_sph) {
     mul_phase_device(p.prec, f, p.d_sph, p.npts, true, p.d_fr, st);
     fr = p.d_fr;
+  }
+  if (!rotate) {
+    run_adjoint(p, fr, g, c, st, msc);
+    return;
   }
   run_adjoint(p, fr, ra, c ? ra + na : nullptr, st);
   rotator_apply(*p.rot, -p.euler[2], -p.euler[1], -p.euler[0], ra, c ? ra + na : nullptr, g, c, st, 1.0, msc);
@@ -934,6 +945,24 @@ int psht_plan_adjoint_packed(psht_plan* plan, const void* f, void* g, void* c, v
     PSHT_REQUIRE(plan && g, PSHT_EINVAL, "plan and g must not be NULL");
     PSHT_REQUIRE(f || plan->p->npts == 0, PSHT_EINVAL, "f must not be NULL");
     exec_adjoint(*plan->p, f, g, c, (cudaStream_t)stream, 2.0);
+  });
+}
+
+int psht_plan_synthesis_inframe(psht_plan* plan, const void* g, const void* c, void* f, void* stream) {
+  return guarded([&] {
+    PSHT_REQUIRE(plan && g, PSHT_EINVAL, "plan and g must not be NULL");
+    PSHT_REQUIRE(f || plan->p->npts == 0, PSHT_EINVAL, "f must not be NULL");
+    PSHT_REQUIRE(plan->p->patch, PSHT_EINVAL, "the plan was not created with PSHT_PATCH_FRAME");
+    exec_synthesis(*plan->p, g, c, f, (cudaStream_t)stream, 1.0, false);
+  });
+}
+
+int psht_plan_adjoint_inframe(psht_plan* plan, const void* f, void* g, void* c, void* stream) {
+  return guarded([&] {
+    PSHT_REQUIRE(plan && g, PSHT_EINVAL, "plan and g must not be NULL");
+    PSHT_REQUIRE(f || plan->p->npts == 0, PSHT_EINVAL, "f must not be NULL");
+    PSHT_REQUIRE(plan->p->patch, PSHT_EINVAL, "the plan was not created with PSHT_PATCH_FRAME");
+    exec_adjoint(*plan->p, f, g, c, (cudaStream_t)stream, 1.0, false);
   });
 }
 

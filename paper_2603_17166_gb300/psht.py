@@ -86,7 +86,7 @@ def lib():
         L.psht_plan_info.argtypes = [P, ctypes.POINTER(PshtInfo)]
         for name in ("psht_plan_synthesis", "psht_plan_adjoint", "psht_plan_synthesis_packed",
                      "psht_plan_adjoint_packed", "psht_plan_synthesis_host", "psht_plan_adjoint_host",
-                     "psht_plan_ring_coeffs"):
+                     "psht_plan_ring_coeffs", "psht_plan_synthesis_inframe", "psht_plan_adjoint_inframe"):
             getattr(L, name).argtypes = [P, P, P, P, P]
         L.psht_plan_destroy.argtypes = [P]
         L.psht_plan_rings.argtypes = [P, P, P, P]
@@ -191,19 +191,26 @@ class Plan:
             raise ValueError(f"a_lm must hold {nalm(self.lmax)} packed coefficients")
         return a
 
-    def synthesis(self, g, c=None, out=None, stream=None, packed_grad: bool = False):
+    def synthesis(self, g, c=None, out=None, stream=None, packed_grad: bool = False, in_frame: bool = False):
         """f_p = -sum (g_lm + i c_lm) sY_lm(theta_p, phi_p) (psht_plan_synthesis); with packed_grad
-        the m > 0 inputs count half (psht_plan_synthesis_packed)."""
+        the m > 0 inputs count half (psht_plan_synthesis_packed); with in_frame the a_lm are in a
+        patch-frame plan's own frame (psht_plan_synthesis_inframe)."""
         torch = _torch()
         g, c = self._alm_in(g), self._alm_in(c)
         f = out if out is not None else torch.empty(self.npts, dtype=self.cdtype, device="cuda")
+        if in_frame and packed_grad:
+            raise ValueError("in_frame and packed_grad do not combine")
         fn = lib().psht_plan_synthesis_packed if packed_grad else lib().psht_plan_synthesis
+        if in_frame:
+            fn = lib().psht_plan_synthesis_inframe
         _check(fn(self._h, _ptr(g), _ptr(c), _ptr(f), _stream(stream)))
         return f
 
-    def adjoint(self, f, g_out=None, c_out=None, want_c: bool = True, stream=None, packed_grad: bool = False):
+    def adjoint(self, f, g_out=None, c_out=None, want_c: bool = True, stream=None, packed_grad: bool = False,
+                in_frame: bool = False):
         """(g~, c~) of adjoint synthesis general (psht_plan_adjoint); with packed_grad the m > 0
-        outputs are doubled (psht_plan_adjoint_packed)."""
+        outputs are doubled (psht_plan_adjoint_packed); with in_frame they stay in a patch-frame
+        plan's own frame (psht_plan_adjoint_inframe)."""
         torch = _torch()
         f = torch.as_tensor(f, device="cuda").to(self.cdtype).contiguous()
         if f.numel() != self.npts:
@@ -211,7 +218,11 @@ class Plan:
         n = nalm(self.lmax)
         g = g_out if g_out is not None else torch.empty(n, dtype=self.cdtype, device="cuda")
         c = (c_out if c_out is not None else torch.empty(n, dtype=self.cdtype, device="cuda")) if want_c else None
+        if in_frame and packed_grad:
+            raise ValueError("in_frame and packed_grad do not combine")
         fn = lib().psht_plan_adjoint_packed if packed_grad else lib().psht_plan_adjoint
+        if in_frame:
+            fn = lib().psht_plan_adjoint_inframe
         _check(fn(self._h, _ptr(f), _ptr(g), _ptr(c), _stream(stream)))
         return g, c
 

@@ -135,3 +135,32 @@ def test_patch_frame_matches_plain_plan():
     fa = a.synthesis(_cu(g, a), _cu(c, a)).cpu().numpy()
     fb = b.synthesis(_cu(g, b), _cu(c, b)).cpu().numpy()
     assert O.rel_l2(fb, fa) <= 10 * eps
+
+
+@pytest.mark.parametrize("prec,eps", [("fp64", 1e-10), ("fp32", 1e-5)])
+def test_in_frame_entry_points(prec, eps):
+    """a_lm already in the plan's frame: synthesis_inframe(D a) = synthesis(a) and
+    D^-1 adjoint_inframe(f) = adjoint(f); a plan without the frame refuses them."""
+    from paper_2603_17166_gb300 import PshtError, Rotator
+
+    rng = np.random.default_rng(43)
+    lmax, s = 110, 2
+    th, ph = _box(rng, 1600)
+    g, c = _alm(rng, lmax, s), _alm(rng, lmax, s)
+    plan = _plan(s, lmax, th, ph, eps, prec)
+    al, be, ga = plan.info["euler"]
+    rot = Rotator(lmax, precision=prec)
+    gr, cr = rot.apply(_cu(g, plan), _cu(c, plan), al, be, ga)
+    f1 = plan.synthesis(gr, cr, in_frame=True).cpu().numpy()
+    f0 = plan.synthesis(_cu(g, plan), _cu(c, plan)).cpu().numpy()
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    assert O.rel_l2(f1, f0) <= tol
+    fin = _cu(rng.standard_normal(th.size) + 1j * rng.standard_normal(th.size), plan)
+    g1, c1 = plan.adjoint(fin, in_frame=True)
+    g1, c1 = rot.apply(g1, c1, -ga, -be, -al)
+    g0, c0 = plan.adjoint(fin)
+    assert O.alm_rel_l2(g1.cpu().numpy(), g0.cpu().numpy(), lmax) <= tol
+    assert O.alm_rel_l2(c1.cpu().numpy(), c0.cpu().numpy(), lmax) <= tol
+    plain = _plan(s, lmax, th, ph, eps, prec, patch=False)
+    with pytest.raises(PshtError):
+        plain.synthesis(_cu(g, plain), in_frame=True)
