@@ -259,7 +259,11 @@ def run_ours(args, rank, world, local_rank):
 
         achieved = tflops("rec_adjoint")
         per_stage = {k: round(v[0] / max(v[1], 1), 4) for k, v in stages.items()}
+        syn_ms = sum(per_stage[k] for k in ("rec_synthesis", "theta_synthesis", "phi_synthesis", "gather"))
+        adj_ms = sum(per_stage[k] for k in ("scatter", "phi_adjoint", "theta_adjoint", "rec_adjoint"))
         entry = dict(value=value, ms_per_step=ms_step, steps=K, warmup=W, eps=eps, plan_s=plan_s,
+                     synthesis=dict(ms=syn_ms, mpoints_per_s=npts / syn_ms / 1e3),
+                     adjoint=dict(ms=adj_ms, mpoints_per_s=npts / adj_ms / 1e3),
                      step_ms_min=min(step_ms), step_ms_max=max(step_ms),
                      stage_ms=per_stage, clocks=clocks,
                      plan=dict(L=info["L"], M=info["M"], W=info["W"], nTheta=info["nTheta"], nphi=info["nphi"],
