@@ -335,6 +335,8 @@ def run_ours(args, rank, world, local_rank):
         line["serving"] = run_serving(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, wl, steps=1, gpu_samples=gpu_samples)
+        if line["cpu_baseline"]["cores"] > 4:  # the paper times its CPU code on 4 cores
+            line["cpu_baseline_4_threads"] = cpu_baseline(args, wl, steps=1, threads=4)
     if dist is not None:
         dist.destroy_process_group()
     return line
@@ -618,13 +620,22 @@ def run_table1(args) -> dict:
 
 
 # ----------------------------------------------------------------------------- oracle arm
-def cpu_baseline(args, wl, steps: int = 1, gpu_samples=None) -> dict:
+def cpu_baseline(args, wl, steps: int = 1, gpu_samples=None, threads=None) -> dict:
     """The FP64 CPU oracle pipeline (as it stands) on a bounded sample of the same workload:
     every `cpu_ring_stride`-th ring for the two recursion stages, the full FFT stages, and
     `cpu_sample_points` points for interpolation and spreading; each part's time is scaled to the
     full workload linearly (ring count, point count).  With gpu_samples ({form: (eps, indices,
-    values)}) it also reports each form's relative L2 error against the oracle's direct sum there."""
+    values)}) it also reports each form's relative L2 error against the oracle's direct sum there.
+    threads: run on that many threads (C part and FFTs), then restore the default."""
     import oracle as O
+
+    if threads:
+        default = O.num_threads()
+        O.set_num_threads(threads)
+        try:
+            return cpu_baseline(args, wl, steps, gpu_samples)
+        finally:
+            O.set_num_threads(default)
 
     accuracy = {}
     for form, (eps, sel, got) in (gpu_samples or {}).items():

@@ -34,14 +34,16 @@ import subprocess
 
 import numpy as np
 
+_WORKERS = [os.cpu_count()]  # FFT threads; set_num_threads changes it with the C part's
+
 try:
     import scipy.fft as _fft
 
     def _fftn(a, axis):
-        return _fft.fft(a, axis=axis, workers=os.cpu_count())
+        return _fft.fft(a, axis=axis, workers=_WORKERS[0])
 
     def _ifftn(a, axis):
-        return _fft.ifft(a, axis=axis, workers=os.cpu_count())
+        return _fft.ifft(a, axis=axis, workers=_WORKERS[0])
 except Exception:  # pragma: no cover - scipy is in every image used here
     def _fftn(a, axis):
         return np.fft.fft(a, axis=axis)
@@ -81,6 +83,7 @@ def _lib():
         lib.orc_direct_adjoint_lm.argtypes = [I, L, P, P, P, I, P, P, P, P]
         lib.orc_rotate_alm.argtypes = [I, D, D, D, P, I, P, P, P]
         lib.orc_num_threads.restype = I
+        lib.orc_set_num_threads.argtypes = [I]
         _lib_handle = lib
     return _lib_handle
 
@@ -88,6 +91,12 @@ def _lib():
 def num_threads() -> int:
     """OpenMP threads the C part uses (all cores in the affinity mask unless OMP_NUM_THREADS)."""
     return int(_lib().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the C part and of the FFTs from now on."""
+    _lib().orc_set_num_threads(int(n))
+    _WORKERS[0] = int(n)
 
 
 def _ptr(a):

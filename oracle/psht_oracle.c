@@ -342,6 +342,16 @@ int orc_num_threads(void) {
 #endif
 }
 
+/* Threads of the following parallel regions (timing runs on fewer cores than the machine has). */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+  extern void omp_set_num_threads(int);
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 /*
  * Selected outputs of the direct adjoint synthesis general: for each (l_k, m_k), m_k >= 0,
  *   ut_{l,m}  = -sum_p f_p N_l d^l_{m,-s}(theta_p) e^{-i m phi_p}
