@@ -50,14 +50,15 @@ constexpr int kRotCH = 512;              // i values staged per chunk
 
 template <typename T>
 struct RotScale;
-// A value is held as d 2^(F k), k <= 0, |d| <= 2^B after each rescale test (every 4 steps); while
-// k < 0 its true size is below 2^(B - F) times the growth of 4 steps (< 2^34 for lmax < 65535), so
-// it is dropped.  FP32: B = 20, F = 100 (dropped below 2^-46); FP64: B = 300, F = 600.
+// A value is held as d 2^(F k), k <= 0, |d| <= 2^B after each rescale test (every 8 steps); while
+// k < 0 its true size is below 2^(B - F) times the growth of 8 steps (< 2^68 for lmax < 65535, one
+// step grows a value by at most sqrt(2 l) + 1), so it is dropped.  FP32: B = 20, F = 120 (dropped
+// below 2^-32; mantissas stay above 2^-109 after a rescale); FP64: B = 300, F = 600.
 template <>
 struct RotScale<float> {
-  static constexpr double LOG_BIG = 20.0, LOG_STEP = 100.0;
+  static constexpr double LOG_BIG = 20.0, LOG_STEP = 120.0;
   __device__ static float big() { return 0x1p20f; }
-  __device__ static float step() { return 0x1p-100f; }
+  __device__ static float step() { return 0x1p-120f; }
 };
 template <>
 struct RotScale<double> {
@@ -280,13 +281,14 @@ __global__ void __launch_bounds__(kRotNT) k_rot_stage(int lmax, const typename C
       }
     };
     int i = ihi;
-    // gated steps in blocks of 4 with a rescale test after each block, until the warp is at scale 0
-    while (!fast && i >= ilo + 3) {
-      step(i, 0, true);
-      step(i - 1, 1, true);
-      step(i - 2, 0, true);
-      step(i - 3, 1, true);
-      i -= 4;
+    // gated steps in blocks of 8 with a rescale test after each block, until the warp is at scale 0
+    while (!fast && i >= ilo + 7) {
+#pragma unroll
+      for (int u8 = 0; u8 < 8; u8 += 2) {
+        step(i - u8, 0, true);
+        step(i - u8 - 1, 1, true);
+      }
+      i -= 8;
       fast = __all_sync(0xffffffffu, rescale());
     }
     if (fast) {
@@ -295,7 +297,7 @@ __global__ void __launch_bounds__(kRotNT) k_rot_stage(int lmax, const typename C
         step(i - 1, 1, false);
       }
     } else {
-      // fewer than 4 steps left in this chunk: gated, then a rescale test
+      // fewer than 8 steps left in this chunk: gated, then a rescale test
       for (; i >= ilo + 1; i -= 2) {
         step(i, 0, true);
         step(i - 1, 1, true);
