@@ -68,8 +68,8 @@ struct TabEntry<float> {
 };
 template <>
 struct TabEntry<double> {
-  double2 ad;  // A, D
-  double2 bc;  // B, C
+  double2 ad;  // A, D + B  (the multiplier of column 1 is D + B - A (1 - x))
+  double2 bc;  // D - B, C  (column 2: D - B - A (1 - x))
 };
 static_assert(sizeof(TabEntry<float>) == 48 && sizeof(TabEntry<double>) == 32, "table record sizes");
 static_assert((kCH * sizeof(TabEntry<float>)) % 16 == 0 && (kCH * sizeof(TabEntry<double>)) % 16 == 0,
@@ -101,8 +101,8 @@ __global__ void k_rec_table(int lmax, int s, TabEntry<T>* __restrict__ tab) {
     }
     TabEntry<T> e;
     if constexpr (sizeof(T) == 8) {
-      e.ad = make_double2(A, D);
-      e.bc = make_double2(B, C);
+      e.ad = make_double2(A, D + B);
+      e.bc = make_double2(D - B, C);
     } else {
       const float ah = (float)A, dh = (float)D;
       const float al = (float)(A - (double)ah), dl = (float)(D - (double)dh), b = (float)B, c = (float)C;
@@ -132,10 +132,12 @@ __device__ __forceinline__ void issue_chunk(TabStage<T, CH>& st, uint64_t* bar, 
   bulk_g2s(st.v, tab + start, bytes, bar);
 }
 
-// FP64 coefficients of one l; t = D - A (1 - x)
+// FP64 coefficients of one l; the column multipliers are D +- B - A (1 - x)
 struct Coef {
-  double A, D, B, C;
-  __device__ __forceinline__ double t(double omx) const { return fma(-A, omx, D); }
+  double A, DP, DM, C;  // A, D + B, D - B, C
+  // multipliers of the two columns (s = 0: B = 0 and only tp is used); one FMA each
+  __device__ __forceinline__ double tp(double omx) const { return fma(-A, omx, DP); }
+  __device__ __forceinline__ double tm(double omx) const { return fma(-A, omx, DM); }
 };
 __device__ __forceinline__ Coef get_coef(const TabEntry<double>* tv, int i) {
   const double2 ad = tv[i].ad, bc = tv[i].bc;
@@ -379,12 +381,11 @@ __device__ __forceinline__ void syn_quad(Cols<double, RPT>& S, SynAcc<double, RP
           A.a[r][2] = fma(pq.z, o2, A.a[r][2]);
           A.a[r][3] = fma(pq.w, o2, A.a[r][3]);
         }
-        const double t = cf.t(S.oh[r]);
         if (SPIN) {
-          reinsch_step(t + cf.B, cf.C, S.e1[r], S.d1[r]);
-          reinsch_step(t - cf.B, cf.C, S.e2[r], S.d2[r]);
+          reinsch_step(cf.tp(S.oh[r]), cf.C, S.e1[r], S.d1[r]);
+          reinsch_step(cf.tm(S.oh[r]), cf.C, S.e2[r], S.d2[r]);
         } else {
-          reinsch_step(t, cf.C, S.e1[r], S.d1[r]);
+          reinsch_step(cf.tp(S.oh[r]), cf.C, S.e1[r], S.d1[r]);
         }
       }
     }
@@ -756,12 +757,11 @@ __device__ __forceinline__ void adj_quad_sums(Cols<double, RPT>& S, const AdjIn<
         const double o2 = SPIN ? ((!SEL || S.k2[r] == 0) ? S.e2[r] : 0.0) : o1;
         p2 = fma(o2, f.f2[r].x, p2);
         p3 = fma(o2, f.f2[r].y, p3);
-        const double t = cf.t(S.oh[r]);
         if (SPIN) {
-          reinsch_step(t + cf.B, cf.C, S.e1[r], S.d1[r]);
-          reinsch_step(t - cf.B, cf.C, S.e2[r], S.d2[r]);
+          reinsch_step(cf.tp(S.oh[r]), cf.C, S.e1[r], S.d1[r]);
+          reinsch_step(cf.tm(S.oh[r]), cf.C, S.e2[r], S.d2[r]);
         } else {
-          reinsch_step(t, cf.C, S.e1[r], S.d1[r]);
+          reinsch_step(cf.tp(S.oh[r]), cf.C, S.e1[r], S.d1[r]);
         }
       }
     }
@@ -804,12 +804,11 @@ __device__ __forceinline__ void adj_quad_steps(Cols<double, RPT>& S, const TabEn
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
       if (r < nr) {
-        const double t = cf.t(S.oh[r]);
         if (SPIN) {
-          reinsch_step(t + cf.B, cf.C, S.e1[r], S.d1[r]);
-          reinsch_step(t - cf.B, cf.C, S.e2[r], S.d2[r]);
+          reinsch_step(cf.tp(S.oh[r]), cf.C, S.e1[r], S.d1[r]);
+          reinsch_step(cf.tm(S.oh[r]), cf.C, S.e2[r], S.d2[r]);
         } else {
-          reinsch_step(t, cf.C, S.e1[r], S.d1[r]);
+          reinsch_step(cf.tp(S.oh[r]), cf.C, S.e1[r], S.d1[r]);
         }
       }
     }
