@@ -253,6 +253,7 @@ void layout(Plan& p, double theta_star) {
     p.dTheta = M_PI * p.eps_apo / (1.0 + p.eps_apo);
   }
   p.alpha = lneps / M_PI;
+  p.omx_tb = (p.prec == 64 && p.eps >= kThreeTermMinEps) ? 1.0 - cos(kThreeTermDeg * M_PI / 180.0) : 3.0;
   p.L = fft_friendly(p.Lmax + 1);
   p.nring = full ? p.L + 1 : p.L;
   p.theta_j.resize(p.nring);

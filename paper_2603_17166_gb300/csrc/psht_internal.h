@@ -39,6 +39,11 @@ struct ScaleConst<double> {
   static constexpr int F = 500;      // exponent step of one rescale
   static constexpr int R_EXP = 400;  // rescale when |y| >= 2^400; dropped region below 2^-100
 };
+// FP64 rings at least this far from the pole (degrees) take the three-term form of the recurrence
+// when eps >= kThreeTermMinEps (its error there stays within a few 1e-13 at lmax 4096)
+constexpr double kThreeTermDeg = 10.0;
+constexpr double kThreeTermMinEps = 1e-11;
+
 template <>
 struct ScaleConst<float> {
   static constexpr int F = 80;
@@ -93,6 +98,9 @@ struct Plan {
   int window = 0;      // PSHT_WINDOW_ES or PSHT_WINDOW_KB
   double kappa = 1.0;  // ring-count factor in Lmax
   int apo_cost = 0;    // PSHT_APO_COST: eps_apo minimising the recursion's step count
+  // FP64 rings with 1 - cos(b) >= omx_tb (b the distance from the pole) take the three-term form of
+  // the recurrence instead of Reinsch's (above 2: none)
+  double omx_tb = 3.0;
   double theta_star = 0, eps_apo = 0, theta_max = 0, dTheta = 0, alpha = 0;
   int Lmax = 0, L = 0, nring = 0, M = 0, W = 0;
   double beta_es = 0;

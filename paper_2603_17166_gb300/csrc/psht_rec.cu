@@ -9,7 +9,10 @@
 //     Delta_{l+1} = (D_l +- B_l - A_l (1 - x)) e_l + C_l Delta_l,   e_{l+1} = e_l + Delta_{l+1},
 // where 1 - x = 2 sin^2(b/2) is exact on the host.  This keeps the recurrence accurate on the
 // rings next to the pole, where A x + B - 2 is far below the rounding of A x + B.  In the FP32
-// form A, D and 1 - x are carried as float pairs (hi + lo).
+// form A, D and 1 - x are carried as float pairs (hi + lo).  In the FP64 form, warps whose rings
+// all lie at least kThreeTermDeg from the pole take the three-term form itself (two FP64
+// operations per column and step instead of three; a few 1e-13 from Reinsch's there), when
+// eps >= kThreeTermMinEps.
 // Every ring is evaluated at b = min(theta_j, pi - theta_j): a ring at theta_j > pi/2 uses
 // d^l_{m,-s}(pi - b) = (-1)^(l+m) d^l_{m,s}(b), i.e. the two columns swapped and the
 // coefficients signed by (-1)^(l+m).
@@ -68,10 +71,11 @@ struct TabEntry<float> {
 };
 template <>
 struct TabEntry<double> {
-  double2 ad;  // A, D + B  (the multiplier of column 1 is D + B - A (1 - x))
+  double2 ad;  // A, D + B  (the Reinsch multiplier of column 1 is D + B - A (1 - x))
   double2 bc;  // D - B, C  (column 2: D - B - A (1 - x))
+  double2 bz;  // B, 0      (three-term form: multipliers A x +- B)
 };
-static_assert(sizeof(TabEntry<float>) == 48 && sizeof(TabEntry<double>) == 32, "table record sizes");
+static_assert(sizeof(TabEntry<float>) == 48 && sizeof(TabEntry<double>) == 48, "table record sizes");
 static_assert((kCH * sizeof(TabEntry<float>)) % 16 == 0 && (kCH * sizeof(TabEntry<double>)) % 16 == 0,
               "bulk copies are whole 16-byte units");
 
@@ -103,6 +107,7 @@ __global__ void k_rec_table(int lmax, int s, TabEntry<T>* __restrict__ tab) {
     if constexpr (sizeof(T) == 8) {
       e.ad = make_double2(A, D + B);
       e.bc = make_double2(D - B, C);
+      e.bz = make_double2(B, 0.0);
     } else {
       const float ah = (float)A, dh = (float)D;
       const float al = (float)(A - (double)ah), dl = (float)(D - (double)dh), b = (float)B, c = (float)C;
@@ -134,14 +139,17 @@ __device__ __forceinline__ void issue_chunk(TabStage<T, CH>& st, uint64_t* bar, 
 
 // FP64 coefficients of one l; the column multipliers are D +- B - A (1 - x)
 struct Coef {
-  double A, DP, DM, C;  // A, D + B, D - B, C
-  // multipliers of the two columns (s = 0: B = 0 and only tp is used); one FMA each
+  double A, DP, DM, C, B;  // A, D + B, D - B, C, B
+  // Reinsch multipliers of the two columns (s = 0: B = 0 and only tp is used); one FMA each
   __device__ __forceinline__ double tp(double omx) const { return fma(-A, omx, DP); }
   __device__ __forceinline__ double tm(double omx) const { return fma(-A, omx, DM); }
+  // three-term multipliers A x + B, A x - B
+  __device__ __forceinline__ double up(double x) const { return fma(A, x, B); }
+  __device__ __forceinline__ double um(double x) const { return fma(A, x, -B); }
 };
 __device__ __forceinline__ Coef get_coef(const TabEntry<double>* tv, int i) {
-  const double2 ad = tv[i].ad, bc = tv[i].bc;
-  return Coef{ad.x, ad.y, bc.x, bc.y};
+  const double2 ad = tv[i].ad, bc = tv[i].bc, bz = tv[i].bz;
+  return Coef{ad.x, ad.y, bc.x, bc.y, bz.x};
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -206,6 +214,25 @@ __device__ __forceinline__ void ring_omx<float>(const RingDev& r, float& oh, flo
 __device__ __forceinline__ void reinsch_step(double t, double C, double& e, double& d) {
   d = fma(t, e, C * d);
   e = e + d;
+}
+// one step of the three-term form, e_{l+1} = u e_l - C e_{l-1}, with ep holding e_{l-1}: two FP64
+// operations instead of Reinsch's three, exact to a few 1e-13 away from the pole but not next to it
+// (u = A x +- B loses 1 - x there); used in FP64 on rings at least kThreeTermDeg from the pole
+__device__ __forceinline__ void three_term_step(double u, double C, double& e, double& ep) {
+  const double n = fma(u, e, -(C * ep));
+  ep = e;
+  e = n;
+}
+// both columns of one ring slot, one l step (oh: 1 - x for Reinsch, x for the three-term form)
+template <bool SPIN, bool TB>
+__device__ __forceinline__ void col_steps(const Coef& cf, double oh, double& e1, double& d1, double& e2, double& d2) {
+  if (TB) {
+    three_term_step(cf.up(oh), cf.C, e1, d1);
+    if (SPIN) three_term_step(cf.um(oh), cf.C, e2, d2);
+  } else {
+    reinsch_step(cf.tp(oh), cf.C, e1, d1);
+    if (SPIN) reinsch_step(cf.tm(oh), cf.C, e2, d2);
+  }
 }
 // the same step for the two rings of a pair in packed FP32x2 arithmetic (per element the same
 // roundings as the scalar step)
@@ -362,7 +389,7 @@ __device__ __forceinline__ float2 summing(float2 e, int ka, int kb) {
 
 // One quad (4 l steps) of the synthesis for the ring slots r < nr of this thread.
 // ACC: add the current column values to the sums; SEL: per column, only where k == 0.
-template <bool SPIN, int RPT, bool ACC, bool SEL>
+template <bool SPIN, int RPT, bool ACC, bool SEL, bool TB = false>
 __device__ __forceinline__ void syn_quad(Cols<double, RPT>& S, SynAcc<double, RPT>& A, const TabEntry<double>* st,
                                          int i0, const Dbl4* sPQ, int nr) {
 #pragma unroll
@@ -381,12 +408,7 @@ __device__ __forceinline__ void syn_quad(Cols<double, RPT>& S, SynAcc<double, RP
           A.a[r][2] = fma(pq.z, o2, A.a[r][2]);
           A.a[r][3] = fma(pq.w, o2, A.a[r][3]);
         }
-        if (SPIN) {
-          reinsch_step(cf.tp(S.oh[r]), cf.C, S.e1[r], S.d1[r]);
-          reinsch_step(cf.tm(S.oh[r]), cf.C, S.e2[r], S.d2[r]);
-        } else {
-          reinsch_step(cf.tp(S.oh[r]), cf.C, S.e1[r], S.d1[r]);
-        }
+        col_steps<SPIN, TB>(cf, S.oh[r], S.e1[r], S.d1[r], S.e2[r], S.d2[r]);
       }
     }
   }
@@ -413,6 +435,42 @@ __device__ __forceinline__ void syn_quad(Cols<float, RPT>& S, SynAcc<float, RPT>
         step_pair<SPIN, RPT>(S, p, cf);
       }
     }
+  }
+}
+
+// FP64 warps whose rings all lie at least kThreeTermDeg from the pole take the three-term form
+// (tb); the FP32 form always takes Reinsch's
+template <bool SPIN, int RPT, bool ACC, bool SEL, typename T, typename PQV>
+__device__ __forceinline__ void syn_quad_d(bool tb, Cols<T, RPT>& S, SynAcc<T, RPT>& A, const TabEntry<T>* st, int i0,
+                                           const PQV* PQ, int nr) {
+  if constexpr (sizeof(T) == 8) {
+    if (tb) {
+      syn_quad<SPIN, RPT, ACC, SEL, true>(S, A, st, i0, PQ, nr);
+      return;
+    }
+  }
+  syn_quad<SPIN, RPT, ACC, SEL>(S, A, st, i0, PQ, nr);
+}
+
+// decide the form of a warp's FP64 columns after init_col and convert them: oh <- x = 1 - (1 - x),
+// d <- e_{l0-1} = 0 (slots >= nr are empty: zero columns)
+template <typename T, int RPT>
+__device__ __forceinline__ bool three_term_setup(Cols<T, RPT>& S, int nr_slots, double omx_tb) {
+  if constexpr (sizeof(T) == 8) {
+    bool ok = true;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r)
+      if (r < nr_slots) ok = ok && S.OH(r) >= omx_tb;
+    if (!__all_sync(0xffffffffu, ok)) return false;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      S.OH(r) = 1.0 - S.OH(r);
+      S.D1(r) = 0.0;
+      S.D2(r) = 0.0;
+    }
+    return true;
+  } else {
+    return false;
   }
 }
 
@@ -615,7 +673,7 @@ __global__ void __launch_bounds__(32) k_rec_syn_w(const RecItem* __restrict__ it
                                                   const typename Cx<T>::V* __restrict__ g,
                                                   const typename Cx<T>::V* __restrict__ c, int lmax, int s, T msc,
                                                   typename Cx<T>::V* __restrict__ F, int Lpad,
-                                                  int* __restrict__ status) {
+                                                  int* __restrict__ status, double omx_tb) {
   static_assert(CH == 32, "one l per lane and chunk");
   using V = typename Cx<T>::V;
   using PQV = typename PQRec<T>::V;
@@ -632,6 +690,8 @@ __global__ void __launch_bounds__(32) k_rec_syn_w(const RecItem* __restrict__ it
   A.zero();
 #pragma unroll
   for (int r = 0; r < RPT; ++r) init_col<T, SPIN, RPT>(S, rings, sd, it.j0, r * 32 + lane, it.nj, r);
+  // slots r with r * 32 + lane < nj hold rings
+  const bool tb = three_term_setup<T, RPT>(S, lane < it.nj ? (it.nj - lane + 31) / 32 : 0, omx_tb);
   const int64_t base = alm_base(lmax, m);
   const bool rf = it.refl != 0;
   const bool m0 = (m == 0);
@@ -682,11 +742,11 @@ __global__ void __launch_bounds__(32) k_rec_syn_w(const RecItem* __restrict__ it
         bool fast, skip;
         classify<T, SPIN, RPT>(S, nr_w, fast, skip);
         if (fast) {
-          if (nr_w >= RPT) syn_quad<SPIN, RPT, true, false>(S, A, st, 4 * q, PQ, RPT);
-          else syn_quad<SPIN, RPT, true, false>(S, A, st, 4 * q, PQ, nr_w);
+          if (nr_w >= RPT) syn_quad_d<SPIN, RPT, true, false>(tb, S, A, st, 4 * q, PQ, RPT);
+          else syn_quad_d<SPIN, RPT, true, false>(tb, S, A, st, 4 * q, PQ, nr_w);
         } else {
-          if (skip) syn_quad<SPIN, RPT, false, false>(S, A, st, 4 * q, PQ, nr_w);
-          else syn_quad<SPIN, RPT, true, true>(S, A, st, 4 * q, PQ, nr_w);
+          if (skip) syn_quad_d<SPIN, RPT, false, false>(tb, S, A, st, 4 * q, PQ, nr_w);
+          else syn_quad_d<SPIN, RPT, true, true>(tb, S, A, st, 4 * q, PQ, nr_w);
           rescale_all<T, SPIN, RPT>(S, nr_w);
         }
       }
@@ -741,7 +801,7 @@ __device__ __forceinline__ T reduce_scatter16(T (&v)[16], int lane) {
   return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);  // lane holds value (lane & 15)
 }
 
-template <bool SPIN, int RPT, bool SEL>
+template <bool SPIN, int RPT, bool SEL, bool TB = false>
 __device__ __forceinline__ void adj_quad_sums(Cols<double, RPT>& S, const AdjIn<double, RPT>& f,
                                               const TabEntry<double>* st, int i0, int nr, double (&v)[16]) {
 #pragma unroll
@@ -757,12 +817,7 @@ __device__ __forceinline__ void adj_quad_sums(Cols<double, RPT>& S, const AdjIn<
         const double o2 = SPIN ? ((!SEL || S.k2[r] == 0) ? S.e2[r] : 0.0) : o1;
         p2 = fma(o2, f.f2[r].x, p2);
         p3 = fma(o2, f.f2[r].y, p3);
-        if (SPIN) {
-          reinsch_step(cf.tp(S.oh[r]), cf.C, S.e1[r], S.d1[r]);
-          reinsch_step(cf.tm(S.oh[r]), cf.C, S.e2[r], S.d2[r]);
-        } else {
-          reinsch_step(cf.tp(S.oh[r]), cf.C, S.e1[r], S.d1[r]);
-        }
+        col_steps<SPIN, TB>(cf, S.oh[r], S.e1[r], S.d1[r], S.e2[r], S.d2[r]);
       }
     }
     v[4 * u + 0] = p0;
@@ -796,22 +851,14 @@ __device__ __forceinline__ void adj_quad_sums(Cols<float, RPT>& S, const AdjIn<f
     v[4 * u + 3] = p3.x + p3.y;
   }
 }
-template <bool SPIN, int RPT>
+template <bool SPIN, int RPT, bool TB = false>
 __device__ __forceinline__ void adj_quad_steps(Cols<double, RPT>& S, const TabEntry<double>* st, int i0, int nr) {
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const Coef cf = get_coef(st, i0 + u);
 #pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-      if (r < nr) {
-        if (SPIN) {
-          reinsch_step(cf.tp(S.oh[r]), cf.C, S.e1[r], S.d1[r]);
-          reinsch_step(cf.tm(S.oh[r]), cf.C, S.e2[r], S.d2[r]);
-        } else {
-          reinsch_step(cf.tp(S.oh[r]), cf.C, S.e1[r], S.d1[r]);
-        }
-      }
-    }
+    for (int r = 0; r < RPT; ++r)
+      if (r < nr) col_steps<SPIN, TB>(cf, S.oh[r], S.e1[r], S.d1[r], S.e2[r], S.d2[r]);
   }
 }
 template <bool SPIN, int RPT>
@@ -825,13 +872,26 @@ __device__ __forceinline__ void adj_quad_steps(Cols<float, RPT>& S, const TabEnt
   }
 }
 
+// the three-term variants exist for FP64 only
+template <bool SPIN, int RPT, bool SEL, bool TB, typename T>
+__device__ __forceinline__ void adj_quad_sums_d(Cols<T, RPT>& S, const AdjIn<T, RPT>& f, const TabEntry<T>* st, int i0,
+                                                int nr, T (&v)[16]) {
+  if constexpr (sizeof(T) == 8) adj_quad_sums<SPIN, RPT, SEL, TB>(S, f, st, i0, nr, v);
+  else adj_quad_sums<SPIN, RPT, SEL>(S, f, st, i0, nr, v);
+}
+template <bool SPIN, int RPT, bool TB, typename T>
+__device__ __forceinline__ void adj_quad_steps_d(Cols<T, RPT>& S, const TabEntry<T>* st, int i0, int nr) {
+  if constexpr (sizeof(T) == 8) adj_quad_steps<SPIN, RPT, TB>(S, st, i0, nr);
+  else adj_quad_steps<SPIN, RPT>(S, st, i0, nr);
+}
+
 template <typename T, bool SPIN, int RPT, int NT>
 __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ rings, const MSeed* __restrict__ mseed,
                                                 const int2* __restrict__ mrange, const TabEntry<T>* __restrict__ tab,
                                                 const typename Cx<T>::V* __restrict__ Ft, int Lpad,
                                                 int lmax, int s, int M, int refl, int accumulate, T msc,
                                                 typename Cx<T>::V* __restrict__ gt, typename Cx<T>::V* __restrict__ ct,
-                                                int* __restrict__ status, int chunk) {
+                                                int* __restrict__ status, int chunk, double omx_tb) {
   using V = typename Cx<T>::V;
   const int m = blockIdx.x;
   const int64_t base = alm_base(lmax, m);
@@ -884,6 +944,7 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
       fin.set(r, rf ? fm : fp, rf ? fp : fm);
     }
   }
+  const bool tb = three_term_setup<T, RPT>(S, lane < wcnt ? (wcnt - lane + 31) / 32 : 0, omx_tb);
   const T sg = (((m - s) & 1) ? (T)1 : (T)-1);  // -(-1)^(m-s)
   const T sm = (m & 1) ? (T)-1 : (T)1;          // (-1)^m
   const int nchunk = (lmax - sd.l0 + kCH) / kCH;
@@ -916,15 +977,22 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
         bool fast, skip;
         classify<T, SPIN, RPT>(S, nr_w, fast, skip);
         if (skip) {
-          adj_quad_steps<SPIN, RPT>(S, st, 4 * q, nr_w);
+          if (tb) adj_quad_steps_d<SPIN, RPT, true>(S, st, 4 * q, nr_w);
+          else adj_quad_steps_d<SPIN, RPT, false>(S, st, 4 * q, nr_w);
           rescale_all<T, SPIN, RPT>(S, nr_w);
         } else {
           T v[16];
           if (fast) {
-            if (nr_w == RPT) adj_quad_sums<SPIN, RPT, false>(S, fin, st, 4 * q, RPT, v);
-            else adj_quad_sums<SPIN, RPT, false>(S, fin, st, 4 * q, nr_w, v);
+            if (tb) {
+              if (nr_w == RPT) adj_quad_sums_d<SPIN, RPT, false, true>(S, fin, st, 4 * q, RPT, v);
+              else adj_quad_sums_d<SPIN, RPT, false, true>(S, fin, st, 4 * q, nr_w, v);
+            } else {
+              if (nr_w == RPT) adj_quad_sums_d<SPIN, RPT, false, false>(S, fin, st, 4 * q, RPT, v);
+              else adj_quad_sums_d<SPIN, RPT, false, false>(S, fin, st, 4 * q, nr_w, v);
+            }
           } else {
-            adj_quad_sums<SPIN, RPT, true>(S, fin, st, 4 * q, nr_w, v);
+            if (tb) adj_quad_sums_d<SPIN, RPT, true, true>(S, fin, st, 4 * q, nr_w, v);
+            else adj_quad_sums_d<SPIN, RPT, true, false>(S, fin, st, 4 * q, nr_w, v);
             rescale_all<T, SPIN, RPT>(S, nr_w);
           }
           tot = reduce_scatter16<T>(v, lane);
@@ -1142,7 +1210,7 @@ void launch_syn_t(Plan& p, const void* g, const void* c, double msc, cudaStream_
     if (i1 > i0)
       k_rec_syn_w<T, SPIN, RPT, 32, 4><<<i1 - i0, 32, 0, st>>>(
           p.d_items + i0, p.d_ring, p.d_mseed, (const TabEntry<T>*)p.d_rtab, (const V*)g, (const V*)c, p.lmax,
-          p.spin, (T)msc, (V*)p.d_F, p.Lpad, p.d_status);
+          p.spin, (T)msc, (V*)p.d_F, p.Lpad, p.d_status, p.omx_tb);
     return;
   }
   k_rec_syn<T, SPIN, RPT, 128><<<p.nitems, 128, 0, st>>>(p.d_items, p.d_ring, p.d_mseed,
@@ -1178,7 +1246,8 @@ void launch_adj_t(Plan& p, void* g, void* c, double msc, cudaStream_t st) {
     for (int chk = 0; chk < nch; ++chk)
       k_rec_adj<T, SPIN, RPT, NT><<<p.lmax + 1, NT, red_bytes, st>>>(
           p.d_ring, p.d_mseed, p.d_mrange + part * (p.lmax + 1), (const TabEntry<T>*)p.d_rtab, (const V*)p.d_F,
-          p.Lpad, p.lmax, p.spin, p.M, part, (part > 0 || chk > 0) ? 1 : 0, (T)msc, (V*)g, (V*)c, p.d_status, chk);
+          p.Lpad, p.lmax, p.spin, p.M, part, (part > 0 || chk > 0) ? 1 : 0, (T)msc, (V*)g, (V*)c, p.d_status, chk,
+          p.omx_tb);
   }
 }
 
