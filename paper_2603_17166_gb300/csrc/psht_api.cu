@@ -618,7 +618,7 @@ Plan* create(int spin, int lmax, const double* theta, const double* phi, int64_t
       p->d_twP = upload(*p, cast_vec<float>(twid(p->nphi)), st);
     }
     // work buffers
-    const size_t cb = prec == 64 ? 16 : 8, rb = prec == 64 ? 8 : 4;
+    const size_t cb = prec == 64 ? 16 : 8;
     p->d_rtab = dalloc(*p, (size_t)rec_table_record_bytes(p->prec) * p->tstride);
     PSHT_CUDA_TRY(cudaMemsetAsync(p->d_rtab, 0, (size_t)rec_table_record_bytes(p->prec) * p->tstride, st));
     p->d_status = (int*)dalloc(*p, sizeof(int));

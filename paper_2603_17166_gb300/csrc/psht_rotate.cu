@@ -75,7 +75,7 @@ struct Vec4<float> {
 };
 template <>
 struct Vec4<double> {
-  using V = double4;
+  using V = double4_32a;
 };
 
 __host__ __device__ inline int64_t tri_off(int l) { return (int64_t)l * (l + 1) / 2; }
