@@ -93,6 +93,7 @@ int psht_plan_create(int spin, int lmax, const double* theta, const double* phi,
 /* Copy the plan's parameters into *info (host memory).  Never fails for a valid plan. */
 int psht_plan_info(const psht_plan* plan, psht_info* info);
 
+
 /*
  * Synthesis general (Sec. I eq. syn) at the plan's points.  g, c: DEVICE packed a_lm (c may be
  * NULL: c = 0); f: DEVICE output, npts complex values in the caller's point order.
@@ -136,6 +137,16 @@ typedef struct {
 /* psht_plan_create with options; opt may be NULL (defaults). */
 int psht_plan_create_ex(int spin, int lmax, const double* theta, const double* phi, int64_t npts, double eps,
                         uint32_t flags, const psht_options* opt, void* stream, psht_plan** out);
+
+/*
+ * The planner alone (Sec. II steps 2-4, II.C-D), on the host, for a given theta_star about the
+ * north pole: fills *info as psht_plan_info would for a plan of npts = 0 (device_bytes: the
+ * estimate for no points), and, where not NULL, the rings' colatitudes theta_j, window weights w_j
+ * and polar cutoffs Mj (HOST arrays of info->nring entries: call once with NULL to learn nring).
+ * opt may be NULL.  No device work.  EINVAL for invalid arguments.
+ */
+int psht_plan_params(int spin, int lmax, double theta_star, double eps, uint32_t flags, const psht_options* opt,
+                     psht_info* info, double* theta_j, double* w_j, int32_t* Mj);
 
 /*
  * Predicted error of the partial-sky route for a statistically isotropic field (Sec. II.E):

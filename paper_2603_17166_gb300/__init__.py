@@ -5,4 +5,5 @@ Fourier-sphere route of Carron & Reinecke (Wigner-d recursion onto apodised ring
 reduced oversampled grid, ES-kernel interpolation), as a C-ABI CUDA library with a thin binding.
 """
 from .psht import (Plan, PshtError, Rotator, Server, adjoint_synthesis, estimate_bytes, estimate_points,  # noqa: F401
-                   lib, nalm, patch_rotation, predict_error, rotate_alm, rotate_points, synthesis)
+                   lib, nalm, patch_rotation, plan_params, predict_error, rotate_alm, rotate_points,
+                   synthesis)

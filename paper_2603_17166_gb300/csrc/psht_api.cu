@@ -880,10 +880,7 @@ int psht_plan_create_ex(int spin, int lmax, const double* theta, const double* p
   });
 }
 
-int psht_plan_info(const psht_plan* plan, psht_info* info) {
-  return guarded([&] {
-    PSHT_REQUIRE(plan && info, PSHT_EINVAL, "plan and info must not be NULL");
-    const Plan& p = *plan->p;
+static void fill_info(const Plan& p, psht_info* info) {
     psht_info i;
     memset(&i, 0, sizeof(i));
     i.spin = p.spin;
@@ -914,6 +911,43 @@ int psht_plan_info(const psht_plan* plan, psht_info* info) {
     i.patch_frame = p.patch;
     for (int k = 0; k < 3; ++k) i.euler[k] = p.euler[k];
     *info = i;
+}
+
+int psht_plan_info(const psht_plan* plan, psht_info* info) {
+  return guarded([&] {
+    PSHT_REQUIRE(plan && info, PSHT_EINVAL, "plan and info must not be NULL");
+    fill_info(*plan->p, info);
+  });
+}
+
+int psht_plan_params(int spin, int lmax, double theta_star, double eps, uint32_t flags, const psht_options* opt,
+                     psht_info* info, double* theta_j, double* w_j, int32_t* Mj) {
+  return guarded([&] {
+    PSHT_REQUIRE(info, PSHT_EINVAL, "info must not be NULL");
+    PSHT_REQUIRE(spin >= 0 && lmax >= spin && lmax <= 65535, PSHT_EINVAL, "invalid spin or lmax");
+    PSHT_REQUIRE(eps >= 1e-14 && eps <= 1e-1, PSHT_EINVAL, "eps must lie in [1e-14, 1e-1]");
+    PSHT_REQUIRE(theta_star >= 0.0 && theta_star <= M_PI, PSHT_EINVAL, "theta_star must lie in [0, pi]");
+    const uint32_t pf = flags & 3u;
+    PSHT_REQUIRE(pf != 3u && (flags & ~15u) == 0u, PSHT_EINVAL, "invalid flags");
+    Plan p;
+    p.spin = spin;
+    p.lmax = lmax;
+    p.eps = eps;
+    p.prec = (pf == PSHT_FP64) ? 64 : (pf == PSHT_FP32) ? 32 : (eps >= 1e-5 ? 32 : 64);
+    p.force_full = (flags & PSHT_FULL_SKY) ? 1 : 0;
+    p.patch = (flags & PSHT_PATCH_FRAME) ? 1 : 0;
+    p.pole = 1;
+    apply_options(p, opt);
+    layout(p, theta_star);
+    for (int j = 0; j < p.nring; ++j) {
+      p.pairs += p.Mj[j] + 1;
+      p.triples += ring_cost(p.lmax, p.spin, p.Mj[j]);
+      if (theta_j) theta_j[j] = p.theta_j[j];
+      if (w_j) w_j[j] = p.w_j[j];
+      if (Mj) Mj[j] = p.Mj[j];
+    }
+    p.bytes = planned_bytes(p);
+    fill_info(p, info);
   });
 }
 

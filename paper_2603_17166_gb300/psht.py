@@ -106,6 +106,8 @@ def lib():
         L.psht_server_get_stats.argtypes = [P, ctypes.POINTER(PshtServerStats)]
         L.psht_server_destroy.argtypes = [P]
         L.psht_estimate_bytes.argtypes = [I, I, D, I64, D, U32]
+        L.psht_plan_params.argtypes = [I, I, D, D, U32, ctypes.POINTER(PshtOptions), ctypes.POINTER(PshtInfo), P, P,
+                                       P]
         L.psht_rotator_create.argtypes = [I, U32, P, ctypes.POINTER(P)]
         L.psht_rotator_apply.argtypes = [P, D, D, D, P, P, P, P, P]
         L.psht_rotator_destroy.argtypes = [P]
@@ -492,3 +494,22 @@ def patch_rotation(theta, phi, stream=None):
     ts = ctypes.c_double()
     _check(lib().psht_patch_rotation(_ptr(theta), _ptr(phi), theta.numel(), eul, ctypes.byref(ts), _stream(stream)))
     return (eul[0], eul[1], eul[2]), ts.value
+
+
+def plan_params(spin: int, lmax: int, theta_star: float, eps: float, precision="auto", full_sky: bool = False,
+                window: str = "es", kappa: float = 1.0, apodisation: str = "paper", patch_frame: bool = False):
+    """The planner's parameters and ring set for theta_star about the north pole, on the host
+    (psht_plan_params): (info dict, theta_j, w_j, Mj)."""
+    flags = _PREC[precision] | (PSHT_FULL_SKY if full_sky else 0) | (PSHT_PATCH_FRAME if patch_frame else 0)
+    opt = PshtOptions(_WINDOW[window], float(kappa), _APO[apodisation])
+    inf = PshtInfo()
+    _check(lib().psht_plan_params(int(spin), int(lmax), float(theta_star), float(eps), flags, ctypes.byref(opt),
+                                  ctypes.byref(inf), None, None, None))
+    n = inf.nring
+    th, w, mj = np.zeros(n), np.zeros(n), np.zeros(n, dtype=np.int32)
+    _check(lib().psht_plan_params(int(spin), int(lmax), float(theta_star), float(eps), flags, ctypes.byref(opt),
+                                  ctypes.byref(inf), ctypes.c_void_p(th.ctypes.data), ctypes.c_void_p(w.ctypes.data),
+                                  ctypes.c_void_p(mj.ctypes.data)))
+    d = {name: getattr(inf, name) for name, _ in PshtInfo._fields_}
+    d["euler"] = tuple(d["euler"])
+    return d, th, w, mj
