@@ -1274,7 +1274,13 @@ int psht_rotate_points(double alpha, double beta, double gamma, const double* th
 
 int psht_patch_rotation(const double* theta, const double* phi, int64_t npts, double* euler, double* theta_star,
                         void* stream) {
-  return guarded([&] { patch_rotation_device(theta, phi, npts, euler, theta_star, (cudaStream_t)stream); });
+  return guarded([&] {
+    PSHT_REQUIRE(npts > 0 && theta && phi && euler, PSHT_EINVAL, "patch rotation: need at least one point");
+    double red[3];
+    reduce_points(theta, phi, npts, red, (cudaStream_t)stream);
+    PSHT_REQUIRE(red[2] == 0.0, PSHT_EINVAL, "theta outside [0, pi], NaN, or non-finite phi in the points");
+    patch_rotation_device(theta, phi, npts, euler, theta_star, (cudaStream_t)stream);
+  });
 }
 
 const char* psht_last_error(void) { return g_err.c_str(); }

@@ -142,3 +142,17 @@ def test_patch_rotation_full_box():
     _, _, rad = O.min_enclosing_cap(th.cpu().numpy()[sel], ph.cpu().numpy()[sel])
     assert rad <= ts + 1e-9
     assert math.radians(33.0) < ts < math.radians(36.0)
+
+
+def test_patch_rotation_rejects_invalid_points():
+    from paper_2603_17166_gb300 import PshtError, patch_rotation
+
+    th = torch.tensor([0.5, float("nan"), 0.7], dtype=torch.float64, device="cuda")
+    ph = torch.tensor([0.1, 0.2, 0.3], dtype=torch.float64, device="cuda")
+    with pytest.raises(PshtError):
+        patch_rotation(th, ph)
+    with pytest.raises(PshtError):
+        patch_rotation(torch.tensor([0.5, 4.0], dtype=torch.float64, device="cuda"), ph[:2])
+    # points not in any open hemisphere (both poles)
+    with pytest.raises(PshtError):
+        patch_rotation(torch.tensor([0.0, math.pi], dtype=torch.float64, device="cuda"), ph[:2])
