@@ -311,13 +311,13 @@ int psht_rotate_points(double alpha, double beta, double gamma, const double* th
                        double* theta_out, double* phi_out, double* psi_out, void* stream);
 
 /*
- * Patch-centred frame (Sec. II, step 1, "centre of the patch at the north pole"): the centre c of
- * the smallest spherical cap holding the points (the direction of the minimum-norm point of their
- * convex hull, by Wolfe's iteration with the linear minimisations on the device), returned as the
- * Euler angles euler[3] = (0, theta_c, pi - phi_c) of a rotation taking c to the north pole, and
- * (if theta_star is not NULL) the cap radius.  theta, phi: DEVICE float64[npts]; euler, theta_star:
- * HOST.  Synchronises `stream`.  EINVAL for NaN, out-of-range or non-finite coordinates and if the points do not lie
- * in an open hemisphere.
+ * Patch-centred frame (Sec. II, step 1: coordinates whose north pole sits at the patch centre): the
+ * centre c of the smallest spherical cap holding the points (the direction of the minimum-norm
+ * point of their convex hull, by Wolfe's iteration with the linear minimisations on the device),
+ * returned as the Euler angles euler[3] = (0, theta_c, pi - phi_c) of a rotation taking c to the
+ * north pole, and (if theta_star is not NULL) the cap radius.  theta, phi: DEVICE float64[npts];
+ * euler, theta_star: HOST.  Synchronises `stream`.  EINVAL for NaN, out-of-range or non-finite
+ * coordinates and if the points do not lie in an open hemisphere.
  */
 int psht_patch_rotation(const double* theta, const double* phi, int64_t npts, double* euler, double* theta_star,
                         void* stream);
