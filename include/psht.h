@@ -49,7 +49,8 @@ extern "C" {
 /* precision / option flags for psht_plan_create */
 #define PSHT_AUTO 0u        /* FP32 form for eps >= 1e-5, FP64 form below                       */
 #define PSHT_FP64 1u        /* FP64 everywhere                                                   */
-#define PSHT_FP32 2u        /* FP32 recursion (FP64 seeds and rescaling), FP32 FFT and kernels   */
+#define PSHT_FP32 2u        /* FP32 recursion (FP64 seeds and rescaling), FP32 FFT and kernels;  */
+                            /* eps >= 1e-6 only (below it the FP64 form is required)             */
 #define PSHT_FULL_SKY 4u    /* full-sky route whatever the points' extent (Sec. I: theta_max = pi, */
                             /* w = 1, Lmax = lmax); the baseline of the paper's speed-ups (Table 1) */
 #define PSHT_PATCH_FRAME 8u /* run in the patch-centred frame (Sec. II step 1): the plan rotates the */
@@ -84,7 +85,8 @@ typedef struct psht_info {
  * Create a plan for synthesis/adjoint at fixed points (Sec. II steps 1-4, parameter choice of
  * Sec. II.C-D).  theta, phi: DEVICE float64[npts], read during this call only.  Synchronises
  * `stream` once (theta* reduction and point binning).  Returns PSHT_EINVAL for spin < 0,
- * lmax < spin, eps outside [1e-14, 1e-1], npts < 0, NaN/out-of-range theta or non-finite phi;
+ * lmax < spin, eps outside [1e-14, 1e-1], PSHT_FP32 with eps < 1e-6, npts < 0, NaN/out-of-range
+ * theta or non-finite phi;
  * PSHT_ENOMEM if the plan does not fit in device memory.  *out receives the plan.
  */
 int psht_plan_create(int spin, int lmax, const double* theta, const double* phi, int64_t npts, double eps,
@@ -339,8 +341,8 @@ int psht_plan_estimate_points(int spin, int lmax, const double* theta, const dou
  *   - nstreams worker threads, each with its own non-blocking CUDA stream, take requests in
  *     arrival order; a request whose plan is in use by another worker is passed over, not waited
  *     on, so independent requests overlap on the GPU.
- *   - Plans are cached by (points_key, spin, lmax, eps, flags): the caller names its point set by
- *     points_key, and equal keys must denote the same theta/phi values.
+ *   - Plans are cached by (points_key, npts, spin, lmax, eps, flags): the caller names its point
+ *     set by points_key, and equal keys with equal npts must denote the same theta/phi values.
  *   - Admission: a new plan is created only if the cached plans plus its estimate fit in the
  *     budget (bytes; 0 = 80 % of the device memory free at creation); least-recently-used idle
  *     plans are evicted to make room; a request that cannot fit yet waits in the queue, and one

@@ -21,9 +21,9 @@ O2  the partial-sky method step by step (Sec. II, steps 1-4), written plainly:
       P5 points:  ES-kernel type-2 NUFFT (Barnett et al. 2019), or the exact non-uniform DFT
       P6 adjoint: the exact transpose of P5 -> P3 followed by the adjoint projection (Sec. I).
 
-Readings where the paper is silent are listed in the design doc; the numerical choices that are not
-in the paper (ring count rounding, polar-optimisation cutoff, NUFFT grid sizes) are written
-out in ``plan_params`` below and mirrored, independently, by the product's planner.
+Where the paper is silent, the numerical choices (ring count rounding, polar-optimisation cutoff,
+NUFFT grid sizes) are written out in ``plan_params`` below; the product's planner makes the same
+choices in its own code.
 """
 from __future__ import annotations
 

@@ -26,13 +26,17 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
   return std::chrono::duration<double, std::milli>(b - a).count();
 }
 
+// The point count is part of the key: a cached plan writes (synthesis) or reads (adjoint) exactly
+// its own npts values, so a request that reuses a points_key with another count gets its own plan
+// instead of a plan sized for a different buffer.
 struct PlanKey {
   uint64_t points;
+  int64_t npts;
   int spin, lmax;
   double eps;
   uint32_t flags;
   bool operator<(const PlanKey& o) const {
-    return std::tie(points, spin, lmax, eps, flags) < std::tie(o.points, o.spin, o.lmax, o.eps, o.flags);
+    return std::tie(points, npts, spin, lmax, eps, flags) < std::tie(o.points, o.npts, o.spin, o.lmax, o.eps, o.flags);
   }
 };
 
@@ -74,7 +78,9 @@ struct Server {
   size_t in_use = 0, peak = 0;
   psht_server_stats stats{};
 
-  static PlanKey key_of(const psht_request& r) { return PlanKey{r.points_key, r.spin, r.lmax, r.eps, r.flags}; }
+  static PlanKey key_of(const psht_request& r) {
+    return PlanKey{r.points_key, r.npts, r.spin, r.lmax, r.eps, r.flags};
+  }
 
   // Evict least-recently-used idle plans until `need` more bytes fit; false (evicting nothing) if
   // even evicting every idle plan would not make room.  Called with mu held; the evicted plans are

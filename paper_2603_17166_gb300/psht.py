@@ -328,9 +328,22 @@ def ring_synthesis_noalloc(spin: int, lmax: int, theta_rings, g, c=None, out=Non
     The library's fixed scratch array is shared by all calls; order overlapping calls yourself."""
     torch = _torch()
     th = torch.as_tensor(theta_rings, dtype=torch.float64, device="cuda").contiguous()
+    if th.dim() != 1:
+        raise ValueError("theta_rings must be a 1-D array of ring colatitudes")
     g = torch.as_tensor(g, device="cuda").to(torch.complex128).contiguous()
     c = None if c is None else torch.as_tensor(c, device="cuda").to(torch.complex128).contiguous()
-    F = out if out is not None else torch.empty((th.numel(), 2 * lmax + 1), dtype=torch.complex128, device="cuda")
+    # the C entry point takes no buffer sizes: check them here, before anything reaches the device
+    n = nalm(int(lmax))
+    if g.numel() != n or (c is not None and c.numel() != n):
+        raise ValueError(f"g and c must hold nalm(lmax) = {n} packed coefficients")
+    shape = (th.numel(), 2 * int(lmax) + 1)
+    if out is not None:
+        if (not out.is_cuda or out.dtype != torch.complex128 or tuple(out.shape) != shape
+                or not out.is_contiguous()):
+            raise ValueError(f"out must be a contiguous complex128 CUDA tensor of shape {shape}")
+        F = out
+    else:
+        F = torch.empty(shape, dtype=torch.complex128, device="cuda")
     _check(lib().psht_ring_synthesis_noalloc(int(spin), int(lmax), _ptr(th), th.numel(), _ptr(g), _ptr(c), _ptr(F),
                                              _stream(stream)))
     return F

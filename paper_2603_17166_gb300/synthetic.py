@@ -221,6 +221,18 @@ def config5(frame: str = "R", n: int = 100_000_000, realisation: int = 0):
     return dict(lmax=lmax, s=2, g=g, c=c, theta=theta, phi=phi)
 
 
+def small_cap(radius_deg: float = 7.0, lmax: int = 4000, s: int = 2, area_deg2: float = 57.0,
+              res_arcmin: float = 0.86, config: int = 6):
+    """A small deep field: area / resolution^2 points uniform in a cap of the given radius around
+    the north pole (the EDFS row of the paper's Table 1: theta* = 7 deg, 57 deg^2 at 0.86', lmax
+    4000, spin 2; its footprint is not available), C_l ~ (l+1)^-2."""
+    n = int(round(area_deg2 * 3600.0 / (res_arcmin * res_arcmin)))
+    g = gaussian_alm(lmax, s, rng(config, "alm", 0), "inv_l2")
+    c = gaussian_alm(lmax, s, rng(config, "alm", 1), "inv_l2") if s else None
+    theta, phi = cap_points(n, radius_deg, rng(config, "points"), "N")
+    return dict(lmax=lmax, s=s, g=g, c=c, theta=theta, phi=phi)
+
+
 def _rotate_from_north(v, centre):
     """Rotation taking the north pole to `centre`, applied to v (inverse of rotate_to_north)."""
     z = np.array([0.0, 0.0, 1.0])

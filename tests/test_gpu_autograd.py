@@ -108,3 +108,92 @@ def test_gradcheck_fp64_small():
     f = _cx(rng, plan.npts, torch.complex128).requires_grad_()
     assert torch.autograd.gradcheck(lambda x: adjoint(plan, x), (f,), eps=1e-6, atol=1e-7, rtol=1e-6,
                                     fast_mode=True)
+
+
+def test_fp32_gradient_matches_direct_adjoint():
+    """The FP32 form's gradient (its own adjoint kernels at eps = 1e-5) against the oracle's direct
+    adjoint of the same band-limited w, times 2 for m > 0: <= 10 eps."""
+    from paper_2603_17166_gb300.autograd import synthesis
+
+    eps = 1e-5
+    rng, plan, th, ph = _setup("fp32", eps, lmax=96, n=4000, seed=14)
+    n = O.nalm(plan.lmax)
+    g = _cx(rng, n, torch.complex64).requires_grad_()
+    c = _cx(rng, n, torch.complex64).requires_grad_()
+    wn = O.direct_synthesis(plan.lmax, plan.spin, O.canonical_alm(rng.standard_normal(n) + 1j * rng.standard_normal(n),
+                                                                  plan.lmax, plan.spin), None, th, ph)
+    w = torch.from_numpy(wn).cuda().to(torch.complex64)
+    torch.sum(w.conj() * synthesis(plan, g, c)).real.backward()
+    gt, ct = O.direct_adjoint(plan.lmax, plan.spin, th, ph, wn)
+    _, m = O.lm_of_index(plan.lmax)
+    fac = np.where(m > 0, 2.0, 1.0)
+    got = np.concatenate([g.grad.cpu().numpy(), c.grad.cpu().numpy()]).astype(np.complex128)
+    assert O.rel_l2(got, np.concatenate([fac * gt, fac * ct])) <= 10 * eps
+
+
+# the ~1% deep field at lmax 6000 with 5e7 points, where the workload list places autograd
+DEEP_LM = [(2, 0), (2, 2), (3, 1), (12, 0), (40, 40), (64, 60), (300, 298)]
+
+
+@pytest.fixture(scope="module")
+def deep_field():
+    """Spin-2 a_lm and points of the deep field, a band-limited w = A a' (FP64 form at eps 1e-12),
+    and the oracle's adjoint of w at DEEP_LM summed over all 5e7 points."""
+    from paper_2603_17166_gb300 import Plan, synthetic
+
+    wl = synthetic.config3(s=2, frame="R")
+    gen = synthetic.rng(3, "alm", 7)
+    a2 = synthetic.gaussian_alm(6000, 2, gen, "inv_l2")
+    plan = Plan(2, 6000, torch.from_numpy(wl["theta"]).cuda(), torch.from_numpy(wl["phi"]).cuda(), 1e-12,
+                precision="fp64")
+    w = plan.synthesis(torch.from_numpy(a2).cuda()).cpu().numpy()
+    plan.close()
+    torch.cuda.empty_cache()
+    ls = np.array([a for a, _ in DEEP_LM])
+    ms = np.array([b for _, b in DEEP_LM])
+    g1, c1 = O.direct_adjoint_lm(2, wl["theta"], wl["phi"], w, ls, ms)
+    return wl, w, ls, ms, g1, c1
+
+
+@pytest.mark.parametrize("prec,eps", [("fp32", 1e-5), ("fp64", 1e-10)])
+def test_autograd_deep_field_lmax6000(deep_field, prec, eps):
+    """At the deep field's full size: the gradient of L = Re <w, synthesis(g, c)> from backward()
+    (the packed adjoint kernels) against central finite differences of L along a random direction
+    (L is linear, so they are exact up to rounding for any step), and against the oracle's direct
+    adjoint times 2 for m > 0 at selected coefficients."""
+    from paper_2603_17166_gb300 import Plan
+    from paper_2603_17166_gb300.autograd import synthesis
+
+    wl, w_np, ls, ms, g1, c1 = deep_field
+    assert wl["theta"].size == 50_000_000
+    plan = Plan(2, 6000, torch.from_numpy(wl["theta"]).cuda(), torch.from_numpy(wl["phi"]).cuda(), eps,
+                precision=prec)
+    cd = plan.cdtype
+    g = torch.from_numpy(wl["g"]).cuda().to(cd).requires_grad_()
+    c = torch.from_numpy(wl["c"]).cuda().to(cd).requires_grad_()
+    w = torch.from_numpy(w_np).cuda().to(cd)
+    torch.sum(w.conj() * synthesis(plan, g, c)).real.backward()
+    assert plan.status() == 0
+    rng = np.random.default_rng(61)
+    n = O.nalm(6000)
+    dg = torch.from_numpy(O.canonical_alm(rng.standard_normal(n) + 1j * rng.standard_normal(n), 6000, 2)).cuda().to(cd)
+    dc = torch.from_numpy(O.canonical_alm(rng.standard_normal(n) + 1j * rng.standard_normal(n), 6000, 2)).cuda().to(cd)
+
+    def loss(a, b):
+        with torch.no_grad():
+            return _re_dot(w, plan.synthesis(a, b))
+
+    h = 0.5
+    fd = (loss(g.detach() + h * dg, c.detach() + h * dc) - loss(g.detach() - h * dg, c.detach() - h * dc)) / (2 * h)
+    pred = _re_dot(g.grad, dg) + _re_dot(c.grad, dc)
+    tol = 1e-10 if prec == "fp64" else 1e-4
+    assert abs(pred - fd) <= tol * abs(fd), (pred, fd)
+    _, mm = O.lm_of_index(6000)
+    idx = O.alm_index(6000, ls, ms)
+    fac = np.where(ms > 0, 2.0, 1.0)
+    ti = torch.from_numpy(idx).cuda()
+    got = np.concatenate([g.grad[ti].cpu().numpy(), c.grad[ti].cpu().numpy()]).astype(np.complex128)
+    assert O.rel_l2(got, np.concatenate([fac * g1, fac * c1])) <= 10 * eps
+    plan.close()
+    del g, c, w
+    torch.cuda.empty_cache()

@@ -12,6 +12,7 @@ eps = 1e-10.  The oracle cannot run the whole problem in seconds, so:
 import numpy as np
 import pytest
 
+import _parity as PP
 import oracle as O
 
 torch = pytest.importorskip("torch")
@@ -50,11 +51,14 @@ def test_synthesis_sampled_points(planned, workload):
     f = plan.synthesis(g, c)
     rng = np.random.default_rng(11)
     sel = rng.choice(workload["theta"].size, size=160, replace=False)
-    # include the extreme points (pole side and cap edge)
-    sel[:2] = [int(np.argmin(workload["theta"])), int(np.argmax(workload["theta"]))]
+    # add the extreme points (pole side and cap edge), the smallest and largest phi, and points whose
+    # ES window starts on a grid tile's first or last row or column
+    P = O.plan_params(4096, 2, eps, workload["theta"])
+    sel = np.unique(np.concatenate([sel, PP.border_sample(P, workload["theta"], workload["phi"])]))
     ref = O.direct_synthesis(4096, 2, workload["g"], workload["c"], workload["theta"][sel], workload["phi"][sel])
     got = f[torch.from_numpy(sel).cuda()].cpu().numpy().astype(np.complex128)
     assert O.rel_l2(got, ref) <= 10 * eps
+    PP.assert_pointwise(got, ref, eps)
     assert torch.isfinite(torch.view_as_real(f)).all()
 
 

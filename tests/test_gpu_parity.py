@@ -9,6 +9,7 @@ import math
 import numpy as np
 import pytest
 
+import _parity as PP
 import oracle as O
 
 torch = pytest.importorskip("torch")
@@ -25,6 +26,15 @@ def _cap(rng, n, radius, pole="N"):
     if pole == "S":
         th = math.pi - th
     return th, rng.uniform(-math.pi, 3 * math.pi, n)
+
+
+def _cap_with_borders(rng, n, radius, pole, lmax, s, eps):
+    """Random cap points plus points on the tile borders, the phi wrap-around, the pole and the cap
+    edge of the plan those points lead to (the added points leave every plan parameter as it is)."""
+    th, ph = _cap(rng, n, radius, pole)
+    P = O.plan_params(lmax, s, eps, th)
+    tb, pb = PP.border_points(P, rng)
+    return np.concatenate([th, tb]), np.concatenate([ph, pb])
 
 
 def _plan(s, lmax, th, ph, eps, prec):
@@ -90,13 +100,15 @@ def test_ring_coefficients_stage_parity(lmax, s, radius, pole, eps, prec):
 @pytest.mark.parametrize("lmax,s,radius,pole,eps,prec", CASES)
 def test_synthesis_against_direct_sum(lmax, s, radius, pole, eps, prec):
     rng = np.random.default_rng(3)
-    th, ph = _cap(rng, 4000, radius, pole)
+    th, ph = _cap_with_borders(rng, 4000, radius, pole, lmax, s, eps)
     g, c = _alm(rng, lmax, s), (_alm(rng, lmax, s) if s else None)
     plan = _plan(s, lmax, th, ph, eps, prec)
     f = plan.synthesis(_cu(g, plan), _cu(c, plan)).cpu().numpy()
     assert plan.status() == 0
     ref = O.direct_synthesis(lmax, s, g, c, th, ph)
     assert O.rel_l2(f, ref) <= 10 * eps
+    PP.assert_pointwise(f, ref, eps)
+    PP.assert_pointwise(f[4000:], ref[4000:], eps, what="border point")
     if prec == "fp64":
         P = O.plan_params(lmax, s, eps, th)
         f2 = O.pipeline_synthesis(P, g, c, th, ph)
@@ -106,7 +118,7 @@ def test_synthesis_against_direct_sum(lmax, s, radius, pole, eps, prec):
 @pytest.mark.parametrize("lmax,s,radius,pole,eps,prec", CASES)
 def test_adjoint_against_direct_sum(lmax, s, radius, pole, eps, prec):
     rng = np.random.default_rng(4)
-    th, ph = _cap(rng, 4000, radius, pole)
+    th, ph = _cap_with_borders(rng, 4000, radius, pole, lmax, s, eps)
     g, c = _alm(rng, lmax, s), _alm(rng, lmax, s)
     plan = _plan(s, lmax, th, ph, eps, prec)
     f = O.direct_synthesis(lmax, s, g, c, th, ph)      # f = A a: the adjoint's accuracy target
@@ -117,6 +129,7 @@ def test_adjoint_against_direct_sum(lmax, s, radius, pole, eps, prec):
     _, m = O.lm_of_index(lmax)
     wgt = np.tile(np.where(m == 0, 1.0, 2.0), 2)
     assert O.rel_l2(np.concatenate([gt, ct]), np.concatenate([gt1, ct1]), wgt) <= 10 * eps
+    PP.assert_pointwise(np.concatenate([gt, ct]), np.concatenate([gt1, ct1]), eps, what="coefficient")
     # written zeros: Im at m = 0 and l < s
     l, m = O.lm_of_index(lmax)
     assert np.all(gt[m == 0].imag == 0) and np.all(ct[m == 0].imag == 0)
@@ -198,7 +211,9 @@ def test_invalid_arguments_are_rejected():
     with pytest.raises(PshtError):
         Plan(0, 8, bad, ph, 1e-8)
     with pytest.raises(PshtError):
-        Plan(0, 8, th, ph, 1e-9, precision="fp32")   # FP32 form needs eps >= 1e-7
+        Plan(0, 8, th, ph, 1e-9, precision="fp32")   # FP32 form needs eps >= 1e-6
+    with pytest.raises(PshtError):
+        Plan(0, 8, th, ph, 9.9e-7, precision="fp32")
 
 
 @pytest.mark.parametrize("prec,eps", [("fp32", 1e-5), ("fp64", 1e-9)])
@@ -299,3 +314,29 @@ def test_host_buffer_entry_points_match_device_ones(prec, eps, s):
         for a, b in ((gt_h, gt_d), (ct_h, ct_d)):
             b = b.cpu().numpy().astype(np.complex128)
             assert O.alm_rel_l2(a.astype(np.complex128), b, lmax) <= tol
+
+
+@pytest.mark.parametrize("eps,cd", [(1e-10, np.complex128), (1e-5, np.complex64)])
+def test_one_shot_calls_with_the_papers_argument_list(eps, cd):
+    """psht_synthesis / psht_adjoint_synthesis take (g, c, spin, lmax, theta, phi, eps) as the
+    problem is stated in Sec. I (eq. syn and the adjoint synthesis general); precision follows eps
+    (FP32 form at eps >= 1e-5).  Against the direct sums, <= 10 eps."""
+    from paper_2603_17166_gb300 import psht
+
+    rng = np.random.default_rng(44)
+    lmax, s = 80, 2
+    th, ph = _cap_with_borders(rng, 3000, 0.4, "S", lmax, s, eps)
+    g, c = _alm(rng, lmax, s), _alm(rng, lmax, s)
+    tt, pt = torch.from_numpy(th).cuda(), torch.from_numpy(ph).cuda()
+    f = psht.synthesis(torch.from_numpy(g).cuda(), torch.from_numpy(c).cuda(), s, lmax, tt, pt, eps)
+    assert f.dtype == (torch.complex128 if cd == np.complex128 else torch.complex64)
+    ref = O.direct_synthesis(lmax, s, g, c, th, ph)
+    got = f.cpu().numpy().astype(np.complex128)
+    assert O.rel_l2(got, ref) <= 10 * eps
+    PP.assert_pointwise(got, ref, eps)
+    gt, ct = psht.adjoint_synthesis(torch.from_numpy(ref).cuda(), s, lmax, tt, pt, eps)
+    g1, c1 = O.direct_adjoint(lmax, s, th, ph, ref)
+    _, m = O.lm_of_index(lmax)
+    wgt = np.tile(np.where(m == 0, 1.0, 2.0), 2)
+    got = np.concatenate([gt.cpu().numpy(), ct.cpu().numpy()]).astype(np.complex128)
+    assert O.rel_l2(got, np.concatenate([g1, c1]), wgt) <= 10 * eps

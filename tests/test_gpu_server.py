@@ -129,3 +129,36 @@ def test_invalid_request_fails_alone():
     assert srv.wait(t_bad)["status"] == -22  # PSHT_EINVAL from the point validation
     assert srv.wait(t_ok)["status"] == 0
     srv.close()
+
+
+def test_reused_key_with_other_point_count_gets_its_own_plan():
+    """A points_key reused for a smaller point set must not run the plan cached for the larger one
+    (that plan writes its own npts values): the point count is part of the cache key, so the
+    second request builds a plan of its own and its result equals that request run alone."""
+    from paper_2603_17166_gb300 import Server
+
+    fd = _fields(1, seed=6)[0]
+    small = dict(fd)
+    k = fd["n"] // 3
+    small.update(theta=fd["theta"][:k].clone(), phi=fd["phi"][:k].clone(), f=fd["f"][:k].clone(), n=k)
+    srv = Server(nstreams=1)
+    t, out_big = _submit(srv, fd, 0)
+    assert srv.wait(t)["status"] == 0
+    t, out_small = _submit(srv, small, 0)
+    r = srv.wait(t)
+    assert r["status"] == 0 and r["plan_cached"] == 0
+    assert out_small[0].numel() == k
+    t, adj_small = _submit(srv, small, 1)
+    assert srv.wait(t)["status"] == 0
+    assert srv.stats()["plans_created"] == 2
+    srv.close()
+    ref = Server(nstreams=1)
+    t, out_ref = _submit(ref, small, 0)
+    assert ref.wait(t)["status"] == 0
+    t, adj_ref = _submit(ref, small, 1)
+    assert ref.wait(t)["status"] == 0
+    ref.close()
+    assert torch.equal(out_small[0], out_ref[0])
+    _close(adj_small, adj_ref, small)
+    # the larger set's own result is the head of nothing in particular: only check it is finite
+    assert torch.isfinite(torch.view_as_real(out_big[0])).all()

@@ -134,3 +134,35 @@ def test_cost_optimal_apodisation_length():
         assert not Q["full"] and Q["eps_apo"] != O.plan_params(lmax2, s, eps2, th)["eps_apo"]
         f = O.pipeline_synthesis(Q, g, None, th, ph)
         assert O.rel_l2(f, O.direct_synthesis(lmax2, s, g, None, th, ph)) <= 10 * eps2
+
+
+def test_legendre_cost_counts_recursion_steps():
+    """legendre_cost (the quantity the cost-minimising apodisation length minimises, Sec. II.C) is
+    the number of (ring, m, l) steps of the per-ring recursion: on ring j every packed coefficient
+    (l, m) with m <= M_j and l >= s is visited once (the recursion of order m starts at
+    l0 = max(m, s) and ends at lmax).  Pinned by counting those coefficients in the packed layout
+    one by one, by the closed form nring * (nalm(lmax) - nalm(s - 1)) when every ring keeps all
+    orders, and by hand on tiny cases, for s = 0 and s = 2 (where orders m < s start at l = s)."""
+    # hand counts: lmax 3, s 0, one ring keeping m <= 1: l = 0..3 (m = 0) and 1..3 (m = 1) -> 4 + 3
+    assert O.legendre_cost(3, 0, [1]) == 7
+    # lmax 3, s 2: m = 0, 1 start at l = 2 (2 steps each), m = 2 at 2 (2), m = 3 at 3 (1)
+    assert O.legendre_cost(3, 2, [3]) == 2 + 2 + 2 + 1
+    assert O.legendre_cost(3, 2, [0, 0]) == 2 * 2
+    rng = np.random.default_rng(17)
+    for lmax, s in ((12, 0), (12, 2), (40, 2), (33, 3), (7, 0)):
+        l, m = O.lm_of_index(lmax)
+        for trial in range(4):
+            nring = int(rng.integers(1, 9))
+            Mj = rng.integers(0, lmax + 1, nring)
+            if trial == 0:
+                Mj[:] = lmax
+            if trial == 1:
+                Mj[:] = rng.integers(0, max(s, 1), nring)
+            brute = 0
+            for Mk in Mj:
+                for li, mi in zip(l, m):
+                    if mi <= Mk and li >= s:
+                        brute += 1
+            assert O.legendre_cost(lmax, s, Mj) == brute, (lmax, s, list(Mj))
+            if trial == 0:
+                assert brute == nring * (O.nalm(lmax) - (O.nalm(s - 1) if s > 0 else 0))
