@@ -50,10 +50,11 @@ def parse():
     ap.add_argument("--forms", default="fp32,fp64", help="comma list of forms to time (fp32 is the headline)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=200, help="requests of the serving run (0: skip)")
+    ap.add_argument("--serve-requests", type=int, default=300,
+                    help="requests of each serving run (0: skip; the full recipe uses 1000)")
     ap.add_argument("--serve-fields", type=int, default=8)
     ap.add_argument("--serve-streams", type=int, default=4)
-    ap.add_argument("--serve-loads", default="0.8", help="offered loads, fractions of single-stream capacity")
+    ap.add_argument("--serve-loads", default="0.5,0.8,1.0", help="offered loads, fractions of single-stream capacity")
     ap.add_argument("--serve-nmax", type=int, default=30_000_000)
     ap.add_argument("--no-frames", action="store_true",
                     help="skip the frame comparison (points as given about the nearer pole vs the patch frame)")
@@ -276,12 +277,14 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
     results = {}
     # kernels of one FP32 step: recursion, Theta FFT, phi FFT, gather; scatter, phi FFT, Theta FFT,
-    # adjoint recursion and its per-order reduction (the grid clearing is a memset, not a kernel)
-    launches_per_step = 9
+    # adjoint recursion (the grid clearing and the zero orders are memsets, not kernels)
+    launches_per_step = 8
     want = set(args.forms.split(","))
     forms = [f for f in (("fp32", EPS32, args.steps), ("fp64", EPS64, max(1, args.steps64))) if f[0] in want]
-    if not forms or forms[0][0] != "fp32":
-        raise SystemExit("--forms must include fp32 (the headline form)")
+    if not forms:
+        raise SystemExit("--forms must name fp32 and/or fp64")
+    if forms[0][0] != "fp32":  # a run of the FP64 form alone (profiling); its line is not the headline
+        forms[0] = ("fp64", EPS64, args.steps)
     headline = None
     gpu_samples = {}
     for name, eps, K in forms:
@@ -379,7 +382,7 @@ def run_ours(args, rank, world, local_rank):
         sel[:2] = [int(np.argmin(wl["theta"])), int(np.argmax(wl["theta"]))]
         gpu_samples[name] = (eps, sel, f[torch.from_numpy(sel).to(dev)].cpu().numpy().astype(np.complex128))
         results[name] = entry
-        if name == "fp32":
+        if headline is None:
             headline = entry
         plan.close()
         del g, c, f, gt, ct
@@ -388,10 +391,12 @@ def run_ours(args, rank, world, local_rank):
     line = {
         "metric": METRIC, "value": headline["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": headline["ms_per_step"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if headline is results.get("fp32") else "f64",
+        "data": "synthetic",
         "config": {"workload": "spin-2 synthesis+adjoint, lmax 4096, ~4% field RA -50..50 dec -70..-42, "
                                f"regular {args.step_arcmin}' grid + 2.5' rms deflections, frame {args.frame}",
-                   "npts": npts, "lmax": LMAX, "spin": SPIN, "eps": EPS32, "form": "fp32",
+                   "npts": npts, "lmax": LMAX, "spin": SPIN, "eps": headline["eps"],
+                   "form": "fp32" if headline is results.get("fp32") else "fp64",
                    "parallelism": "replicas" if world > 1 else "single-gpu",
                    "l2": "per-step working set larger than L2 (no flush)"},
         "roofline": headline["roofline"], "clocks": headline["clocks"], "e2e": headline.get("e2e"),
@@ -689,15 +694,25 @@ def run_serving(args, dev) -> dict:
         bad = sum(1 for x in res if x["status"] != 0)
         lat = np.array([x["total_ms"] for x in res])
         slow = np.array([x["total_ms"] / alone[(r["field"], r["op"])] for x, r in zip(res, reqs)])
+        prec = np.array([x["precision"] for x in res])
+        per_form = {}
+        for form, pv in (("fp32", 32), ("fp64", 64)):
+            sel = lat[prec == pv]
+            if sel.size:
+                per_form[form] = dict(requests=int(sel.size), p50_ms=float(np.percentile(sel, 50)),
+                                      p99_ms=float(np.percentile(sel, 99)))
+        bsz = np.array([x.get("batch", 1) for x in res])
         runs.append(dict(load=load, lambda_rps=lam, p50_ms=float(np.percentile(lat, 50)),
                          p99_ms=float(np.percentile(lat, 99)), mean_ms=float(lat.mean()), max_ms=float(lat.max()),
                          p99_slowdown=float(np.percentile(slow, 99)), completed_rps=len(res) / wall,
-                         aggregate_mpts=pts / wall / 1e6, failed=bad))
+                         aggregate_mpts=pts / wall / 1e6, failed=bad, per_form=per_form,
+                         mean_batch=float(bsz.mean()), batched_fraction=float(np.mean(bsz > 1))))
     st = srv.stats()
     srv.close()
     head = min(runs, key=lambda x: abs(x["load"] - 0.8))
     return dict(p99_ms=head["p99_ms"], p50_ms=head["p50_ms"], load=head["load"],
-                aggregate_mpts=head["aggregate_mpts"], requests=len(reqs),
+                aggregate_mpts=head["aggregate_mpts"], requests=len(reqs), per_form=head["per_form"],
+                batches=st["batches"], batched_requests=st["batched_requests"],
                 fields=len(fields), streams=args.serve_streams, capacity_rps=capacity,
                 mean_service_ms=mean_service, plan_ms_mean=float(np.mean(plan_ms)) if plan_ms else None,
                 runs=runs, cache_hits=st["cache_hits"], plans_created=st["plans_created"],

@@ -165,6 +165,25 @@ int psht_predict_error(int spin, int lmax, double theta_star, double eps, const 
                        const double* beta, int n, double* rel_rms, void* stream);
 
 /*
+ * Batched forms: nsets independent transforms on one plan, with the same results as nsets calls of
+ * psht_plan_synthesis / psht_plan_adjoint.  Up to 4 sets share one pass of the Wigner-d recursion
+ * (the recursion's columns of every (ring, m, l) are evaluated once and applied to each set: the
+ * recursion costs about 1.5-2.5x a single set's for 4 sets instead of 4x); the FFT, interpolation
+ * and spreading stages run set by set.  g, c, f: HOST arrays of nsets DEVICE pointers, laid out as
+ * for the single-set calls; c may be NULL (c = 0 for every set in the synthesis, no c~ in the
+ * adjoint) or hold NULL entries.  nsets in [1, PSHT_MAX_BATCH]; larger batches run in groups of 4.
+ * The first call with more than one set allocates device buffers for 3 extra sets (ring
+ * coefficients, and in the FP32 form an accumulator of 16 B per coefficient each), which the plan
+ * keeps (psht_plan_info's device_bytes includes them from then on).  A PSHT_PATCH_FRAME plan runs
+ * the sets one after the other.  Asynchronous on `stream`; errors as for the single-set calls.
+ */
+#define PSHT_MAX_BATCH 64
+int psht_plan_synthesis_batch(psht_plan* plan, int nsets, const void* const* g, const void* const* c, void* const* f,
+                              void* stream);
+int psht_plan_adjoint_batch(psht_plan* plan, int nsets, const void* const* f, void* const* g, void* const* c,
+                            void* stream);
+
+/*
  * Packed-gradient forms, for automatic differentiation over the packed a_lm arrays.  The transpose
  * above pairs with the inner product that counts each m > 0 entry twice (it stands for m and -m,
  * eq. syn's reality condition), while a gradient over the packed storage counts every stored
@@ -341,6 +360,10 @@ int psht_plan_estimate_points(int spin, int lmax, const double* theta, const dou
  *   - nstreams worker threads, each with its own non-blocking CUDA stream, take requests in
  *     arrival order; a request whose plan is in use by another worker is passed over, not waited
  *     on, so independent requests overlap on the GPU.
+ *   - Continuous batching: when a worker starts a request, every request queued for the same plan
+ *     and the same operation (up to 8) joins it and the group runs as one batched call
+ *     (psht_plan_synthesis_batch / psht_plan_adjoint_batch), so requests that piled up while the
+ *     plan was busy share its recursion pass.
  *   - Plans are cached by (points_key, npts, spin, lmax, eps, flags): the caller names its point
  *     set by points_key, and equal keys with equal npts must denote the same theta/phi values.
  *   - Admission: a new plan is created only if the cached plans plus its estimate fit in the
@@ -377,10 +400,13 @@ typedef struct {
   double plan_ms;      /* plan creation (0 when cached)                                        */
   double exec_ms;      /* transform, until its stream completed                                */
   double total_ms;     /* submission to completion                                             */
+  int batch;           /* requests in the batched call this request ran in (1: alone)          */
 } psht_result;
 typedef struct {
   int64_t submitted, completed, failed, plans_created, cache_hits, evictions;
   size_t budget, bytes_in_use, bytes_peak;
+  int64_t batches;           /* plan calls made (a batch of several requests counts once)        */
+  int64_t batched_requests;  /* requests that ran in a batch of more than one                    */
 } psht_server_stats;
 
 /* Start nstreams (1..64) workers on the current device.  *out receives the server. */

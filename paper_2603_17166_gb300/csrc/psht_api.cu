@@ -186,7 +186,7 @@ std::vector<T> cast_vec(const std::vector<double>& v) {
 
 // ---------------------------------------------------------------------------------------------
 // P1-P2 and the grid: everything that depends on (spin, lmax, eps, precision, theta*, pole)
-int64_t adj_part_elems(const Plan& p);
+
 
 // (ring, m, l) steps of the recursion on one ring with cutoff M: sum_{m=0}^{M} (lmax + 1 - max(m, s))
 int64_t ring_cost(int lmax, int s, int M) {
@@ -281,71 +281,34 @@ void layout(Plan& p, double theta_star) {
   p.Lpad = (p.nring + 31) / 32 * 32;
   p.padq = 8;
   p.gstride = (p.nphi + 2 * p.padq + 7) / 8 * 8;
-  p.TR = 16;
-  p.TQ = 32;
+  // point tiles of TR x TQ base cells: FP32 32 x 16 (its spreading kernel gives each of a warp's
+  // lanes one base row), FP64 16 x 32
+  p.TR = p.prec == 32 ? 32 : 16;
+  p.TQ = p.prec == 32 ? 16 : 32;
   p.ntr = (p.nrows - 1) / p.TR + 1;
   p.ntq = (p.nphi + p.padq) / p.TQ + 1;
   p.nalm = (int64_t)(p.lmax + 1) * (p.lmax + 2) / 2;
   p.tstride = p.nalm + 64;  // one chunk of zero records after the last order
   // launch shapes of the recursion
+  // rings per lane of the one-warp synthesis: FP64 1, FP32 one packed pair (2 rings per lane measured
+  // faster than 4 at lmax 4096: the same issue rate, and items of 64 rings leave fewer idle slots)
   p.syn_rpt = (p.prec == 64) ? 1 : 2;
   p.syn_threads = 32;  // one warp per synthesis item (k_rec_syn_w)
-  // adjoint: all active rings of one order m in one CTA, (rings per thread, threads) from the
-  // instantiated shapes, more rings per thread in FP32 to amortise the per-l warp reduction
-  // FP32: one warp per item of 32 adj_rpt rings with per-item partial sums reduced per m
-  // (k_rec_adj_w, k_adj_reduce) while that buffer stays within 4 GB, else the block form below.
-  // Block form (FP64, large FP32 plans): one CTA per m and chunk of adj_rpt * adj_threads rings.
-  constexpr double kMaxPartBytes = 4e9;
-  p.adj_rpt = p.nring <= 256 ? 2 : (p.nring <= 512 ? 4 : 8);  // fewest idle ring slots per CTA
+  // adjoint.  FP32: one warp per item of 32 adj_rpt rings (k_rec_adj_w), the items of an order
+  // meeting in a float4-per-coefficient accumulator.  FP64: one CTA per m and chunk of
+  // adj_rpt * adj_threads rings (k_rec_adj), (rings per thread, threads) from the instantiated
+  // shapes with the fewest idle ring slots.
+  p.adj_rpt = p.nring <= 256 ? 2 : (p.nring <= 512 ? 4 : 8);
   p.adj_threads = 128;
   if (p.prec == 32) {
     p.adj_threads = 32;
-    p.adj_rpt = 4;
-    if (adj_part_elems(p) * 4.0 > kMaxPartBytes) p.adj_rpt = 8;
-    if (adj_part_elems(p) * 4.0 > kMaxPartBytes) {
-      p.adj_rpt = 4;
-      p.adj_threads = 256;
-    }
+    p.adj_rpt = 4;  // two packed pairs per lane (8 rings per lane measured slower: 128 registers)
   }
   // FFTs longer than one CTA's shared memory run on global buffers (psht_fft.cu)
   constexpr int kMaxLen = 1 << 22;
   PSHT_REQUIRE(p.nTheta <= kMaxLen && p.nphi <= kMaxLen, PSHT_ENOTSUP,
                "FFT length above " + std::to_string(kMaxLen) + " (Theta " + std::to_string(p.nTheta) + ", phi " +
                    std::to_string(p.nphi) + ")");
-}
-
-// Walk the (m, ring part) active ranges in the order of the work items: fn(m, part, lo, hi) for
-// every non-empty range.  Ring j is active for m when M_j >= m; a ring at theta_j > pi/2 from the
-// plan's pole is in part 1 (evaluated by reflection).
-template <class Fn>
-void for_active_ranges(const Plan& p, Fn&& fn) {
-  std::vector<int> refl(p.nring);
-  for (int j = 0; j < p.nring; ++j) {
-    const double bj = p.beta_j[j];
-    refl[j] = p.pole > 0 ? (bj > 0.5 * M_PI) : (bj < 0.5 * M_PI);
-  }
-  for (int m = 0; m <= p.M; ++m) {
-    for (int part = 0; part < 2; ++part) {
-      int lo = -1, hi = -1;
-      for (int j = 0; j < p.nring; ++j)
-        if (p.Mj[j] >= m && refl[j] == part) {
-          if (lo < 0) lo = j;
-          hi = j + 1;
-        }
-      if (lo >= 0) fn(m, part, lo, hi);
-    }
-  }
-}
-
-// elements of the per-item partial sums of the one-warp adjoint (0 when it is not used)
-int64_t adj_part_elems(const Plan& p) {
-  if (p.adj_threads != 32) return 0;
-  const int cap = 32 * p.adj_rpt;
-  int64_t e = 0;
-  for_active_ranges(p, [&](int m, int, int lo, int hi) {
-    e += (int64_t)((hi - lo + cap - 1) / cap) * 4 * (p.lmax - std::max(m, p.spin) + 1);
-  });
-  return e;
 }
 
 size_t planned_bytes(const Plan& p) {
@@ -359,13 +322,14 @@ size_t planned_bytes(const Plan& p) {
   b += p.prec == 64 ? (size_t)p.npts * 2 * p.W * 8 : (size_t)p.npts * 8;  // weights / fractions
   b += (size_t)(p.nTheta + 2 * p.L + p.nphi) * (cb + 4);       // twiddles + permutations
   b += fft_scratch_elems(p) * cb;                              // long-FFT buffers
-  b += (size_t)adj_part_elems(p) * rb;                         // one-warp adjoint partial sums
+  if (p.adj_threads == 32) b += (size_t)p.nalm * 16 + (size_t)(p.lmax + 1) * 4;  // FP32 adjoint accumulator
   // small tables: rings, seeds, ring ranges, deconvolution, weights, work items (upper bounds)
   b += (size_t)p.nring * (sizeof(RingDev) + rb) + (size_t)(p.lmax + 1) * (sizeof(MSeed) + 4 * sizeof(int2));
   b += (size_t)(2 * p.L + 2 * p.M + 2) * rb;
   const size_t items = (size_t)(p.M + 1) * (2 + (size_t)p.nring / 32);  // items hold >= 32 rings, one per part
   b += items * (sizeof(RecItem) + sizeof(AdjItem));
   b += ((size_t)p.ntr * p.ntq + (size_t)p.npts / 2048 + 1) * sizeof(TileItem);
+  if (p.prec == 32) b += ((size_t)p.ntr * p.ntq * p.TR + 1) * sizeof(int);  // per-row point offsets
   if (p.patch) {  // rotator, rotated a_lm, spin phases and the adjoint's rotated input
     b += rotator_bytes(p.lmax, p.prec) + 2 * (size_t)p.nalm * cb;
     if (p.spin > 0) b += 2 * (size_t)p.npts * cb;
@@ -514,8 +478,6 @@ Plan* create(int spin, int lmax, const double* theta, const double* phi, int64_t
     // per order m and ring part (0: direct, 1: reflected) the active rings M_j >= m form one
     // contiguous range (M_j is unimodal in j, the reflection flag monotone)
     std::vector<int2> mr(2 * (size_t)(lmax + 1), make_int2(0, 0));
-    std::vector<RecItem> items;
-    const int cap = p->syn_rpt * p->syn_threads;
     for (int m = 0; m <= p->M; ++m) {
       for (int part = 0; part < 2; ++part) {
         int lo = -1, hi = -1;
@@ -526,42 +488,96 @@ Plan* create(int spin, int lmax, const double* theta, const double* phi, int64_t
           }
         if (lo < 0) continue;
         mr[(size_t)part * (lmax + 1) + m] = make_int2(lo, hi);
-        const int n = hi - lo, nchunk = (n + cap - 1) / cap;
-        for (int c = 0; c < nchunk; ++c) {
-          const int a = lo + (int)((int64_t)n * c / nchunk), b = lo + (int)((int64_t)n * (c + 1) / nchunk);
-          items.push_back(RecItem{m, a, b - a, part});
-        }
-        p->pairs += n;
-        p->triples += (int64_t)n * (lmax - std::max(m, spin) + 1);
+        p->pairs += hi - lo;
+        p->triples += (int64_t)(hi - lo) * (lmax - std::max(m, spin) + 1);
+      }
+    }
+    // Mirror pairs (full-sky plans): ring jm - j lies at pi - b_j, so by d^l_{m,-s}(pi - b) =
+    // (-1)^(l+m) d^l_{m,s}(b) it shares the Wigner columns of ring j.  An order whose reflected
+    // active rings are exactly the mirrors of its direct ones (the equator ring, its own mirror,
+    // aside) evaluates the columns once per pair.  pair[m] = the paired direct rings [a, b), eq[m] =
+    // the equator ring when it is active and unpaired (else -1).
+    const int jm = p->nring - 1;
+    std::vector<int2> pair(lmax + 1, make_int2(0, 0));
+    std::vector<int> eqr(lmax + 1, -1), mmode(lmax + 1, 0);
+    bool any_mirror = false;
+    if (p->full && p->has_refl) {
+      const int eq = (jm % 2 == 0) ? jm / 2 : -1;
+      for (int m = 0; m <= p->M; ++m) {
+        const int2 D = mr[m], R = mr[(size_t)(lmax + 1) + m];
+        if (D.y <= D.x || R.y <= R.x) continue;
+        const int a = jm - (R.y - 1), b = jm - R.x + 1;  // mirror of the reflected range
+        int e = -1;
+        bool ok = (D.x == a && D.y == b);
+        if (!ok && eq >= 0 && D.x == a && D.y == b + 1 && b == eq) ok = true, e = eq;
+        if (!ok && eq >= 0 && D.x == a - 1 && D.y == b && a - 1 == eq) ok = true, e = eq;
+        if (!ok || refl[a] != 0) continue;
+        pair[m] = make_int2(a, b);
+        eqr[m] = e;
+        mmode[m] = 1;
+        any_mirror = true;
+      }
+    }
+    std::vector<RecItem> items, mitems;
+    const int cap = p->syn_rpt * p->syn_threads;
+    auto chunks = [](int lo, int hi, int cp, auto&& emit) {
+      const int n = hi - lo, nchunk = (n + cp - 1) / cp;
+      for (int c = 0; c < nchunk; ++c)
+        emit(lo + (int)((int64_t)n * c / nchunk), lo + (int)((int64_t)n * (c + 1) / nchunk));
+    };
+    for (int m = 0; m <= p->M; ++m) {
+      if (mmode[m]) {
+        chunks(pair[m].x, pair[m].y, cap, [&](int a, int b) { mitems.push_back(RecItem{m, a, b - a, 0}); });
+        if (eqr[m] >= 0) items.push_back(RecItem{m, eqr[m], 1, 0});
+        continue;
+      }
+      for (int part = 0; part < 2; ++part) {
+        const int2 r = mr[(size_t)part * (lmax + 1) + m];
+        if (r.y > r.x) chunks(r.x, r.y, cap, [&](int a, int b) { items.push_back(RecItem{m, a, b - a, part}); });
       }
     }
     p->d_mrange = (int2*)upload(*p, mr, st);
     p->nitems = (int)items.size();
     p->d_items = (RecItem*)upload(*p, items, st);
+    p->nmitems = (int)mitems.size();
+    if (p->nmitems > 0) p->d_mitems = (RecItem*)upload(*p, mitems, st);
+    if (any_mirror && prec == 64) p->d_mmode = (int*)upload(*p, mmode, st);
     if (p->adj_threads == 32) {  // one-warp adjoint: items of at most 32 adj_rpt rings, per-m spans
       const int acap = 32 * p->adj_rpt;
-      std::vector<AdjItem> ai;
-      std::vector<int2> span(lmax + 1, make_int2(0, 0));
-      int64_t off = 0;
-      for_active_ranges(*p, [&](int m, int part, int lo, int hi) {
-        const int n = hi - lo, nch = (n + acap - 1) / acap;
-        if (span[m].y == 0) span[m].x = (int)ai.size();
-        for (int c = 0; c < nch; ++c) {
-          const int a = lo + (int)((int64_t)n * c / nch), b = lo + (int)((int64_t)n * (c + 1) / nch);
-          ai.push_back(AdjItem{m, a, b - a, part, off});
-          off += 4 * (int64_t)(lmax - std::max(m, spin) + 1);
+      std::vector<AdjItem> ai, mai;
+      std::vector<int2> span(lmax + 1, make_int2(0, 0));  // .y: items of order m (both lists)
+      for (int m = 0; m <= p->M; ++m) {
+        span[m].x = (int)ai.size();
+        if (mmode[m]) {
+          chunks(pair[m].x, pair[m].y, acap, [&](int a, int b) { mai.push_back(AdjItem{m, a, b - a, 0, 0}); });
+          if (eqr[m] >= 0) ai.push_back(AdjItem{m, eqr[m], 1, 0, 0});
+        } else {
+          for (int part = 0; part < 2; ++part) {
+            const int2 r = mr[(size_t)part * (lmax + 1) + m];
+            if (r.y > r.x)
+              chunks(r.x, r.y, acap, [&](int a, int b) { ai.push_back(AdjItem{m, a, b - a, part, 0}); });
+          }
         }
-        span[m].y += nch;
-      });
-      PSHT_REQUIRE(off == adj_part_elems(*p), PSHT_ECUDA, "internal: adjoint item layout mismatch");
+      }
+      for (const AdjItem& x : ai) ++span[x.m].y;
+      for (const AdjItem& x : mai) ++span[x.m].y;
+      for (AdjItem& x : ai) x.nitems = span[x.m].y;
+      for (AdjItem& x : mai) x.nitems = span[x.m].y;
       p->naitems = (int)ai.size();
-      p->part_elems = off;
       p->d_aitems = ai.empty() ? nullptr : (AdjItem*)upload(*p, ai, st);
+      p->nmaitems = (int)mai.size();
+      if (p->nmaitems > 0) p->d_maitems = (AdjItem*)upload(*p, mai, st);
       p->d_aspan = (int2*)upload(*p, span, st);
-      p->d_part = dalloc(*p, (size_t)std::max<int64_t>(off, 1) * (prec == 64 ? 8 : 4));
+      // accumulator and arrival counters start at zero; every call leaves them at zero
+      p->d_acc = dalloc(*p, (size_t)p->nalm * 16);
+      p->d_cnt = (int*)dalloc(*p, (size_t)(lmax + 1) * sizeof(int));
+      PSHT_CUDA_TRY(cudaMemsetAsync(p->d_acc, 0, (size_t)p->nalm * 16, st));
+      PSHT_CUDA_TRY(cudaMemsetAsync(p->d_cnt, 0, (size_t)(lmax + 1) * sizeof(int), st));
       // order chunks for the host-buffer entry points: kChunks ranges of m with about equal
-      // recursion work (ring count x l range of the synthesis items), split at order boundaries
+      // recursion work (ring count x l range of the synthesis items), split at order boundaries;
+      // plans with mirror pairs run unchunked (no chunk table)
       constexpr int kChunks = 8;
+      if (!any_mirror) {
       std::vector<double> cum(items.size() + 1, 0.0);
       for (size_t i = 0; i < items.size(); ++i)
         cum[i + 1] = cum[i] + (double)items[i].nj * (lmax - std::max(items[i].m, spin) + 1);
@@ -580,6 +596,7 @@ Plan* create(int spin, int lmax, const double* theta, const double* phi, int64_t
         while (ia < (int)ai.size() && ai[ia].m < mb) ++ia;
         p->chunk_item.push_back(it);
         p->chunk_aitem.push_back(ia);
+      }
       }
     }
     // deconvolution tables, ring weights, FFT twiddles and digit-reversal tables
@@ -604,6 +621,18 @@ Plan* create(int spin, int lmax, const double* theta, const double* phi, int64_t
       }
       return t;
     };
+    // FP32 form: e^{-2 pi i t/n} as tw[t & 63] tw[64 + (t >> 6)], the 64 fine and n/64 + 1 coarse
+    // factors (psht_common.cuh, twiddle<float2>)
+    auto twid_split = [](int n) {
+      const int nb = n / 64 + 1;
+      std::vector<double> t(2 * (size_t)(64 + nb));
+      for (int k = 0; k < 64 + nb; ++k) {
+        const double a = 2.0 * M_PI * (k < 64 ? k : 64.0 * (k - 64)) / n;
+        t[2 * k] = cos(a);
+        t[2 * k + 1] = -sin(a);
+      }
+      return t;
+    };
     if (prec == 64) {
       p->d_sT = upload(*p, sT, st);
       p->d_sP = upload(*p, sP, st);
@@ -615,9 +644,9 @@ Plan* create(int spin, int lmax, const double* theta, const double* phi, int64_t
       p->d_sT = upload(*p, cast_vec<float>(sT), st);
       p->d_sP = upload(*p, cast_vec<float>(sP), st);
       p->d_w = upload(*p, cast_vec<float>(p->w_j), st);
-      p->d_tw2L = upload(*p, cast_vec<float>(twid(2 * p->L)), st);
-      p->d_tw4L = upload(*p, cast_vec<float>(twid(4 * p->L)), st);
-      p->d_twP = upload(*p, cast_vec<float>(twid(p->nphi)), st);
+      p->d_tw2L = upload(*p, cast_vec<float>(twid_split(2 * p->L)), st);
+      p->d_tw4L = upload(*p, cast_vec<float>(twid_split(4 * p->L)), st);
+      p->d_twP = upload(*p, cast_vec<float>(twid_split(p->nphi)), st);
     }
     // work buffers
     const size_t cb = prec == 64 ? 16 : 8;
@@ -715,6 +744,82 @@ void run_adjoint(Plan& p, const void* f, void* g, void* c, cudaStream_t st, doub
   staged(p, 5, st, [&] { launch_phi_adjoint(p, st); });
   staged(p, 6, st, [&] { launch_theta_adjoint(p, st); });
   staged(p, 7, st, [&] { launch_rec_adjoint(p, g, c, st, msc); });
+}
+
+// Batched execution: groups of up to kBatchGroup sets share one recursion launch (the Wigner
+// columns are evaluated once per (ring, m, l) for the whole group); the FFT, gather and scatter
+// stages run per set on the group's own ring-coefficient buffers.
+constexpr int kBatchGroup = 4;
+
+void ensure_batch(Plan& p, int nsets, cudaStream_t st) {
+  const int need = std::min(nsets, kBatchGroup) - 1;
+  const size_t cb = p.prec == 64 ? 16 : 8;
+  while ((int)p.d_Fb.size() < need) {
+    p.d_Fb.push_back(dalloc(p, (size_t)p.ncols * p.Lpad * cb));
+    if (p.adj_threads == 32) {  // FP32 adjoint accumulator of the extra set (zero between calls)
+      void* a = dalloc(p, (size_t)p.nalm * 16);
+      PSHT_CUDA_TRY(cudaMemsetAsync(a, 0, (size_t)p.nalm * 16, st));
+      p.d_accb.push_back(a);
+    } else {
+      p.d_accb.push_back(nullptr);
+    }
+  }
+}
+
+void run_synthesis_batch(Plan& p, int nsets, const void* const* g, const void* const* c, void* const* f,
+                         cudaStream_t st, double msc = 1.0) {
+  ensure_batch(p, nsets, st);
+  void* const F0 = p.d_F;
+  for (int k0 = 0; k0 < nsets; k0 += kBatchGroup) {
+    const int n = std::min(kBatchGroup, nsets - k0);
+    void* Fs[kBatchGroup] = {F0};
+    for (int k = 1; k < n; ++k) Fs[k] = p.d_Fb[k - 1];
+    staged(p, 0, st, [&] { launch_rec_synthesis_sets(p, n, g + k0, c ? c + k0 : nullptr, Fs, st, msc); });
+    try {
+      for (int k = 0; k < n; ++k) {
+        p.d_F = Fs[k];
+        staged(p, 1, st, [&] { launch_theta_synthesis(p, st); });
+        staged(p, 2, st, [&] { launch_phi_synthesis(p, st); });
+        staged(p, 3, st, [&] { launch_gather(p, f[k0 + k], st); });
+      }
+    } catch (...) {
+      p.d_F = F0;
+      throw;
+    }
+    p.d_F = F0;
+  }
+}
+
+void run_adjoint_batch(Plan& p, int nsets, const void* const* f, void* const* g, void* const* c, cudaStream_t st,
+                       double msc = 1.0) {
+  ensure_batch(p, nsets, st);
+  const size_t cb = p.prec == 64 ? 16 : 8;
+  void* const F0 = p.d_F;
+  for (int k0 = 0; k0 < nsets; k0 += kBatchGroup) {
+    const int n = std::min(kBatchGroup, nsets - k0);
+    void* Fs[kBatchGroup] = {F0};
+    void* accs[kBatchGroup] = {p.d_acc};
+    for (int k = 1; k < n; ++k) {
+      Fs[k] = p.d_Fb[k - 1];
+      accs[k] = p.d_accb[k - 1];
+    }
+    try {
+      for (int k = 0; k < n; ++k) {
+        staged(p, 4, st, [&] {
+          PSHT_CUDA_TRY(cudaMemsetAsync(p.d_G, 0, (size_t)p.nrows * p.gstride * cb, st));
+          launch_scatter(p, f[k0 + k], st);
+        });
+        staged(p, 5, st, [&] { launch_phi_adjoint(p, st); });
+        p.d_F = Fs[k];
+        staged(p, 6, st, [&] { launch_theta_adjoint(p, st); });
+        p.d_F = F0;
+      }
+    } catch (...) {
+      p.d_F = F0;
+      throw;
+    }
+    staged(p, 7, st, [&] { launch_rec_adjoint_sets(p, n, Fs, accs, g + k0, c ? c + k0 : nullptr, st, msc); });
+  }
 }
 
 // Synthesis and adjoint as the entry points see them: in a patch-frame plan the a_lm are rotated
@@ -966,6 +1071,41 @@ int psht_plan_adjoint(psht_plan* plan, const void* f, void* g, void* c, void* st
     PSHT_REQUIRE(plan && g, PSHT_EINVAL, "plan and g must not be NULL");
     PSHT_REQUIRE(f || plan->p->npts == 0, PSHT_EINVAL, "f must not be NULL");
     exec_adjoint(*plan->p, f, g, c, (cudaStream_t)stream);
+  });
+}
+
+int psht_plan_synthesis_batch(psht_plan* plan, int nsets, const void* const* g, const void* const* c, void* const* f,
+                              void* stream) {
+  return guarded([&] {
+    PSHT_REQUIRE(plan && g && f, PSHT_EINVAL, "plan, g and f must not be NULL");
+    PSHT_REQUIRE(nsets >= 1 && nsets <= PSHT_MAX_BATCH, PSHT_EINVAL, "nsets must lie in [1, PSHT_MAX_BATCH]");
+    Plan& p = *plan->p;
+    for (int k = 0; k < nsets; ++k) {
+      PSHT_REQUIRE(g[k], PSHT_EINVAL, "g[k] must not be NULL");
+      PSHT_REQUIRE(f[k] || p.npts == 0, PSHT_EINVAL, "f[k] must not be NULL");
+    }
+    if (p.patch) {  // the rotation works on one set at a time
+      for (int k = 0; k < nsets; ++k) exec_synthesis(p, g[k], c ? c[k] : nullptr, f[k], (cudaStream_t)stream);
+      return;
+    }
+    run_synthesis_batch(p, nsets, g, c, f, (cudaStream_t)stream);
+  });
+}
+int psht_plan_adjoint_batch(psht_plan* plan, int nsets, const void* const* f, void* const* g, void* const* c,
+                            void* stream) {
+  return guarded([&] {
+    PSHT_REQUIRE(plan && g && f, PSHT_EINVAL, "plan, f and g must not be NULL");
+    PSHT_REQUIRE(nsets >= 1 && nsets <= PSHT_MAX_BATCH, PSHT_EINVAL, "nsets must lie in [1, PSHT_MAX_BATCH]");
+    Plan& p = *plan->p;
+    for (int k = 0; k < nsets; ++k) {
+      PSHT_REQUIRE(g[k], PSHT_EINVAL, "g[k] must not be NULL");
+      PSHT_REQUIRE(f[k] || p.npts == 0, PSHT_EINVAL, "f[k] must not be NULL");
+    }
+    if (p.patch) {
+      for (int k = 0; k < nsets; ++k) exec_adjoint(p, f[k], g[k], c ? c[k] : nullptr, (cudaStream_t)stream);
+      return;
+    }
+    run_adjoint_batch(p, nsets, f, g, c, (cudaStream_t)stream);
   });
 }
 

@@ -152,13 +152,40 @@ struct Dft<7, INV, V> {
 };
 
 // ---------------------------------------------------------------------------------------------
+// Shared-memory FFT buffer with one pad element after every 16: the butterflies of the late DIF
+// (early DIT) stages read with power-of-two strides, which would put a warp's lanes on a few
+// banks; with the pad the strides 2, 4, 8 and 16 spread over all of them.
+template <typename V>
+struct PadBuf {
+  V* p;
+  __device__ __forceinline__ V& operator[](int i) const { return p[i + (i >> 4)]; }
+};
+__host__ __device__ constexpr int padded_len(int n) { return n + (n >> 4) + 1; }
+
+// Twiddle e^{-2 pi i t/N}.  FP64: a full table tw[t].  FP32: the product of two short tables,
+// tw[t mod 64] e^{-2 pi i 64 floor(t/64)/N} = tw[t & 63] tw[64 + (t >> 6)] (64 + N/64 + 1 entries),
+// which stay in L1 next to the shared-memory buffers (the full tables did not); one extra complex
+// multiply, error ~1e-7.
+template <typename V>
+__device__ __forceinline__ V twiddle(const V* __restrict__ tw, int t);
+template <>
+__device__ __forceinline__ double2 twiddle<double2>(const double2* __restrict__ tw, int t) {
+  return __ldg(&tw[t]);
+}
+template <>
+__device__ __forceinline__ float2 twiddle<float2>(const float2* __restrict__ tw, int t) {
+  const float2 a = __ldg(&tw[t & 63]), b = __ldg(&tw[64 + (t >> 6)]);
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// ---------------------------------------------------------------------------------------------
 // In-place mixed-radix FFT of length N in shared memory, all threads of the block cooperate.
 // DIF (Gentleman-Sande): natural-order input, output frequency k at position perm[k].
 // DIT (transpose of DIF): input n placed at perm[n], natural-order output.
 // tw[t] = e^{-2 pi i t/N}; INV uses conj twiddles (unnormalised inverse).
 // Each butterfly reads and writes the same R positions, so one buffer and R registers suffice.
-template <int R, bool INV, bool DIF, typename V>
-__device__ __forceinline__ void fft_stage(V* buf, int N, int Nc, const V* __restrict__ tw) {
+template <int R, bool INV, bool DIF, typename V, typename B>
+__device__ __forceinline__ void fft_stage(B buf, int N, int Nc, const V* __restrict__ tw) {
   const int s = Nc / R;
   const int nb = N / R;
   const int tstride = N / Nc;
@@ -171,7 +198,7 @@ __device__ __forceinline__ void fft_stage(V* buf, int N, int Nc, const V* __rest
     if (!DIF) {
 #pragma unroll
       for (int q = 1; q < R; ++q) {
-        V w = __ldg(&tw[j * q * tstride]);
+        const V w = twiddle<V>(tw, j * q * tstride);
         v[q] = INV ? cmulc(v[q], w) : cmul(v[q], w);
       }
     }
@@ -179,7 +206,7 @@ __device__ __forceinline__ void fft_stage(V* buf, int N, int Nc, const V* __rest
     if (DIF) {
 #pragma unroll
       for (int q = 1; q < R; ++q) {
-        V w = __ldg(&tw[j * q * tstride]);
+        const V w = twiddle<V>(tw, j * q * tstride);
         v[q] = INV ? cmulc(v[q], w) : cmul(v[q], w);
       }
     }
@@ -188,37 +215,37 @@ __device__ __forceinline__ void fft_stage(V* buf, int N, int Nc, const V* __rest
   }
 }
 
-template <bool INV, bool DIF, typename V>
-__device__ __forceinline__ void fft_stage_dispatch(int R, V* buf, int N, int Nc, const V* tw) {
+template <bool INV, bool DIF, typename V, typename B>
+__device__ __forceinline__ void fft_stage_dispatch(int R, B buf, int N, int Nc, const V* tw) {
   switch (R) {
-    case 8: fft_stage<8, INV, DIF>(buf, N, Nc, tw); break;
-    case 4: fft_stage<4, INV, DIF>(buf, N, Nc, tw); break;
-    case 2: fft_stage<2, INV, DIF>(buf, N, Nc, tw); break;
-    case 3: fft_stage<3, INV, DIF>(buf, N, Nc, tw); break;
-    case 5: fft_stage<5, INV, DIF>(buf, N, Nc, tw); break;
-    case 7: fft_stage<7, INV, DIF>(buf, N, Nc, tw); break;
+    case 8: fft_stage<8, INV, DIF, V>(buf, N, Nc, tw); break;
+    case 4: fft_stage<4, INV, DIF, V>(buf, N, Nc, tw); break;
+    case 2: fft_stage<2, INV, DIF, V>(buf, N, Nc, tw); break;
+    case 3: fft_stage<3, INV, DIF, V>(buf, N, Nc, tw); break;
+    case 5: fft_stage<5, INV, DIF, V>(buf, N, Nc, tw); break;
+    case 7: fft_stage<7, INV, DIF, V>(buf, N, Nc, tw); break;
     default: break;
   }
 }
 
 // The caller syncs before the call; the function syncs after every stage.
-template <bool INV, typename V>
-__device__ void fft_dif(V* buf, const FftDev& f, const V* tw) {
+template <bool INV, typename V, typename B>
+__device__ void fft_dif(B buf, const FftDev& f, const V* tw) {
   int Nc = f.n;
   for (int st = 0; st < f.nst; ++st) {
     const int R = f.rad[st];
-    fft_stage_dispatch<INV, true>(R, buf, f.n, Nc, tw);
+    fft_stage_dispatch<INV, true, V>(R, buf, f.n, Nc, tw);
     Nc /= R;
     __syncthreads();
   }
 }
-template <bool INV, typename V>
-__device__ void fft_dit(V* buf, const FftDev& f, const V* tw) {
+template <bool INV, typename V, typename B>
+__device__ void fft_dit(B buf, const FftDev& f, const V* tw) {
   int Nc = 1;
   for (int st = f.nst - 1; st >= 0; --st) {
     const int R = f.rad[st];
     Nc *= R;
-    fft_stage_dispatch<INV, false>(R, buf, f.n, Nc, tw);
+    fft_stage_dispatch<INV, false, V>(R, buf, f.n, Nc, tw);
     __syncthreads();
   }
 }

@@ -19,8 +19,9 @@ namespace psht {
 namespace {
 
 constexpr int kFftThreads = 512;
-constexpr int kMaxLenF64 = 14336;  // complex128 elements in 224 KiB of shared memory
-constexpr int kMaxLenF32 = 28672;  // complex64
+// longest transforms held in one CTA's shared memory (227 KiB) with the padded layout (PadBuf)
+constexpr int kMaxLenF64 = 13600;  // complex128
+constexpr int kMaxLenF32 = 27200;  // complex64
 // |n| <= L-1 values held per thread while the buffer is re-laid out (2L <= max length / 2)
 // threads of the Theta kernels per launch mode (see k_theta_syn)
 __host__ __device__ constexpr int theta_threads(int mode) { return mode == 1 ? 256 : kFftThreads; }
@@ -51,7 +52,8 @@ __global__ void __launch_bounds__(theta_threads(MODE)) k_theta_syn(const typenam
   constexpr bool STG = MODE != 0;  // |n| <= L-1 values staged behind the transform, not in registers
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N2 = 2 * L, N4 = 4 * L;
-  V* buf = GM ? scratch + (int64_t)blockIdx.x * (N4 + N2) : reinterpret_cast<V*>(smraw);
+  V* const raw = GM ? scratch + (int64_t)blockIdx.x * (padded_len(N4) + N2) : reinterpret_cast<V*>(smraw);
+  const PadBuf<V> buf{raw};
   auto body = [&](const int mi) {
   const int m = col_m(mi), am = m < 0 ? -m : m;
   const T sigma = ((s + am) & 1) ? (T)-1 : (T)1;
@@ -73,7 +75,7 @@ __global__ void __launch_bounds__(theta_threads(MODE)) k_theta_syn(const typenam
   // collect b[n] = H[n] sT(n) sP(m), |n| <= L-1, then lay them out for the inverse DIT of length 4L
   const T sp = sP[m + M];
   if constexpr (STG) {
-    V* stg = buf + N4;
+    V* stg = raw + padded_len(N4);
     for (int i = threadIdx.x; i < N2 - 1; i += blockDim.x) {
       const int n = i - (L - 1);
       stg[i] = cscale(buf[perm2L[n < 0 ? n + N2 : n]], sT[i] * sp);
@@ -134,7 +136,7 @@ __global__ void __launch_bounds__(kFftThreads) k_phi_syn(const typename Cx<T>::V
   using V = typename Cx<T>::V;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int nphi = fP.n;
-  V* buf = GM ? scratch + (int64_t)blockIdx.x * nphi : reinterpret_cast<V*>(smraw);
+  const PadBuf<V> buf{GM ? scratch + (int64_t)blockIdx.x * padded_len(nphi) : reinterpret_cast<V*>(smraw)};
   auto body = [&](const int row) {
   for (int k = threadIdx.x; k < nphi; k += blockDim.x) buf[k] = mk((T)0, (T)0);
   __syncthreads();
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(kFftThreads) k_phi_adj(const typename Cx<T>::V
   using V = typename Cx<T>::V;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int nphi = fP.n;
-  V* buf = GM ? scratch + (int64_t)blockIdx.x * nphi : reinterpret_cast<V*>(smraw);
+  const PadBuf<V> buf{GM ? scratch + (int64_t)blockIdx.x * padded_len(nphi) : reinterpret_cast<V*>(smraw)};
   auto body = [&](const int row) {
   const V* Gr = G + (int64_t)row * gstride;
   // fold every stored column qs (true column qs - padq) onto q = (qs - padq) mod nphi
@@ -232,7 +234,8 @@ __global__ void __launch_bounds__(theta_threads(MODE)) k_theta_adj(const typenam
   constexpr bool STG = MODE != 0;  // |n| <= L-1 values staged behind the transform, not in registers
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N2 = 2 * L, N4 = 4 * L;
-  V* buf = GM ? scratch + (int64_t)blockIdx.x * (N4 + N2) : reinterpret_cast<V*>(smraw);
+  V* const raw = GM ? scratch + (int64_t)blockIdx.x * (padded_len(N4) + N2) : reinterpret_cast<V*>(smraw);
+  const PadBuf<V> buf{raw};
   auto body = [&](const int mi) {
   const int m = col_m(mi), am = m < 0 ? -m : m;
   const T sigma = ((s + am) & 1) ? (T)-1 : (T)1;
@@ -248,7 +251,7 @@ __global__ void __launch_bounds__(theta_threads(MODE)) k_theta_adj(const typenam
   fft_dif<false>(buf, f4L, tw4L);
   const T sp = sP[m + M];
   if constexpr (STG) {
-    V* stg = buf + N4;
+    V* stg = raw + padded_len(N4);
     for (int i = threadIdx.x; i < N2 - 1; i += blockDim.x) {
       const int n = i - (L - 1);
       stg[i] = cscale(buf[perm4L[n < 0 ? n + N4 : n]], sT[i] * sp);
@@ -337,8 +340,8 @@ bool phi_gm(const Plan& p) { return p.nphi > max_fft_len(p.prec); }
 
 size_t fft_scratch_elems(const Plan& p) {
   size_t e = 0;
-  if (theta_gm(p)) e = std::max(e, (size_t)std::min(p.ncols, kGmCtas) * 6 * p.L);
-  if (phi_gm(p)) e = std::max(e, (size_t)std::min(p.nrows, kGmCtas) * p.nphi);
+  if (theta_gm(p)) e = std::max(e, (size_t)std::min(p.ncols, kGmCtas) * (padded_len(4 * p.L) + 2 * p.L));
+  if (phi_gm(p)) e = std::max(e, (size_t)std::min(p.nrows, kGmCtas) * padded_len(p.nphi));
   return e;
 }
 
@@ -346,14 +349,20 @@ size_t fft_scratch_elems(const Plan& p) {
 template <typename T>
 int theta_mode(const Plan& p) {
   if (theta_gm(p)) return 2;
-  return (size_t)6 * p.L * sizeof(typename Cx<T>::V) <= kMaxSmem ? 1 : 0;
+  return (size_t)(padded_len(4 * p.L) + 2 * p.L) * sizeof(typename Cx<T>::V) <= kMaxSmem ? 1 : 0;
+}
+// shared memory of the Theta kernels: the padded 4L buffer, plus the 2L staging in mode 1
+template <typename T>
+size_t theta_smem(const Plan& p, int mode) {
+  if (mode == 2) return 0;
+  return (size_t)(padded_len(4 * p.L) + (mode == 1 ? 2 * p.L : 0)) * sizeof(typename Cx<T>::V);
 }
 
 template <typename T>
 void theta_syn_t(Plan& p, cudaStream_t st) {
   using V = typename Cx<T>::V;
   const int mode = theta_mode<T>(p);
-  const size_t smem = mode == 2 ? 0 : (size_t)(mode == 1 ? 6 : 4) * p.L * sizeof(V);
+  const size_t smem = theta_smem<T>(p, mode);
   const auto fn = mode == 2 ? k_theta_syn<T, 2> : (mode == 1 ? k_theta_syn<T, 1> : k_theta_syn<T, 0>);
   if (mode != 2) set_smem<T>((const void*)fn, smem);
   fn<<<mode == 2 ? std::min(p.ncols, kGmCtas) : p.ncols, theta_threads(mode), smem, st>>>(
@@ -366,7 +375,7 @@ template <typename T>
 void theta_adj_t(Plan& p, cudaStream_t st) {
   using V = typename Cx<T>::V;
   const int mode = theta_mode<T>(p);
-  const size_t smem = mode == 2 ? 0 : (size_t)(mode == 1 ? 6 : 4) * p.L * sizeof(V);
+  const size_t smem = theta_smem<T>(p, mode);
   const auto fn = mode == 2 ? k_theta_adj<T, 2> : (mode == 1 ? k_theta_adj<T, 1> : k_theta_adj<T, 0>);
   if (mode != 2) set_smem<T>((const void*)fn, smem);
   fn<<<mode == 2 ? std::min(p.ncols, kGmCtas) : p.ncols, theta_threads(mode), smem, st>>>(
@@ -379,7 +388,7 @@ template <typename T>
 void phi_syn_t(Plan& p, cudaStream_t st) {
   using V = typename Cx<T>::V;
   const bool gm = phi_gm(p);
-  const size_t smem = gm ? 0 : (size_t)p.nphi * sizeof(V);
+  const size_t smem = gm ? 0 : (size_t)padded_len(p.nphi) * sizeof(V);
   const auto fn = gm ? k_phi_syn<T, true> : k_phi_syn<T, false>;
   if (!gm) set_smem<T>((const void*)fn, smem);
   fn<<<gm ? std::min(p.nrows, kGmCtas) : p.nrows, kFftThreads, smem, st>>>(
@@ -391,7 +400,7 @@ template <typename T>
 void phi_adj_t(Plan& p, cudaStream_t st) {
   using V = typename Cx<T>::V;
   const bool gm = phi_gm(p);
-  const size_t smem = gm ? 0 : (size_t)p.nphi * sizeof(V);
+  const size_t smem = gm ? 0 : (size_t)padded_len(p.nphi) * sizeof(V);
   const auto fn = gm ? k_phi_adj<T, true> : k_phi_adj<T, false>;
   if (!gm) set_smem<T>((const void*)fn, smem);
   fn<<<gm ? std::min(p.nrows, kGmCtas) : p.nrows, kFftThreads, smem, st>>>(

@@ -73,7 +73,7 @@ struct RecItem {    // one CTA of the synthesis recursion: order m, rings [j0, j
 struct AdjItem {    // one warp of the FP32 adjoint recursion: order m, rings [j0, j0 + nj)
   int m, j0, nj;
   int refl;
-  int64_t off;      // first element of its partial sums: 4 values per l = l0 .. lmax
+  int nitems;       // items of order m (1: the item projects its own sums; else they meet in d_acc)
 };
 
 struct TileItem {   // one CTA of the gather/scatter: a tile and a slice of its sorted points
@@ -127,11 +127,21 @@ struct Plan {
   int* d_status = nullptr;      // device error word (bounded waits that gave up), read by psht_plan_status
   RecItem* d_items = nullptr;
   int nitems = 0;
+  // full-sky plans: rings j and nring - 1 - j lie at b and pi - b and share their Wigner columns;
+  // orders whose reflected active rings are exactly the mirrors of their direct ones run as pairs
+  RecItem* d_mitems = nullptr;  // synthesis items of mirror pairs (direct rings j of the pairs)
+  int nmitems = 0;
+  AdjItem* d_maitems = nullptr; // FP32 adjoint items of mirror pairs
+  int nmaitems = 0;
+  int* d_mmode = nullptr;       // per m: 1 if the order runs as mirror pairs (FP64 block adjoint), else null
   AdjItem* d_aitems = nullptr;  // adjoint as one warp per item (adj_threads == 32)
   int naitems = 0;
   int2* d_aspan = nullptr;      // per m: first adjoint item, item count
-  void* d_part = nullptr;       // per-item partial sums, T [sum over items of 4 (lmax - l0 + 1)]
-  int64_t part_elems = 0;
+  void* d_acc = nullptr;        // FP32 adjoint: float4 [nalm], the sums of orders with several items
+  int* d_cnt = nullptr;         // FP32 adjoint: per m, items of that order finished in the current call
+  // batched execution (psht_plan_*_batch): ring coefficients and (FP32) accumulators of the sets
+  // after the first of a group, allocated on the first batched call
+  std::vector<void*> d_Fb, d_accb;
   void* d_F = nullptr;          // complex T [ncols][Lpad]
   void* d_X = nullptr;          // complex T [nrows][ncols]
   void* d_G = nullptr;          // complex T [nrows][gstride]
@@ -148,6 +158,7 @@ struct Plan {
   void* d_fscratch = nullptr;   // global FFT buffers for lengths beyond shared memory (else null)
   // points (sorted by tile)
   TileItem* d_titems = nullptr;
+  int* d_roff = nullptr;        // FP32 form: first sorted point of each (tile, base row), ntr ntq TR + 1 entries
   int ntitems = 0;
   int32_t* d_pidx = nullptr;    // original index of sorted point
   int32_t* d_pcell = nullptr;   // (r0 - tile row origin) | (q0 + padq - tile col origin) << 16
@@ -189,6 +200,14 @@ void build_rec_table(Plan& p, cudaStream_t st);
 // msc: weight of the m > 0 a_lm entries (read by the synthesis, written by the adjoint)
 void launch_rec_synthesis(Plan& p, const void* g, const void* c, cudaStream_t st, double msc = 1.0);
 void launch_rec_adjoint(Plan& p, void* g, void* c, cudaStream_t st, double msc = 1.0);
+// several sets in one pass (the Wigner columns of every (ring, m, l) evaluated once for all sets):
+// synthesis of a_lm sets (g[k], c[k]) into ring coefficients F[k]; adjoint of ring coefficients F[k]
+// into (g[k], c[k]), the FP32 form accumulating orders with several items in acc[k] (float4[nalm],
+// zero on entry and on exit).  c may be null (no c sets).
+void launch_rec_synthesis_sets(Plan& p, int nsets, const void* const* g, const void* const* c, void* const* F,
+                               cudaStream_t st, double msc = 1.0);
+void launch_rec_adjoint_sets(Plan& p, int nsets, void* const* F, void* const* acc, void* const* g, void* const* c,
+                             cudaStream_t st, double msc = 1.0);
 void launch_theta_synthesis(Plan& p, cudaStream_t st);
 void launch_phi_synthesis(Plan& p, cudaStream_t st);
 void launch_phi_adjoint(Plan& p, cudaStream_t st);

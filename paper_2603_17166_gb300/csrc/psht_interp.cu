@@ -147,6 +147,12 @@ __device__ __forceinline__ double es_psi(double z, double beta) {
   return exp(beta * (sqrt(1.0 - z * z) - 1.0));
 }
 
+// first sorted point of every (tile, base row): the scanned count at key (tile, row, column 0)
+__global__ void k_row_offsets(const int* __restrict__ cnt, int64_t nr, int TQ, int* __restrict__ roff) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < nr) roff[i] = cnt[i * TQ];
+}
+
 __global__ void k_tile_offsets(const int* __restrict__ cnt, int ntiles, int per_tile, int* __restrict__ toff) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t <= ntiles) toff[t] = cnt[(int64_t)t * per_tile];
@@ -342,6 +348,86 @@ __global__ void __launch_bounds__(NT) k_scatter(const TileItem* __restrict__ ite
   }
 }
 
+// Spreading in the FP32 form, one warp per tile of 32 base rows x 16 base columns (the plan's tile
+// shape in that form).  Lane i takes the points whose window starts on the tile's base row i, in
+// their sorted (column) order, one point per step.  Within one row a of the windows the 32 lanes
+// update 32 different grid rows (i + a), so no two lanes touch the same cell and each lane issues
+// its W loads, multiply-adds and stores of that row back to back; a __syncwarp after each window
+// row orders them against the next row, which the neighbouring lane updated.  The warp's private
+// tile is stored column-major with a column pitch P of 48 cells (a multiple of 16 eight-byte banks),
+// so a warp access to (row i + a, column q_i + b) hits bank (i + a) mod 16 in each half-warp: no
+// bank conflicts whatever the lanes' columns.  The tile is then added to the grid with one vector
+// atomic per nonzero cell.
+constexpr int kRowTR = 32, kRowTQ = 16, kRowP = 48, kRowWarps = 8;
+
+__device__ __forceinline__ void red_add_v2(float2* addr, float2 v) {
+  asm volatile("red.relaxed.gpu.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+
+template <int W>
+__global__ void __launch_bounds__(kRowWarps * 32) k_scatter_rows(const int* __restrict__ roff, int ntiles, int ntq,
+                                                                 const int32_t* __restrict__ pidx,
+                                                                 const int32_t* __restrict__ pcell,
+                                                                 const float* __restrict__ pf, int64_t npts,
+                                                                 const float2* __restrict__ f, float2* __restrict__ G,
+                                                                 int nrows, int gstride, float beta) {
+  static_assert(kRowTR + W - 1 <= kRowP, "window rows exceed the column pitch");
+  constexpr int COLS = kRowTQ + W - 1, ROWS = kRowTR + W - 1;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * kRowWarps + warp;
+  if (t >= ntiles) return;
+  const int s0 = roff[t * kRowTR + lane], s1 = roff[t * kRowTR + lane + 1];
+  int cnt = s1 - s0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt = max(cnt, __shfl_xor_sync(0xffffffffu, cnt, o));
+  if (cnt == 0) return;  // no points in the tile
+  float2* tw = reinterpret_cast<float2*>(smraw) + warp * COLS * kRowP;
+  for (int e = lane; e < COLS * kRowP; e += 32) tw[e] = make_float2(0.f, 0.f);
+  __syncwarp();
+  for (int k = 0; k < cnt; ++k) {
+    const int pt = s0 + k;
+    const bool on = pt < s1;
+    int lq = 0;
+    float wr[W], wq[W];
+    float2 fv = make_float2(0.f, 0.f);
+    if (on) {
+      lq = pcell[pt] >> 16;
+      Weights<float, W>::get(nullptr, pf, npts, pt, beta, wr, wq);
+      fv = f[pidx[pt]];
+    }
+    float2* col = tw + lq * kRowP + lane;
+#pragma unroll
+    for (int a = 0; a < W; ++a) {
+      if (on) {
+        const float vr = wr[a] * fv.x, vi = wr[a] * fv.y;
+        float2 x[W];
+#pragma unroll
+        for (int b = 0; b < W; ++b) x[b] = col[b * kRowP + a];
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+          x[b].x = fmaf(wq[b], vr, x[b].x);
+          x[b].y = fmaf(wq[b], vi, x[b].y);
+        }
+#pragma unroll
+        for (int b = 0; b < W; ++b) col[b * kRowP + a] = x[b];
+      }
+      __syncwarp();
+    }
+  }
+  // add the tile to the grid: lanes walk the rows of one column at a time (conflict-free reads)
+  const int tr = t / ntq, tq = t - tr * ntq;
+  const int row0 = tr * kRowTR, col0 = tq * kRowTQ;
+  for (int c = 0; c < COLS; ++c) {
+    const int gc = col0 + c;
+    for (int r = lane; r < ROWS; r += 32) {
+      const float2 v = tw[c * kRowP + r];
+      const int gr = row0 + r;
+      if ((v.x != 0.f || v.y != 0.f) && gr < nrows && gc < gstride) red_add_v2(G + (int64_t)gr * gstride + gc, v);
+    }
+  }
+}
+
 template <typename T, int W>
 void run_gather(Plan& p, void* f, cudaStream_t st) {
   using V = typename Cx<T>::V;
@@ -355,6 +441,16 @@ void run_gather(Plan& p, void* f, cudaStream_t st) {
 template <typename T, int W>
 void run_scatter(Plan& p, const void* f, cudaStream_t st) {
   using V = typename Cx<T>::V;
+  if constexpr (sizeof(T) == 4) {  // the FP32 form's tiles are 32 x 16 with per-row point ranges
+    const int ntiles = p.ntr * p.ntq;
+    const size_t smem = (size_t)kRowWarps * (kRowTQ + W - 1) * kRowP * sizeof(float2);
+    PSHT_CUDA_TRY(cudaFuncSetAttribute((const void*)k_scatter_rows<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+    k_scatter_rows<W><<<(ntiles + kRowWarps - 1) / kRowWarps, kRowWarps * 32, smem, st>>>(
+        p.d_roff, ntiles, p.ntq, p.d_pidx, p.d_pcell, p.d_pfrac, p.npts, (const float2*)f, (float2*)p.d_G, p.nrows,
+        p.gstride, (float)p.beta_es);
+    return;
+  }
   constexpr int NT = sizeof(T) == 8 ? 128 : 256;
   const size_t smem = (size_t)(NT / 32) * (p.TR + W - 1) * (p.TQ + W - 1) * sizeof(V);
   PSHT_CUDA_TRY(cudaFuncSetAttribute((const void*)k_scatter<T, W, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -468,6 +564,15 @@ void bin_points(Plan& p, const double* theta, const double* phi, cudaStream_t st
     p.allocs.push_back(p.d_titems);
     p.bytes += sizeof(TileItem) * items.size();
     PSHT_CUDA_TRY(cudaMemcpyAsync(p.d_titems, items.data(), sizeof(TileItem) * items.size(), cudaMemcpyHostToDevice, st));
+  }
+  if (p.prec == 32) {  // per (tile, base row) first sorted point, for the FP32 spreading kernel
+    PSHT_REQUIRE(p.TR == kRowTR && p.TQ == kRowTQ, PSHT_ECUDA, "internal: FP32 tile shape");
+    const int64_t nr = (int64_t)ntiles * p.TR + 1;
+    PSHT_CUDA_TRY(cudaMalloc((void**)&p.d_roff, sizeof(int) * nr));
+    p.allocs.push_back(p.d_roff);
+    p.bytes += sizeof(int) * nr;
+    k_row_offsets<<<(int)((nr + 255) / 256), 256, 0, st>>>(d_cnt, nr, p.TQ, p.d_roff);
+    PSHT_CUDA_TRY(cudaGetLastError());
   }
   PSHT_CUDA_TRY(cudaMemsetAsync(d_cur, 0, sizeof(int) * nkeys, st));
   if (n > 0)

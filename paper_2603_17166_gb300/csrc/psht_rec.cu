@@ -24,9 +24,15 @@
 //   ut_{l,m} = -sum_j e1_l(j) Ft_j[m],   ut_{l,-m} = -(-1)^(m-s) sum_j e2_l(j) Ft_j[-m]
 //   g~ = (ut_lm + (-1)^m conj ut_{l,-m})/2,   c~ = (ut_lm - (-1)^m conj ut_{l,-m})/(2i)
 //
-// Data movement: per CTA the recurrence table of its order m is streamed through shared memory
-// in chunks of 64 l by TMA bulk copies (cp.async.bulk, completion on an mbarrier, two stages in
-// flight); the a_lm column is prefetched through registers two chunks ahead.
+// Data movement: the recurrence table of an item's order m is streamed through shared memory by
+// TMA bulk copies (cp.async.bulk, completion on an mbarrier, every wait bounded).  The one-warp
+// kernels (k_rec_syn_w, k_rec_adj_w) copy chunks of 32 l with four stages in flight and prefetch
+// the a_lm one chunk ahead through registers; the FP64 block adjoint (k_rec_adj) copies chunks of
+// 64 l with two stages in flight.
+//
+// Kernels: k_rec_syn_w (synthesis, both forms; NS a_lm sets per pass, or mirror pairs of full-sky
+// plans), k_rec_adj_w (FP32 adjoint; NS sets, or mirror pairs), k_rec_adj (FP64 adjoint, one CTA per
+// order; mirror-pair orders in launches of their own), k_rec_table (the recurrence table).
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -387,50 +393,66 @@ __device__ __forceinline__ float2 summing(float2 e, int ka, int kb) {
   return make_float2(ka == 0 ? e.x : 0.f, kb == 0 ? e.y : 0.f);
 }
 
-// One quad (4 l steps) of the synthesis for the ring slots r < nr of this thread.
-// ACC: add the current column values to the sums; SEL: per column, only where k == 0.
-template <bool SPIN, int RPT, bool ACC, bool SEL, bool TB = false>
-__device__ __forceinline__ void syn_quad(Cols<double, RPT>& S, SynAcc<double, RPT>& A, const TabEntry<double>* st,
-                                         int i0, const Dbl4* sPQ, int nr) {
+// One quad (4 l steps) of the synthesis for the ring slots r < nr of this thread, for NS sets of
+// a_lm at once: the two Wigner columns of every (ring, l) are computed once and feed the sums of
+// every set (P, Q of set k at sPQ[k * pqs + i]).  ACC: add the current column values to the sums;
+// SEL: per column, only where k == 0.
+template <bool SPIN, int RPT, bool ACC, bool SEL, bool TB, int NS>
+__device__ __forceinline__ void syn_quad(Cols<double, RPT>& S, SynAcc<double, RPT> (&A)[NS],
+                                         const TabEntry<double>* st, int i0, const Dbl4* sPQ, int pqs, int nr) {
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int i = i0 + u;
     const Coef cf = get_coef(st, i);
-    const Dbl4 pq = sPQ[i];
+    Dbl4 pq[NS];
+    if (ACC) {
+#pragma unroll
+      for (int k = 0; k < NS; ++k) pq[k] = sPQ[k * pqs + i];
+    }
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
       if (r < nr) {
         if (ACC) {
           const double o1 = (!SEL || S.k1[r] == 0) ? S.e1[r] : 0.0;
-          A.a[r][0] = fma(pq.x, o1, A.a[r][0]);
-          A.a[r][1] = fma(pq.y, o1, A.a[r][1]);
           const double o2 = SPIN ? ((!SEL || S.k2[r] == 0) ? S.e2[r] : 0.0) : o1;
-          A.a[r][2] = fma(pq.z, o2, A.a[r][2]);
-          A.a[r][3] = fma(pq.w, o2, A.a[r][3]);
+#pragma unroll
+          for (int k = 0; k < NS; ++k) {
+            A[k].a[r][0] = fma(pq[k].x, o1, A[k].a[r][0]);
+            A[k].a[r][1] = fma(pq[k].y, o1, A[k].a[r][1]);
+            A[k].a[r][2] = fma(pq[k].z, o2, A[k].a[r][2]);
+            A[k].a[r][3] = fma(pq[k].w, o2, A[k].a[r][3]);
+          }
         }
         col_steps<SPIN, TB>(cf, S.oh[r], S.e1[r], S.d1[r], S.e2[r], S.d2[r]);
       }
     }
   }
 }
-template <bool SPIN, int RPT, bool ACC, bool SEL>
-__device__ __forceinline__ void syn_quad(Cols<float, RPT>& S, SynAcc<float, RPT>& A, const TabEntry<float>* st,
-                                         int i0, const PQ2* sPQ, int nr) {
+template <bool SPIN, int RPT, bool ACC, bool SEL, int NS>
+__device__ __forceinline__ void syn_quad(Cols<float, RPT>& S, SynAcc<float, RPT> (&A)[NS], const TabEntry<float>* st,
+                                         int i0, const PQ2* sPQ, int pqs, int nr) {
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int i = i0 + u;
     const TabEntry<float> cf = st[i];
-    const PQ2 pq = sPQ[i];
+    PQ2 pq[NS];
+    if (ACC) {
+#pragma unroll
+      for (int k = 0; k < NS; ++k) pq[k] = sPQ[k * pqs + i];
+    }
 #pragma unroll
     for (int p = 0; p < RPT / 2; ++p) {
       if (2 * p < nr) {  // the second slot of the last pair may be empty: zero values, zero sums
         if (ACC) {
           const float2 o1 = SEL ? summing(S.e1[p], S.k1[2 * p], S.k1[2 * p + 1]) : S.e1[p];
-          A.a[p][0] = __ffma2_rn(lo2(pq.p), o1, A.a[p][0]);
-          A.a[p][1] = __ffma2_rn(hi2(pq.p), o1, A.a[p][1]);
           const float2 o2 = SPIN ? (SEL ? summing(S.e2[p], S.k2[2 * p], S.k2[2 * p + 1]) : S.e2[p]) : o1;
-          A.a[p][2] = __ffma2_rn(lo2(pq.q), o2, A.a[p][2]);
-          A.a[p][3] = __ffma2_rn(hi2(pq.q), o2, A.a[p][3]);
+#pragma unroll
+          for (int k = 0; k < NS; ++k) {
+            A[k].a[p][0] = __ffma2_rn(lo2(pq[k].p), o1, A[k].a[p][0]);
+            A[k].a[p][1] = __ffma2_rn(hi2(pq[k].p), o1, A[k].a[p][1]);
+            A[k].a[p][2] = __ffma2_rn(lo2(pq[k].q), o2, A[k].a[p][2]);
+            A[k].a[p][3] = __ffma2_rn(hi2(pq[k].q), o2, A[k].a[p][3]);
+          }
         }
         step_pair<SPIN, RPT>(S, p, cf);
       }
@@ -440,16 +462,15 @@ __device__ __forceinline__ void syn_quad(Cols<float, RPT>& S, SynAcc<float, RPT>
 
 // FP64 warps whose rings all lie at least kThreeTermDeg from the pole take the three-term form
 // (tb); the FP32 form always takes Reinsch's
-template <bool SPIN, int RPT, bool ACC, bool SEL, typename T, typename PQV>
-__device__ __forceinline__ void syn_quad_d(bool tb, Cols<T, RPT>& S, SynAcc<T, RPT>& A, const TabEntry<T>* st, int i0,
-                                           const PQV* PQ, int nr) {
+template <bool SPIN, int RPT, bool ACC, bool SEL, int NS, typename T, typename PQV>
+__device__ __forceinline__ void syn_quad_d(bool tb, Cols<T, RPT>& S, SynAcc<T, RPT> (&A)[NS], const TabEntry<T>* st,
+                                           int i0, const PQV* PQ, int pqs, int nr) {
   if constexpr (sizeof(T) == 8) {
-    if (tb) {
-      syn_quad<SPIN, RPT, ACC, SEL, true>(S, A, st, i0, PQ, nr);
-      return;
-    }
+    if (tb) syn_quad<SPIN, RPT, ACC, SEL, true, NS>(S, A, st, i0, PQ, pqs, nr);
+    else syn_quad<SPIN, RPT, ACC, SEL, false, NS>(S, A, st, i0, PQ, pqs, nr);
+  } else {
+    syn_quad<SPIN, RPT, ACC, SEL, NS>(S, A, st, i0, PQ, pqs, nr);
   }
-  syn_quad<SPIN, RPT, ACC, SEL>(S, A, st, i0, PQ, nr);
 }
 
 // decide the form of a warp's FP64 columns after init_col and convert them: oh <- x = 1 - (1 - x),
@@ -534,170 +555,61 @@ __device__ __forceinline__ void init_col(Cols<T, RPT>& S, const RingDev* __restr
 }
 
 // ---------------------------------------------------------------------------------------------
-// synthesis: one CTA of NT threads per RecItem (order m, rings j0 .. j0+nj-1), RPT rings per thread.
-// Ring slots: warp w owns rings w*32*RPT + r*32 + lane (consecutive rings per warp, so the warp's
-// columns leave the dropped region together); slots r >= nr_w are empty for the whole warp.
-template <typename T, bool SPIN, int RPT, int NT>
-__global__ void __launch_bounds__(NT) k_rec_syn(const RecItem* __restrict__ items, const RingDev* __restrict__ rings,
-                                                const MSeed* __restrict__ mseed, const TabEntry<T>* __restrict__ tab,
-                                                const typename Cx<T>::V* __restrict__ g,
-                                                const typename Cx<T>::V* __restrict__ c, int lmax, int s, T msc,
-                                                typename Cx<T>::V* __restrict__ F, int Lpad, int* __restrict__ status) {
-  using V = typename Cx<T>::V;
-  const RecItem it = items[blockIdx.x];
-  const int m = it.m;
-  const MSeed sd = mseed[m];
-  __shared__ __align__(16) TabStage<T> stg[2];
-  using PQV = typename PQRec<T>::V;
-  __shared__ __align__(16) PQV sPQ[2][kCH];  // P and Q per l
-  __shared__ __align__(8) uint64_t bar[2];
-  __shared__ int sfail;
+// a_lm and ring-coefficient pointers of the NS sets of one synthesis launch (c may be null)
+template <typename T, int NS>
+struct SynSets {
+  const typename Cx<T>::V* g[NS];
+  const typename Cx<T>::V* c[NS];
+  typename Cx<T>::V* F[NS];
+};
 
-  // ring slots of 32 consecutive rings; the ceil(nj/32) slots are dealt to the warps in contiguous
-  // runs differing by at most one, so a warp's columns leave the dropped region together and the
-  // warps carry equal work; ring = wbase + r*32 + lane, slots r >= nr_w are empty for the warp
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int wbase, wcnt, nr_w;
-  slot_range(it.nj, NT / 32, warp, wbase, wcnt, nr_w);
-  Cols<T, RPT> S;
-  SynAcc<T, RPT> A;
-  A.zero();
-#pragma unroll
-  for (int r = 0; r < RPT; ++r) init_col<T, SPIN, RPT>(S, rings, sd, it.j0 + wbase, r * 32 + lane, wcnt, r);
-  const int64_t base = alm_base(lmax, m);
-  const bool rf = it.refl != 0;
-  const bool m0 = (m == 0);
-  const int nchunk = (lmax - sd.l0 + kCH) / kCH;
-
-  // prologue: table chunks 0 and 1 by TMA, a_lm chunks 0 and 1 into shared memory, chunk 2 into
-  // registers
-  if (threadIdx.x == 0) {
-    sfail = 0;
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    issue_chunk<T>(stg[0], &bar[0], tab, base + sd.l0);
-    if (nchunk > 1) issue_chunk<T>(stg[1], &bar[1], tab, base + sd.l0 + kCH);
-  }
-  for (int cc = 0; cc < 2 && cc < nchunk; ++cc) {
-    for (int i = threadIdx.x; i < kCH; i += NT) {
-      const int l = sd.l0 + cc * kCH + i;
-      V P = mk((T)0, (T)0), Q = mk((T)0, (T)0);
-      if (l <= lmax) make_pq<V, T>(g[base + l], c ? c[base + l] : mk((T)0, (T)0), m0, rf, l + m, msc, P, Q);
-      sPQ[cc][i] = pq_rec(P, Q);
-    }
-  }
-  V pg = mk((T)0, (T)0), pc = mk((T)0, (T)0);  // a_lm two chunks ahead
-  if (threadIdx.x < kCH) {
-    const int l = sd.l0 + 2 * kCH + threadIdx.x;
-    if (l <= lmax) {
-      pg = g[base + l];
-      if (c) pc = c[base + l];
-    }
-  }
-  __syncthreads();
-
-  for (int ch = 0; ch < nchunk; ++ch) {
-    const int sidx = ch & 1;
-    const int lc = sd.l0 + ch * kCH;
-    if (!mbar_wait(&bar[sidx], (ch >> 1) & 1)) {
-      atomicExch(status, 1);
-      sfail = 1;
-    }
-    const int nq = (min(kCH, lmax - lc + 1) + 3) >> 2;
-    if (nr_w > 0 && !sfail) {
-      const TabEntry<T>* st = stg[sidx].v;
-      const PQV* PQ = sPQ[sidx];
-      for (int q = 0; q < nq; ++q) {
-        bool fast, skip;
-        classify<T, SPIN, RPT>(S, nr_w, fast, skip);
-        if (fast) {
-          if (nr_w == RPT) syn_quad<SPIN, RPT, true, false>(S, A, st, 4 * q, PQ, RPT);
-          else syn_quad<SPIN, RPT, true, false>(S, A, st, 4 * q, PQ, nr_w);
-        } else {
-          if (skip) syn_quad<SPIN, RPT, false, false>(S, A, st, 4 * q, PQ, nr_w);
-          else syn_quad<SPIN, RPT, true, true>(S, A, st, 4 * q, PQ, nr_w);
-          rescale_all<T, SPIN, RPT>(S, nr_w);
-        }
-      }
-    }
-    __syncthreads();  // everyone is done with stage sidx
-    if (sfail) {
-      if (threadIdx.x == 0) mbar_wait(&bar[sidx ^ 1], ((ch + 1) >> 1) & 1);  // drain the other stage
-      return;
-    }
-    if (ch + 2 < nchunk) {
-      if (threadIdx.x == 0) issue_chunk<T>(stg[sidx], &bar[sidx], tab, base + lc + 2 * kCH);
-      if (threadIdx.x < kCH) {
-        const int l = lc + 2 * kCH + threadIdx.x;
-        V Pn = mk((T)0, (T)0), Qn = mk((T)0, (T)0);
-        if (l <= lmax) make_pq<V, T>(pg, pc, m0, rf, l + m, msc, Pn, Qn);
-        sPQ[sidx][threadIdx.x] = pq_rec(Pn, Qn);
-        pg = pc = mk((T)0, (T)0);
-        const int l3 = l + kCH;
-        if (l3 <= lmax) {
-          pg = g[base + l3];
-          if (c) pc = c[base + l3];
-        }
-      }
-    }
-  }
-  const T sgn_s = (s & 1) ? (T)1 : (T)-1;  // -(-1)^s
-#pragma unroll
-  for (int r = 0; r < RPT; ++r) {
-    const int jj = r * 32 + lane;
-    if (jj < wcnt) {
-      const int j = it.j0 + wbase + jj;
-      // direct rings: F[m] <- column 1, F[-m] <- column 2; reflected rings: swapped
-      const T a0 = A.get(r, 0), a1 = A.get(r, 1), a2 = A.get(r, 2), a3 = A.get(r, 3);
-      const V fpos = rf ? mk(-a2, -a3) : mk(-a0, -a1);
-      const V fneg = rf ? mk(sgn_s * a0, sgn_s * a1) : mk(sgn_s * a2, sgn_s * a3);
-      F[(int64_t)col_of(m) * Lpad + j] = fpos;
-      if (!m0) F[(int64_t)col_of(-m) * Lpad + j] = fneg;
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------------------------
 // synthesis, one warp per CTA: the CTA's RecItem (order m, at most 32 RPT rings) is processed by a
 // single warp, so there is no block barrier and a warp never waits for another warp's rings.  The
 // warp stages its own table chunks of CH l (bulk copies issued by lane 0, NST stages in flight,
-// completion on mbarriers) and its own P/Q values (lane i computes l = lc + i, i < CH, from a_lm
-// loaded one chunk ahead).  Ring slots: ring = r*32 + lane; slots r >= ceil(nj/32) are empty.
-template <typename T, bool SPIN, int RPT, int CH, int NST>
+// completion on mbarriers) and its own P/Q values of every set (lane i computes l = lc + i, i < CH,
+// from a_lm loaded one chunk ahead).  Ring slots: ring = r*32 + lane; slots r >= ceil(nj/32) are
+// empty.  NS sets of a_lm share one pass over the table and one evaluation of the Wigner columns.
+//
+// MIR (mirror pairs, full-sky plans, NS = 1): the item's rings j (all at b <= pi/2) stand for the
+// pairs (j, jm - j): ring jm - j lies at pi - b, where d^l_{m,-s}(pi - b) = (-1)^(l+m) d^l_{m,s}(b),
+// so one evaluation of the two columns at b serves both.  The pair runs as two internal sets of
+// the same a_lm: set 0 the direct ring, set 1 the mirror ring with the reflected combination of P
+// and Q, written to ring jm - j.
+template <typename T, bool SPIN, int RPT, int CH, int NST, int NS, bool MIR>
 __global__ void __launch_bounds__(32) k_rec_syn_w(const RecItem* __restrict__ items, const RingDev* __restrict__ rings,
                                                   const MSeed* __restrict__ mseed, const TabEntry<T>* __restrict__ tab,
-                                                  const typename Cx<T>::V* __restrict__ g,
-                                                  const typename Cx<T>::V* __restrict__ c, int lmax, int s, T msc,
-                                                  typename Cx<T>::V* __restrict__ F, int Lpad,
-                                                  int* __restrict__ status, double omx_tb) {
+                                                  const SynSets<T, NS> sets, int lmax, int s, T msc, int Lpad,
+                                                  int* __restrict__ status, double omx_tb, int jm) {
   static_assert(CH == 32, "one l per lane and chunk");
+  static_assert(!MIR || NS == 1, "mirror pairs take one a_lm set");
+  constexpr int NI = MIR ? 2 : NS;  // internal sets: the a_lm sets, or a ring and its mirror
   using V = typename Cx<T>::V;
   using PQV = typename PQRec<T>::V;
   const RecItem it = items[blockIdx.x];
   const int m = it.m;
   const MSeed sd = mseed[m];
   __shared__ __align__(16) TabStage<T, CH> stg[NST];
-  __shared__ __align__(16) PQV sPQ[NST][CH];
+  __shared__ __align__(16) PQV sPQ[NI][NST][CH];
   __shared__ __align__(8) uint64_t bar[NST];
+  constexpr int pqs = NST * CH;  // set stride of sPQ
   const int lane = threadIdx.x;
   const int nr_w = (it.nj + 31) >> 5;
   Cols<T, RPT> S;
-  SynAcc<T, RPT> A;
-  A.zero();
+  SynAcc<T, RPT> A[NI];
+#pragma unroll
+  for (int k = 0; k < NI; ++k) A[k].zero();
 #pragma unroll
   for (int r = 0; r < RPT; ++r) init_col<T, SPIN, RPT>(S, rings, sd, it.j0, r * 32 + lane, it.nj, r);
   // slots r with r * 32 + lane < nj hold rings
   const bool tb = three_term_setup<T, RPT>(S, lane < it.nj ? (it.nj - lane + 31) / 32 : 0, omx_tb);
   const int64_t base = alm_base(lmax, m);
-  const bool rf = it.refl != 0;
+  const bool rf = !MIR && it.refl != 0;
   const bool m0 = (m == 0);
   const int nchunk = (lmax - sd.l0 + CH) / CH;
   const V z = mk((T)0, (T)0);
-
+  // internal set q: its a_lm set and whether its rings take the reflected combination
+  const auto set_of = [&](int q) { return MIR ? 0 : q; };
+  const auto refl_of = [&](int q) { return MIR ? (q == 1) : rf; };
   if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < NST; ++k) mbar_init(&bar[k], 1);
@@ -708,16 +620,25 @@ __global__ void __launch_bounds__(32) k_rec_syn_w(const RecItem* __restrict__ it
     for (int k = 0; k < NST && k < nchunk; ++k) issue_chunk<T, CH>(stg[k], &bar[k], tab, base + sd.l0 + k * CH);
   for (int k = 0; k < NST && k < nchunk; ++k) {
     const int l = sd.l0 + k * CH + lane;
-    V P = z, Q = z;
-    if (l <= lmax) make_pq<V, T>(g[base + l], c ? c[base + l] : z, m0, rf, l + m, msc, P, Q);
-    sPQ[k][lane] = pq_rec(P, Q);
+#pragma unroll
+    for (int q = 0; q < NI; ++q) {
+      V P = z, Q = z;
+      const int qs = set_of(q);
+      if (l <= lmax)
+        make_pq<V, T>(sets.g[qs][base + l], sets.c[qs] ? sets.c[qs][base + l] : z, m0, refl_of(q), l + m, msc, P, Q);
+      sPQ[q][k][lane] = pq_rec(P, Q);
+    }
   }
-  V pg = z, pc = z;  // a_lm of chunk NST (the next to be staged)
+  V pg[NS], pc[NS];  // a_lm of chunk NST (the next to be staged)
   {
     const int l = sd.l0 + NST * CH + lane;
-    if (l <= lmax) {
-      pg = g[base + l];
-      if (c) pc = c[base + l];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+      pg[q] = pc[q] = z;
+      if (l <= lmax) {
+        pg[q] = sets.g[q][base + l];
+        if (sets.c[q]) pc[q] = sets.c[q][base + l];
+      }
     }
   }
   __syncwarp();
@@ -737,16 +658,16 @@ __global__ void __launch_bounds__(32) k_rec_syn_w(const RecItem* __restrict__ it
     const int nq = (min(CH, lmax - lc + 1) + 3) >> 2;
     if (nr_w > 0) {
       const TabEntry<T>* st = stg[sidx].v;
-      const PQV* PQ = sPQ[sidx];
+      const PQV* PQ = &sPQ[0][sidx][0];
       for (int q = 0; q < nq; ++q) {
         bool fast, skip;
         classify<T, SPIN, RPT>(S, nr_w, fast, skip);
         if (fast) {
-          if (nr_w >= RPT) syn_quad_d<SPIN, RPT, true, false>(tb, S, A, st, 4 * q, PQ, RPT);
-          else syn_quad_d<SPIN, RPT, true, false>(tb, S, A, st, 4 * q, PQ, nr_w);
+          if (nr_w >= RPT) syn_quad_d<SPIN, RPT, true, false, NI>(tb, S, A, st, 4 * q, PQ, pqs, RPT);
+          else syn_quad_d<SPIN, RPT, true, false, NI>(tb, S, A, st, 4 * q, PQ, pqs, nr_w);
         } else {
-          if (skip) syn_quad_d<SPIN, RPT, false, false>(tb, S, A, st, 4 * q, PQ, nr_w);
-          else syn_quad_d<SPIN, RPT, true, true>(tb, S, A, st, 4 * q, PQ, nr_w);
+          if (skip) syn_quad_d<SPIN, RPT, false, false, NI>(tb, S, A, st, 4 * q, PQ, pqs, nr_w);
+          else syn_quad_d<SPIN, RPT, true, true, NI>(tb, S, A, st, 4 * q, PQ, pqs, nr_w);
           rescale_all<T, SPIN, RPT>(S, nr_w);
         }
       }
@@ -755,14 +676,21 @@ __global__ void __launch_bounds__(32) k_rec_syn_w(const RecItem* __restrict__ it
     if (ch + NST < nchunk) {
       if (lane == 0) issue_chunk<T, CH>(stg[sidx], &bar[sidx], tab, base + lc + NST * CH);
       const int l = lc + NST * CH + lane;
-      V P = z, Q = z;
-      if (l <= lmax) make_pq<V, T>(pg, pc, m0, rf, l + m, msc, P, Q);
-      sPQ[sidx][lane] = pq_rec(P, Q);
-      pg = pc = z;
       const int l2 = l + CH;
-      if (l2 <= lmax) {
-        pg = g[base + l2];
-        if (c) pc = c[base + l2];
+#pragma unroll
+      for (int q = 0; q < NI; ++q) {
+        V P = z, Q = z;
+        const int qs = set_of(q);
+        if (l <= lmax) make_pq<V, T>(pg[qs], pc[qs], m0, refl_of(q), l + m, msc, P, Q);
+        sPQ[q][sidx][lane] = pq_rec(P, Q);
+      }
+#pragma unroll
+      for (int q = 0; q < NS; ++q) {
+        pg[q] = pc[q] = z;
+        if (l2 <= lmax) {
+          pg[q] = sets.g[q][base + l2];
+          if (sets.c[q]) pc[q] = sets.c[q][base + l2];
+        }
       }
     }
     __syncwarp();
@@ -773,11 +701,18 @@ __global__ void __launch_bounds__(32) k_rec_syn_w(const RecItem* __restrict__ it
     const int jj = r * 32 + lane;
     if (jj < it.nj) {
       const int j = it.j0 + jj;
-      const T a0 = A.get(r, 0), a1 = A.get(r, 1), a2 = A.get(r, 2), a3 = A.get(r, 3);
-      const V fpos = rf ? mk(-a2, -a3) : mk(-a0, -a1);
-      const V fneg = rf ? mk(sgn_s * a0, sgn_s * a1) : mk(sgn_s * a2, sgn_s * a3);
-      F[(int64_t)col_of(m) * Lpad + j] = fpos;
-      if (!m0) F[(int64_t)col_of(-m) * Lpad + j] = fneg;
+#pragma unroll
+      for (int q = 0; q < NI; ++q) {
+        if (MIR && q == 1 && jm - j == j) continue;  // the equator ring is its own mirror
+        const T a0 = A[q].get(r, 0), a1 = A[q].get(r, 1), a2 = A[q].get(r, 2), a3 = A[q].get(r, 3);
+        const bool rq = refl_of(q);
+        const V fpos = rq ? mk(-a2, -a3) : mk(-a0, -a1);
+        const V fneg = rq ? mk(sgn_s * a0, sgn_s * a1) : mk(sgn_s * a2, sgn_s * a3);
+        V* Fq = sets.F[set_of(q)];
+        const int jq = (MIR && q == 1) ? jm - j : j;
+        Fq[(int64_t)col_of(m) * Lpad + jq] = fpos;
+        if (!m0) Fq[(int64_t)col_of(-m) * Lpad + jq] = fneg;
+      }
     }
   }
 }
@@ -824,6 +759,39 @@ __device__ __forceinline__ void adj_quad_sums(Cols<double, RPT>& S, const AdjIn<
     v[4 * u + 1] = p1;
     v[4 * u + 2] = p2;
     v[4 * u + 3] = p3;
+  }
+}
+// mirror pairs (full-sky plans): sums of the direct rings against f plus (-1)^(l+m) times the
+// column-swapped sums of their mirror rings against fm (reflected convention), lpm = l0 of the quad + m
+template <bool SPIN, int RPT, bool SEL, bool TB>
+__device__ __forceinline__ void adj_quad_sums_mir(Cols<double, RPT>& S, const AdjIn<double, RPT>& f,
+                                                  const AdjIn<double, RPT>& fm, const TabEntry<double>* st, int i0,
+                                                  int nr, int lpm, double (&v)[16]) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const Coef cf = get_coef(st, i0 + u);
+    double d0 = 0, d1 = 0, d2 = 0, d3 = 0, e0 = 0, e1 = 0, e2 = 0, e3 = 0;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      if (r < nr) {
+        const double o1 = (!SEL || S.k1[r] == 0) ? S.e1[r] : 0.0;
+        const double o2 = SPIN ? ((!SEL || S.k2[r] == 0) ? S.e2[r] : 0.0) : o1;
+        d0 = fma(o1, f.f1[r].x, d0);
+        d1 = fma(o1, f.f1[r].y, d1);
+        d2 = fma(o2, f.f2[r].x, d2);
+        d3 = fma(o2, f.f2[r].y, d3);
+        e0 = fma(o1, fm.f1[r].x, e0);
+        e1 = fma(o1, fm.f1[r].y, e1);
+        e2 = fma(o2, fm.f2[r].x, e2);
+        e3 = fma(o2, fm.f2[r].y, e3);
+        col_steps<SPIN, TB>(cf, S.oh[r], S.e1[r], S.d1[r], S.e2[r], S.d2[r]);
+      }
+    }
+    const double sl = ((lpm + u) & 1) ? -1.0 : 1.0;
+    v[4 * u + 0] = fma(sl, e2, d0);
+    v[4 * u + 1] = fma(sl, e3, d1);
+    v[4 * u + 2] = fma(sl, e0, d2);
+    v[4 * u + 3] = fma(sl, e1, d3);
   }
 }
 template <bool SPIN, int RPT, bool SEL>
@@ -885,17 +853,23 @@ __device__ __forceinline__ void adj_quad_steps_d(Cols<T, RPT>& S, const TabEntry
   else adj_quad_steps<SPIN, RPT>(S, st, i0, nr);
 }
 
-template <typename T, bool SPIN, int RPT, int NT>
+// MIR: orders whose reflected rings are the mirrors jm - j of their direct rings (mmode[m] = 1,
+// full-sky plans) run in the direct part's launches with both rings of each pair per slot; the
+// launches of the other mode leave those orders alone (the first launch writes their zeros).
+template <typename T, bool SPIN, int RPT, int NT, bool MIR>
 __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ rings, const MSeed* __restrict__ mseed,
                                                 const int2* __restrict__ mrange, const TabEntry<T>* __restrict__ tab,
                                                 const typename Cx<T>::V* __restrict__ Ft, int Lpad,
                                                 int lmax, int s, int M, int refl, int accumulate, T msc,
                                                 typename Cx<T>::V* __restrict__ gt, typename Cx<T>::V* __restrict__ ct,
-                                                int* __restrict__ status, int chunk, double omx_tb) {
+                                                int* __restrict__ status, int chunk, double omx_tb,
+                                                const int* __restrict__ mmode, int jm) {
   using V = typename Cx<T>::V;
   const int m = blockIdx.x;
   const int64_t base = alm_base(lmax, m);
-  if (m > M) {  // beyond the polar-optimisation cutoff on every ring: transpose of a zero block
+  if (m > M || (mmode && (m <= M) && ((mmode[m] != 0) != MIR))) {
+    // beyond the polar-optimisation cutoff on every ring (transpose of a zero block), or an order
+    // of the other mode: the first launch writes zeros, the others add nothing
     if (accumulate) return;
     for (int l = m + threadIdx.x; l <= lmax; l += blockDim.x) {
       gt[base + l] = mk((T)0, (T)0);
@@ -931,12 +905,22 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
   slot_range(nact, NW, warp, wbase, wcnt, nr_w);
 
   Cols<T, RPT> S;
-  AdjIn<T, RPT> fin;  // ring values paired with column 1 / column 2
+  AdjIn<T, RPT> fin;               // ring values paired with column 1 / column 2
+  AdjIn<T, MIR ? RPT : 1> fmir;    // the mirror rings' values, reflected convention (MIR only)
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
     const int jj = r * 32 + lane;
     init_col<T, SPIN, RPT>(S, rings, sd, rr.x + wbase, jj, wcnt, r);
     fin.set(r, mk((T)0, (T)0), mk((T)0, (T)0));
+    if constexpr (MIR) {
+      fmir.set(r, mk((T)0, (T)0), mk((T)0, (T)0));
+      const int j = rr.x + wbase + jj;
+      if (jj < wcnt && jm - j != j) {  // the equator ring is its own mirror
+        const V fp = Ft[(int64_t)col_of(m) * Lpad + jm - j];
+        const V fm = m0 ? mk((T)0, (T)0) : Ft[(int64_t)col_of(-m) * Lpad + jm - j];
+        fmir.set(r, fm, fp);
+      }
+    }
     if (jj < wcnt) {
       const int j = rr.x + wbase + jj;
       const V fp = Ft[(int64_t)col_of(m) * Lpad + j];
@@ -982,7 +966,17 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
           rescale_all<T, SPIN, RPT>(S, nr_w);
         } else {
           T v[16];
-          if (fast) {
+          if constexpr (MIR) {
+            const int lpm = lc + 4 * q + m;
+            if (fast) {
+              if (tb) adj_quad_sums_mir<SPIN, RPT, false, true>(S, fin, fmir, st, 4 * q, nr_w, lpm, v);
+              else adj_quad_sums_mir<SPIN, RPT, false, false>(S, fin, fmir, st, 4 * q, nr_w, lpm, v);
+            } else {
+              if (tb) adj_quad_sums_mir<SPIN, RPT, true, true>(S, fin, fmir, st, 4 * q, nr_w, lpm, v);
+              else adj_quad_sums_mir<SPIN, RPT, true, false>(S, fin, fmir, st, 4 * q, nr_w, lpm, v);
+              rescale_all<T, SPIN, RPT>(S, nr_w);
+            }
+          } else if (fast) {
             if (tb) {
               if (nr_w == RPT) adj_quad_sums_d<SPIN, RPT, false, true>(S, fin, st, 4 * q, RPT, v);
               else adj_quad_sums_d<SPIN, RPT, false, true>(S, fin, st, 4 * q, nr_w, v);
@@ -1060,46 +1054,177 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
 
 // ---------------------------------------------------------------------------------------------
 // adjoint, one warp per CTA (FP32 form): the warp's item is (m, up to 32 RPT rings), with the
-// table staged as in k_rec_syn_w.  Per quad of l the warp's 16 partial sums are reduced across
-// the lanes (reduce_scatter16) and written to the item's slice of the partial-sum array, already
-// in the direct-ring convention (reflected rings: columns swapped, signed by (-1)^(l+m)); the
-// items of one m are then summed and projected by k_adj_reduce.  No block barrier, no atomics,
-// and the result does not depend on scheduling.
-template <typename T, bool SPIN, int RPT, int CH, int NST>
-__global__ void __launch_bounds__(32) k_rec_adj_w(const AdjItem* __restrict__ items, const RingDev* __restrict__ rings,
-                                                  const MSeed* __restrict__ mseed, const TabEntry<T>* __restrict__ tab,
-                                                  const typename Cx<T>::V* __restrict__ Ft, int Lpad, int lmax,
-                                                  T* __restrict__ part, int* __restrict__ status) {
-  static_assert(CH % 4 == 0, "whole quads per chunk");
-  using V = typename Cx<T>::V;
+// table staged as in k_rec_syn_w.  Per l each lane adds up its own rings' 4 products (Re, Im of
+// the two columns) and stores them as one float4 row entry of a per-warp 8 x 32 shared array;
+// after every 8 l (two quads) the warp sums the array's columns, lane i taking row i & 7 and a
+// quarter of the columns (read swizzled so that no two lanes of an 8-lane phase share a bank
+// group), then two shuffles combine the quarters: ~9 instructions per l and lane against ~20 for
+// a shuffle reduce-scatter of the same sums.  The row totals (already in the direct-ring
+// convention: reflected rings swap the column pairs and carry (-1)^(l+m)) then either
+//   * go straight through the projection of the adjoint synthesis general formula to (g~, c~)
+//     when the order m has a single item, or
+//   * are added by one vector reduction (red.global.add.v4.f32) into the plan's accumulator of 4
+//     floats per (l, m); the last item of m to finish (a per-m arrival counter) projects the
+//     accumulated sums, writes (g~, c~) and clears the accumulator and the counter for the next
+//     call.  The summation order of the reductions is not fixed, so for such orders the result
+//     may differ between calls in the last bits.
+// No block barrier and no waiting on other warps.  The projection:
+//   ut_{l,m} = -Qp, ut_{l,-m} = -(-1)^(m-s) Qm, g~ = (ut_lm + (-1)^m conj ut_{l,-m})/2,
+//   c~ = (ut_lm - (-1)^m conj ut_{l,-m})/(2i), zero below l0; msc weights m > 0 (1, or 2 in the
+//   packed-gradient form).
+__device__ __forceinline__ void adj_project(float4 q, bool m0, float sg, float sm, float msc, float2& gv,
+                                            float2& cv) {
+  const float ar = -q.x, ai = -q.y;
+  const float br = sg * q.z, bi = sg * q.w;
+  if (m0) {
+    gv = make_float2(ar, 0.f);
+    cv = make_float2(ai, 0.f);
+  } else {
+    const float wr = sm * br, wi = -sm * bi;  // (-1)^m conj(ut_{l,-m})
+    gv = make_float2(msc * 0.5f * (ar + wr), msc * 0.5f * (ai + wi));
+    cv = make_float2(msc * 0.5f * (ai - wi), msc * -0.5f * (ar - wr));
+  }
+}
+__device__ __forceinline__ void red_add_v4(float4* addr, float4 v) {
+  asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(v.x), "f"(v.y),
+               "f"(v.z), "f"(v.w)
+               : "memory");
+}
+
+// one quad (4 l steps) of the adjoint for the ring pairs of this thread and NS sets: per l the
+// lane's sums over its rings (Re, Im against column 1; Re, Im against column 2) of set k go to row
+// (row0 + u) of red[k]; the Wigner columns are evaluated once for all sets
+template <bool SPIN, int RPT, bool SEL, int NS>
+__device__ __forceinline__ void adj_quad_rows(Cols<float, RPT>& S, const AdjIn<float, RPT> (&f)[NS],
+                                              const TabEntry<float>* st, int i0, int nr, float4 (*red)[8][32],
+                                              int row0, int lane) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const TabEntry<float> cf = st[i0 + u];
+    float2 p[NS][4];  // (even slot, odd slot) partial sums of each set
+#pragma unroll
+    for (int k = 0; k < NS; ++k) p[k][0] = p[k][1] = p[k][2] = p[k][3] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < RPT / 2; ++q) {
+      if (2 * q < nr) {
+        const float2 o1 = SEL ? summing(S.e1[q], S.k1[2 * q], S.k1[2 * q + 1]) : S.e1[q];
+        const float2 o2 = SPIN ? (SEL ? summing(S.e2[q], S.k2[2 * q], S.k2[2 * q + 1]) : S.e2[q]) : o1;
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+          p[k][0] = __ffma2_rn(o1, f[k].x1[q], p[k][0]);
+          p[k][1] = __ffma2_rn(o1, f[k].y1[q], p[k][1]);
+          p[k][2] = __ffma2_rn(o2, f[k].x2[q], p[k][2]);
+          p[k][3] = __ffma2_rn(o2, f[k].y2[q], p[k][3]);
+        }
+        step_pair<SPIN, RPT>(S, q, cf);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NS; ++k)
+      red[k][row0 + u][lane] =
+          make_float4(p[k][0].x + p[k][0].y, p[k][1].x + p[k][1].y, p[k][2].x + p[k][2].y, p[k][3].x + p[k][3].y);
+  }
+}
+
+// the same for mirror pairs (one set): the lane's direct rings give sums against F~_j (fd), their
+// mirrors jm - j sums against F~_{jm-j} taken in the reflected convention (fm); per l the mirror
+// part joins as (-1)^(l+m) times its column-swapped sums, so one row holds both
+template <bool SPIN, int RPT, bool SEL>
+__device__ __forceinline__ void adj_quad_rows_mir(Cols<float, RPT>& S, const AdjIn<float, RPT>& fd,
+                                                  const AdjIn<float, RPT>& fm, const TabEntry<float>* st, int i0,
+                                                  int nr, float4 (*red)[32], int row0, int lane, int lpm) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const TabEntry<float> cf = st[i0 + u];
+    float2 d[4], e[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) d[k] = e[k] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < RPT / 2; ++q) {
+      if (2 * q < nr) {
+        const float2 o1 = SEL ? summing(S.e1[q], S.k1[2 * q], S.k1[2 * q + 1]) : S.e1[q];
+        const float2 o2 = SPIN ? (SEL ? summing(S.e2[q], S.k2[2 * q], S.k2[2 * q + 1]) : S.e2[q]) : o1;
+        d[0] = __ffma2_rn(o1, fd.x1[q], d[0]);
+        d[1] = __ffma2_rn(o1, fd.y1[q], d[1]);
+        d[2] = __ffma2_rn(o2, fd.x2[q], d[2]);
+        d[3] = __ffma2_rn(o2, fd.y2[q], d[3]);
+        e[0] = __ffma2_rn(o1, fm.x1[q], e[0]);
+        e[1] = __ffma2_rn(o1, fm.y1[q], e[1]);
+        e[2] = __ffma2_rn(o2, fm.x2[q], e[2]);
+        e[3] = __ffma2_rn(o2, fm.y2[q], e[3]);
+        step_pair<SPIN, RPT>(S, q, cf);
+      }
+    }
+    const float sl = ((lpm + u) & 1) ? -1.f : 1.f;  // (-1)^(l+m)
+    red[row0 + u][lane] = make_float4(fmaf(sl, e[2].x + e[2].y, d[0].x + d[0].y),
+                                      fmaf(sl, e[3].x + e[3].y, d[1].x + d[1].y),
+                                      fmaf(sl, e[0].x + e[0].y, d[2].x + d[2].y),
+                                      fmaf(sl, e[1].x + e[1].y, d[3].x + d[3].y));
+  }
+}
+
+// ring coefficients in, accumulators and outputs of the NS sets of one adjoint launch (ct may be null)
+template <int NS>
+struct AdjSets {
+  const float2* Ft[NS];
+  float4* acc[NS];
+  float2* gt[NS];
+  float2* ct[NS];
+};
+
+// MIR (mirror pairs of full-sky plans, NS = 1): the item's rings j stand for the pairs (j, jm - j),
+// whose two columns are shared (d^l_{m,-s}(pi - b) = (-1)^(l+m) d^l_{m,s}(b)); see adj_quad_rows_mir.
+template <bool SPIN, int RPT, int CH, int NST, int NS, bool MIR>
+__global__ void __launch_bounds__(32, NS == 1 ? (MIR ? 16 : (RPT >= 8 ? 16 : 20)) : (NS == 2 ? 12 : 8))
+    k_rec_adj_w(const AdjItem* __restrict__ items, const RingDev* __restrict__ rings, const MSeed* __restrict__ mseed,
+                const TabEntry<float>* __restrict__ tab, const AdjSets<NS> sets, int Lpad, int lmax, int s, float msc,
+                int* __restrict__ cnt, int* __restrict__ status, int jm) {
+  static_assert(CH % 8 == 0, "whole flushes of 8 l per chunk");
+  static_assert(!MIR || NS == 1, "mirror pairs take one set");
   const AdjItem it = items[blockIdx.x];
   const int m = it.m;
   const MSeed sd = mseed[m];
-  __shared__ __align__(16) TabStage<T, CH> stg[NST];
+  __shared__ __align__(16) TabStage<float, CH> stg[NST];
+  __shared__ __align__(16) float4 red[NS][8][32];
   __shared__ __align__(8) uint64_t bar[NST];
   const int lane = threadIdx.x;
   const int nr_w = (it.nj + 31) >> 5;
   const bool m0 = (m == 0);
-  const bool rf = it.refl != 0;
-  const V z = mk((T)0, (T)0);
-  Cols<T, RPT> S;
-  AdjIn<T, RPT> fin;
+  const bool rf = !MIR && it.refl != 0;
+  const bool direct = it.nitems == 1;
+  const float2 z = make_float2(0.f, 0.f);
+  Cols<float, RPT> S;
+  AdjIn<float, RPT> fin[NS];
+  AdjIn<float, MIR ? RPT : 2> fmir;  // mirror rings' inputs in the reflected convention (MIR only)
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
     const int jj = r * 32 + lane;
-    init_col<T, SPIN, RPT>(S, rings, sd, it.j0, jj, it.nj, r);
-    fin.set(r, z, z);
-    if (jj < it.nj) {
+    init_col<float, SPIN, RPT>(S, rings, sd, it.j0, jj, it.nj, r);
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      fin[k].set(r, z, z);
+      if (jj < it.nj) {
+        const int j = it.j0 + jj;
+        const float2 fp = sets.Ft[k][(int64_t)col_of(m) * Lpad + j];
+        const float2 fm = m0 ? z : sets.Ft[k][(int64_t)col_of(-m) * Lpad + j];
+        fin[k].set(r, rf ? fm : fp, rf ? fp : fm);
+      }
+    }
+    if constexpr (MIR) {
+      fmir.set(r, z, z);
       const int j = it.j0 + jj;
-      const V fp = Ft[(int64_t)col_of(m) * Lpad + j];
-      const V fm = m0 ? z : Ft[(int64_t)col_of(-m) * Lpad + j];
-      fin.set(r, rf ? fm : fp, rf ? fp : fm);
+      if (jj < it.nj && jm - j != j) {  // the equator ring is its own mirror
+        const float2 fp = sets.Ft[0][(int64_t)col_of(m) * Lpad + jm - j];
+        const float2 fm = m0 ? z : sets.Ft[0][(int64_t)col_of(-m) * Lpad + jm - j];
+        fmir.set(r, fm, fp);
+      }
     }
   }
   const int64_t base = alm_base(lmax, m);
   const int nl = lmax - sd.l0 + 1;
   const int nchunk = (nl + CH - 1) / CH;
-  T* out = part + it.off;
+  const float sg = (((m - s) & 1) ? 1.f : -1.f);  // -(-1)^(m-s)
+  const float sm = (m & 1) ? -1.f : 1.f;          // (-1)^m
   if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < NST; ++k) mbar_init(&bar[k], 1);
@@ -1107,9 +1232,11 @@ __global__ void __launch_bounds__(32) k_rec_adj_w(const AdjItem* __restrict__ it
   }
   __syncwarp();
   if (lane == 0)
-    for (int k = 0; k < NST && k < nchunk; ++k) issue_chunk<T, CH>(stg[k], &bar[k], tab, base + sd.l0 + k * CH);
+    for (int k = 0; k < NST && k < nchunk; ++k) issue_chunk<float, CH>(stg[k], &bar[k], tab, base + sd.l0 + k * CH);
   __syncwarp();
+  const int rr = lane & 7, cg = lane >> 3;  // flush: row and column quarter of this lane
 
+  bool failed = false;
   for (int ch = 0; ch < nchunk; ++ch) {
     const int sidx = ch % NST;
     const bool ok = mbar_wait(&bar[sidx], (uint32_t)((ch / NST) & 1));
@@ -1119,117 +1246,234 @@ __global__ void __launch_bounds__(32) k_rec_adj_w(const AdjItem* __restrict__ it
         for (int k = ch + 1; k < nchunk && k < ch + NST; ++k)  // drain the copies still in flight
           mbar_wait(&bar[k % NST], (uint32_t)((k / NST) & 1));
       }
-      return;
+      failed = true;
+      break;
     }
-    const int li0 = ch * CH;  // index of l = l0 + li0 in the item's slice
+    const int li0 = ch * CH;  // index of l = l0 + li0 in the order's l range
     const int nq = (min(CH, nl - li0) + 3) >> 2;
-    const TabEntry<T>* st = stg[sidx].v;
+    const TabEntry<float>* st = stg[sidx].v;
     for (int q = 0; q < nq; ++q) {
-      T tot = (T)0;
       bool fast, skip;
-      classify<T, SPIN, RPT>(S, nr_w, fast, skip);
+      classify<float, SPIN, RPT>(S, nr_w, fast, skip);
+      const int row0 = (q & 1) * 4;
       if (skip) {
         adj_quad_steps<SPIN, RPT>(S, st, 4 * q, nr_w);
-        rescale_all<T, SPIN, RPT>(S, nr_w);
-      } else {
-        T v[16];
-        if (fast) {
-          if (nr_w >= RPT) adj_quad_sums<SPIN, RPT, false>(S, fin, st, 4 * q, RPT, v);
-          else adj_quad_sums<SPIN, RPT, false>(S, fin, st, 4 * q, nr_w, v);
-        } else {
-          adj_quad_sums<SPIN, RPT, true>(S, fin, st, 4 * q, nr_w, v);
-          rescale_all<T, SPIN, RPT>(S, nr_w);
+        rescale_all<float, SPIN, RPT>(S, nr_w);
+#pragma unroll
+        for (int k = 0; k < NS; ++k)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) red[k][row0 + u][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+      } else if constexpr (MIR) {
+        const int lpm = sd.l0 + li0 + 4 * q + m;
+        if (fast) adj_quad_rows_mir<SPIN, RPT, false>(S, fin[0], fmir, st, 4 * q, nr_w, red[0], row0, lane, lpm);
+        else {
+          adj_quad_rows_mir<SPIN, RPT, true>(S, fin[0], fmir, st, 4 * q, nr_w, red[0], row0, lane, lpm);
+          rescale_all<float, SPIN, RPT>(S, nr_w);
         }
-        tot = reduce_scatter16<T>(v, lane);  // lane < 16: sum (lane & 3) of l = 4q + (lane >> 2)
+      } else if (fast) {
+        if (nr_w >= RPT) adj_quad_rows<SPIN, RPT, false, NS>(S, fin, st, 4 * q, RPT, red, row0, lane);
+        else adj_quad_rows<SPIN, RPT, false, NS>(S, fin, st, 4 * q, nr_w, red, row0, lane);
+      } else {
+        adj_quad_rows<SPIN, RPT, true, NS>(S, fin, st, 4 * q, nr_w, red, row0, lane);
+        rescale_all<float, SPIN, RPT>(S, nr_w);
       }
-      const int li = li0 + 4 * q + ((lane >> 2) & 3);
-      if (rf) {  // sums against d_{m,-s}(theta) and d_{m,s}(theta): swap the column pairs, sign (-1)^(l+m)
-        const T other = __shfl_xor_sync(0xffffffffu, tot, 2);
-        tot = (((sd.l0 + li + m) & 1) ? (T)-1 : (T)1) * other;
+      if ((q & 1) || q == nq - 1) {  // flush rows 0 .. 8 (or 4) of red: l = l0 + li0 + 4 (q & ~1) + row
+        __syncwarp();
+        const int li = li0 + 4 * (q & ~1) + lane;
+        const bool out = lane < ((q & 1) ? 8 : 4) && li < nl;
+        const int l = sd.l0 + li;
+        const float sl = ((l + m) & 1) ? -1.f : 1.f;
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+          float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) {
+            const float4 x = red[k][rr][cg * 8 + (kk ^ rr)];
+            a.x += x.x;
+            a.y += x.y;
+            a.z += x.z;
+            a.w += x.w;
+          }
+#pragma unroll
+          for (int o = 8; o <= 16; o <<= 1) {
+            a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
+            a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
+            a.z += __shfl_xor_sync(0xffffffffu, a.z, o);
+            a.w += __shfl_xor_sync(0xffffffffu, a.w, o);
+          }
+          if (out) {
+            // sums against d_{m,-s}(theta) and d_{m,s}(theta): reflected rings swap the column
+            // pairs and carry (-1)^(l+m)
+            if (rf) a = make_float4(sl * a.z, sl * a.w, sl * a.x, sl * a.y);
+            if (direct) {
+              float2 gv, cv;
+              adj_project(a, m0, sg, sm, msc, gv, cv);
+              sets.gt[k][base + l] = gv;
+              if (sets.ct[k]) sets.ct[k][base + l] = cv;
+            } else {
+              red_add_v4(&sets.acc[k][base + l], a);
+            }
+          }
+        }
+        __syncwarp();
       }
-      if (lane < 16 && li < nl) out[4 * (int64_t)li + (lane & 3)] = tot;
     }
     __syncwarp();  // every lane is done with stage sidx
-    if (ch + NST < nchunk && lane == 0) issue_chunk<T, CH>(stg[sidx], &bar[sidx], tab, base + sd.l0 + (ch + NST) * CH);
+    if (ch + NST < nchunk && lane == 0) issue_chunk<float, CH>(stg[sidx], &bar[sidx], tab, base + sd.l0 + (ch + NST) * CH);
     __syncwarp();
   }
-}
-
-// Sum of the adjoint items of order m (m_first + blockIdx.x) and the projection of the adjoint synthesis
-// general formula: ut_{l,m} = -Qp, ut_{l,-m} = -(-1)^(m-s) Qm, g~ = (ut_lm + (-1)^m conj ut_{l,-m})/2,
-// c~ = (ut_lm - (-1)^m conj ut_{l,-m})/(2i); zero below l0 and for orders without active rings.
-template <typename T>
-__global__ void k_adj_reduce(const AdjItem* __restrict__ items, const int2* __restrict__ aspan,
-                             const MSeed* __restrict__ mseed, const T* __restrict__ part, int lmax, int s, T msc,
-                             int m_first, typename Cx<T>::V* __restrict__ gt, typename Cx<T>::V* __restrict__ ct) {
-  using V = typename Cx<T>::V;
-  constexpr int kMaxItems = 64;
-  __shared__ int64_t off[kMaxItems];
-  const int m = m_first + blockIdx.x;
-  const int2 sp = aspan[m];
-  const int64_t base = alm_base(lmax, m);
-  const int l0 = sp.y > 0 ? mseed[m].l0 : lmax + 1;
-  for (int k = threadIdx.x; k < sp.y && k < kMaxItems; k += blockDim.x) off[k] = items[sp.x + k].off;
-  __syncthreads();
-  const bool m0 = (m == 0);
-  const T sg = (((m - s) & 1) ? (T)1 : (T)-1);  // -(-1)^(m-s)
-  const T sm = (m & 1) ? (T)-1 : (T)1;          // (-1)^m
-  for (int l = m + threadIdx.x; l <= lmax; l += blockDim.x) {
-    V gv = mk((T)0, (T)0), cv = gv;
-    if (l >= l0) {
-      T q0 = 0, q1 = 0, q2 = 0, q3 = 0;
-      const int64_t li = 4 * (int64_t)(l - l0);
-      for (int k = 0; k < sp.y; ++k) {
-        const int64_t o = (k < kMaxItems ? off[k] : items[sp.x + k].off) + li;
-        q0 += part[o];
-        q1 += part[o + 1];
-        q2 += part[o + 2];
-        q3 += part[o + 3];
-      }
-      const T ar = -q0, ai = -q1;
-      const T br = sg * q2, bi = sg * q3;
-      if (m0) {
-        gv = mk(ar, (T)0);
-        cv = mk(ai, (T)0);
-      } else {
-        const T wr = sm * br, wi = -sm * bi;  // (-1)^m conj(ut_{l,-m})
-        gv = mk(msc * (T)0.5 * (ar + wr), msc * (T)0.5 * (ai + wi));
-        cv = mk(msc * (T)0.5 * (ai - wi), msc * (T)-0.5 * (ar - wr));
+  if (direct) {  // entries below l0 (orders m < s) are zero
+    for (int l = m + lane; l < sd.l0; l += 32) {
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        sets.gt[k][base + l] = z;
+        if (sets.ct[k]) sets.ct[k][base + l] = z;
       }
     }
-    gt[base + l] = gv;
-    if (ct) ct[base + l] = cv;
-  }
-}
-
-template <typename T, bool SPIN, int RPT>
-void launch_syn_t(Plan& p, const void* g, const void* c, double msc, cudaStream_t st) {
-  using V = typename Cx<T>::V;
-  if (p.syn_threads == 32) {  // one warp per item (items of at most 32 RPT rings)
-    const int i0 = p.r_item0, i1 = p.r_item1 < 0 ? p.nitems : p.r_item1;
-    if (i1 > i0)
-      k_rec_syn_w<T, SPIN, RPT, 32, 4><<<i1 - i0, 32, 0, st>>>(
-          p.d_items + i0, p.d_ring, p.d_mseed, (const TabEntry<T>*)p.d_rtab, (const V*)g, (const V*)c, p.lmax,
-          p.spin, (T)msc, (V*)p.d_F, p.Lpad, p.d_status, p.omx_tb);
     return;
   }
-  k_rec_syn<T, SPIN, RPT, 128><<<p.nitems, 128, 0, st>>>(p.d_items, p.d_ring, p.d_mseed,
-                                                          (const TabEntry<T>*)p.d_rtab, (const V*)g, (const V*)c, p.lmax, p.spin, (T)msc,
-                                                          (V*)p.d_F, p.Lpad, p.d_status);
+  // arrival of this item; the last of the order's items projects the accumulated sums
+  __threadfence();
+  __syncwarp();
+  int prev = 0;
+  if (lane == 0) prev = atomicAdd(&cnt[m], 1);
+  prev = __shfl_sync(0xffffffffu, prev, 0);
+  if (prev != it.nitems - 1) return;
+  __threadfence();
+  for (int l = m + lane; l <= lmax; l += 32) {
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      float2 gv = z, cv = z;
+      if (l >= sd.l0) {
+        const float4 q = __ldcg(&sets.acc[k][base + l]);
+        if (!failed) adj_project(q, m0, sg, sm, msc, gv, cv);
+        __stcg(&sets.acc[k][base + l], make_float4(0.f, 0.f, 0.f, 0.f));
+      }
+      sets.gt[k][base + l] = gv;
+      if (sets.ct[k]) sets.ct[k][base + l] = cv;
+    }
+  }
+  if (lane == 0) cnt[m] = 0;
 }
 
-template <typename T, bool SPIN, int RPT>
-void launch_adj_w(Plan& p, void* g, void* c, double msc, cudaStream_t st) {
+// orders without active rings (m > M) project to zero: (g~, c~) of orders [m_lo, m_hi)
+template <typename V>
+void zero_orders(const Plan& p, void* g, void* c, int m_lo, int m_hi, cudaStream_t st) {
+  if (m_hi <= m_lo) return;
+  // first packed index of order m: the orders m' < m hold lmax - m' + 1 entries each
+  const auto off = [&](int m) { return (size_t)((int64_t)m * (2 * p.lmax + 3 - m) / 2); };
+  const size_t b0 = off(m_lo) * sizeof(V), b1 = off(m_hi) * sizeof(V);
+  PSHT_CUDA_TRY(cudaMemsetAsync((char*)g + b0, 0, b1 - b0, st));
+  if (c) PSHT_CUDA_TRY(cudaMemsetAsync((char*)c + b0, 0, b1 - b0, st));
+}
+
+// one launch of the synthesis recursion for NS sets (items of the plan's current item range)
+template <typename T, bool SPIN, int RPT, int NS>
+void launch_syn_ns(Plan& p, const void* const* g, const void* const* c, void* const* F, double msc, cudaStream_t st) {
   using V = typename Cx<T>::V;
+  const int i0 = p.r_item0, i1 = p.r_item1 < 0 ? p.nitems : p.r_item1;
+  SynSets<T, NS> ss;
+  for (int k = 0; k < NS; ++k) {
+    ss.g[k] = (const V*)g[k];
+    ss.c[k] = c ? (const V*)c[k] : nullptr;
+    ss.F[k] = (V*)F[k];
+  }
+  const int jm = p.nring - 1;
+  if (i1 > i0)
+    k_rec_syn_w<T, SPIN, RPT, 32, 4, NS, false><<<i1 - i0, 32, 0, st>>>(p.d_items + i0, p.d_ring, p.d_mseed,
+                                                                        (const TabEntry<T>*)p.d_rtab, ss, p.lmax,
+                                                                        p.spin, (T)msc, p.Lpad, p.d_status, p.omx_tb,
+                                                                        jm);
+  // mirror pairs of full-sky plans, one set at a time (they are never split into order chunks)
+  if (p.nmitems > 0 && p.r_item1 < 0) {
+    for (int k = 0; k < NS; ++k) {
+      SynSets<T, 1> s1;
+      s1.g[0] = ss.g[k];
+      s1.c[0] = ss.c[k];
+      s1.F[0] = ss.F[k];
+      k_rec_syn_w<T, SPIN, RPT, 32, 4, 1, true><<<p.nmitems, 32, 0, st>>>(
+          p.d_mitems, p.d_ring, p.d_mseed, (const TabEntry<T>*)p.d_rtab, s1, p.lmax, p.spin, (T)msc, p.Lpad,
+          p.d_status, p.omx_tb, jm);
+    }
+  }
+}
+// nsets sets in launches of 4, 2 and 1 sets
+template <typename T, bool SPIN, int RPT>
+void launch_syn_t(Plan& p, int nsets, const void* const* g, const void* const* c, void* const* F, double msc,
+                  cudaStream_t st) {
+  for (int k = 0; k < nsets;) {
+    const int left = nsets - k;
+    const void* const* ck = c ? c + k : nullptr;
+    if (left >= 4) {
+      launch_syn_ns<T, SPIN, RPT, 4>(p, g + k, ck, F + k, msc, st);
+      k += 4;
+    } else if (left >= 2) {
+      launch_syn_ns<T, SPIN, RPT, 2>(p, g + k, ck, F + k, msc, st);
+      k += 2;
+    } else {
+      launch_syn_ns<T, SPIN, RPT, 1>(p, g + k, ck, F + k, msc, st);
+      k += 1;
+    }
+  }
+}
+
+// one launch of the FP32 adjoint recursion for NS sets, then the zero orders of each set
+template <bool SPIN, int RPT, int NS>
+void launch_adj_ns(Plan& p, void* const* F, void* const* acc, void* const* g, void* const* c, double msc,
+                   cudaStream_t st) {
   const int i0 = p.r_aitem0, i1 = p.r_aitem1 < 0 ? p.naitems : p.r_aitem1;
   const int m0 = p.r_m0, m1 = p.r_m1 < 0 ? p.lmax + 1 : p.r_m1;
+  AdjSets<NS> as;
+  for (int k = 0; k < NS; ++k) {
+    as.Ft[k] = (const float2*)F[k];
+    as.acc[k] = (float4*)acc[k];
+    as.gt[k] = (float2*)g[k];
+    as.ct[k] = c ? (float2*)c[k] : nullptr;
+  }
+  const int jm = p.nring - 1;
   if (i1 > i0)
-    k_rec_adj_w<T, SPIN, RPT, 32, 4><<<i1 - i0, 32, 0, st>>>(p.d_aitems + i0, p.d_ring, p.d_mseed,
-                                                              (const TabEntry<T>*)p.d_rtab, (const V*)p.d_F, p.Lpad,
-                                                              p.lmax, (T*)p.d_part, p.d_status);
-  if (m1 > m0)
-    k_adj_reduce<T><<<m1 - m0, 256, 0, st>>>(p.d_aitems, p.d_aspan, p.d_mseed, (const T*)p.d_part, p.lmax, p.spin,
-                                             (T)msc, m0, (V*)g, (V*)c);
+    k_rec_adj_w<SPIN, RPT, 32, 4, NS, false><<<i1 - i0, 32, 0, st>>>(p.d_aitems + i0, p.d_ring, p.d_mseed,
+                                                                      (const TabEntry<float>*)p.d_rtab, as, p.Lpad,
+                                                                      p.lmax, p.spin, (float)msc, p.d_cnt, p.d_status,
+                                                                      jm);
+  // mirror pairs of full-sky plans, one set at a time (never split into order chunks); their
+  // orders' other items ran above, and the arrival counters join the two launches
+  if (p.nmaitems > 0 && p.r_aitem1 < 0) {
+    for (int k = 0; k < NS; ++k) {
+      AdjSets<1> a1;
+      a1.Ft[0] = as.Ft[k];
+      a1.acc[0] = as.acc[k];
+      a1.gt[0] = as.gt[k];
+      a1.ct[0] = as.ct[k];
+      k_rec_adj_w<SPIN, RPT, 32, 4, 1, true><<<p.nmaitems, 32, 0, st>>>(
+          p.d_maitems, p.d_ring, p.d_mseed, (const TabEntry<float>*)p.d_rtab, a1, p.Lpad, p.lmax, p.spin, (float)msc,
+          p.d_cnt, p.d_status, jm);
+    }
+  }
+  for (int k = 0; k < NS; ++k) zero_orders<float2>(p, g[k], c ? c[k] : nullptr, std::max(m0, p.M + 1), m1, st);
+}
+template <bool SPIN, int RPT>
+void launch_adj_w(Plan& p, int nsets, void* const* F, void* const* acc, void* const* g, void* const* c, double msc,
+                  cudaStream_t st) {
+  if (p.nmaitems > 0) {  // mirror pairs: the arrival counters count each item once per launch pair
+    for (int k = 0; k < nsets; ++k)
+      launch_adj_ns<SPIN, RPT, 1>(p, F + k, acc + k, g + k, c ? c + k : nullptr, msc, st);
+    return;
+  }
+  for (int k = 0; k < nsets;) {
+    const int left = nsets - k;
+    void* const* ck = c ? c + k : nullptr;
+    if (left >= 4) {
+      launch_adj_ns<SPIN, RPT, 4>(p, F + k, acc + k, g + k, ck, msc, st);
+      k += 4;
+    } else if (left >= 2) {
+      launch_adj_ns<SPIN, RPT, 2>(p, F + k, acc + k, g + k, ck, msc, st);
+      k += 2;
+    } else {
+      launch_adj_ns<SPIN, RPT, 1>(p, F + k, acc + k, g + k, ck, msc, st);
+      k += 1;
+    }
+  }
 }
 
 template <typename T, bool SPIN, int RPT, int NT>
@@ -1238,45 +1482,61 @@ void launch_adj_t(Plan& p, void* g, void* c, double msc, cudaStream_t st) {
   // one launch per ring part (rings at theta <= pi/2, then reflected rings at theta > pi/2) and
   // per chunk of RPT * NT rings of it; every launch after the first adds to the output
   const size_t red_bytes = (size_t)2 * (NT / 32) * kCH * sizeof(typename Cx4<T>::V);
-  PSHT_CUDA_TRY(cudaFuncSetAttribute((const void*)k_rec_adj<T, SPIN, RPT, NT>,
+  PSHT_CUDA_TRY(cudaFuncSetAttribute((const void*)k_rec_adj<T, SPIN, RPT, NT, false>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red_bytes));
   const int nch = (p.nring + RPT * NT - 1) / (RPT * NT);
+  const int jm = p.nring - 1;
+  const int2* mr0 = p.d_mrange;
   for (int part = 0; part < 2; ++part) {
     if (part == 1 && !p.has_refl) break;
     for (int chk = 0; chk < nch; ++chk)
-      k_rec_adj<T, SPIN, RPT, NT><<<p.lmax + 1, NT, red_bytes, st>>>(
-          p.d_ring, p.d_mseed, p.d_mrange + part * (p.lmax + 1), (const TabEntry<T>*)p.d_rtab, (const V*)p.d_F,
+      k_rec_adj<T, SPIN, RPT, NT, false><<<p.lmax + 1, NT, red_bytes, st>>>(
+          p.d_ring, p.d_mseed, mr0 + part * (p.lmax + 1), (const TabEntry<T>*)p.d_rtab, (const V*)p.d_F,
           p.Lpad, p.lmax, p.spin, p.M, part, (part > 0 || chk > 0) ? 1 : 0, (T)msc, (V*)g, (V*)c, p.d_status, chk,
-          p.omx_tb);
+          p.omx_tb, p.d_mmode, jm);
+    if (part == 0 && p.d_mmode) {  // mirror-pair orders of full-sky plans: direct rings with their mirrors
+      PSHT_CUDA_TRY(cudaFuncSetAttribute((const void*)k_rec_adj<T, SPIN, RPT, NT, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red_bytes));
+      for (int chk = 0; chk < nch; ++chk)
+        k_rec_adj<T, SPIN, RPT, NT, true><<<p.lmax + 1, NT, red_bytes, st>>>(
+            p.d_ring, p.d_mseed, mr0, (const TabEntry<T>*)p.d_rtab, (const V*)p.d_F, p.Lpad, p.lmax, p.spin, p.M, 0,
+            1, (T)msc, (V*)g, (V*)c, p.d_status, chk, p.omx_tb, p.d_mmode, jm);
+    }
   }
 }
 
 template <typename T, bool SPIN>
-void launch_syn_s(Plan& p, const void* g, const void* c, double msc, cudaStream_t st) {
-  switch (p.syn_rpt) {
-    case 1: launch_syn_t<T, SPIN, sizeof(T) == 8 ? 1 : 2>(p, g, c, msc, st); break;  // FP32 slots come in pairs
-    case 2: launch_syn_t<T, SPIN, 2>(p, g, c, msc, st); break;
-    default: launch_syn_t<T, SPIN, 4>(p, g, c, msc, st); break;
+void launch_syn_s(Plan& p, int nsets, const void* const* g, const void* const* c, void* const* F, double msc,
+                  cudaStream_t st) {
+  if constexpr (sizeof(T) == 8) {
+    launch_syn_t<T, SPIN, 1>(p, nsets, g, c, F, msc, st);  // FP64: one ring per lane (syn_rpt 1)
+  } else {
+    launch_syn_t<T, SPIN, 2>(p, nsets, g, c, F, msc, st);  // FP32 slots come in pairs (syn_rpt 2)
   }
 }
 template <typename T, bool SPIN>
-void launch_adj_s(Plan& p, void* g, void* c, double msc, cudaStream_t st) {
-  if (p.adj_threads == 32) {  // one warp per item, FP32 form
-    if constexpr (sizeof(T) == 4) {
-      if (p.adj_rpt == 8) launch_adj_w<T, SPIN, 8>(p, g, c, msc, st);
-      else if (p.adj_rpt == 2) launch_adj_w<T, SPIN, 2>(p, g, c, msc, st);
-      else launch_adj_w<T, SPIN, 4>(p, g, c, msc, st);
-      return;
+void launch_adj_s(Plan& p, int nsets, void* const* F, void* const* acc, void* const* g, void* const* c, double msc,
+                  cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {  // FP32: one warp per item, the sets in one launch
+    launch_adj_w<SPIN, 4>(p, nsets, F, acc, g, c, msc, st);  // adj_rpt 4
+    return;
+  } else {
+    // FP64 block form, one set at a time.  (rings per thread, threads) of one launch chunk are
+    // chosen by the planner
+    void* const F0 = p.d_F;
+    for (int k = 0; k < nsets; ++k) {
+      p.d_F = F[k];
+      void* ck = c ? c[k] : nullptr;
+      switch (p.adj_rpt * 10000 + p.adj_threads) {
+        case 20128: launch_adj_t<T, SPIN, 2, 128>(p, g[k], ck, msc, st); break;
+        case 40128: launch_adj_t<T, SPIN, 4, 128>(p, g[k], ck, msc, st); break;
+        case 40256: launch_adj_t<T, SPIN, 4, 256>(p, g[k], ck, msc, st); break;
+        case 80128: launch_adj_t<T, SPIN, 8, 128>(p, g[k], ck, msc, st); break;
+        case 80256: launch_adj_t<T, SPIN, 8, 256>(p, g[k], ck, msc, st); break;
+        default: launch_adj_t<T, SPIN, 8, 512>(p, g[k], ck, msc, st); break;
+      }
     }
-  }
-  // (rings per thread, threads) of one launch chunk; chosen by the planner
-  switch (p.adj_rpt * 10000 + p.adj_threads) {
-    case 20128: launch_adj_t<T, SPIN, 2, 128>(p, g, c, msc, st); break;
-    case 40128: launch_adj_t<T, SPIN, 4, 128>(p, g, c, msc, st); break;
-    case 40256: launch_adj_t<T, SPIN, 4, 256>(p, g, c, msc, st); break;
-    case 80128: launch_adj_t<T, SPIN, 8, 128>(p, g, c, msc, st); break;
-    case 80256: launch_adj_t<T, SPIN, 8, 256>(p, g, c, msc, st); break;
-    default: launch_adj_t<T, SPIN, 8, 512>(p, g, c, msc, st); break;
+    p.d_F = F0;
   }
 }
 
@@ -1294,27 +1554,41 @@ void build_rec_table(Plan& p, cudaStream_t st) {
   PSHT_CUDA_TRY(cudaGetLastError());
 }
 
-void launch_rec_synthesis(Plan& p, const void* g, const void* c, cudaStream_t st, double msc) {
-  if (p.nitems == 0) return;
+void launch_rec_synthesis_sets(Plan& p, int nsets, const void* const* g, const void* const* c, void* const* F,
+                               cudaStream_t st, double msc) {
+  if (p.nitems == 0 || nsets <= 0) return;
   if (p.prec == 64) {
-    if (p.spin) launch_syn_s<double, true>(p, g, c, msc, st);
-    else launch_syn_s<double, false>(p, g, c, msc, st);
+    if (p.spin) launch_syn_s<double, true>(p, nsets, g, c, F, msc, st);
+    else launch_syn_s<double, false>(p, nsets, g, c, F, msc, st);
   } else {
-    if (p.spin) launch_syn_s<float, true>(p, g, c, msc, st);
-    else launch_syn_s<float, false>(p, g, c, msc, st);
+    if (p.spin) launch_syn_s<float, true>(p, nsets, g, c, F, msc, st);
+    else launch_syn_s<float, false>(p, nsets, g, c, F, msc, st);
+  }
+  PSHT_CUDA_TRY(cudaGetLastError());
+}
+
+void launch_rec_synthesis(Plan& p, const void* g, const void* c, cudaStream_t st, double msc) {
+  void* F = p.d_F;
+  launch_rec_synthesis_sets(p, 1, &g, c ? &c : nullptr, &F, st, msc);
+}
+
+void launch_rec_adjoint_sets(Plan& p, int nsets, void* const* F, void* const* acc, void* const* g, void* const* c,
+                             cudaStream_t st, double msc) {
+  if (nsets <= 0) return;
+  if (p.prec == 64) {
+    if (p.spin) launch_adj_s<double, true>(p, nsets, F, acc, g, c, msc, st);
+    else launch_adj_s<double, false>(p, nsets, F, acc, g, c, msc, st);
+  } else {
+    if (p.spin) launch_adj_s<float, true>(p, nsets, F, acc, g, c, msc, st);
+    else launch_adj_s<float, false>(p, nsets, F, acc, g, c, msc, st);
   }
   PSHT_CUDA_TRY(cudaGetLastError());
 }
 
 void launch_rec_adjoint(Plan& p, void* g, void* c, cudaStream_t st, double msc) {
-  if (p.prec == 64) {
-    if (p.spin) launch_adj_s<double, true>(p, g, c, msc, st);
-    else launch_adj_s<double, false>(p, g, c, msc, st);
-  } else {
-    if (p.spin) launch_adj_s<float, true>(p, g, c, msc, st);
-    else launch_adj_s<float, false>(p, g, c, msc, st);
-  }
-  PSHT_CUDA_TRY(cudaGetLastError());
+  void* F = p.d_F;
+  void* acc = p.d_acc;
+  launch_rec_adjoint_sets(p, 1, &F, &acc, &g, c ? &c : nullptr, st, msc);
 }
 
 }  // namespace psht

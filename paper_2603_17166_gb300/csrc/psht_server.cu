@@ -200,6 +200,23 @@ struct Server {
     }
   }
 
+  // Move every queued job with the same plan key and operation as `first` (up to kMaxBatch in all)
+  // out of the queue: they run as one batch on the plan (psht_plan_*_batch).  Called with mu held.
+  static constexpr int kMaxBatch = 8;
+  std::vector<Job> take_batch(const Job& first) {
+    std::vector<Job> b{first};
+    const PlanKey k = key_of(first.req);
+    for (auto it = queue.begin(); it != queue.end() && (int)b.size() < kMaxBatch;) {
+      if (it->req.op == first.req.op && !(key_of(it->req) < k) && !(k < key_of(it->req))) {
+        b.push_back(*it);
+        it = queue.erase(it);
+      } else {
+        ++it;
+      }
+    }
+    return b;
+  }
+
   void run(int w, cudaStream_t st, const Job& job, bool cached, size_t est) {
     const psht_request& r = job.req;
     const PlanKey k = key_of(r);
@@ -207,7 +224,6 @@ struct Server {
     res.worker = w;
     res.plan_cached = cached ? 1 : 0;
     const Clock::time_point t0 = Clock::now();
-    res.queue_ms = ms_between(job.t_submit, t0);
     psht_plan* plan = nullptr;
     int rc = PSHT_OK;
     {
@@ -235,25 +251,65 @@ struct Server {
     }
     const Clock::time_point t1 = Clock::now();
     res.plan_ms = cached ? 0.0 : ms_between(t0, t1);
+    // the requests queued for the same plan and operation join this one (continuous batching: they
+    // arrived while the plan was busy or being built)
+    std::vector<Job> batch{job};
     if (rc == PSHT_OK) {
-      rc = (r.op == PSHT_OP_SYNTHESIS) ? psht_plan_synthesis(plan, r.in_a, r.in_b, r.out_a, st)
-           : (r.op == PSHT_OP_ADJOINT) ? psht_plan_adjoint(plan, r.in_a, r.out_a, r.out_b, st)
-                                       : PSHT_EINVAL;
+      std::lock_guard<std::mutex> g(mu);
+      batch = take_batch(job);
+      stats.batches += 1;
+      if (batch.size() > 1) stats.batched_requests += (int64_t)batch.size();
+    }
+    const int n = (int)batch.size();
+    if (rc == PSHT_OK) {
+      std::vector<const void*> ia(n), ib(n);
+      std::vector<void*> oa(n), ob(n);
+      bool any_b = false;
+      for (int i = 0; i < n; ++i) {
+        const psht_request& q = batch[i].req;
+        ia[i] = q.in_a;
+        ib[i] = q.in_b;
+        oa[i] = q.out_a;
+        ob[i] = q.out_b;
+        any_b = any_b || (r.op == PSHT_OP_SYNTHESIS ? q.in_b != nullptr : q.out_b != nullptr);
+      }
+      if (n == 1)
+        rc = (r.op == PSHT_OP_SYNTHESIS) ? psht_plan_synthesis(plan, r.in_a, r.in_b, r.out_a, st)
+             : (r.op == PSHT_OP_ADJOINT) ? psht_plan_adjoint(plan, r.in_a, r.out_a, r.out_b, st)
+                                         : PSHT_EINVAL;
+      else
+        rc = (r.op == PSHT_OP_SYNTHESIS)
+                 ? psht_plan_synthesis_batch(plan, n, ia.data(), any_b ? ib.data() : nullptr, oa.data(), st)
+                 : psht_plan_adjoint_batch(plan, n, ia.data(), oa.data(), any_b ? ob.data() : nullptr, st);
       if (rc == PSHT_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = PSHT_ECUDA;
     }
     const Clock::time_point t2 = Clock::now();
     res.exec_ms = ms_between(t1, t2);
-    res.total_ms = ms_between(job.t_submit, t2);
     res.status = rc;
+    res.batch = n;
     {
       std::lock_guard<std::mutex> g(mu);
       auto c = cache.find(k);
       if (c != cache.end()) {
         c->second.busy = false;
         res.precision = c->second.precision;
+        if (rc == PSHT_OK && plan) {  // a first batched call adds the plan's batch buffers
+          psht_info inf;
+          psht_plan_info(plan, &inf);
+          if (inf.device_bytes > c->second.bytes) {
+            in_use += inf.device_bytes - c->second.bytes;
+            c->second.bytes = inf.device_bytes;
+            peak = std::max(peak, in_use);
+          }
+        }
       }
     }
-    finish(job, res);
+    for (const Job& j : batch) {
+      psht_result rj = res;
+      rj.queue_ms = ms_between(j.t_submit, t0);
+      rj.total_ms = ms_between(j.t_submit, t2);
+      finish(j, rj);
+    }
   }
 };
 

@@ -57,7 +57,7 @@ class PshtResult(ctypes.Structure):
     _fields_ = [
         ("status", ctypes.c_int), ("worker", ctypes.c_int), ("plan_cached", ctypes.c_int),
         ("precision", ctypes.c_int), ("queue_ms", ctypes.c_double), ("plan_ms", ctypes.c_double),
-        ("exec_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
+        ("exec_ms", ctypes.c_double), ("total_ms", ctypes.c_double), ("batch", ctypes.c_int),
     ]
 
 
@@ -66,6 +66,7 @@ class PshtServerStats(ctypes.Structure):
         ("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
         ("plans_created", ctypes.c_int64), ("cache_hits", ctypes.c_int64), ("evictions", ctypes.c_int64),
         ("budget", ctypes.c_size_t), ("bytes_in_use", ctypes.c_size_t), ("bytes_peak", ctypes.c_size_t),
+        ("batches", ctypes.c_int64), ("batched_requests", ctypes.c_int64),
     ]
 
 
@@ -88,6 +89,8 @@ def lib():
                      "psht_plan_adjoint_packed", "psht_plan_synthesis_host", "psht_plan_adjoint_host",
                      "psht_plan_ring_coeffs", "psht_plan_synthesis_inframe", "psht_plan_adjoint_inframe"):
             getattr(L, name).argtypes = [P, P, P, P, P]
+        L.psht_plan_synthesis_batch.argtypes = [P, I, P, P, P, P]
+        L.psht_plan_adjoint_batch.argtypes = [P, I, P, P, P, P]
         L.psht_plan_destroy.argtypes = [P]
         L.psht_plan_rings.argtypes = [P, P, P, P]
         L.psht_synthesis.argtypes = [P, P, I, I, P, P, I64, D, P, P]
@@ -227,6 +230,47 @@ class Plan:
             fn = lib().psht_plan_adjoint_inframe
         _check(fn(self._h, _ptr(f), _ptr(g), _ptr(c), _stream(stream)))
         return g, c
+
+    def synthesis_batch(self, gs, cs=None, outs=None, stream=None):
+        """Synthesis of several a_lm sets on this plan (psht_plan_synthesis_batch): the sets share the
+        Wigner-d recursion's column evaluations.  gs: list of packed a_lm; cs: None or a list of
+        the same length (entries may be None); returns the list of maps."""
+        torch = _torch()
+        n = len(gs)
+        gs = [self._alm_in(g) for g in gs]
+        cs = [None] * n if cs is None else [self._alm_in(c) for c in cs]
+        if len(cs) != n:
+            raise ValueError("gs and cs must have the same length")
+        fs = list(outs) if outs is not None else [torch.empty(self.npts, dtype=self.cdtype, device="cuda")
+                                                    for _ in range(n)]
+        for f in fs:
+            if f.numel() != self.npts or f.dtype != self.cdtype or not f.is_contiguous():
+                raise ValueError("outs must be contiguous tensors of one value per point in the plan's precision")
+        arr = ctypes.c_void_p * n
+        ga = arr(*[g.data_ptr() for g in gs])
+        ca = arr(*[0 if c is None else c.data_ptr() for c in cs])
+        fa = arr(*[f.data_ptr() for f in fs])
+        _check(lib().psht_plan_synthesis_batch(self._h, n, ga, None if all(c is None for c in cs) else ca, fa,
+                                               _stream(stream)))
+        return fs
+
+    def adjoint_batch(self, fs, want_c: bool = True, stream=None):
+        """Adjoint of several maps on this plan (psht_plan_adjoint_batch) -> list of (g~, c~)."""
+        torch = _torch()
+        n = len(fs)
+        fs = [torch.as_tensor(f, device="cuda").to(self.cdtype).contiguous() for f in fs]
+        for f in fs:
+            if f.numel() != self.npts:
+                raise ValueError("f must hold one value per point")
+        na = nalm(self.lmax)
+        gs = [torch.empty(na, dtype=self.cdtype, device="cuda") for _ in range(n)]
+        cs = [torch.empty(na, dtype=self.cdtype, device="cuda") for _ in range(n)] if want_c else None
+        arr = ctypes.c_void_p * n
+        _check(lib().psht_plan_adjoint_batch(self._h, n, arr(*[f.data_ptr() for f in fs]),
+                                             arr(*[g.data_ptr() for g in gs]),
+                                             None if cs is None else arr(*[c.data_ptr() for c in cs]),
+                                             _stream(stream)))
+        return [(g, None if cs is None else cs[k]) for k, g in enumerate(gs)]
 
     def synthesis_host(self, g: np.ndarray, c, f: np.ndarray, stream=None):
         """Host-buffer synthesis (psht_plan_synthesis_host); g, c, f numpy arrays (pinned memory ok)."""

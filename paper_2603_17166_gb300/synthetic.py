@@ -275,7 +275,8 @@ SERVING_EPS = (1e-5, 1e-8, 1e-10)
 
 def serving_workload(n_fields: int = 8, n_requests: int = 200, nmax: int = 30_000_000, lmax_max: int = 8192):
     """Mixed request stream: a pool of fields (patch, points, lmax, spin, eps) and a request
-    sequence over it.  Per field: lmax from {1024, 2048, 4096, 8192} (capped at lmax_max), spin 0 or
+    sequence over it.  Per field: lmax from {1024, 2048, 4096, 8192} (capped at lmax_max; field i
+    takes the (i mod 4)-th value, so that a pool of 4 or more fields holds every lmax), spin 0 or
     2, cap (centre dec U[-90, -30]) or RA/dec box 50/50, sky fraction log-uniform on [0.1 %, 4 %],
     N log-uniform on [1e5, nmax], eps from {1e-5 (FP32 form), 1e-8, 1e-10}.  Requests: field
     uniform over the pool, synthesis or adjoint 50/50, unit-rate Poisson arrival times (scale them
@@ -287,7 +288,7 @@ def serving_workload(n_fields: int = 8, n_requests: int = 200, nmax: int = 30_00
     fields = []
     lms = [l for l in SERVING_LMAX if l <= lmax_max] or [lmax_max]
     for i in range(n_fields):
-        lmax = int(gq.choice(lms))
+        lmax = int(lms[i % len(lms)])
         s = int(gq.choice([0, 2]))
         shape = "cap" if gq.uniform() < 0.5 else "box"
         dec_c = float(gq.uniform(-90.0, -30.0))

@@ -1,8 +1,9 @@
 """Shared checks of the GPU parity tests: a per-point error bound beside the relative L2 error, and
 points placed on the grid-tile borders, on the phi wrap-around, on the cap edge and on the pole.
 
-The CUDA library bins points into tiles of TR x TQ fine-grid cells by the base cell of their ES
-window, r0 = ceil(t - W/2) and q0 = ceil(u - W/2), where t = Theta nTheta / 2pi and
+The CUDA library bins points into tiles of TR x TQ fine-grid cells (32 x 16 in the FP32 form, 16 x 32
+in the FP64 form) by the base cell of their ES window, r0 = ceil(t - W/2) and q0 = ceil(u - W/2),
+where t = Theta nTheta / 2pi and
 u = phi nphi / 2pi are the fine-grid coordinates (Sec. II step 3: Theta = pi beta / theta_max);
 the tile row is (r0 - r_lo) div TR and the tile column (q0 + PADQ) div TQ.  A tile-seam, halo or
 wrap-around mistake shows at the points whose base cell sits on a tile's first or last row or
@@ -13,7 +14,8 @@ import math
 
 import numpy as np
 
-TR, TQ, PADQ = 16, 32, 8  # the library's tile shape and left halo of the grid rows
+PADQ = 8  # left halo of the library's grid rows
+TILES = {"fp32": (32, 16), "fp64": (16, 32)}  # the library's tile shape (TR, TQ) per form
 
 
 def assert_pointwise(got, ref, eps, C=30.0, what="point"):
@@ -37,13 +39,14 @@ def _theta_of_beta(P, beta):
     return beta if P["pole"] == "N" else math.pi - beta
 
 
-def border_points(P, rng, per_row=6):
+def border_points(P, rng, prec="fp64", per_row=6):
     """Extra points (theta, phi) inside the plan's cap (beta <= theta*, so theta* and every plan
     parameter stay the same) that sit on tile borders and at the phi wrap-around:
       * t at the first and last base rows of every tile row (and just across them);
       * u at the first and last base columns of the first tiles, of the last tile and of a middle
         one (and just across them), and phi = 0, 2 pi (1 - 2^-52), -1e-14, 2 pi + 1e-14, 6 pi + 0.3;
       * the pole itself (beta = 0) and the cap edge (beta = theta*)."""
+    TR, TQ = TILES[prec]
     W, r_lo, nphi = P["W"], P["r_lo"], P["nphi"]
     t_star = P["theta_star"] * P["nTheta"] / (2.0 * P["theta_max"])
     ts = []
@@ -77,11 +80,12 @@ def border_points(P, rng, per_row=6):
     return th[keep], np.array(ph)[keep]
 
 
-def border_sample(P, theta, phi, k_each=8):
+def border_sample(P, theta, phi, k_each=8, prec="fp64"):
     """Indices of existing points next to tile borders and the phi wrap-around, for workloads too
     large to add points to: the k_each points with the smallest and the largest phi mod 2 pi, and
     those whose base row or column lies on a tile's first or last row or column with the window
     start closest to a cell boundary; plus the pole-side and cap-edge extremes."""
+    TR, TQ = TILES[prec]
     theta = np.asarray(theta, dtype=np.float64)
     phi = np.asarray(phi, dtype=np.float64)
     beta = theta if P["pole"] == "N" else math.pi - theta

@@ -23,11 +23,11 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def _sample(theta, phi, k, seed, s, lmax, eps, k_each=8):
+def _sample(theta, phi, k, seed, s, lmax, eps, k_each=8, prec="fp64"):
     rng = np.random.default_rng(seed)
     sel = rng.choice(theta.size, size=k, replace=False)
     P = O.plan_params(lmax, s, eps, theta)
-    return np.unique(np.concatenate([sel, PP.border_sample(P, theta, phi, k_each)]))
+    return np.unique(np.concatenate([sel, PP.border_sample(P, theta, phi, k_each, prec)]))
 
 
 def _check_synthesis(wl, eps, prec, k, seed):
@@ -39,7 +39,7 @@ def _check_synthesis(wl, eps, prec, k, seed):
     g = torch.from_numpy(wl["g"]).cuda().to(plan.cdtype)
     c = None if wl["c"] is None else torch.from_numpy(wl["c"]).cuda().to(plan.cdtype)
     f = plan.synthesis(g, c)
-    sel = _sample(wl["theta"], wl["phi"], k, seed, wl["s"], wl["lmax"], eps)
+    sel = _sample(wl["theta"], wl["phi"], k, seed, wl["s"], wl["lmax"], eps, prec=prec)
     ref = O.direct_synthesis(wl["lmax"], wl["s"], wl["g"], wl["c"], wl["theta"][sel], wl["phi"][sel])
     got = f[torch.from_numpy(sel).cuda()].cpu().numpy().astype(np.complex128)
     err = O.rel_l2(got, ref)
@@ -89,7 +89,8 @@ def wide_lmax16384():
     from paper_2603_17166_gb300 import synthetic
 
     wl = synthetic.config5(frame="R")
-    sel = _sample(wl["theta"], wl["phi"], 16, 51, 2, 16384, 1e-10, k_each=2)
+    sel = np.unique(np.concatenate([_sample(wl["theta"], wl["phi"], 16, 51, 2, 16384, 1e-10, k_each=2),
+                                    _sample(wl["theta"], wl["phi"], 0, 52, 2, 16384, 1e-5, k_each=1, prec="fp32")]))
     ref = O.direct_synthesis(wl["lmax"], wl["s"], wl["g"], wl["c"], wl["theta"][sel], wl["phi"][sel])
     return wl, sel, ref
 

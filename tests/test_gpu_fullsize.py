@@ -54,7 +54,8 @@ def test_synthesis_sampled_points(planned, workload):
     # add the extreme points (pole side and cap edge), the smallest and largest phi, and points whose
     # ES window starts on a grid tile's first or last row or column
     P = O.plan_params(4096, 2, eps, workload["theta"])
-    sel = np.unique(np.concatenate([sel, PP.border_sample(P, workload["theta"], workload["phi"])]))
+    prec = "fp32" if plan.precision == 32 else "fp64"
+    sel = np.unique(np.concatenate([sel, PP.border_sample(P, workload["theta"], workload["phi"], prec=prec)]))
     ref = O.direct_synthesis(4096, 2, workload["g"], workload["c"], workload["theta"][sel], workload["phi"][sel])
     got = f[torch.from_numpy(sel).cuda()].cpu().numpy().astype(np.complex128)
     assert O.rel_l2(got, ref) <= 10 * eps

@@ -28,12 +28,12 @@ def _cap(rng, n, radius, pole="N"):
     return th, rng.uniform(-math.pi, 3 * math.pi, n)
 
 
-def _cap_with_borders(rng, n, radius, pole, lmax, s, eps):
+def _cap_with_borders(rng, n, radius, pole, lmax, s, eps, prec):
     """Random cap points plus points on the tile borders, the phi wrap-around, the pole and the cap
     edge of the plan those points lead to (the added points leave every plan parameter as it is)."""
     th, ph = _cap(rng, n, radius, pole)
     P = O.plan_params(lmax, s, eps, th)
-    tb, pb = PP.border_points(P, rng)
+    tb, pb = PP.border_points(P, rng, prec)
     return np.concatenate([th, tb]), np.concatenate([ph, pb])
 
 
@@ -100,7 +100,7 @@ def test_ring_coefficients_stage_parity(lmax, s, radius, pole, eps, prec):
 @pytest.mark.parametrize("lmax,s,radius,pole,eps,prec", CASES)
 def test_synthesis_against_direct_sum(lmax, s, radius, pole, eps, prec):
     rng = np.random.default_rng(3)
-    th, ph = _cap_with_borders(rng, 4000, radius, pole, lmax, s, eps)
+    th, ph = _cap_with_borders(rng, 4000, radius, pole, lmax, s, eps, prec)
     g, c = _alm(rng, lmax, s), (_alm(rng, lmax, s) if s else None)
     plan = _plan(s, lmax, th, ph, eps, prec)
     f = plan.synthesis(_cu(g, plan), _cu(c, plan)).cpu().numpy()
@@ -118,7 +118,7 @@ def test_synthesis_against_direct_sum(lmax, s, radius, pole, eps, prec):
 @pytest.mark.parametrize("lmax,s,radius,pole,eps,prec", CASES)
 def test_adjoint_against_direct_sum(lmax, s, radius, pole, eps, prec):
     rng = np.random.default_rng(4)
-    th, ph = _cap_with_borders(rng, 4000, radius, pole, lmax, s, eps)
+    th, ph = _cap_with_borders(rng, 4000, radius, pole, lmax, s, eps, prec)
     g, c = _alm(rng, lmax, s), _alm(rng, lmax, s)
     plan = _plan(s, lmax, th, ph, eps, prec)
     f = O.direct_synthesis(lmax, s, g, c, th, ph)      # f = A a: the adjoint's accuracy target
@@ -325,7 +325,7 @@ def test_one_shot_calls_with_the_papers_argument_list(eps, cd):
 
     rng = np.random.default_rng(44)
     lmax, s = 80, 2
-    th, ph = _cap_with_borders(rng, 3000, 0.4, "S", lmax, s, eps)
+    th, ph = _cap_with_borders(rng, 3000, 0.4, "S", lmax, s, eps, "fp32" if eps >= 1e-5 else "fp64")
     g, c = _alm(rng, lmax, s), _alm(rng, lmax, s)
     tt, pt = torch.from_numpy(th).cuda(), torch.from_numpy(ph).cuda()
     f = psht.synthesis(torch.from_numpy(g).cuda(), torch.from_numpy(c).cuda(), s, lmax, tt, pt, eps)
@@ -340,3 +340,47 @@ def test_one_shot_calls_with_the_papers_argument_list(eps, cd):
     wgt = np.tile(np.where(m == 0, 1.0, 2.0), 2)
     got = np.concatenate([gt.cpu().numpy(), ct.cpu().numpy()]).astype(np.complex128)
     assert O.rel_l2(got, np.concatenate([g1, c1]), wgt) <= 10 * eps
+
+
+@pytest.mark.parametrize("lmax,s,prec,eps,pole", [(40, 1, "fp64", 1e-10, "N"), (48, 2, "fp64", 1e-9, "S"),
+                                                   (40, 2, "fp32", 1e-5, "N"), (48, 0, "fp32", 1e-5, "S"),
+                                                   (48, 3, "fp64", 1e-10, "N")])
+def test_full_sky_mirror_pairs(lmax, s, prec, eps, pole):
+    """Full-sky plans evaluate the rings at b and pi - b as pairs sharing their Wigner columns
+    (d^l_{m,-s}(pi - b) = (-1)^(l+m) d^l_{m,s}(b)).  lmax 40 has an equator ring (its own mirror),
+    lmax 48 has none; odd spins check the signs.  Ring coefficients against the oracle's ring
+    synthesis, synthesis and adjoint against the direct sums, and the adjoint identity."""
+    from paper_2603_17166_gb300 import Plan
+
+    rng = np.random.default_rng(lmax + 10 * s)
+    th, ph = _cap(rng, 3000, 0.6, pole)
+    g, c = _alm(rng, lmax, s), (_alm(rng, lmax, s) if s else None)
+    plan = Plan(s, lmax, torch.from_numpy(th).cuda(), torch.from_numpy(ph).cuda(), eps, precision=prec,
+                full_sky=True)
+    i = plan.info
+    assert i["full_sky"] == 1 and i["nring"] == i["L"] + 1
+    tj, _, _ = plan.rings()
+    F = plan.ring_coeffs(_cu(g, plan), _cu(c, plan)).cpu().numpy().astype(np.complex128)
+    Fo = O.ring_synthesis(lmax, s, i["M"], g, c, tj)
+    assert O.rel_l2(F, Fo) < (1e-12 if prec == "fp64" else 2e-5)
+    # rings past the equator, each against the oracle alone
+    for j in (i["nring"] - 1, i["nring"] - 2, i["nring"] // 2 + 1):
+        assert O.rel_l2(F[j], Fo[j]) < (1e-11 if prec == "fp64" else 1e-4), j
+    f = plan.synthesis(_cu(g, plan), _cu(c, plan)).cpu().numpy().astype(np.complex128)
+    ref = O.direct_synthesis(lmax, s, g, c, th, ph)
+    assert O.rel_l2(f, ref) <= 10 * eps
+    gt, ct = plan.adjoint(_cu(ref, plan))
+    g1, c1 = O.direct_adjoint(lmax, s, th, ph, ref)
+    _, m = O.lm_of_index(lmax)
+    wgt = np.tile(np.where(m == 0, 1.0, 2.0), 2)
+    got = np.concatenate([gt.cpu().numpy(), ct.cpu().numpy()]).astype(np.complex128)
+    assert O.rel_l2(got, np.concatenate([g1, c1]), wgt) <= 10 * eps
+    fr = rng.standard_normal(th.size) + 1j * rng.standard_normal(th.size)
+    gr, cr = plan.adjoint(_cu(fr, plan))
+    gg = _alm(rng, lmax, s)
+    cc = _alm(rng, lmax, s)
+    Aa = plan.synthesis(_cu(gg, plan), _cu(cc, plan)).cpu().numpy().astype(np.complex128)
+    lhs = O.map_dot(fr, Aa)
+    rhs = O.alm_dot(gr.cpu().numpy().astype(np.complex128), gg, lmax) + \
+        O.alm_dot(cr.cpu().numpy().astype(np.complex128), cc, lmax)
+    assert abs(lhs - rhs) <= (1e-12 if prec == "fp64" else 1e-5) * abs(lhs)

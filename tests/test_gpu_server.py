@@ -84,7 +84,9 @@ def test_mix_matches_alone():
             _close(out, ref, fields[i])
     assert st["completed"] == 20 and st["failed"] == 0
     assert st["plans_created"] == len({i for i, _ in reqs})
-    assert st["cache_hits"] == 20 - st["plans_created"]
+    # every plan call either built its plan or found it cached; a batch of k requests is one call
+    assert st["batches"] == st["plans_created"] + st["cache_hits"]
+    assert sum(1.0 / r["batch"] for r, _ in res) == pytest.approx(st["batches"])
     assert len({r["worker"] for r, _ in res}) > 1
 
 
@@ -162,3 +164,40 @@ def test_reused_key_with_other_point_count_gets_its_own_plan():
     _close(adj_small, adj_ref, small)
     # the larger set's own result is the head of nothing in particular: only check it is finite
     assert torch.isfinite(torch.view_as_real(out_big[0])).all()
+
+
+def test_queued_requests_on_one_plan_run_batched():
+    """Requests for one plan and operation that queue up while the plan is busy join the next call as
+    a batch (continuous batching); each result equals the same request run alone."""
+    from paper_2603_17166_gb300 import Server
+
+    fd = _fields(1, seed=7)[0]
+    gen = np.random.default_rng(10)
+    gs = [torch.from_numpy(np.ascontiguousarray(
+        (gen.standard_normal(fd["na"]) + 1j * gen.standard_normal(fd["na"])))).cuda().to(fd["cd"])
+          for _ in range(6)]
+    for g in gs:
+        g[: fd["lmax"] + 1] = g[: fd["lmax"] + 1].real.to(fd["cd"])
+    srv1 = Server(nstreams=1)
+    alone = []
+    for g in gs:
+        f = dict(fd)
+        f["g"] = g
+        t, out = _submit(srv1, f, 0)
+        assert srv1.wait(t)["status"] == 0
+        alone.append(out[0])
+    srv1.close()
+    srv = Server(nstreams=1)
+    pend = []
+    for g in gs:  # submitted back to back: the first runs, the others queue behind it
+        f = dict(fd)
+        f["g"] = g
+        pend.append(_submit(srv, f, 0))
+    res = [(srv.wait(t), out) for t, out in pend]
+    st = srv.stats()
+    srv.close()
+    assert all(r["status"] == 0 for r, _ in res)
+    assert max(r["batch"] for r, _ in res) > 1
+    assert st["batched_requests"] >= 2 and st["batches"] < len(gs)
+    for (r, out), ref in zip(res, alone):
+        assert torch.equal(out[0], ref)
