@@ -163,10 +163,10 @@ STAGE_KERNELS = {
     "theta_synthesis": {"fp32": "k_theta_syn", "fp64": "k_theta_syn"},
     "phi_synthesis": {"fp32": "k_phi_syn", "fp64": "k_phi_syn"},
     "gather": {"fp32": "k_gather", "fp64": "k_gather"},
-    "scatter": {"fp32": "k_scatter", "fp64": "k_scatter"},
+    "scatter": {"fp32": "k_scatter_rows", "fp64": "k_scatter"},
     "phi_adjoint": {"fp32": "k_phi_adj", "fp64": "k_phi_adj"},
     "theta_adjoint": {"fp32": "k_theta_adj", "fp64": "k_theta_adj"},
-    "rec_adjoint": {"fp32": "k_rec_adj_w + k_adj_reduce", "fp64": "k_rec_adj"},
+    "rec_adjoint": {"fp32": "k_rec_adj_w", "fp64": "k_rec_adj"},
 }
 
 
@@ -176,9 +176,11 @@ def stage_rooflines(info: dict, stage_ms: dict, form: str, spin: int) -> dict:
       Theta stages: ring coefficients (nring x (2M+1)) and kept rows (nrows x (2M+1)), complex;
       phi stages: kept rows (nrows x (2M+1)) and grid rows (nrows x nphi), complex;
       gather / scatter: per point its coordinates (theta, phi: 16 B) and value (one complex), plus
-      the grid rows once (nrows x nphi complex); in the FP64 form also 5 W^2 flops per point (W^2
-      complex-by-real multiply-adds of 4 flops and the W^2 weight products) against the FP64 peak,
-      which bounds those kernels there (an FP64 exp or FMA costs 1/64 of the FP32 rate on this part).
+      the grid rows once (nrows x nphi complex); in the FP64 form also the separable kernel's flops
+      per point against the FP64 peak, which bounds those kernels there (an FP64 FMA costs 1/64 of
+      the FP32 rate on this part): gather 4 W^2 + 4 W (a complex-by-real multiply-add per cell, then
+      one per window row), scatter 4 W^2 + 2 W (a complex-by-real product per window row, then a
+      multiply-add per cell).
     Returns {stage: {...}} with ms per launch, bound, achieved, peak, unit, frac."""
     cb = 16 if form == "fp64" else 8
     ncols = 2 * info["M"] + 1
@@ -209,7 +211,8 @@ def stage_rooflines(info: dict, stage_ms: dict, form: str, spin: int) -> dict:
             ach = w / (ms * 1e-3) / 1e9
             e.update(bytes=w, achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm, peak_note=hbm_note)
         if form == "fp64" and st in ("gather", "scatter"):
-            fl = 5.0 * info["W"] ** 2 * info["npts"]
+            W = info["W"]
+            fl = (4.0 * W * W + (4.0 if st == "gather" else 2.0) * W) * info["npts"]
             a2 = fl / (ms * 1e-3) / 1e12
             e["alu"] = dict(flops=fl, achieved=a2, peak=alu, unit="TFLOP/s", frac=a2 / alu, peak_note=alu_note)
         out[st] = e

@@ -152,15 +152,17 @@ struct Dft<7, INV, V> {
 };
 
 // ---------------------------------------------------------------------------------------------
-// Shared-memory FFT buffer with one pad element after every 16: the butterflies of the late DIF
-// (early DIT) stages read with power-of-two strides, which would put a warp's lanes on a few
-// banks; with the pad the strides 2, 4, 8 and 16 spread over all of them.
+// Shared-memory FFT buffer with one pad element after every 32: the butterflies of the late DIF
+// (early DIT) stages read with power-of-two strides, which put a warp's lanes on a few banks
+// (stride 8 or 16: 8- to 16-way conflicts); with the pad those strides cost at most two ways,
+// while the stride-1 accesses of the early stages stay on whole 256-byte rows (a pad after
+// every 16 measured more conflicts in total: it splits those rows).
 template <typename V>
 struct PadBuf {
   V* p;
-  __device__ __forceinline__ V& operator[](int i) const { return p[i + (i >> 4)]; }
+  __device__ __forceinline__ V& operator[](int i) const { return p[i + (i >> 5)]; }
 };
-__host__ __device__ constexpr int padded_len(int n) { return n + (n >> 4) + 1; }
+__host__ __device__ constexpr int padded_len(int n) { return n + (n >> 5) + 1; }
 
 // Twiddle e^{-2 pi i t/N}.  FP64: a full table tw[t].  FP32: the product of two short tables,
 // tw[t mod 64] e^{-2 pi i 64 floor(t/64)/N} = tw[t & 63] tw[64 + (t >> 6)] (64 + N/64 + 1 entries),

@@ -20,8 +20,8 @@ namespace {
 
 constexpr int kFftThreads = 512;
 // longest transforms held in one CTA's shared memory (227 KiB) with the padded layout (PadBuf)
-constexpr int kMaxLenF64 = 13600;  // complex128
-constexpr int kMaxLenF32 = 27200;  // complex64
+constexpr int kMaxLenF64 = 14000;  // complex128
+constexpr int kMaxLenF32 = 28000;  // complex64
 // |n| <= L-1 values held per thread while the buffer is re-laid out (2L <= max length / 2)
 // threads of the Theta kernels per launch mode (see k_theta_syn)
 __host__ __device__ constexpr int theta_threads(int mode) { return mode == 1 ? 256 : kFftThreads; }

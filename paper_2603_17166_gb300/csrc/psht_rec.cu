@@ -63,8 +63,8 @@ struct Cx4<float> {
 __device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
 
-// One record of the recurrence table per packed (l, m), so that a chunk of 64 l is one contiguous
-// bulk copy and one l is a few vector shared-memory loads.  The FP32 form works on pairs of rings
+// One record of the recurrence table per packed (l, m), so that a chunk of l values is one
+// contiguous bulk copy and one l is a few vector shared-memory loads.  The FP32 form works on pairs of rings
 // with packed FP32x2 instructions, so its record holds every coefficient twice (one per ring of
 // the pair) and A negated: the packed operands come straight from shared memory.
 template <typename T>
@@ -1237,6 +1237,7 @@ __global__ void __launch_bounds__(32, NS == 1 ? (MIR ? 16 : (RPT >= 8 ? 16 : 20)
   const int rr = lane & 7, cg = lane >> 3;  // flush: row and column quarter of this lane
 
   bool failed = false;
+  bool blk_any = false;  // a quad of the current 8-l block had summing columns (warp-uniform)
   for (int ch = 0; ch < nchunk; ++ch) {
     const int sidx = ch % NST;
     const bool ok = mbar_wait(&bar[sidx], (uint32_t)((ch / NST) & 1));
@@ -1255,6 +1256,7 @@ __global__ void __launch_bounds__(32, NS == 1 ? (MIR ? 16 : (RPT >= 8 ? 16 : 20)
     for (int q = 0; q < nq; ++q) {
       bool fast, skip;
       classify<float, SPIN, RPT>(S, nr_w, fast, skip);
+      blk_any = blk_any || !skip;
       const int row0 = (q & 1) * 4;
       if (skip) {
         adj_quad_steps<SPIN, RPT>(S, st, 4 * q, nr_w);
@@ -1277,7 +1279,19 @@ __global__ void __launch_bounds__(32, NS == 1 ? (MIR ? 16 : (RPT >= 8 ? 16 : 20)
         adj_quad_rows<SPIN, RPT, true, NS>(S, fin, st, 4 * q, nr_w, red, row0, lane);
         rescale_all<float, SPIN, RPT>(S, nr_w);
       }
-      if ((q & 1) || q == nq - 1) {  // flush rows 0 .. 8 (or 4) of red: l = l0 + li0 + 4 (q & ~1) + row
+      if (((q & 1) || q == nq - 1) && !blk_any) {
+        // every column of the block still below the working range: the sums are zero (single-item
+        // orders write the zero projection, the others have nothing to add)
+        const int li = li0 + 4 * (q & ~1) + lane;
+        if (direct && lane < ((q & 1) ? 8 : 4) && li < nl) {
+#pragma unroll
+          for (int k = 0; k < NS; ++k) {
+            sets.gt[k][base + sd.l0 + li] = z;
+            if (sets.ct[k]) sets.ct[k][base + sd.l0 + li] = z;
+          }
+        }
+      } else if ((q & 1) || q == nq - 1) {  // flush rows 0 .. 8 (or 4) of red: l = l0 + li0 + 4 (q & ~1) + row
+        blk_any = false;
         __syncwarp();
         const int li = li0 + 4 * (q & ~1) + lane;
         const bool out = lane < ((q & 1) ? 8 : 4) && li < nl;
@@ -1556,7 +1570,7 @@ void build_rec_table(Plan& p, cudaStream_t st) {
 
 void launch_rec_synthesis_sets(Plan& p, int nsets, const void* const* g, const void* const* c, void* const* F,
                                cudaStream_t st, double msc) {
-  if (p.nitems == 0 || nsets <= 0) return;
+  if ((p.nitems == 0 && p.nmitems == 0) || nsets <= 0) return;  // full-sky plans may hold mirror items only
   if (p.prec == 64) {
     if (p.spin) launch_syn_s<double, true>(p, nsets, g, c, F, msc, st);
     else launch_syn_s<double, false>(p, nsets, g, c, F, msc, st);

@@ -278,7 +278,8 @@ def serving_workload(n_fields: int = 8, n_requests: int = 200, nmax: int = 30_00
     sequence over it.  Per field: lmax from {1024, 2048, 4096, 8192} (capped at lmax_max; field i
     takes the (i mod 4)-th value, so that a pool of 4 or more fields holds every lmax), spin 0 or
     2, cap (centre dec U[-90, -30]) or RA/dec box 50/50, sky fraction log-uniform on [0.1 %, 4 %],
-    N log-uniform on [1e5, nmax], eps from {1e-5 (FP32 form), 1e-8, 1e-10}.  Requests: field
+    N log-uniform on [1e5, nmax], eps from {1e-5 (FP32 form), 1e-8, 1e-10} (field i takes the
+    (i mod 3)-th, so that every form is in a pool of 3 or more fields).  Requests: field
     uniform over the pool, synthesis or adjoint 50/50, unit-rate Poisson arrival times (scale them
     by 1/lambda).  a_lm and point data are drawn per field."""
     gq = rng(4, "stream", 1)  # field parameters
@@ -294,7 +295,7 @@ def serving_workload(n_fields: int = 8, n_requests: int = 200, nmax: int = 30_00
         dec_c = float(gq.uniform(-90.0, -30.0))
         fsky = float(math.exp(gq.uniform(math.log(1e-3), math.log(4e-2))))
         n = int(math.exp(gq.uniform(math.log(1e5), math.log(nmax))))
-        eps = float(gq.choice(SERVING_EPS))
+        eps = float(SERVING_EPS[i % len(SERVING_EPS)])
         th, ph = patch_points(n, shape, dec_c, fsky, gp)
         g = gaussian_alm(lmax, s, ga, "inv_l2")
         c = gaussian_alm(lmax, s, ga, "inv_l2") if s else None
