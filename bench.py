@@ -153,9 +153,14 @@ def hbm_peak():
     return 6800.0, "of fallback (6.8 TB/s, one earlier GB300 measurement)"
 
 
-# DRAM bytes (read + write) per launch of the dominant kernel, from an ncu capture of the current
-# kernel (profiles/); None where no capture of the current kernel exists.
-KERNEL_TRAFFIC = {}
+# DRAM bytes (read + write) per launch of a stage's kernel, from an ncu capture of the current
+# kernel (profiles/k_rec_fp32_spin2_lmax4096.md, profiles/fp64_kernels_spin2_lmax4096.md; the
+# recursion's size does not depend on the point count); None where no capture of the current
+# kernel exists.
+KERNEL_TRAFFIC = {("fp32", "rec_adjoint"): 535.763712e6 + 229.814272e6,
+                  ("fp32", "rec_synthesis"): 472.998144e6 + 22.789120e6,
+                  ("fp64", "rec_adjoint"): 416.974592e6 + 221.827328e6,
+                  ("fp64", "rec_synthesis"): 614.166528e6 + 50.765568e6}
 
 # kernel names of each stage per form (the launch list in profiles/ has them all)
 STAGE_KERNELS = {
@@ -695,6 +700,11 @@ def run_serving(args, dev) -> dict:
         wall = time.perf_counter() - start
         pts = sum(fields[r["field"]]["npts"] for r, x in zip(reqs, res) if x["status"] == 0)
         bad = sum(1 for x in res if x["status"] != 0)
+        failures = {}
+        for x in res:
+            if x["status"] != 0:
+                key = f'{x["status"]}: {x.get("message", "")}'
+                failures[key] = failures.get(key, 0) + 1
         lat = np.array([x["total_ms"] for x in res])
         slow = np.array([x["total_ms"] / alone[(r["field"], r["op"])] for x, r in zip(res, reqs)])
         prec = np.array([x["precision"] for x in res])
@@ -708,7 +718,7 @@ def run_serving(args, dev) -> dict:
         runs.append(dict(load=load, lambda_rps=lam, p50_ms=float(np.percentile(lat, 50)),
                          p99_ms=float(np.percentile(lat, 99)), mean_ms=float(lat.mean()), max_ms=float(lat.max()),
                          p99_slowdown=float(np.percentile(slow, 99)), completed_rps=len(res) / wall,
-                         aggregate_mpts=pts / wall / 1e6, failed=bad, per_form=per_form,
+                         aggregate_mpts=pts / wall / 1e6, failed=bad, failures=failures, per_form=per_form,
                          mean_batch=float(bsz.mean()), batched_fraction=float(np.mean(bsz > 1))))
     st = srv.stats()
     srv.close()

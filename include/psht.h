@@ -401,6 +401,7 @@ typedef struct {
   double exec_ms;      /* transform, until its stream completed                                */
   double total_ms;     /* submission to completion                                             */
   int batch;           /* requests in the batched call this request ran in (1: alone)          */
+  char message[192];   /* on failure, the library's message for it ("" on success)             */
 } psht_result;
 typedef struct {
   int64_t submitted, completed, failed, plans_created, cache_hits, evictions;

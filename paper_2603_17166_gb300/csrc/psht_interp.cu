@@ -201,9 +201,8 @@ struct Weights<double, W> {
 };
 template <int W>
 struct Weights<float, W> {
-  __device__ __forceinline__ static void get(const double*, const float* pf, int64_t n, int64_t pt, float beta,
-                                             float* wr, float* wq) {
-    const float ft = pf[pt], fu = pf[n + pt];
+  // the kernel values of the W rows and W columns from the in-cell offsets t - r0 and u - q0
+  __device__ __forceinline__ static void from(float ft, float fu, float beta, float* wr, float* wq) {
     const float sc = 2.0f / W;
 #pragma unroll
     for (int a = 0; a < W; ++a) {
@@ -211,6 +210,10 @@ struct Weights<float, W> {
       wr[a] = __expf(beta * (sqrtf(fmaxf(0.0f, 1.0f - zr * zr)) - 1.0f));
       wq[a] = __expf(beta * (sqrtf(fmaxf(0.0f, 1.0f - zq * zq)) - 1.0f));
     }
+  }
+  __device__ __forceinline__ static void get(const double*, const float* pf, int64_t n, int64_t pt, float beta,
+                                             float* wr, float* wq) {
+    from(pf[pt], pf[n + pt], beta, wr, wq);
   }
 };
 
@@ -235,8 +238,16 @@ __global__ void __launch_bounds__(kInterpThreads) k_gather(const TileItem* __res
     tile[e] = (gr < nrows && gc < gstride) ? G[(int64_t)gr * gstride + gc] : mk((T)0, (T)0);
   }
   __syncthreads();
-  for (int pt = it.p0 + threadIdx.x; pt < it.p0 + it.np; pt += blockDim.x) {
-    const int cell = pcell[pt];
+  // the next point's cell and output index are loaded one iteration ahead of their use
+  const int pend = it.p0 + it.np;
+  int pt = it.p0 + threadIdx.x;
+  int cell_n = pt < pend ? pcell[pt] : 0, idx_n = pt < pend ? pidx[pt] : 0;
+  for (; pt < pend; pt += blockDim.x) {
+    const int cell = cell_n, idx = idx_n;
+    if (pt + (int)blockDim.x < pend) {
+      cell_n = pcell[pt + blockDim.x];
+      idx_n = pidx[pt + blockDim.x];
+    }
     const int lr = cell & 0xffff, lq = cell >> 16;
     T wr[W], wq[W];
     Weights<T, W>::get(pw, pf, npts, pt, beta, wr, wq);
@@ -254,7 +265,7 @@ __global__ void __launch_bounds__(kInterpThreads) k_gather(const TileItem* __res
       accr = fma(wr[a], rr, accr);
       acci = fma(wr[a], ri, acci);
     }
-    f[pidx[pt]] = mk(accr, acci);
+    f[idx] = mk(accr, acci);
   }
 }
 
@@ -383,18 +394,40 @@ __global__ void __launch_bounds__(kRowWarps * 32) k_scatter_rows(const int* __re
   for (int o = 16; o > 0; o >>= 1) cnt = max(cnt, __shfl_xor_sync(0xffffffffu, cnt, o));
   if (cnt == 0) return;  // no points in the tile
   float2* tw = reinterpret_cast<float2*>(smraw) + warp * COLS * kRowP;
-  for (int e = lane; e < COLS * kRowP; e += 32) tw[e] = make_float2(0.f, 0.f);
+  // per-point inputs loaded ahead of their use: the cell and offsets one step ahead, the value
+  // (a read at the caller's point order, so a random one) one step ahead with its index two
+  // steps ahead, so that no step waits on a dependent pair of loads
+  const float2 z = make_float2(0.f, 0.f);
+  int cell_n = 0, idx_nn = 0;
+  float ft_n = 0.f, fu_n = 0.f;
+  float2 fv_n = z;
+  if (s0 < s1) {
+    cell_n = pcell[s0];
+    ft_n = pf[s0];
+    fu_n = pf[npts + s0];
+    fv_n = f[pidx[s0]];
+  }
+  if (s0 + 1 < s1) idx_nn = pidx[s0 + 1];
+  for (int e = lane; e < COLS * kRowP; e += 32) tw[e] = z;
   __syncwarp();
   for (int k = 0; k < cnt; ++k) {
     const int pt = s0 + k;
     const bool on = pt < s1;
+    const int cell = cell_n;
+    const float ft = ft_n, fu = fu_n;
+    const float2 fv = fv_n;
+    if (pt + 1 < s1) {
+      cell_n = pcell[pt + 1];
+      ft_n = pf[pt + 1];
+      fu_n = pf[npts + pt + 1];
+      fv_n = f[idx_nn];
+    }
+    if (pt + 2 < s1) idx_nn = pidx[pt + 2];
     int lq = 0;
     float wr[W], wq[W];
-    float2 fv = make_float2(0.f, 0.f);
     if (on) {
-      lq = pcell[pt] >> 16;
-      Weights<float, W>::get(nullptr, pf, npts, pt, beta, wr, wq);
-      fv = f[pidx[pt]];
+      lq = cell >> 16;
+      Weights<float, W>::from(ft, fu, beta, wr, wq);
     }
     float2* col = tw + lq * kRowP + lane;
 #pragma unroll

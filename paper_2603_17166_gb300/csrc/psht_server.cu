@@ -116,11 +116,20 @@ struct Server {
     cv_work.notify_all();
   }
 
+  static void set_message(psht_result& r, int rc) {
+    r.message[0] = '\0';
+    if (rc != PSHT_OK) {
+      strncpy(r.message, psht_last_error(), sizeof(r.message) - 1);
+      r.message[sizeof(r.message) - 1] = '\0';
+    }
+  }
+
   void fail(const Job& j, int rc, int w) {
     psht_result res{};
     res.status = rc;
     res.worker = w;
     res.total_ms = ms_between(j.t_submit, Clock::now());
+    set_message(res, rc);
     finish(j, res);
   }
 
@@ -287,6 +296,7 @@ struct Server {
     res.exec_ms = ms_between(t1, t2);
     res.status = rc;
     res.batch = n;
+    set_message(res, rc);
     {
       std::lock_guard<std::mutex> g(mu);
       auto c = cache.find(k);

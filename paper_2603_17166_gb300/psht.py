@@ -58,6 +58,7 @@ class PshtResult(ctypes.Structure):
         ("status", ctypes.c_int), ("worker", ctypes.c_int), ("plan_cached", ctypes.c_int),
         ("precision", ctypes.c_int), ("queue_ms", ctypes.c_double), ("plan_ms", ctypes.c_double),
         ("exec_ms", ctypes.c_double), ("total_ms", ctypes.c_double), ("batch", ctypes.c_int),
+        ("message", ctypes.c_char * 192),
     ]
 
 
@@ -421,7 +422,9 @@ class Server:
         res = PshtResult()
         _check(lib().psht_server_wait(self._h, int(ticket), ctypes.byref(res)))
         self._keep.pop(ticket, None)
-        return {name: getattr(res, name) for name, _ in PshtResult._fields_}
+        out = {name: getattr(res, name) for name, _ in PshtResult._fields_}
+        out["message"] = res.message.decode(errors="replace")
+        return out
 
     def stats(self) -> dict:
         st = PshtServerStats()
