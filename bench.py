@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=300,
                     help="requests of each serving run (0: skip; the full recipe uses 1000)")
     ap.add_argument("--serve-fields", type=int, default=8)
+    ap.add_argument("--serve-saturation", type=int, default=120,
+                    help="requests submitted at once to measure saturation throughput, batched and not")
     ap.add_argument("--serve-streams", type=int, default=4)
     ap.add_argument("--serve-loads", default="0.5,0.8,1.0", help="offered loads, fractions of single-stream capacity")
     ap.add_argument("--serve-nmax", type=int, default=30_000_000)
@@ -720,11 +722,29 @@ def run_serving(args, dev) -> dict:
                          p99_slowdown=float(np.percentile(slow, 99)), completed_rps=len(res) / wall,
                          aggregate_mpts=pts / wall / 1e6, failed=bad, failures=failures, per_form=per_form,
                          mean_batch=float(bsz.mean()), batched_fraction=float(np.mean(bsz > 1))))
+    # saturation: the first requests all submitted at once, with the server's batching and with
+    # batches of one, so that the gain of the batched recursion passes shows on the same mix
+    saturation = {}
+    nsat = min(len(reqs), args.serve_saturation)
+    for label, mb in (("batched", 8), ("unbatched", 1)):
+        if nsat == 0:
+            break
+        srv.set_batch_limit(mb)
+        start = time.perf_counter()
+        tickets = [submit(r["field"], r["op"]) for r in reqs[:nsat]]
+        res = [srv.wait(t) for t in tickets]
+        wall = time.perf_counter() - start
+        pts = sum(fields[r["field"]]["npts"] for r, x in zip(reqs[:nsat], res) if x["status"] == 0)
+        saturation[label] = dict(requests=nsat, wall_s=wall, aggregate_mpts=pts / wall / 1e6,
+                                 completed_rps=nsat / wall, failed=sum(1 for x in res if x["status"] != 0),
+                                 mean_batch=float(np.mean([x.get("batch", 1) for x in res])))
+    srv.set_batch_limit(8)
     st = srv.stats()
     srv.close()
     head = min(runs, key=lambda x: abs(x["load"] - 0.8))
     return dict(p99_ms=head["p99_ms"], p50_ms=head["p50_ms"], load=head["load"],
                 aggregate_mpts=head["aggregate_mpts"], requests=len(reqs), per_form=head["per_form"],
+                saturation=saturation,
                 batches=st["batches"], batched_requests=st["batched_requests"],
                 fields=len(fields), streams=args.serve_streams, capacity_rps=capacity,
                 mean_service_ms=mean_service, plan_ms_mean=float(np.mean(plan_ms)) if plan_ms else None,

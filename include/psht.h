@@ -412,6 +412,9 @@ typedef struct {
 
 /* Start nstreams (1..64) workers on the current device.  *out receives the server. */
 int psht_server_create(int nstreams, size_t budget_bytes, psht_server** out);
+/* Largest batch the workers form (1..8, default 8; 1 runs every request alone).  Takes effect for
+ * requests started after the call. */
+int psht_server_set_batch_limit(psht_server* server, int max_batch);
 /* Queue a request (copied); *ticket identifies it for psht_server_wait. */
 int psht_server_submit(psht_server* server, const psht_request* request, int64_t* ticket);
 /* Block until the ticket's request has finished; writes its result.  Each ticket is waited once. */

@@ -36,6 +36,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include "psht_common.cuh"
 
 namespace psht {
@@ -506,19 +508,32 @@ __device__ __forceinline__ void rescale_all(Cols<T, RPT>& S, int nr) {
   }
 }
 
-// warp-uniform classification of the warp's columns: all summing / all still dropped
+// warp-uniform classification of the warp's columns: all summing / all still dropped.  vm: bit r
+// set when slot r of this lane holds a ring; empty slots (zero values, zero counts) count as
+// summing for the first test and are left out of the second, so that a part-filled warp still
+// skips the sums while all of its rings are below the working range
 template <typename T, bool SPIN, int RPT>
-__device__ __forceinline__ void classify(const Cols<T, RPT>& S, int nr, bool& fast, bool& skip) {
+__device__ __forceinline__ void classify(const Cols<T, RPT>& S, int nr, unsigned vm, bool& fast, bool& skip) {
   bool in2 = true, in1 = true;
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
     if (r < nr) {
       in2 = in2 && S.k1[r] == 0 && S.k2[r] == 0;
-      in1 = in1 && S.k1[r] > 0 && (!SPIN || S.k2[r] > 0);
+      if ((vm >> r) & 1u) in1 = in1 && S.k1[r] > 0 && (!SPIN || S.k2[r] > 0);
     }
   }
   fast = __all_sync(0xffffffffu, in2);
   skip = !fast && __all_sync(0xffffffffu, in1);
+}
+
+// slots of this lane that hold rings (ring r * 32 + lane < n), as the bit mask classify takes
+template <int RPT>
+__device__ __forceinline__ unsigned slot_mask(int n, int lane) {
+  unsigned vm = 0;
+#pragma unroll
+  for (int r = 0; r < RPT; ++r)
+    if (r * 32 + lane < n) vm |= 1u << r;
+  return vm;
 }
 
 // warp w of nw takes 32-ring slots [s0, s1) of the ceil(n/32) slots: first ring wbase, wcnt rings
@@ -554,6 +569,78 @@ __device__ __forceinline__ void init_col(Cols<T, RPT>& S, const RingDev* __restr
   S.D2(r) = S.E2(r);
 }
 
+// FP32 ring slots of a work item from the plan's start states (st, kk at the item's first entry):
+// 1 - x from the ring table, the two columns, their differences and scale counts at the item's
+// first working l (empty slots: zero values, zero counts, as init_col leaves them)
+template <bool SPIN, int RPT>
+__device__ __forceinline__ void load_start(Cols<float, RPT>& S, const RingDev* __restrict__ rings,
+                                           const float4* __restrict__ st, const int* __restrict__ kk, int jfirst,
+                                           int nj, int lane) {
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const int jj = r * 32 + lane;
+    if (jj < nj) {
+      const RingDev& rg = rings[jfirst + jj];
+      S.OH(r) = rg.ohi;
+      S.OL(r) = rg.olo;
+    } else {
+      S.OH(r) = S.OL(r) = 0.f;
+    }
+    const float4 v = st[jj];
+    const int k = kk[jj];
+    S.E1(r) = v.x;
+    S.D1(r) = v.y;
+    S.E2(r) = SPIN ? v.z : 0.f;
+    S.D2(r) = SPIN ? v.w : 0.f;
+    S.k1[r] = k & 0xffff;
+    S.k2[r] = SPIN ? (k >> 16) : 0;
+  }
+}
+
+// Start states of FP32 work items (plan time, one warp per item).  From the seeds at l0 the warp
+// takes quads of 4 steps, with the arithmetic and the rescaling of the kernels' quads, while every
+// column of its rings is still below the working range (empty slots do not count), and records the
+// state at the first quad that has a working column.  Starting there, a kernel computes exactly
+// what it would have computed from l0: the quads before it add nothing to any sum.  The quads read
+// table records up to l + 3 <= lmax + 3, inside the table's zero padding.
+template <bool SPIN, int RPT, typename Item>
+__global__ void __launch_bounds__(32) k_rec_start(const Item* __restrict__ items, const RingDev* __restrict__ rings,
+                                                  const MSeed* __restrict__ mseed,
+                                                  const TabEntry<float>* __restrict__ tab, int lmax, RecStart out) {
+  const Item it = items[blockIdx.x];
+  const int lane = threadIdx.x;
+  const MSeed sd = mseed[it.m];
+  const int nr_w = (it.nj + 31) >> 5;
+  Cols<float, RPT> S;
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) init_col<float, SPIN, RPT>(S, rings, sd, it.j0, r * 32 + lane, it.nj, r);
+  const TabEntry<float>* tv = tab + alm_base(lmax, it.m);
+  int l = sd.l0;
+  while (l <= lmax) {
+    bool dropped = true;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r)
+      if (r < nr_w && r * 32 + lane < it.nj) dropped = dropped && S.k1[r] > 0 && (!SPIN || S.k2[r] > 0);
+    if (!__all_sync(0xffffffffu, dropped)) break;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const TabEntry<float> cf = tv[l + u];
+#pragma unroll
+      for (int p = 0; p < RPT / 2; ++p)
+        if (2 * p < nr_w) step_pair<SPIN, RPT>(S, p, cf);
+    }
+    rescale_all<float, SPIN, RPT>(S, nr_w);
+    l += 4;
+  }
+  if (lane == 0) out.ls[blockIdx.x] = l;
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const int64_t idx = ((int64_t)blockIdx.x * RPT + r) * 32 + lane;
+    out.st[idx] = make_float4(S.E1(r), S.D1(r), S.E2(r), S.D2(r));
+    out.kk[idx] = S.k1[r] | (S.k2[r] << 16);
+  }
+}
+
 // ---------------------------------------------------------------------------------------------
 // a_lm and ring-coefficient pointers of the NS sets of one synthesis launch (c may be null)
 template <typename T, int NS>
@@ -579,7 +666,9 @@ template <typename T, bool SPIN, int RPT, int CH, int NST, int NS, bool MIR>
 __global__ void __launch_bounds__(32) k_rec_syn_w(const RecItem* __restrict__ items, const RingDev* __restrict__ rings,
                                                   const MSeed* __restrict__ mseed, const TabEntry<T>* __restrict__ tab,
                                                   const SynSets<T, NS> sets, int lmax, int s, T msc, int Lpad,
-                                                  int* __restrict__ status, double omx_tb, int jm) {
+                                                  int* __restrict__ status, double omx_tb, int jm,
+                                                  const int* __restrict__ sls, const float4* __restrict__ sst,
+                                                  const int* __restrict__ skk) {
   static_assert(CH == 32, "one l per lane and chunk");
   static_assert(!MIR || NS == 1, "mirror pairs take one a_lm set");
   constexpr int NI = MIR ? 2 : NS;  // internal sets: the a_lm sets, or a ring and its mirror
@@ -594,18 +683,28 @@ __global__ void __launch_bounds__(32) k_rec_syn_w(const RecItem* __restrict__ it
   constexpr int pqs = NST * CH;  // set stride of sPQ
   const int lane = threadIdx.x;
   const int nr_w = (it.nj + 31) >> 5;
+  const unsigned vm = slot_mask<RPT>(it.nj, lane);
   Cols<T, RPT> S;
   SynAcc<T, RPT> A[NI];
 #pragma unroll
   for (int k = 0; k < NI; ++k) A[k].zero();
+  // first l of the recursion: the FP32 form starts at the item's first working l (plan start
+  // states), the FP64 form at l0 from the seeds
+  int lb = sd.l0;
+  if constexpr (sizeof(T) == 4) {
+    const int64_t so = (int64_t)blockIdx.x * RPT * 32;
+    load_start<SPIN, RPT>(S, rings, sst + so, skk + so, it.j0, it.nj, lane);
+    lb = sls[blockIdx.x];
+  } else {
 #pragma unroll
-  for (int r = 0; r < RPT; ++r) init_col<T, SPIN, RPT>(S, rings, sd, it.j0, r * 32 + lane, it.nj, r);
+    for (int r = 0; r < RPT; ++r) init_col<T, SPIN, RPT>(S, rings, sd, it.j0, r * 32 + lane, it.nj, r);
+  }
   // slots r with r * 32 + lane < nj hold rings
   const bool tb = three_term_setup<T, RPT>(S, lane < it.nj ? (it.nj - lane + 31) / 32 : 0, omx_tb);
   const int64_t base = alm_base(lmax, m);
   const bool rf = !MIR && it.refl != 0;
   const bool m0 = (m == 0);
-  const int nchunk = (lmax - sd.l0 + CH) / CH;
+  const int nchunk = max(0, (lmax - lb + CH) / CH);
   const V z = mk((T)0, (T)0);
   // internal set q: its a_lm set and whether its rings take the reflected combination
   const auto set_of = [&](int q) { return MIR ? 0 : q; };
@@ -617,9 +716,9 @@ __global__ void __launch_bounds__(32) k_rec_syn_w(const RecItem* __restrict__ it
   }
   __syncwarp();
   if (lane == 0)
-    for (int k = 0; k < NST && k < nchunk; ++k) issue_chunk<T, CH>(stg[k], &bar[k], tab, base + sd.l0 + k * CH);
+    for (int k = 0; k < NST && k < nchunk; ++k) issue_chunk<T, CH>(stg[k], &bar[k], tab, base + lb + k * CH);
   for (int k = 0; k < NST && k < nchunk; ++k) {
-    const int l = sd.l0 + k * CH + lane;
+    const int l = lb + k * CH + lane;
 #pragma unroll
     for (int q = 0; q < NI; ++q) {
       V P = z, Q = z;
@@ -631,7 +730,7 @@ __global__ void __launch_bounds__(32) k_rec_syn_w(const RecItem* __restrict__ it
   }
   V pg[NS], pc[NS];  // a_lm of chunk NST (the next to be staged)
   {
-    const int l = sd.l0 + NST * CH + lane;
+    const int l = lb + NST * CH + lane;
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
       pg[q] = pc[q] = z;
@@ -654,14 +753,14 @@ __global__ void __launch_bounds__(32) k_rec_syn_w(const RecItem* __restrict__ it
       }
       return;
     }
-    const int lc = sd.l0 + ch * CH;
+    const int lc = lb + ch * CH;
     const int nq = (min(CH, lmax - lc + 1) + 3) >> 2;
     if (nr_w > 0) {
       const TabEntry<T>* st = stg[sidx].v;
       const PQV* PQ = &sPQ[0][sidx][0];
       for (int q = 0; q < nq; ++q) {
         bool fast, skip;
-        classify<T, SPIN, RPT>(S, nr_w, fast, skip);
+        classify<T, SPIN, RPT>(S, nr_w, vm, fast, skip);
         if (fast) {
           if (nr_w >= RPT) syn_quad_d<SPIN, RPT, true, false, NI>(tb, S, A, st, 4 * q, PQ, pqs, RPT);
           else syn_quad_d<SPIN, RPT, true, false, NI>(tb, S, A, st, 4 * q, PQ, pqs, nr_w);
@@ -929,6 +1028,7 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
     }
   }
   const bool tb = three_term_setup<T, RPT>(S, lane < wcnt ? (wcnt - lane + 31) / 32 : 0, omx_tb);
+  const unsigned vm = slot_mask<RPT>(wcnt, lane);
   const T sg = (((m - s) & 1) ? (T)1 : (T)-1);  // -(-1)^(m-s)
   const T sm = (m & 1) ? (T)-1 : (T)1;          // (-1)^m
   const int nchunk = (lmax - sd.l0 + kCH) / kCH;
@@ -959,7 +1059,7 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
       T tot = (T)0;
       if (nr_w > 0 && !sfail) {
         bool fast, skip;
-        classify<T, SPIN, RPT>(S, nr_w, fast, skip);
+        classify<T, SPIN, RPT>(S, nr_w, vm, fast, skip);
         if (skip) {
           if (tb) adj_quad_steps_d<SPIN, RPT, true>(S, st, 4 * q, nr_w);
           else adj_quad_steps_d<SPIN, RPT, false>(S, st, 4 * q, nr_w);
@@ -1178,7 +1278,8 @@ template <bool SPIN, int RPT, int CH, int NST, int NS, bool MIR>
 __global__ void __launch_bounds__(32, NS == 1 ? (MIR ? 16 : (RPT >= 8 ? 16 : 20)) : (NS == 2 ? 12 : 8))
     k_rec_adj_w(const AdjItem* __restrict__ items, const RingDev* __restrict__ rings, const MSeed* __restrict__ mseed,
                 const TabEntry<float>* __restrict__ tab, const AdjSets<NS> sets, int Lpad, int lmax, int s, float msc,
-                int* __restrict__ cnt, int* __restrict__ status, int jm) {
+                int* __restrict__ cnt, int* __restrict__ status, int jm, const int* __restrict__ sls,
+                const float4* __restrict__ sst, const int* __restrict__ skk) {
   static_assert(CH % 8 == 0, "whole flushes of 8 l per chunk");
   static_assert(!MIR || NS == 1, "mirror pairs take one set");
   const AdjItem it = items[blockIdx.x];
@@ -1189,6 +1290,7 @@ __global__ void __launch_bounds__(32, NS == 1 ? (MIR ? 16 : (RPT >= 8 ? 16 : 20)
   __shared__ __align__(8) uint64_t bar[NST];
   const int lane = threadIdx.x;
   const int nr_w = (it.nj + 31) >> 5;
+  const unsigned vm = slot_mask<RPT>(it.nj, lane);
   const bool m0 = (m == 0);
   const bool rf = !MIR && it.refl != 0;
   const bool direct = it.nitems == 1;
@@ -1196,10 +1298,14 @@ __global__ void __launch_bounds__(32, NS == 1 ? (MIR ? 16 : (RPT >= 8 ? 16 : 20)
   Cols<float, RPT> S;
   AdjIn<float, RPT> fin[NS];
   AdjIn<float, MIR ? RPT : 2> fmir;  // mirror rings' inputs in the reflected convention (MIR only)
+  {  // columns at the item's first working l (plan start states)
+    const int64_t so = (int64_t)blockIdx.x * RPT * 32;
+    load_start<SPIN, RPT>(S, rings, sst + so, skk + so, it.j0, it.nj, lane);
+  }
+  const int lb = sls[blockIdx.x];
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
     const int jj = r * 32 + lane;
-    init_col<float, SPIN, RPT>(S, rings, sd, it.j0, jj, it.nj, r);
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
       fin[k].set(r, z, z);
@@ -1221,8 +1327,8 @@ __global__ void __launch_bounds__(32, NS == 1 ? (MIR ? 16 : (RPT >= 8 ? 16 : 20)
     }
   }
   const int64_t base = alm_base(lmax, m);
-  const int nl = lmax - sd.l0 + 1;
-  const int nchunk = (nl + CH - 1) / CH;
+  const int nl = lmax - lb + 1;  // l = lb + li, li < nl (nl <= 0: no working column)
+  const int nchunk = nl > 0 ? (nl + CH - 1) / CH : 0;
   const float sg = (((m - s) & 1) ? 1.f : -1.f);  // -(-1)^(m-s)
   const float sm = (m & 1) ? -1.f : 1.f;          // (-1)^m
   if (lane == 0) {
@@ -1232,7 +1338,7 @@ __global__ void __launch_bounds__(32, NS == 1 ? (MIR ? 16 : (RPT >= 8 ? 16 : 20)
   }
   __syncwarp();
   if (lane == 0)
-    for (int k = 0; k < NST && k < nchunk; ++k) issue_chunk<float, CH>(stg[k], &bar[k], tab, base + sd.l0 + k * CH);
+    for (int k = 0; k < NST && k < nchunk; ++k) issue_chunk<float, CH>(stg[k], &bar[k], tab, base + lb + k * CH);
   __syncwarp();
   const int rr = lane & 7, cg = lane >> 3;  // flush: row and column quarter of this lane
 
@@ -1255,7 +1361,7 @@ __global__ void __launch_bounds__(32, NS == 1 ? (MIR ? 16 : (RPT >= 8 ? 16 : 20)
     const TabEntry<float>* st = stg[sidx].v;
     for (int q = 0; q < nq; ++q) {
       bool fast, skip;
-      classify<float, SPIN, RPT>(S, nr_w, fast, skip);
+      classify<float, SPIN, RPT>(S, nr_w, vm, fast, skip);
       blk_any = blk_any || !skip;
       const int row0 = (q & 1) * 4;
       if (skip) {
@@ -1266,7 +1372,7 @@ __global__ void __launch_bounds__(32, NS == 1 ? (MIR ? 16 : (RPT >= 8 ? 16 : 20)
 #pragma unroll
           for (int u = 0; u < 4; ++u) red[k][row0 + u][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
       } else if constexpr (MIR) {
-        const int lpm = sd.l0 + li0 + 4 * q + m;
+        const int lpm = lb + li0 + 4 * q + m;
         if (fast) adj_quad_rows_mir<SPIN, RPT, false>(S, fin[0], fmir, st, 4 * q, nr_w, red[0], row0, lane, lpm);
         else {
           adj_quad_rows_mir<SPIN, RPT, true>(S, fin[0], fmir, st, 4 * q, nr_w, red[0], row0, lane, lpm);
@@ -1286,8 +1392,8 @@ __global__ void __launch_bounds__(32, NS == 1 ? (MIR ? 16 : (RPT >= 8 ? 16 : 20)
         if (direct && lane < ((q & 1) ? 8 : 4) && li < nl) {
 #pragma unroll
           for (int k = 0; k < NS; ++k) {
-            sets.gt[k][base + sd.l0 + li] = z;
-            if (sets.ct[k]) sets.ct[k][base + sd.l0 + li] = z;
+            sets.gt[k][base + lb + li] = z;
+            if (sets.ct[k]) sets.ct[k][base + lb + li] = z;
           }
         }
       } else if ((q & 1) || q == nq - 1) {  // flush rows 0 .. 8 (or 4) of red: l = l0 + li0 + 4 (q & ~1) + row
@@ -1295,7 +1401,7 @@ __global__ void __launch_bounds__(32, NS == 1 ? (MIR ? 16 : (RPT >= 8 ? 16 : 20)
         __syncwarp();
         const int li = li0 + 4 * (q & ~1) + lane;
         const bool out = lane < ((q & 1) ? 8 : 4) && li < nl;
-        const int l = sd.l0 + li;
+        const int l = lb + li;
         const float sl = ((l + m) & 1) ? -1.f : 1.f;
 #pragma unroll
         for (int k = 0; k < NS; ++k) {
@@ -1333,11 +1439,11 @@ __global__ void __launch_bounds__(32, NS == 1 ? (MIR ? 16 : (RPT >= 8 ? 16 : 20)
       }
     }
     __syncwarp();  // every lane is done with stage sidx
-    if (ch + NST < nchunk && lane == 0) issue_chunk<float, CH>(stg[sidx], &bar[sidx], tab, base + sd.l0 + (ch + NST) * CH);
+    if (ch + NST < nchunk && lane == 0) issue_chunk<float, CH>(stg[sidx], &bar[sidx], tab, base + lb + (ch + NST) * CH);
     __syncwarp();
   }
-  if (direct) {  // entries below l0 (orders m < s) are zero
-    for (int l = m + lane; l < sd.l0; l += 32) {
+  if (direct) {  // entries below the first working l (and below l0 for orders m < s) are zero
+    for (int l = m + lane; l < lb && l <= lmax; l += 32) {
 #pragma unroll
       for (int k = 0; k < NS; ++k) {
         sets.gt[k][base + l] = z;
@@ -1393,11 +1499,14 @@ void launch_syn_ns(Plan& p, const void* const* g, const void* const* c, void* co
     ss.F[k] = (V*)F[k];
   }
   const int jm = p.nring - 1;
+  // FP32: the items' start states, from the first item of the launch (FP64: none)
+  const bool f32 = sizeof(T) == 4;
+  const int64_t so = (int64_t)i0 * RPT * 32;
   if (i1 > i0)
-    k_rec_syn_w<T, SPIN, RPT, 32, 4, NS, false><<<i1 - i0, 32, 0, st>>>(p.d_items + i0, p.d_ring, p.d_mseed,
-                                                                        (const TabEntry<T>*)p.d_rtab, ss, p.lmax,
-                                                                        p.spin, (T)msc, p.Lpad, p.d_status, p.omx_tb,
-                                                                        jm);
+    k_rec_syn_w<T, SPIN, RPT, 32, 4, NS, false><<<i1 - i0, 32, 0, st>>>(
+        p.d_items + i0, p.d_ring, p.d_mseed, (const TabEntry<T>*)p.d_rtab, ss, p.lmax, p.spin, (T)msc, p.Lpad,
+        p.d_status, p.omx_tb, jm, f32 ? p.s_items.ls + i0 : nullptr, f32 ? p.s_items.st + so : nullptr,
+        f32 ? p.s_items.kk + so : nullptr);
   // mirror pairs of full-sky plans, one set at a time (they are never split into order chunks)
   if (p.nmitems > 0 && p.r_item1 < 0) {
     for (int k = 0; k < NS; ++k) {
@@ -1407,7 +1516,7 @@ void launch_syn_ns(Plan& p, const void* const* g, const void* const* c, void* co
       s1.F[0] = ss.F[k];
       k_rec_syn_w<T, SPIN, RPT, 32, 4, 1, true><<<p.nmitems, 32, 0, st>>>(
           p.d_mitems, p.d_ring, p.d_mseed, (const TabEntry<T>*)p.d_rtab, s1, p.lmax, p.spin, (T)msc, p.Lpad,
-          p.d_status, p.omx_tb, jm);
+          p.d_status, p.omx_tb, jm, p.s_mitems.ls, p.s_mitems.st, p.s_mitems.kk);
     }
   }
 }
@@ -1445,11 +1554,11 @@ void launch_adj_ns(Plan& p, void* const* F, void* const* acc, void* const* g, vo
     as.ct[k] = c ? (float2*)c[k] : nullptr;
   }
   const int jm = p.nring - 1;
+  const int64_t so = (int64_t)i0 * RPT * 32;
   if (i1 > i0)
-    k_rec_adj_w<SPIN, RPT, 32, 4, NS, false><<<i1 - i0, 32, 0, st>>>(p.d_aitems + i0, p.d_ring, p.d_mseed,
-                                                                      (const TabEntry<float>*)p.d_rtab, as, p.Lpad,
-                                                                      p.lmax, p.spin, (float)msc, p.d_cnt, p.d_status,
-                                                                      jm);
+    k_rec_adj_w<SPIN, RPT, 32, 4, NS, false><<<i1 - i0, 32, 0, st>>>(
+        p.d_aitems + i0, p.d_ring, p.d_mseed, (const TabEntry<float>*)p.d_rtab, as, p.Lpad, p.lmax, p.spin,
+        (float)msc, p.d_cnt, p.d_status, jm, p.s_aitems.ls + i0, p.s_aitems.st + so, p.s_aitems.kk + so);
   // mirror pairs of full-sky plans, one set at a time (never split into order chunks); their
   // orders' other items ran above, and the arrival counters join the two launches
   if (p.nmaitems > 0 && p.r_aitem1 < 0) {
@@ -1461,7 +1570,7 @@ void launch_adj_ns(Plan& p, void* const* F, void* const* acc, void* const* g, vo
       a1.ct[0] = as.ct[k];
       k_rec_adj_w<SPIN, RPT, 32, 4, 1, true><<<p.nmaitems, 32, 0, st>>>(
           p.d_maitems, p.d_ring, p.d_mseed, (const TabEntry<float>*)p.d_rtab, a1, p.Lpad, p.lmax, p.spin, (float)msc,
-          p.d_cnt, p.d_status, jm);
+          p.d_cnt, p.d_status, jm, p.s_maitems.ls, p.s_maitems.st, p.s_maitems.kk);
     }
   }
   for (int k = 0; k < NS; ++k) zero_orders<float2>(p, g[k], c ? c[k] : nullptr, std::max(m0, p.M + 1), m1, st);
@@ -1565,6 +1674,28 @@ void build_rec_table(Plan& p, cudaStream_t st) {
   const dim3 grid(p.lmax + 1, (p.lmax + 1 + nth - 1) / nth);  // blocks past lmax - m exit at once
   if (p.prec == 64) k_rec_table<double><<<grid, nth, 0, st>>>(p.lmax, p.spin, (TabEntry<double>*)p.d_rtab);
   else k_rec_table<float><<<grid, nth, 0, st>>>(p.lmax, p.spin, (TabEntry<float>*)p.d_rtab);
+  PSHT_CUDA_TRY(cudaGetLastError());
+}
+
+void build_rec_starts(Plan& p, cudaStream_t st) {
+  if (p.prec != 32) return;
+  PSHT_REQUIRE(p.syn_rpt == 2 && p.syn_threads == 32 && p.adj_rpt == 4 && p.adj_threads == 32, PSHT_ECUDA,
+               "internal: FP32 recursion shapes");
+  const auto* tab = (const TabEntry<float>*)p.d_rtab;
+  const auto run = [&](auto spin) {
+    constexpr bool S = decltype(spin)::value;
+    if (p.nitems > 0)
+      k_rec_start<S, 2, RecItem><<<p.nitems, 32, 0, st>>>(p.d_items, p.d_ring, p.d_mseed, tab, p.lmax, p.s_items);
+    if (p.nmitems > 0)
+      k_rec_start<S, 2, RecItem><<<p.nmitems, 32, 0, st>>>(p.d_mitems, p.d_ring, p.d_mseed, tab, p.lmax, p.s_mitems);
+    if (p.naitems > 0)
+      k_rec_start<S, 4, AdjItem><<<p.naitems, 32, 0, st>>>(p.d_aitems, p.d_ring, p.d_mseed, tab, p.lmax, p.s_aitems);
+    if (p.nmaitems > 0)
+      k_rec_start<S, 4, AdjItem><<<p.nmaitems, 32, 0, st>>>(p.d_maitems, p.d_ring, p.d_mseed, tab, p.lmax,
+                                                             p.s_maitems);
+  };
+  if (p.spin) run(std::true_type{});
+  else run(std::false_type{});
   PSHT_CUDA_TRY(cudaGetLastError());
 }
 

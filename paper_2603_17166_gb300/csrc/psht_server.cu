@@ -212,10 +212,11 @@ struct Server {
   // Move every queued job with the same plan key and operation as `first` (up to kMaxBatch in all)
   // out of the queue: they run as one batch on the plan (psht_plan_*_batch).  Called with mu held.
   static constexpr int kMaxBatch = 8;
+  int max_batch = kMaxBatch;  // psht_server_set_batch_limit
   std::vector<Job> take_batch(const Job& first) {
     std::vector<Job> b{first};
     const PlanKey k = key_of(first.req);
-    for (auto it = queue.begin(); it != queue.end() && (int)b.size() < kMaxBatch;) {
+    for (auto it = queue.begin(); it != queue.end() && (int)b.size() < max_batch;) {
       if (it->req.op == first.req.op && !(key_of(it->req) < k) && !(k < key_of(it->req))) {
         b.push_back(*it);
         it = queue.erase(it);
@@ -367,6 +368,16 @@ int psht_server_create(int nstreams, size_t budget_bytes, psht_server** out) {
   }
   for (int i = 0; i < nstreams; ++i) s->workers.emplace_back([s, i] { s->worker(i); });
   *out = new psht_server{s};
+  return PSHT_OK;
+}
+
+int psht_server_set_batch_limit(psht_server* server, int max_batch) {
+  if (!server || max_batch < 1 || max_batch > Server::kMaxBatch) {
+    psht::set_error("psht_server_set_batch_limit: server must not be NULL and max_batch must lie in [1, 8]");
+    return PSHT_EINVAL;
+  }
+  std::lock_guard<std::mutex> g(server->s->mu);
+  server->s->max_batch = max_batch;
   return PSHT_OK;
 }
 

@@ -109,6 +109,7 @@ def lib():
         L.psht_server_wait.argtypes = [P, I64, ctypes.POINTER(PshtResult)]
         L.psht_server_get_stats.argtypes = [P, ctypes.POINTER(PshtServerStats)]
         L.psht_server_destroy.argtypes = [P]
+        L.psht_server_set_batch_limit.argtypes = [P, I]
         L.psht_estimate_bytes.argtypes = [I, I, D, I64, D, U32]
         L.psht_plan_params.argtypes = [I, I, D, D, U32, ctypes.POINTER(PshtOptions), ctypes.POINTER(PshtInfo), P, P,
                                        P]
@@ -401,11 +402,17 @@ class Server:
 
     SYNTHESIS, ADJOINT = 0, 1
 
-    def __init__(self, nstreams: int = 4, budget_bytes: int = 0):
+    def __init__(self, nstreams: int = 4, budget_bytes: int = 0, max_batch: int = 8):
         _torch().cuda.current_device()
         self._h = ctypes.c_void_p()
         _check(lib().psht_server_create(int(nstreams), int(budget_bytes), ctypes.byref(self._h)))
         self._keep = {}
+        if max_batch != 8:
+            self.set_batch_limit(max_batch)
+
+    def set_batch_limit(self, max_batch: int):
+        """Largest batch the workers form (psht_server_set_batch_limit; 1 = no batching)."""
+        _check(lib().psht_server_set_batch_limit(self._h, int(max_batch)))
 
     def submit(self, op: int, points_key: int, spin: int, lmax: int, eps: float, theta, phi, in_a, in_b=None,
                out_a=None, out_b=None, precision="auto") -> int:

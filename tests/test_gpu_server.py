@@ -201,3 +201,23 @@ def test_queued_requests_on_one_plan_run_batched():
     assert st["batched_requests"] >= 2 and st["batches"] < len(gs)
     for (r, out), ref in zip(res, alone):
         assert torch.equal(out[0], ref)
+
+
+def test_batch_limit_one_runs_every_request_alone():
+    """psht_server_set_batch_limit(1): queued requests for one plan still run, one call each; the limit
+    is checked (1..8)."""
+    from paper_2603_17166_gb300 import PshtError, Server
+
+    fd = _fields(1, seed=8)[0]
+    srv = Server(nstreams=1, max_batch=1)
+    pend = [_submit(srv, fd, 0) for _ in range(4)]
+    res = [(srv.wait(t), out) for t, out in pend]
+    st = srv.stats()
+    assert all(r["status"] == 0 and r["batch"] == 1 for r, _ in res)
+    assert st["batched_requests"] == 0 and st["batches"] == 4
+    for r, out in res[1:]:
+        assert torch.equal(out[0], res[0][1][0])
+    for bad in (0, 9):
+        with pytest.raises(PshtError):
+            srv.set_batch_limit(bad)
+    srv.close()
