@@ -9,7 +9,10 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <map>
+#include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "psht_internal.h"
@@ -18,6 +21,28 @@ namespace psht {
 
 static thread_local std::string g_err;
 void set_error(const std::string& msg) { g_err = msg; }
+
+void allow_dynamic_smem(const void* fn, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> granted;  // (kernel, device) -> bytes allowed
+  int dev = 0;
+  PSHT_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> g(mu);
+  const auto key = std::make_pair(fn, dev);
+  auto it = granted.find(key);
+  if (it == granted.end()) {
+    cudaFuncAttributes fa;
+    PSHT_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
+    int optin = 0;
+    PSHT_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const int most = optin - (int)fa.sharedSizeBytes;
+    PSHT_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, most));
+    it = granted.emplace(key, (size_t)std::max(most, 0)).first;
+  }
+  PSHT_REQUIRE(bytes <= it->second, PSHT_ENOTSUP,
+               "a kernel needs " + std::to_string(bytes) + " B of shared memory, above the device's " +
+                   std::to_string(it->second));
+}
 
 namespace {
 
@@ -319,7 +344,7 @@ size_t planned_bytes(const Plan& p) {
   b += (size_t)p.nrows * p.ncols * cb;                         // Theta-stage rows
   b += (size_t)p.nrows * p.gstride * cb;                       // grid
   b += (size_t)p.npts * 8;                                     // index + cell
-  b += p.prec == 64 ? (size_t)p.npts * 2 * p.W * 8 : (size_t)p.npts * 8;  // weights / fractions
+  b += p.prec == 64 ? (size_t)p.npts * 2 * p.W * 8 : (size_t)p.npts * 8;  // weights / offsets
   b += (size_t)(p.nTheta + 2 * p.L + p.nphi) * (cb + 4);       // twiddles + permutations
   b += fft_scratch_elems(p) * cb;                              // long-FFT buffers
   if (p.adj_threads == 32) b += (size_t)p.nalm * 16 + (size_t)(p.lmax + 1) * 4;  // FP32 adjoint accumulator
@@ -677,10 +702,13 @@ Plan* create(int spin, int lmax, const double* theta, const double* phi, int64_t
       build_rec_starts(*p, st);
     }
     // step 3 for the points: Theta_p, tiles, sorted layout (and FP64 kernel weights)
-    p->d_pidx = (int32_t*)dalloc(*p, (size_t)std::max<int64_t>(npts, 1) * 4);
-    p->d_pcell = (int32_t*)dalloc(*p, (size_t)std::max<int64_t>(npts, 1) * 4);
-    if (prec == 64) p->d_pw = dalloc(*p, (size_t)std::max<int64_t>(npts, 1) * 2 * p->W * 8);
-    else p->d_pfrac = (float*)dalloc(*p, (size_t)std::max<int64_t>(npts, 1) * 2 * 4);
+    if (prec == 64) {
+      p->d_pidx = (int32_t*)dalloc(*p, (size_t)std::max<int64_t>(npts, 1) * 4);
+      p->d_pcell = (int32_t*)dalloc(*p, (size_t)std::max<int64_t>(npts, 1) * 4);
+      p->d_pw = dalloc(*p, (size_t)std::max<int64_t>(npts, 1) * 2 * p->W * 8);
+    } else {  // one 16-byte record per point: a single load per point in the spreading kernel
+      p->d_prec = (int4*)dalloc(*p, (size_t)std::max<int64_t>(npts, 1) * sizeof(int4));
+    }
     bin_points(*p, theta, phi, st);
     if (p->patch) {
       p->rot = rotator_create(lmax, prec, st);

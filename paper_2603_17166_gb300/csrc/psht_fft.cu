@@ -321,10 +321,6 @@ __global__ void k_export_rings(const typename Cx<T>::V* __restrict__ F, int Lpad
   }
 }
 
-template <typename T>
-void set_smem(const void* fn, size_t bytes) {
-  PSHT_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-}
 
 }  // namespace
 
@@ -364,7 +360,7 @@ void theta_syn_t(Plan& p, cudaStream_t st) {
   const int mode = theta_mode<T>(p);
   const size_t smem = theta_smem<T>(p, mode);
   const auto fn = mode == 2 ? k_theta_syn<T, 2> : (mode == 1 ? k_theta_syn<T, 1> : k_theta_syn<T, 0>);
-  if (mode != 2) set_smem<T>((const void*)fn, smem);
+  if (mode != 2) allow_dynamic_smem((const void*)fn, smem);
   fn<<<mode == 2 ? std::min(p.ncols, kGmCtas) : p.ncols, theta_threads(mode), smem, st>>>(
       (const V*)p.d_F, p.Lpad, (const T*)p.d_w, p.nring, p.d_mrange, p.lmax + 1, p.spin, p.L, (const T*)p.d_sT,
       (const T*)p.d_sP, p.M, p.f2L, (const V*)p.d_tw2L, p.d_perm2L, p.f4L, (const V*)p.d_tw4L, p.d_perm4L, p.r_lo,
@@ -377,7 +373,7 @@ void theta_adj_t(Plan& p, cudaStream_t st) {
   const int mode = theta_mode<T>(p);
   const size_t smem = theta_smem<T>(p, mode);
   const auto fn = mode == 2 ? k_theta_adj<T, 2> : (mode == 1 ? k_theta_adj<T, 1> : k_theta_adj<T, 0>);
-  if (mode != 2) set_smem<T>((const void*)fn, smem);
+  if (mode != 2) allow_dynamic_smem((const void*)fn, smem);
   fn<<<mode == 2 ? std::min(p.ncols, kGmCtas) : p.ncols, theta_threads(mode), smem, st>>>(
       (const V*)p.d_X, p.ncols, p.r_lo, p.nrows, (const T*)p.d_w, p.nring, p.spin, p.L, (const T*)p.d_sT,
       (const T*)p.d_sP, p.M, p.f2L, (const V*)p.d_tw2L, p.d_perm2L, p.f4L, (const V*)p.d_tw4L, p.d_perm4L,
@@ -390,7 +386,7 @@ void phi_syn_t(Plan& p, cudaStream_t st) {
   const bool gm = phi_gm(p);
   const size_t smem = gm ? 0 : (size_t)padded_len(p.nphi) * sizeof(V);
   const auto fn = gm ? k_phi_syn<T, true> : k_phi_syn<T, false>;
-  if (!gm) set_smem<T>((const void*)fn, smem);
+  if (!gm) allow_dynamic_smem((const void*)fn, smem);
   fn<<<gm ? std::min(p.nrows, kGmCtas) : p.nrows, kFftThreads, smem, st>>>(
       (const V*)p.d_X, p.ncols, p.fP, (const V*)p.d_twP, p.d_permP, p.padq, p.gstride, (V*)p.d_G, p.nrows,
       (V*)p.d_fscratch);
@@ -402,7 +398,7 @@ void phi_adj_t(Plan& p, cudaStream_t st) {
   const bool gm = phi_gm(p);
   const size_t smem = gm ? 0 : (size_t)padded_len(p.nphi) * sizeof(V);
   const auto fn = gm ? k_phi_adj<T, true> : k_phi_adj<T, false>;
-  if (!gm) set_smem<T>((const void*)fn, smem);
+  if (!gm) allow_dynamic_smem((const void*)fn, smem);
   fn<<<gm ? std::min(p.nrows, kGmCtas) : p.nrows, kFftThreads, smem, st>>>(
       (const V*)p.d_G, p.gstride, p.padq, p.fP, (const V*)p.d_twP, p.d_permP, (V*)p.d_X, p.ncols, p.nrows,
       (V*)p.d_fscratch);

@@ -172,10 +172,10 @@ struct Plan {
   TileItem* d_titems = nullptr;
   int* d_roff = nullptr;        // FP32 form: first sorted point of each (tile, base row), ntr ntq TR + 1 entries
   int ntitems = 0;
-  int32_t* d_pidx = nullptr;    // original index of sorted point
-  int32_t* d_pcell = nullptr;   // (r0 - tile row origin) | (q0 + padq - tile col origin) << 16
+  int32_t* d_pidx = nullptr;    // FP64 form: original index of sorted point
+  int32_t* d_pcell = nullptr;   // FP64 form: (r0 - tile row origin) | (q0 + padq - tile col origin) << 16
   void* d_pw = nullptr;         // FP64 form: weights [2W][npts] (psi_r[i], then psi_q[k])
-  float* d_pfrac = nullptr;     // FP32 form: [2][npts] t - r0, u - q0
+  int4* d_prec = nullptr;       // FP32 form, per sorted point: (index, cell, bits of t - r0, bits of u - q0)
   void* d_io_a = nullptr;       // device staging for the host-buffer entry points (lazy)
   void* d_io_f = nullptr;
   // host-buffer entry points: the recursions run in chunks of orders m so that the a_lm copies
@@ -205,6 +205,13 @@ struct Plan {
   std::vector<StageRec> recs;
   std::vector<cudaEvent_t> evpool;
 };
+
+// Let kernel fn use at least `bytes` of dynamic shared memory.  The attribute is set once per
+// kernel and device, to the most the device grants the kernel, and never lowered: a kernel whose
+// dynamic size depends on the plan (the FFT stages) is launched by several host threads at once
+// (the request server), and a per-launch setting lowered by one thread between another thread's
+// setting and launch made that launch fail ("too many resources requested").
+void allow_dynamic_smem(const void* fn, size_t bytes);
 
 // kernels / launchers ---------------------------------------------------------------------------
 int rec_table_record_bytes(int prec);  // bytes per (l, m) record of the recurrence table

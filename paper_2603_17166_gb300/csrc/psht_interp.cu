@@ -161,7 +161,7 @@ __global__ void k_tile_offsets(const int* __restrict__ cnt, int ntiles, int per_
 __global__ void k_bin_scatter(const double* __restrict__ theta, const double* __restrict__ phi, int64_t n, BinGeom g,
                               const int* __restrict__ key_of, const int* __restrict__ offsets,
                               int* __restrict__ cursor, int32_t* __restrict__ pidx, int32_t* __restrict__ pcell,
-                              double* __restrict__ pw, float* __restrict__ pfrac, double beta_es) {
+                              double* __restrict__ pw, int4* __restrict__ prec, double beta_es) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int key = key_of[i];
     if (key < 0) continue;
@@ -169,18 +169,19 @@ __global__ void k_bin_scatter(const double* __restrict__ theta, const double* __
     point_tu(g, theta[i], phi[i], t, u);
     const int r0 = (int)ceil(t - 0.5 * g.W), q0 = (int)ceil(u - 0.5 * g.W);
     const int pos = offsets[key] + atomicAdd(&cursor[key], 1);
-    pidx[pos] = (int32_t)i;
     const int lq = key % g.TQ, lr = (key / g.TQ) % g.TR;
-    pcell[pos] = (int32_t)(lr | (lq << 16));
+    const int32_t cell = (int32_t)(lr | (lq << 16));
+    if (prec) {  // FP32 form: one record
+      prec[pos] = make_int4((int)i, cell, __float_as_int((float)(t - (double)r0)), __float_as_int((float)(u - (double)q0)));
+      continue;
+    }
+    pidx[pos] = (int32_t)i;
+    pcell[pos] = cell;
     if (pw) {
       for (int a = 0; a < g.W; ++a) {
         pw[(int64_t)a * n + pos] = es_psi(2.0 * (t - (double)(r0 + a)) / g.W, beta_es);
         pw[(int64_t)(g.W + a) * n + pos] = es_psi(2.0 * (u - (double)(q0 + a)) / g.W, beta_es);
       }
-    }
-    if (pfrac) {
-      pfrac[pos] = (float)(t - (double)r0);
-      pfrac[n + pos] = (float)(u - (double)q0);
     }
   }
 }
@@ -190,8 +191,7 @@ template <typename T, int W>
 struct Weights;
 template <int W>
 struct Weights<double, W> {
-  __device__ __forceinline__ static void get(const double* pw, const float*, int64_t n, int64_t pt, double, double* wr,
-                                             double* wq) {
+  __device__ __forceinline__ static void get(const double* pw, int64_t n, int64_t pt, double* wr, double* wq) {
 #pragma unroll
     for (int a = 0; a < W; ++a) {
       wr[a] = pw[(int64_t)a * n + pt];
@@ -211,18 +211,38 @@ struct Weights<float, W> {
       wq[a] = __expf(beta * (sqrtf(fmaxf(0.0f, 1.0f - zq * zq)) - 1.0f));
     }
   }
-  __device__ __forceinline__ static void get(const double*, const float* pf, int64_t n, int64_t pt, float beta,
-                                             float* wr, float* wq) {
-    from(pf[pt], pf[n + pt], beta, wr, wq);
-  }
 };
+
+// the interpolated value at one point from the shared tile: window rows lr .. lr+W-1, columns
+// lq .. lq+W-1 of the tile, weights wr (rows) and wq (columns)
+template <typename T, int W>
+__device__ __forceinline__ typename Cx<T>::V interp_point(const typename Cx<T>::V* tile, int pitch, int cell,
+                                                          const T* wr, const T* wq) {
+  using V = typename Cx<T>::V;
+  const int lr = cell & 0xffff, lq = cell >> 16;
+  T accr = 0, acci = 0;
+#pragma unroll
+  for (int a = 0; a < W; ++a) {
+    const V* tp = tile + (lr + a) * pitch + lq;
+    T rr = 0, ri = 0;
+#pragma unroll
+    for (int b = 0; b < W; ++b) {
+      const V gv = tp[b];
+      rr = fma(wq[b], gv.x, rr);
+      ri = fma(wq[b], gv.y, ri);
+    }
+    accr = fma(wr[a], rr, accr);
+    acci = fma(wr[a], ri, acci);
+  }
+  return mk(accr, acci);
+}
 
 template <typename T, int W>
 __global__ void __launch_bounds__(kInterpThreads) k_gather(const TileItem* __restrict__ items,
                                                            const int32_t* __restrict__ pidx,
                                                            const int32_t* __restrict__ pcell,
                                                            const double* __restrict__ pw,
-                                                           const float* __restrict__ pf, int64_t npts,
+                                                           const int4* __restrict__ prec, int64_t npts,
                                                            const typename Cx<T>::V* __restrict__ G, int nrows,
                                                            int gstride, int TR, int TQ, T beta,
                                                            typename Cx<T>::V* __restrict__ f) {
@@ -238,34 +258,30 @@ __global__ void __launch_bounds__(kInterpThreads) k_gather(const TileItem* __res
     tile[e] = (gr < nrows && gc < gstride) ? G[(int64_t)gr * gstride + gc] : mk((T)0, (T)0);
   }
   __syncthreads();
-  // the next point's cell and output index are loaded one iteration ahead of their use
+  // the next point's record (FP32) or cell and output index (FP64) are loaded one iteration ahead
   const int pend = it.p0 + it.np;
   int pt = it.p0 + threadIdx.x;
-  int cell_n = pt < pend ? pcell[pt] : 0, idx_n = pt < pend ? pidx[pt] : 0;
-  for (; pt < pend; pt += blockDim.x) {
-    const int cell = cell_n, idx = idx_n;
-    if (pt + (int)blockDim.x < pend) {
-      cell_n = pcell[pt + blockDim.x];
-      idx_n = pidx[pt + blockDim.x];
+  if constexpr (sizeof(T) == 4) {
+    int4 rn = pt < pend ? prec[pt] : make_int4(0, 0, 0, 0);
+    for (; pt < pend; pt += blockDim.x) {
+      const int4 rc = rn;
+      if (pt + (int)blockDim.x < pend) rn = prec[pt + blockDim.x];
+      T wr[W], wq[W];
+      Weights<T, W>::from(__int_as_float(rc.z), __int_as_float(rc.w), beta, wr, wq);
+      f[rc.x] = interp_point<T, W>(tile, pitch, rc.y, wr, wq);
     }
-    const int lr = cell & 0xffff, lq = cell >> 16;
-    T wr[W], wq[W];
-    Weights<T, W>::get(pw, pf, npts, pt, beta, wr, wq);
-    T accr = 0, acci = 0;
-#pragma unroll
-    for (int a = 0; a < W; ++a) {
-      const V* tp = tile + (lr + a) * pitch + lq;
-      T rr = 0, ri = 0;
-#pragma unroll
-      for (int b = 0; b < W; ++b) {
-        const V gv = tp[b];
-        rr = fma(wq[b], gv.x, rr);
-        ri = fma(wq[b], gv.y, ri);
+  } else {
+    int cell_n = pt < pend ? pcell[pt] : 0, idx_n = pt < pend ? pidx[pt] : 0;
+    for (; pt < pend; pt += blockDim.x) {
+      const int cell = cell_n, idx = idx_n;
+      if (pt + (int)blockDim.x < pend) {
+        cell_n = pcell[pt + blockDim.x];
+        idx_n = pidx[pt + blockDim.x];
       }
-      accr = fma(wr[a], rr, accr);
-      acci = fma(wr[a], ri, acci);
+      T wr[W], wq[W];
+      Weights<T, W>::get(pw, npts, pt, wr, wq);
+      f[idx] = interp_point<T, W>(tile, pitch, cell, wr, wq);
     }
-    f[idx] = mk(accr, acci);
   }
 }
 
@@ -277,8 +293,7 @@ __global__ void __launch_bounds__(kInterpThreads) k_gather(const TileItem* __res
 template <typename T, int W, int NT>
 __global__ void __launch_bounds__(NT) k_scatter(const TileItem* __restrict__ items, const int32_t* __restrict__ pidx,
                                                 const int32_t* __restrict__ pcell, const double* __restrict__ pw,
-                                                const float* __restrict__ pf, int64_t npts,
-                                                const typename Cx<T>::V* __restrict__ f,
+                                                int64_t npts, const typename Cx<T>::V* __restrict__ f,
                                                 typename Cx<T>::V* __restrict__ G, int nrows, int gstride, int TR,
                                                 int TQ, T beta) {
   using V = typename Cx<T>::V;
@@ -312,7 +327,7 @@ __global__ void __launch_bounds__(NT) k_scatter(const TileItem* __restrict__ ite
       lr = cell & 0xffff;
       lq = cell >> 16;
       key = lr * pitch + lq;
-      Weights<T, W>::get(pw, pf, npts, pt, beta, wr, wq);
+      Weights<T, W>::get(pw, npts, pt, wr, wq);
       fv = f[pidx[pt]];
     } else {
 #pragma unroll
@@ -377,9 +392,7 @@ __device__ __forceinline__ void red_add_v2(float2* addr, float2 v) {
 
 template <int W>
 __global__ void __launch_bounds__(kRowWarps * 32) k_scatter_rows(const int* __restrict__ roff, int ntiles, int ntq,
-                                                                 const int32_t* __restrict__ pidx,
-                                                                 const int32_t* __restrict__ pcell,
-                                                                 const float* __restrict__ pf, int64_t npts,
+                                                                 const int4* __restrict__ prec,
                                                                  const float2* __restrict__ f, float2* __restrict__ G,
                                                                  int nrows, int gstride, float beta) {
   static_assert(kRowTR + W - 1 <= kRowP, "window rows exceed the column pitch");
@@ -394,40 +407,35 @@ __global__ void __launch_bounds__(kRowWarps * 32) k_scatter_rows(const int* __re
   for (int o = 16; o > 0; o >>= 1) cnt = max(cnt, __shfl_xor_sync(0xffffffffu, cnt, o));
   if (cnt == 0) return;  // no points in the tile
   float2* tw = reinterpret_cast<float2*>(smraw) + warp * COLS * kRowP;
-  // per-point inputs loaded ahead of their use: the cell and offsets one step ahead, the value
-  // (a read at the caller's point order, so a random one) one step ahead with its index two
-  // steps ahead, so that no step waits on a dependent pair of loads
+  // per-point inputs loaded ahead of their use: the point's 16-byte record (index, cell, offsets)
+  // two steps ahead, its value (a read at the caller's point order, so a random one) one step
+  // ahead, so that no step waits on a dependent pair of loads
   const float2 z = make_float2(0.f, 0.f);
-  int cell_n = 0, idx_nn = 0;
-  float ft_n = 0.f, fu_n = 0.f;
+  const int4 z4 = make_int4(0, 0, 0, 0);
+  int4 rec_n = z4, rec_nn = z4;
   float2 fv_n = z;
   if (s0 < s1) {
-    cell_n = pcell[s0];
-    ft_n = pf[s0];
-    fu_n = pf[npts + s0];
-    fv_n = f[pidx[s0]];
+    rec_n = prec[s0];
+    fv_n = f[rec_n.x];
   }
-  if (s0 + 1 < s1) idx_nn = pidx[s0 + 1];
+  if (s0 + 1 < s1) rec_nn = prec[s0 + 1];
   for (int e = lane; e < COLS * kRowP; e += 32) tw[e] = z;
   __syncwarp();
   for (int k = 0; k < cnt; ++k) {
     const int pt = s0 + k;
     const bool on = pt < s1;
-    const int cell = cell_n;
-    const float ft = ft_n, fu = fu_n;
+    const int4 rc = rec_n;
     const float2 fv = fv_n;
     if (pt + 1 < s1) {
-      cell_n = pcell[pt + 1];
-      ft_n = pf[pt + 1];
-      fu_n = pf[npts + pt + 1];
-      fv_n = f[idx_nn];
+      rec_n = rec_nn;
+      fv_n = f[rec_nn.x];
     }
-    if (pt + 2 < s1) idx_nn = pidx[pt + 2];
+    if (pt + 2 < s1) rec_nn = prec[pt + 2];
     int lq = 0;
     float wr[W], wq[W];
     if (on) {
-      lq = cell >> 16;
-      Weights<float, W>::from(ft, fu, beta, wr, wq);
+      lq = rc.y >> 16;
+      Weights<float, W>::from(__int_as_float(rc.z), __int_as_float(rc.w), beta, wr, wq);
     }
     float2* col = tw + lq * kRowP + lane;
 #pragma unroll
@@ -465,10 +473,9 @@ template <typename T, int W>
 void run_gather(Plan& p, void* f, cudaStream_t st) {
   using V = typename Cx<T>::V;
   const size_t smem = (size_t)(p.TR + W - 1) * (p.TQ + W - 1) * sizeof(V);
-  PSHT_CUDA_TRY(cudaFuncSetAttribute((const void*)k_gather<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
+  allow_dynamic_smem((const void*)k_gather<T, W>, smem);
   k_gather<T, W><<<p.ntitems, kInterpThreads, smem, st>>>(p.d_titems, p.d_pidx, p.d_pcell, (const double*)p.d_pw,
-                                                          p.d_pfrac, p.npts, (const V*)p.d_G, p.nrows, p.gstride,
+                                                          p.d_prec, p.npts, (const V*)p.d_G, p.nrows, p.gstride,
                                                           p.TR, p.TQ, (T)p.beta_es, (V*)f);
 }
 template <typename T, int W>
@@ -477,20 +484,17 @@ void run_scatter(Plan& p, const void* f, cudaStream_t st) {
   if constexpr (sizeof(T) == 4) {  // the FP32 form's tiles are 32 x 16 with per-row point ranges
     const int ntiles = p.ntr * p.ntq;
     const size_t smem = (size_t)kRowWarps * (kRowTQ + W - 1) * kRowP * sizeof(float2);
-    PSHT_CUDA_TRY(cudaFuncSetAttribute((const void*)k_scatter_rows<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem));
+    allow_dynamic_smem((const void*)k_scatter_rows<W>, smem);
     k_scatter_rows<W><<<(ntiles + kRowWarps - 1) / kRowWarps, kRowWarps * 32, smem, st>>>(
-        p.d_roff, ntiles, p.ntq, p.d_pidx, p.d_pcell, p.d_pfrac, p.npts, (const float2*)f, (float2*)p.d_G, p.nrows,
-        p.gstride, (float)p.beta_es);
-    return;
+        p.d_roff, ntiles, p.ntq, p.d_prec, (const float2*)f, (float2*)p.d_G, p.nrows, p.gstride, (float)p.beta_es);
+  } else {  // FP64: the generic tile kernel with a private tile per warp
+    constexpr int NT = 128;
+    const size_t smem = (size_t)(NT / 32) * (p.TR + W - 1) * (p.TQ + W - 1) * sizeof(V);
+    allow_dynamic_smem((const void*)k_scatter<T, W, NT>, smem);
+    k_scatter<T, W, NT><<<p.ntitems, NT, smem, st>>>(p.d_titems, p.d_pidx, p.d_pcell, (const double*)p.d_pw, p.npts,
+                                                     (const V*)f, (V*)p.d_G, p.nrows, p.gstride, p.TR, p.TQ,
+                                                     (T)p.beta_es);
   }
-  constexpr int NT = sizeof(T) == 8 ? 128 : 256;
-  const size_t smem = (size_t)(NT / 32) * (p.TR + W - 1) * (p.TQ + W - 1) * sizeof(V);
-  PSHT_CUDA_TRY(cudaFuncSetAttribute((const void*)k_scatter<T, W, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
-  k_scatter<T, W, NT><<<p.ntitems, NT, smem, st>>>(p.d_titems, p.d_pidx, p.d_pcell, (const double*)p.d_pw,
-                                                   p.d_pfrac, p.npts, (const V*)f, (V*)p.d_G, p.nrows, p.gstride,
-                                                   p.TR, p.TQ, (T)p.beta_es);
 }
 
 template <typename T, bool GATHER>
@@ -610,7 +614,7 @@ void bin_points(Plan& p, const double* theta, const double* phi, cudaStream_t st
   PSHT_CUDA_TRY(cudaMemsetAsync(d_cur, 0, sizeof(int) * nkeys, st));
   if (n > 0)
     k_bin_scatter<<<nbl, kBinThreads, 0, st>>>(theta, phi, n, g, d_key, d_cnt, d_cur, p.d_pidx, p.d_pcell,
-                                               (double*)p.d_pw, p.d_pfrac, p.beta_es);
+                                               (double*)p.d_pw, p.d_prec, p.beta_es);
   PSHT_CUDA_TRY(cudaGetLastError());
   PSHT_CUDA_TRY(cudaFreeAsync(d_key, st));
   PSHT_CUDA_TRY(cudaFreeAsync(d_cnt, st));

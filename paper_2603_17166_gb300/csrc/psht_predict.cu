@@ -144,7 +144,7 @@ void predict_error_device(const Plan& p, const std::vector<MSeed>& seeds, const 
     k_cm<<<(lmax + 128) / 128, 128, 0, st>>>(lmax, p.spin, d_seed, d_cl, d_cp, d_cm);
     PSHT_CUDA_TRY(cudaGetLastError());
     const size_t smem = sizeof(double) * 2 * (L + 1);
-    PSHT_CUDA_TRY(cudaFuncSetAttribute((const void*)k_sigma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    allow_dynamic_smem((const void*)k_sigma, smem);
     k_sigma<<<n, 256, smem, st>>>(lmax, L, p.theta_max, d_w, d_beta, d_cp, d_cm, d_out);
     PSHT_CUDA_TRY(cudaGetLastError());
     std::vector<double> cp(lmax + 1), cm(lmax + 1);

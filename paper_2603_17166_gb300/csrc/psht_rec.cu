@@ -1605,8 +1605,7 @@ void launch_adj_t(Plan& p, void* g, void* c, double msc, cudaStream_t st) {
   // one launch per ring part (rings at theta <= pi/2, then reflected rings at theta > pi/2) and
   // per chunk of RPT * NT rings of it; every launch after the first adds to the output
   const size_t red_bytes = (size_t)2 * (NT / 32) * kCH * sizeof(typename Cx4<T>::V);
-  PSHT_CUDA_TRY(cudaFuncSetAttribute((const void*)k_rec_adj<T, SPIN, RPT, NT, false>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red_bytes));
+  allow_dynamic_smem((const void*)k_rec_adj<T, SPIN, RPT, NT, false>, red_bytes);
   const int nch = (p.nring + RPT * NT - 1) / (RPT * NT);
   const int jm = p.nring - 1;
   const int2* mr0 = p.d_mrange;
@@ -1618,8 +1617,7 @@ void launch_adj_t(Plan& p, void* g, void* c, double msc, cudaStream_t st) {
           p.Lpad, p.lmax, p.spin, p.M, part, (part > 0 || chk > 0) ? 1 : 0, (T)msc, (V*)g, (V*)c, p.d_status, chk,
           p.omx_tb, p.d_mmode, jm);
     if (part == 0 && p.d_mmode) {  // mirror-pair orders of full-sky plans: direct rings with their mirrors
-      PSHT_CUDA_TRY(cudaFuncSetAttribute((const void*)k_rec_adj<T, SPIN, RPT, NT, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red_bytes));
+      allow_dynamic_smem((const void*)k_rec_adj<T, SPIN, RPT, NT, true>, red_bytes);
       for (int chk = 0; chk < nch; ++chk)
         k_rec_adj<T, SPIN, RPT, NT, true><<<p.lmax + 1, NT, red_bytes, st>>>(
             p.d_ring, p.d_mseed, mr0, (const TabEntry<T>*)p.d_rtab, (const V*)p.d_F, p.Lpad, p.lmax, p.spin, p.M, 0,
