@@ -355,9 +355,10 @@ size_t planned_bytes(const Plan& p) {
   b += items * (sizeof(RecItem) + sizeof(AdjItem));
   b += ((size_t)p.ntr * p.ntq + (size_t)p.npts / 2048 + 1) * sizeof(TileItem);
   if (p.prec == 32) b += ((size_t)p.ntr * p.ntq * p.TR + 1) * sizeof(int);  // per-row point offsets
-  if (p.prec == 32) {  // recursion start states: per order and ring part at most one part-filled item
-    const size_t scap = 32 * (size_t)p.syn_rpt, acap = 32 * (size_t)p.adj_rpt;
-    b += (size_t)(p.M + 1) * ((p.nring + 2 * scap) * 20 + (p.nring + 2 * acap) * 20 + 4 * (4 + (size_t)p.nring / 32));
+  {  // recursion start states: per order and ring part at most one part-filled item
+    const size_t scap = 32 * (size_t)p.syn_rpt, acap = 32 * (size_t)p.adj_rpt, sb = p.prec == 64 ? 36 : 20;
+    b += (size_t)(p.M + 1) * ((p.nring + 2 * scap) * sb + 4 * (4 + (size_t)p.nring / 32));
+    if (p.prec == 32) b += (size_t)(p.M + 1) * (p.nring + 2 * acap) * sb;
   }
   if (p.patch) {  // rotator, rotated a_lm, spin phases and the adjoint's rotated input
     b += rotator_bytes(p.lmax, p.prec) + 2 * (size_t)p.nalm * cb;
@@ -688,17 +689,20 @@ Plan* create(int spin, int lmax, const double* theta, const double* phi, int64_t
     p->d_G = dalloc(*p, (size_t)p->nrows * p->gstride * cb);
     if (const size_t fe = fft_scratch_elems(*p)) p->d_fscratch = dalloc(*p, fe * cb);
     build_rec_table(*p, st);
-    if (prec == 32) {  // start states of the FP32 recursion items (after the table they are stepped with)
+    {  // start states of the one-warp recursion items (after the table they are stepped with)
+      const size_t sb = 4 * (size_t)(prec == 64 ? 8 : 4);  // (e1, d1, e2, d2) per slot
       const auto alloc_start = [&](RecStart& r, int n, int slots) {
         if (n <= 0) return;
         r.ls = (int*)dalloc(*p, (size_t)n * sizeof(int));
-        r.st = (float4*)dalloc(*p, (size_t)n * slots * sizeof(float4));
+        r.st = dalloc(*p, (size_t)n * slots * sb);
         r.kk = (int*)dalloc(*p, (size_t)n * slots * sizeof(int));
       };
       alloc_start(p->s_items, p->nitems, 32 * p->syn_rpt);
       alloc_start(p->s_mitems, p->nmitems, 32 * p->syn_rpt);
-      alloc_start(p->s_aitems, p->naitems, 32 * p->adj_rpt);
-      alloc_start(p->s_maitems, p->nmaitems, 32 * p->adj_rpt);
+      if (prec == 32) {
+        alloc_start(p->s_aitems, p->naitems, 32 * p->adj_rpt);
+        alloc_start(p->s_maitems, p->nmaitems, 32 * p->adj_rpt);
+      }
       build_rec_starts(*p, st);
     }
     // step 3 for the points: Theta_p, tiles, sorted layout (and FP64 kernel weights)

@@ -76,13 +76,15 @@ struct AdjItem {    // one warp of the FP32 adjoint recursion: order m, rings [j
   int nitems;       // items of order m (1: the item projects its own sums; else they meet in d_acc)
 };
 
-// FP32 recursion: where each work item (a warp's rings of one order) starts.  Below the first l at
-// which any of the item's Wigner columns reaches the working range (2^-60) the kernels would only
-// step dropped columns and sum nothing; the plan steps those l once, with the same FP32 arithmetic
-// and rescaling, and keeps each ring slot's state there, so every call starts at that l.
+// One-warp recursion items (FP32 synthesis and adjoint, FP64 synthesis): where each item (a warp's
+// rings of one order) starts.  Below the first l at which any of the item's Wigner columns reaches
+// the working range the kernels would only step dropped columns and sum nothing; the plan steps
+// those l once, with the kernels' arithmetic and rescaling, and keeps each ring slot's state there,
+// so every call starts at that l.
 struct RecStart {
   int* ls = nullptr;        // per item: first l of its first quad with a working column (> lmax: none)
-  float4* st = nullptr;     // per item x slot x lane: (e1, Delta1, e2, Delta2) at ls, scaled as the kernels scale
+  void* st = nullptr;       // per item x slot x lane: (e1, d1, e2, d2) at ls, scaled as the kernels scale
+                            // (FP32 float4; FP64 four doubles, d = e_{l-1} in the three-term form)
   int* kk = nullptr;        // per item x slot x lane: scale counts k1 | k2 << 16
 };
 
@@ -149,7 +151,8 @@ struct Plan {
   int2* d_aspan = nullptr;      // per m: first adjoint item, item count
   void* d_acc = nullptr;        // FP32 adjoint: float4 [nalm], the sums of orders with several items
   int* d_cnt = nullptr;         // FP32 adjoint: per m, items of that order finished in the current call
-  // FP32 form: start states of the synthesis items, mirror items, adjoint items and mirror adjoint items
+  // start states of the synthesis items, mirror items (both forms), FP32 adjoint items and FP32
+  // mirror adjoint items
   RecStart s_items, s_mitems, s_aitems, s_maitems;
   // batched execution (psht_plan_*_batch): ring coefficients and (FP32) accumulators of the sets
   // after the first of a group, allocated on the first batched call
@@ -216,7 +219,7 @@ void allow_dynamic_smem(const void* fn, size_t bytes);
 // kernels / launchers ---------------------------------------------------------------------------
 int rec_table_record_bytes(int prec);  // bytes per (l, m) record of the recurrence table
 void build_rec_table(Plan& p, cudaStream_t st);
-// FP32 plans, after build_rec_table: fill the start states (buffers allocated by the planner)
+// after build_rec_table: fill the start states (buffers allocated by the planner)
 void build_rec_starts(Plan& p, cudaStream_t st);
 // msc: weight of the m > 0 a_lm entries (read by the synthesis, written by the adjoint)
 void launch_rec_synthesis(Plan& p, const void* g, const void* c, cudaStream_t st, double msc = 1.0);

@@ -475,10 +475,11 @@ __device__ __forceinline__ void syn_quad_d(bool tb, Cols<T, RPT>& S, SynAcc<T, R
   }
 }
 
-// decide the form of a warp's FP64 columns after init_col and convert them: oh <- x = 1 - (1 - x),
-// d <- e_{l0-1} = 0 (slots >= nr are empty: zero columns)
+// decide the form of a warp's FP64 columns and convert them: oh <- x = 1 - (1 - x), and after
+// init_col (fresh) d <- e_{l0-1} = 0 (slots >= nr are empty: zero columns).  Start states taken
+// in the three-term form already hold e_{l-1} in d (fresh = false).
 template <typename T, int RPT>
-__device__ __forceinline__ bool three_term_setup(Cols<T, RPT>& S, int nr_slots, double omx_tb) {
+__device__ __forceinline__ bool three_term_setup(Cols<T, RPT>& S, int nr_slots, double omx_tb, bool fresh = true) {
   if constexpr (sizeof(T) == 8) {
     bool ok = true;
 #pragma unroll
@@ -488,8 +489,10 @@ __device__ __forceinline__ bool three_term_setup(Cols<T, RPT>& S, int nr_slots, 
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
       S.OH(r) = 1.0 - S.OH(r);
-      S.D1(r) = 0.0;
-      S.D2(r) = 0.0;
+      if (fresh) {
+        S.D1(r) = 0.0;
+        S.D2(r) = 0.0;
+      }
     }
     return true;
   } else {
@@ -569,75 +572,37 @@ __device__ __forceinline__ void init_col(Cols<T, RPT>& S, const RingDev* __restr
   S.D2(r) = S.E2(r);
 }
 
-// FP32 ring slots of a work item from the plan's start states (st, kk at the item's first entry):
-// 1 - x from the ring table, the two columns, their differences and scale counts at the item's
-// first working l (empty slots: zero values, zero counts, as init_col leaves them)
-template <bool SPIN, int RPT>
-__device__ __forceinline__ void load_start(Cols<float, RPT>& S, const RingDev* __restrict__ rings,
-                                           const float4* __restrict__ st, const int* __restrict__ kk, int jfirst,
-                                           int nj, int lane) {
+// Ring slots of a work item from the plan's start states (st, kk at the item's first slot): 1 - x
+// from the ring table, the two columns, their differences (FP64 three-term form: e_{l-1}) and
+// scale counts at the item's first working l (empty slots: zero values, zero counts, as init_col
+// leaves them).  FP32 states are float4 (e1, d1, e2, d2), FP64 states four doubles.
+template <typename T, bool SPIN, int RPT>
+__device__ __forceinline__ void load_start(Cols<T, RPT>& S, const RingDev* __restrict__ rings, const void* st,
+                                           const int* __restrict__ kk, int jfirst, int nj, int lane) {
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
     const int jj = r * 32 + lane;
     if (jj < nj) {
-      const RingDev& rg = rings[jfirst + jj];
-      S.OH(r) = rg.ohi;
-      S.OL(r) = rg.olo;
+      ring_omx<T>(rings[jfirst + jj], S.OH(r), S.OL(r));
     } else {
-      S.OH(r) = S.OL(r) = 0.f;
+      S.OH(r) = S.OL(r) = (T)0;
     }
-    const float4 v = st[jj];
+    T e1, d1, e2, d2;
+    if constexpr (sizeof(T) == 4) {
+      const float4 v = reinterpret_cast<const float4*>(st)[jj];
+      e1 = v.x, d1 = v.y, e2 = v.z, d2 = v.w;
+    } else {
+      const double2* q = reinterpret_cast<const double2*>(st) + 2 * jj;
+      const double2 a = q[0], b = q[1];
+      e1 = a.x, d1 = a.y, e2 = b.x, d2 = b.y;
+    }
     const int k = kk[jj];
-    S.E1(r) = v.x;
-    S.D1(r) = v.y;
-    S.E2(r) = SPIN ? v.z : 0.f;
-    S.D2(r) = SPIN ? v.w : 0.f;
+    S.E1(r) = e1;
+    S.D1(r) = d1;
+    S.E2(r) = SPIN ? e2 : (T)0;
+    S.D2(r) = SPIN ? d2 : (T)0;
     S.k1[r] = k & 0xffff;
     S.k2[r] = SPIN ? (k >> 16) : 0;
-  }
-}
-
-// Start states of FP32 work items (plan time, one warp per item).  From the seeds at l0 the warp
-// takes quads of 4 steps, with the arithmetic and the rescaling of the kernels' quads, while every
-// column of its rings is still below the working range (empty slots do not count), and records the
-// state at the first quad that has a working column.  Starting there, a kernel computes exactly
-// what it would have computed from l0: the quads before it add nothing to any sum.  The quads read
-// table records up to l + 3 <= lmax + 3, inside the table's zero padding.
-template <bool SPIN, int RPT, typename Item>
-__global__ void __launch_bounds__(32) k_rec_start(const Item* __restrict__ items, const RingDev* __restrict__ rings,
-                                                  const MSeed* __restrict__ mseed,
-                                                  const TabEntry<float>* __restrict__ tab, int lmax, RecStart out) {
-  const Item it = items[blockIdx.x];
-  const int lane = threadIdx.x;
-  const MSeed sd = mseed[it.m];
-  const int nr_w = (it.nj + 31) >> 5;
-  Cols<float, RPT> S;
-#pragma unroll
-  for (int r = 0; r < RPT; ++r) init_col<float, SPIN, RPT>(S, rings, sd, it.j0, r * 32 + lane, it.nj, r);
-  const TabEntry<float>* tv = tab + alm_base(lmax, it.m);
-  int l = sd.l0;
-  while (l <= lmax) {
-    bool dropped = true;
-#pragma unroll
-    for (int r = 0; r < RPT; ++r)
-      if (r < nr_w && r * 32 + lane < it.nj) dropped = dropped && S.k1[r] > 0 && (!SPIN || S.k2[r] > 0);
-    if (!__all_sync(0xffffffffu, dropped)) break;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const TabEntry<float> cf = tv[l + u];
-#pragma unroll
-      for (int p = 0; p < RPT / 2; ++p)
-        if (2 * p < nr_w) step_pair<SPIN, RPT>(S, p, cf);
-    }
-    rescale_all<float, SPIN, RPT>(S, nr_w);
-    l += 4;
-  }
-  if (lane == 0) out.ls[blockIdx.x] = l;
-#pragma unroll
-  for (int r = 0; r < RPT; ++r) {
-    const int64_t idx = ((int64_t)blockIdx.x * RPT + r) * 32 + lane;
-    out.st[idx] = make_float4(S.E1(r), S.D1(r), S.E2(r), S.D2(r));
-    out.kk[idx] = S.k1[r] | (S.k2[r] << 16);
   }
 }
 
@@ -667,7 +632,7 @@ __global__ void __launch_bounds__(32) k_rec_syn_w(const RecItem* __restrict__ it
                                                   const MSeed* __restrict__ mseed, const TabEntry<T>* __restrict__ tab,
                                                   const SynSets<T, NS> sets, int lmax, int s, T msc, int Lpad,
                                                   int* __restrict__ status, double omx_tb, int jm,
-                                                  const int* __restrict__ sls, const float4* __restrict__ sst,
+                                                  const int* __restrict__ sls, const void* __restrict__ sst,
                                                   const int* __restrict__ skk) {
   static_assert(CH == 32, "one l per lane and chunk");
   static_assert(!MIR || NS == 1, "mirror pairs take one a_lm set");
@@ -688,19 +653,19 @@ __global__ void __launch_bounds__(32) k_rec_syn_w(const RecItem* __restrict__ it
   SynAcc<T, RPT> A[NI];
 #pragma unroll
   for (int k = 0; k < NI; ++k) A[k].zero();
-  // first l of the recursion: the FP32 form starts at the item's first working l (plan start
-  // states), the FP64 form at l0 from the seeds
+  // first l of the recursion: the item's first working l, from the plan's start states (sls null:
+  // l0, from the seeds)
   int lb = sd.l0;
-  if constexpr (sizeof(T) == 4) {
+  if (sls) {
     const int64_t so = (int64_t)blockIdx.x * RPT * 32;
-    load_start<SPIN, RPT>(S, rings, sst + so, skk + so, it.j0, it.nj, lane);
+    load_start<T, SPIN, RPT>(S, rings, (const unsigned char*)sst + so * 4 * sizeof(T), skk + so, it.j0, it.nj, lane);
     lb = sls[blockIdx.x];
   } else {
 #pragma unroll
     for (int r = 0; r < RPT; ++r) init_col<T, SPIN, RPT>(S, rings, sd, it.j0, r * 32 + lane, it.nj, r);
   }
   // slots r with r * 32 + lane < nj hold rings
-  const bool tb = three_term_setup<T, RPT>(S, lane < it.nj ? (it.nj - lane + 31) / 32 : 0, omx_tb);
+  const bool tb = three_term_setup<T, RPT>(S, lane < it.nj ? (it.nj - lane + 31) / 32 : 0, omx_tb, !sls);
   const int64_t base = alm_base(lmax, m);
   const bool rf = !MIR && it.refl != 0;
   const bool m0 = (m == 0);
@@ -936,6 +901,63 @@ __device__ __forceinline__ void adj_quad_steps(Cols<float, RPT>& S, const TabEnt
 #pragma unroll
     for (int p = 0; p < RPT / 2; ++p)
       if (2 * p < nr) step_pair<SPIN, RPT>(S, p, cf);
+  }
+}
+
+// Start states of work items (plan time, one warp per item).  From the seeds at l0 the warp takes
+// quads of 4 steps, with the arithmetic, the form (FP64: Reinsch's or the three-term one, decided
+// as the kernels decide it) and the rescaling of the kernels' quads, while every column of its
+// rings is still below the working range (empty slots do not count), and records the state at the
+// first quad that has a working column.  Starting there, a kernel computes exactly what it would
+// have computed from l0: the quads before it add nothing to any sum.  The quads read table records
+// up to l + 3 <= lmax + 3, inside the table's zero padding.
+template <typename T, bool SPIN, int RPT, typename Item>
+__global__ void __launch_bounds__(32) k_rec_start(const Item* __restrict__ items, const RingDev* __restrict__ rings,
+                                                  const MSeed* __restrict__ mseed, const TabEntry<T>* __restrict__ tab,
+                                                  int lmax, double omx_tb, RecStart out) {
+  const Item it = items[blockIdx.x];
+  const int lane = threadIdx.x;
+  const MSeed sd = mseed[it.m];
+  const int nr_w = (it.nj + 31) >> 5;
+  Cols<T, RPT> S;
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) init_col<T, SPIN, RPT>(S, rings, sd, it.j0, r * 32 + lane, it.nj, r);
+  const bool tb = three_term_setup<T, RPT>(S, lane < it.nj ? (it.nj - lane + 31) / 32 : 0, omx_tb);
+  const TabEntry<T>* tv = tab + alm_base(lmax, it.m);
+  int l = sd.l0;
+  while (l <= lmax) {
+    bool dropped = true;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r)
+      if (r < nr_w && r * 32 + lane < it.nj) dropped = dropped && S.k1[r] > 0 && (!SPIN || S.k2[r] > 0);
+    if (!__all_sync(0xffffffffu, dropped)) break;
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const TabEntry<float> cf = tv[l + u];
+#pragma unroll
+        for (int p = 0; p < RPT / 2; ++p)
+          if (2 * p < nr_w) step_pair<SPIN, RPT>(S, p, cf);
+      }
+    } else {
+      if (tb) adj_quad_steps<SPIN, RPT, true>(S, tv, l, nr_w);
+      else adj_quad_steps<SPIN, RPT, false>(S, tv, l, nr_w);
+    }
+    rescale_all<T, SPIN, RPT>(S, nr_w);
+    l += 4;
+  }
+  if (lane == 0) out.ls[blockIdx.x] = l;
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const int64_t idx = ((int64_t)blockIdx.x * RPT + r) * 32 + lane;
+    if constexpr (sizeof(T) == 4) {
+      reinterpret_cast<float4*>(out.st)[idx] = make_float4(S.E1(r), S.D1(r), S.E2(r), S.D2(r));
+    } else {
+      double2* q = reinterpret_cast<double2*>(out.st) + 2 * idx;
+      q[0] = make_double2(S.E1(r), S.D1(r));
+      q[1] = make_double2(S.E2(r), S.D2(r));
+    }
+    out.kk[idx] = S.k1[r] | (S.k2[r] << 16);
   }
 }
 
@@ -1279,7 +1301,7 @@ __global__ void __launch_bounds__(32, NS == 1 ? (MIR ? 16 : (RPT >= 8 ? 16 : 20)
     k_rec_adj_w(const AdjItem* __restrict__ items, const RingDev* __restrict__ rings, const MSeed* __restrict__ mseed,
                 const TabEntry<float>* __restrict__ tab, const AdjSets<NS> sets, int Lpad, int lmax, int s, float msc,
                 int* __restrict__ cnt, int* __restrict__ status, int jm, const int* __restrict__ sls,
-                const float4* __restrict__ sst, const int* __restrict__ skk) {
+                const void* __restrict__ sst, const int* __restrict__ skk) {
   static_assert(CH % 8 == 0, "whole flushes of 8 l per chunk");
   static_assert(!MIR || NS == 1, "mirror pairs take one set");
   const AdjItem it = items[blockIdx.x];
@@ -1300,7 +1322,7 @@ __global__ void __launch_bounds__(32, NS == 1 ? (MIR ? 16 : (RPT >= 8 ? 16 : 20)
   AdjIn<float, MIR ? RPT : 2> fmir;  // mirror rings' inputs in the reflected convention (MIR only)
   {  // columns at the item's first working l (plan start states)
     const int64_t so = (int64_t)blockIdx.x * RPT * 32;
-    load_start<SPIN, RPT>(S, rings, sst + so, skk + so, it.j0, it.nj, lane);
+    load_start<float, SPIN, RPT>(S, rings, reinterpret_cast<const float4*>(sst) + so, skk + so, it.j0, it.nj, lane);
   }
   const int lb = sls[blockIdx.x];
 #pragma unroll
@@ -1499,14 +1521,13 @@ void launch_syn_ns(Plan& p, const void* const* g, const void* const* c, void* co
     ss.F[k] = (V*)F[k];
   }
   const int jm = p.nring - 1;
-  // FP32: the items' start states, from the first item of the launch (FP64: none)
-  const bool f32 = sizeof(T) == 4;
+  // the items' start states, from the first item of the launch
   const int64_t so = (int64_t)i0 * RPT * 32;
   if (i1 > i0)
     k_rec_syn_w<T, SPIN, RPT, 32, 4, NS, false><<<i1 - i0, 32, 0, st>>>(
         p.d_items + i0, p.d_ring, p.d_mseed, (const TabEntry<T>*)p.d_rtab, ss, p.lmax, p.spin, (T)msc, p.Lpad,
-        p.d_status, p.omx_tb, jm, f32 ? p.s_items.ls + i0 : nullptr, f32 ? p.s_items.st + so : nullptr,
-        f32 ? p.s_items.kk + so : nullptr);
+        p.d_status, p.omx_tb, jm, p.s_items.ls + i0, (const unsigned char*)p.s_items.st + so * 4 * sizeof(T),
+        p.s_items.kk + so);
   // mirror pairs of full-sky plans, one set at a time (they are never split into order chunks)
   if (p.nmitems > 0 && p.r_item1 < 0) {
     for (int k = 0; k < NS; ++k) {
@@ -1558,7 +1579,7 @@ void launch_adj_ns(Plan& p, void* const* F, void* const* acc, void* const* g, vo
   if (i1 > i0)
     k_rec_adj_w<SPIN, RPT, 32, 4, NS, false><<<i1 - i0, 32, 0, st>>>(
         p.d_aitems + i0, p.d_ring, p.d_mseed, (const TabEntry<float>*)p.d_rtab, as, p.Lpad, p.lmax, p.spin,
-        (float)msc, p.d_cnt, p.d_status, jm, p.s_aitems.ls + i0, p.s_aitems.st + so, p.s_aitems.kk + so);
+        (float)msc, p.d_cnt, p.d_status, jm, p.s_aitems.ls + i0, reinterpret_cast<const float4*>(p.s_aitems.st) + so, p.s_aitems.kk + so);
   // mirror pairs of full-sky plans, one set at a time (never split into order chunks); their
   // orders' other items ran above, and the arrival counters join the two launches
   if (p.nmaitems > 0 && p.r_aitem1 < 0) {
@@ -1676,24 +1697,35 @@ void build_rec_table(Plan& p, cudaStream_t st) {
 }
 
 void build_rec_starts(Plan& p, cudaStream_t st) {
-  if (p.prec != 32) return;
-  PSHT_REQUIRE(p.syn_rpt == 2 && p.syn_threads == 32 && p.adj_rpt == 4 && p.adj_threads == 32, PSHT_ECUDA,
-               "internal: FP32 recursion shapes");
-  const auto* tab = (const TabEntry<float>*)p.d_rtab;
-  const auto run = [&](auto spin) {
+  PSHT_REQUIRE(p.syn_threads == 32 && p.syn_rpt == (p.prec == 64 ? 1 : 2), PSHT_ECUDA, "internal: synthesis shape");
+  PSHT_REQUIRE(p.prec == 64 || (p.adj_rpt == 4 && p.adj_threads == 32), PSHT_ECUDA, "internal: FP32 adjoint shape");
+  const auto run = [&](auto tag, auto spin) {
+    using T = decltype(tag);
     constexpr bool S = decltype(spin)::value;
+    constexpr int SR = sizeof(T) == 8 ? 1 : 2;
+    const auto* tab = (const TabEntry<T>*)p.d_rtab;
     if (p.nitems > 0)
-      k_rec_start<S, 2, RecItem><<<p.nitems, 32, 0, st>>>(p.d_items, p.d_ring, p.d_mseed, tab, p.lmax, p.s_items);
+      k_rec_start<T, S, SR, RecItem><<<p.nitems, 32, 0, st>>>(p.d_items, p.d_ring, p.d_mseed, tab, p.lmax, p.omx_tb,
+                                                               p.s_items);
     if (p.nmitems > 0)
-      k_rec_start<S, 2, RecItem><<<p.nmitems, 32, 0, st>>>(p.d_mitems, p.d_ring, p.d_mseed, tab, p.lmax, p.s_mitems);
-    if (p.naitems > 0)
-      k_rec_start<S, 4, AdjItem><<<p.naitems, 32, 0, st>>>(p.d_aitems, p.d_ring, p.d_mseed, tab, p.lmax, p.s_aitems);
-    if (p.nmaitems > 0)
-      k_rec_start<S, 4, AdjItem><<<p.nmaitems, 32, 0, st>>>(p.d_maitems, p.d_ring, p.d_mseed, tab, p.lmax,
-                                                             p.s_maitems);
+      k_rec_start<T, S, SR, RecItem><<<p.nmitems, 32, 0, st>>>(p.d_mitems, p.d_ring, p.d_mseed, tab, p.lmax,
+                                                                p.omx_tb, p.s_mitems);
+    if constexpr (sizeof(T) == 4) {
+      if (p.naitems > 0)
+        k_rec_start<float, S, 4, AdjItem><<<p.naitems, 32, 0, st>>>(p.d_aitems, p.d_ring, p.d_mseed, tab, p.lmax,
+                                                                    p.omx_tb, p.s_aitems);
+      if (p.nmaitems > 0)
+        k_rec_start<float, S, 4, AdjItem><<<p.nmaitems, 32, 0, st>>>(p.d_maitems, p.d_ring, p.d_mseed, tab, p.lmax,
+                                                                     p.omx_tb, p.s_maitems);
+    }
   };
-  if (p.spin) run(std::true_type{});
-  else run(std::false_type{});
+  if (p.prec == 64) {
+    if (p.spin) run(0.0, std::true_type{});
+    else run(0.0, std::false_type{});
+  } else {
+    if (p.spin) run(0.0f, std::true_type{});
+    else run(0.0f, std::false_type{});
+  }
   PSHT_CUDA_TRY(cudaGetLastError());
 }
 
