@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <initializer_list>
 #include <map>
 #include <mutex>
 #include <string>
@@ -603,30 +604,34 @@ Plan* create(int spin, int lmax, const double* theta, const double* phi, int64_t
       p->d_cnt = (int*)dalloc(*p, (size_t)(lmax + 1) * sizeof(int));
       PSHT_CUDA_TRY(cudaMemsetAsync(p->d_acc, 0, (size_t)p->nalm * 16, st));
       PSHT_CUDA_TRY(cudaMemsetAsync(p->d_cnt, 0, (size_t)(lmax + 1) * sizeof(int), st));
-      // order chunks for the host-buffer entry points: kChunks ranges of m with about equal
-      // recursion work (ring count x l range of the synthesis items), split at order boundaries;
-      // plans with mirror pairs run unchunked (no chunk table)
-      constexpr int kChunks = 8;
+      // order chunks for the host-buffer entry points, split at order boundaries by recursion
+      // work (ring count x l range of the items): the synthesis in 10 / 30 / 60 % of its work, so
+      // that only the first tenth of the a_lm upload is not hidden behind a recursion launch (the
+      // upload of a part takes about a third of its recursion's time); the adjoint in 60 / 30 /
+      // 10 %, so that only the last tenth of the download follows the last launch.  Three launches
+      // each: every launch adds its tail (its longest warps), so few chunks beat many.  Plans with
+      // mirror pairs run unchunked (no chunk table).
       if (!any_mirror) {
-      std::vector<double> cum(items.size() + 1, 0.0);
-      for (size_t i = 0; i < items.size(); ++i)
-        cum[i + 1] = cum[i] + (double)items[i].nj * (lmax - std::max(items[i].m, spin) + 1);
-      p->chunk_m.assign(1, 0);
-      for (int k = 1; k < kChunks; ++k) {
-        const double target = cum.back() * k / kChunks;
-        size_t i = std::lower_bound(cum.begin(), cum.end(), target) - cum.begin();
-        if (i >= items.size()) break;
-        const int mb = items[i].m;
-        if (mb > p->chunk_m.back()) p->chunk_m.push_back(mb);
-      }
-      p->chunk_m.push_back(p->M + 1);
-      for (int mb : p->chunk_m) {
-        int it = 0, ia = 0;
-        while (it < (int)items.size() && items[it].m < mb) ++it;
-        while (ia < (int)ai.size() && ai[ia].m < mb) ++ia;
-        p->chunk_item.push_back(it);
-        p->chunk_aitem.push_back(ia);
-      }
+        const auto split = [&](const auto& its, std::initializer_list<double> fr, std::vector<int>& cm,
+                               std::vector<int>& ci) {
+          std::vector<double> cum(its.size() + 1, 0.0);
+          for (size_t i = 0; i < its.size(); ++i)
+            cum[i + 1] = cum[i] + (double)its[i].nj * (lmax - std::max(its[i].m, spin) + 1);
+          cm.assign(1, 0);
+          for (double f : fr) {
+            const size_t i = std::lower_bound(cum.begin(), cum.end(), cum.back() * f) - cum.begin();
+            if (i >= its.size()) break;
+            if (its[i].m > cm.back()) cm.push_back(its[i].m);
+          }
+          cm.push_back(p->M + 1);
+          for (int mb : cm) {
+            int it = 0;
+            while (it < (int)its.size() && its[it].m < mb) ++it;
+            ci.push_back(it);
+          }
+        };
+        split(items, {0.1, 0.4}, p->chunk_m, p->chunk_item);
+        split(ai, {0.6, 0.9}, p->achunk_m, p->chunk_aitem);
       }
     }
     // deconvolution tables, ring weights, FFT twiddles and digit-reversal tables
@@ -920,7 +925,7 @@ void ensure_io(Plan& p) {
   if (!p.d_io_f) p.d_io_f = dalloc(p, (size_t)std::max<int64_t>(p.npts, 1) * cb);
   if (!p.chunk_m.empty() && !p.copy_st) {
     PSHT_CUDA_TRY(cudaStreamCreateWithFlags(&p.copy_st, cudaStreamNonBlocking));
-    p.chunk_ev.resize(p.chunk_m.size() + 1);
+    p.chunk_ev.resize(std::max(p.chunk_m.size(), p.achunk_m.size()) + 1);
     for (auto& e : p.chunk_ev) PSHT_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
 }
@@ -974,7 +979,7 @@ void synthesis_host_chunked(Plan& p, const void* g, const void* c, void* f, cuda
 void adjoint_host_chunked(Plan& p, const void* f, void* g, void* c, cudaStream_t st) {
   const size_t cb = p.prec == 64 ? 16 : 8, na = (size_t)p.nalm * cb;
   char* da = (char*)p.d_io_a;
-  const int K = (int)p.chunk_m.size() - 1;
+  const int K = (int)p.achunk_m.size() - 1;
   PSHT_CUDA_TRY(cudaMemcpyAsync(p.d_io_f, f, (size_t)p.npts * cb, cudaMemcpyHostToDevice, st));
   staged(p, 4, st, [&] {
     PSHT_CUDA_TRY(cudaMemsetAsync(p.d_G, 0, (size_t)p.nrows * p.gstride * cb, st));
@@ -987,8 +992,8 @@ void adjoint_host_chunked(Plan& p, const void* f, void* g, void* c, cudaStream_t
     for (int k = 0; k < K; ++k) {
       p.r_aitem0 = p.chunk_aitem[k];
       p.r_aitem1 = p.chunk_aitem[k + 1];
-      p.r_m0 = p.chunk_m[k];
-      p.r_m1 = k + 1 < K ? p.chunk_m[k + 1] : p.lmax + 1;  // the last chunk also writes the zero orders
+      p.r_m0 = p.achunk_m[k];
+      p.r_m1 = k + 1 < K ? p.achunk_m[k + 1] : p.lmax + 1;  // the last chunk also writes the zero orders
       launch_rec_adjoint(p, da, c ? da + na : nullptr, st);
       PSHT_CUDA_TRY(cudaEventRecord(p.chunk_ev[k], st));
       PSHT_CUDA_TRY(cudaStreamWaitEvent(p.copy_st, p.chunk_ev[k], 0));

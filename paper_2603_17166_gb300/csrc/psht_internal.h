@@ -182,8 +182,9 @@ struct Plan {
   void* d_io_a = nullptr;       // device staging for the host-buffer entry points (lazy)
   void* d_io_f = nullptr;
   // host-buffer entry points: the recursions run in chunks of orders m so that the a_lm copies
-  // overlap them (FP32 form); chunk k covers m in [chunk_m[k], chunk_m[k+1])
-  std::vector<int> chunk_m, chunk_item, chunk_aitem;
+  // overlap them (FP32 form); synthesis chunk k covers m in [chunk_m[k], chunk_m[k+1]) and items
+  // [chunk_item[k], chunk_item[k+1]), adjoint chunks likewise from achunk_m and chunk_aitem
+  std::vector<int> chunk_m, chunk_item, achunk_m, chunk_aitem;
   cudaStream_t copy_st = nullptr;
   std::vector<cudaEvent_t> chunk_ev;
   // item and order ranges of the next recursion launch (-1: all); set only around chunked launches
