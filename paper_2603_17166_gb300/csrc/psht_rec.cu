@@ -17,7 +17,9 @@
 // d^l_{m,-s}(pi - b) = (-1)^(l+m) d^l_{m,s}(b), i.e. the two columns swapped and the
 // coefficients signed by (-1)^(l+m).
 // Seeds are Wigner's closed form at l0 = max(m, s) in FP64 log2 form; values too small for the
-// working precision are carried as e 2^(-F k) and join the sums once k = 0.
+// working precision are carried as e 2^(-F k) and join the sums once k = 0.  The one-warp kernels
+// start each item at the first quad of l in which any of its columns has joined: the plan steps
+// the quads below it once (k_rec_start) and keeps the columns' state there.
 //
 // Synthesis (eq. syn on ring j):   F_j[m] = -sum_l (g + i c)_lm e1_l,   F_j[-m] = -(-1)^s sum_l (g* + i c*)_lm e2_l
 // Adjoint (transpose, then the projection of the adjoint synthesis general formula, Sec. I):
@@ -32,7 +34,8 @@
 //
 // Kernels: k_rec_syn_w (synthesis, both forms; NS a_lm sets per pass, or mirror pairs of full-sky
 // plans), k_rec_adj_w (FP32 adjoint; NS sets, or mirror pairs), k_rec_adj (FP64 adjoint, one CTA per
-// order; mirror-pair orders in launches of their own), k_rec_table (the recurrence table).
+// order; mirror-pair orders in launches of their own), k_rec_table (the recurrence table),
+// k_rec_start (the items' start states, plan time).
 #include <cuda_runtime.h>
 #include <math.h>
 
