@@ -360,6 +360,12 @@ size_t planned_bytes(const Plan& p) {
     const size_t scap = 32 * (size_t)p.syn_rpt, acap = 32 * (size_t)p.adj_rpt, sb = p.prec == 64 ? 36 : 20;
     b += (size_t)(p.M + 1) * ((p.nring + 2 * scap) * sb + 4 * (4 + (size_t)p.nring / 32));
     if (p.prec == 32) b += (size_t)(p.M + 1) * (p.nring + 2 * acap) * sb;
+    // FP64 block adjoint: every active (ring, order) pair once (36 B), and per (ring part, ring
+    // chunk, order) an offset and a start l (12 B)
+    if (p.prec == 64) {
+      const size_t cr = (size_t)p.adj_rpt * p.adj_threads, nch = (p.nring + cr - 1) / cr;
+      b += (size_t)(p.M + 1) * ((size_t)p.nring * 36 + 2 * nch * 12);
+    }
   }
   if (p.patch) {  // rotator, rotated a_lm, spin phases and the adjoint's rotated input
     b += rotator_bytes(p.lmax, p.prec) + 2 * (size_t)p.nalm * cb;
@@ -707,6 +713,24 @@ Plan* create(int spin, int lmax, const double* theta, const double* phi, int64_t
       if (prec == 32) {
         alloc_start(p->s_aitems, p->naitems, 32 * p->adj_rpt);
         alloc_start(p->s_maitems, p->nmaitems, 32 * p->adj_rpt);
+      } else {  // FP64 block adjoint: per (ring part, ring chunk, order) the chunk's active rings
+        const int cr = p->adj_rpt * p->adj_threads, nch = (p->nring + cr - 1) / cr;
+        const int nparts = p->has_refl ? 2 : 1;
+        std::vector<int64_t> off((size_t)nparts * nch * (p->M + 1));
+        int64_t tot = 0;
+        for (int part = 0; part < nparts; ++part)
+          for (int chk = 0; chk < nch; ++chk)
+            for (int m = 0; m <= p->M; ++m) {
+              off[((size_t)part * nch + chk) * (p->M + 1) + m] = tot;
+              const int2 r = mr[(size_t)part * (lmax + 1) + m];
+              const int a = r.x + chk * cr, b = std::min(r.y, a + cr);
+              tot += std::max(0, b - a);
+            }
+        p->badj_nch = nch;
+        p->s_badj_off = (int64_t*)upload(*p, off, st);
+        p->s_badj.ls = (int*)dalloc(*p, off.size() * sizeof(int));
+        p->s_badj.st = dalloc(*p, (size_t)std::max<int64_t>(tot, 1) * 4 * sizeof(double));
+        p->s_badj.kk = (int*)dalloc(*p, (size_t)std::max<int64_t>(tot, 1) * sizeof(int));
       }
       build_rec_starts(*p, st);
     }

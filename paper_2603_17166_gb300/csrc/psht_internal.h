@@ -154,6 +154,12 @@ struct Plan {
   // start states of the synthesis items, mirror items (both forms), FP32 adjoint items and FP32
   // mirror adjoint items
   RecStart s_items, s_mitems, s_aitems, s_maitems;
+  // FP64 block adjoint: per launch (ring part x ring chunk) and order m, the CTA's first working l
+  // (s_badj.ls[launch * (M + 1) + m]) and each active ring's state there (four doubles and the
+  // scale counts at s_badj_off[launch * (M + 1) + m] + the ring's index in the chunk)
+  RecStart s_badj;
+  int64_t* s_badj_off = nullptr;
+  int badj_nch = 0;  // ring chunks per part
   // batched execution (psht_plan_*_batch): ring coefficients and (FP32) accumulators of the sets
   // after the first of a group, allocated on the first batched call
   std::vector<void*> d_Fb, d_accb;

@@ -977,6 +977,62 @@ __device__ __forceinline__ void adj_quad_steps_d(Cols<T, RPT>& S, const TabEntry
   else adj_quad_steps<SPIN, RPT>(S, st, i0, nr);
 }
 
+// Start states of the FP64 block adjoint (plan time): one CTA per order over the same rings and
+// ring slots as k_rec_adj for one ring chunk of one ring part.  The CTA takes quads of 4 steps, as
+// the kernel's warps take them while all their columns are dropped, as long as every column of
+// every warp is still below the working range, and records the CTA's first working l (ls[m]) and
+// each active ring's state there (at off[m] + the ring's index in the chunk).
+template <bool SPIN, int RPT, int NT>
+__global__ void __launch_bounds__(NT) k_rec_adj_start(const RingDev* __restrict__ rings,
+                                                      const MSeed* __restrict__ mseed,
+                                                      const int2* __restrict__ mrange,
+                                                      const TabEntry<double>* __restrict__ tab, int lmax, int M,
+                                                      int chunk, double omx_tb, const int64_t* __restrict__ off,
+                                                      int* __restrict__ ls, double2* __restrict__ st,
+                                                      int* __restrict__ kk) {
+  const int m = blockIdx.x;
+  if (m > M) return;
+  const MSeed sd = mseed[m];
+  int2 rr = mrange[m];
+  rr.x += chunk * RPT * NT;
+  rr.y = min(rr.y, rr.x + RPT * NT);
+  const int nact = max(0, rr.y - rr.x);
+  constexpr int NW = NT / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int wbase, wcnt, nr_w;
+  slot_range(nact, NW, warp, wbase, wcnt, nr_w);
+  Cols<double, RPT> S;
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) init_col<double, SPIN, RPT>(S, rings, sd, rr.x + wbase, r * 32 + lane, wcnt, r);
+  const bool tb = three_term_setup<double, RPT>(S, lane < wcnt ? (wcnt - lane + 31) / 32 : 0, omx_tb);
+  const TabEntry<double>* tv = tab + alm_base(lmax, m);
+  int l = sd.l0;
+  while (nact > 0 && l <= lmax) {  // l and nact are the same in every thread of the CTA
+    bool dropped = true;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r)
+      if (r < nr_w && r * 32 + lane < wcnt) dropped = dropped && S.k1[r] > 0 && (!SPIN || S.k2[r] > 0);
+    if (!__syncthreads_and(dropped)) break;
+    if (nr_w > 0) {
+      if (tb) adj_quad_steps<SPIN, RPT, true>(S, tv, l, nr_w);
+      else adj_quad_steps<SPIN, RPT, false>(S, tv, l, nr_w);
+      rescale_all<double, SPIN, RPT>(S, nr_w);
+    }
+    l += 4;
+  }
+  if (threadIdx.x == 0) ls[m] = l;
+  const int64_t o = off[m] + wbase;
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const int jj = r * 32 + lane;
+    if (jj < wcnt) {
+      st[2 * (o + jj)] = make_double2(S.E1(r), S.D1(r));
+      st[2 * (o + jj) + 1] = make_double2(S.E2(r), S.D2(r));
+      kk[o + jj] = S.k1[r] | (S.k2[r] << 16);
+    }
+  }
+}
+
 // MIR: orders whose reflected rings are the mirrors jm - j of their direct rings (mmode[m] = 1,
 // full-sky plans) run in the direct part's launches with both rings of each pair per slot; the
 // launches of the other mode leave those orders alone (the first launch writes their zeros).
@@ -987,7 +1043,9 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
                                                 int lmax, int s, int M, int refl, int accumulate, T msc,
                                                 typename Cx<T>::V* __restrict__ gt, typename Cx<T>::V* __restrict__ ct,
                                                 int* __restrict__ status, int chunk, double omx_tb,
-                                                const int* __restrict__ mmode, int jm) {
+                                                const int* __restrict__ mmode, int jm,
+                                                const int* __restrict__ sls, const int64_t* __restrict__ soff,
+                                                const double2* __restrict__ sst, const int* __restrict__ skk) {
   using V = typename Cx<T>::V;
   const int m = blockIdx.x;
   const int64_t base = alm_base(lmax, m);
@@ -1019,7 +1077,9 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
   extern __shared__ __align__(16) unsigned char red_raw[];
   V4* red = reinterpret_cast<V4*>(red_raw);  // [2][NW][kCH]: double buffer of per-warp partial sums
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int l = m + threadIdx.x; !accumulate && l < sd.l0 && l <= lmax; l += blockDim.x) {
+  // first l: the CTA's first working l from the plan's start states (sls null: l0, from the seeds)
+  const int lb = sls ? sls[m] : sd.l0;
+  for (int l = m + threadIdx.x; !accumulate && l < lb && l <= lmax; l += blockDim.x) {
     gt[base + l] = mk((T)0, (T)0);
     if (ct) ct[base + l] = mk((T)0, (T)0);
   }
@@ -1034,7 +1094,26 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
     const int jj = r * 32 + lane;
-    init_col<T, SPIN, RPT>(S, rings, sd, rr.x + wbase, jj, wcnt, r);
+    if (sls) {  // the ring's state at lb (empty slots: zero values and counts, as init_col leaves them)
+      S.OH(r) = S.OL(r) = S.E1(r) = S.D1(r) = S.E2(r) = S.D2(r) = (T)0;
+      S.k1[r] = S.k2[r] = 0;
+      if (jj < wcnt) {
+        ring_omx<T>(rings[rr.x + wbase + jj], S.OH(r), S.OL(r));
+        const int64_t o = soff[m] + wbase + jj;
+        const double2 a = sst[2 * o], b = sst[2 * o + 1];
+        const int k = skk[o];
+        S.E1(r) = (T)a.x;
+        S.D1(r) = (T)a.y;
+        if (SPIN) {
+          S.E2(r) = (T)b.x;
+          S.D2(r) = (T)b.y;
+          S.k2[r] = k >> 16;
+        }
+        S.k1[r] = k & 0xffff;
+      }
+    } else {
+      init_col<T, SPIN, RPT>(S, rings, sd, rr.x + wbase, jj, wcnt, r);
+    }
     fin.set(r, mk((T)0, (T)0), mk((T)0, (T)0));
     if constexpr (MIR) {
       fmir.set(r, mk((T)0, (T)0), mk((T)0, (T)0));
@@ -1052,11 +1131,11 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
       fin.set(r, rf ? fm : fp, rf ? fp : fm);
     }
   }
-  const bool tb = three_term_setup<T, RPT>(S, lane < wcnt ? (wcnt - lane + 31) / 32 : 0, omx_tb);
+  const bool tb = three_term_setup<T, RPT>(S, lane < wcnt ? (wcnt - lane + 31) / 32 : 0, omx_tb, !sls);
   const unsigned vm = slot_mask<RPT>(wcnt, lane);
   const T sg = (((m - s) & 1) ? (T)1 : (T)-1);  // -(-1)^(m-s)
   const T sm = (m & 1) ? (T)-1 : (T)1;          // (-1)^m
-  const int nchunk = (lmax - sd.l0 + kCH) / kCH;
+  const int nchunk = max(0, (lmax - lb + kCH) / kCH);
   if (threadIdx.x == 0) {
     sfail = 0;
     mbar_init(&bar[0], 1);
@@ -1065,13 +1144,13 @@ __global__ void __launch_bounds__(NT) k_rec_adj(const RingDev* __restrict__ ring
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    issue_chunk<T>(stg[0], &bar[0], tab, base + sd.l0);
-    if (nchunk > 1) issue_chunk<T>(stg[1], &bar[1], tab, base + sd.l0 + kCH);
+    if (nchunk > 0) issue_chunk<T>(stg[0], &bar[0], tab, base + lb);
+    if (nchunk > 1) issue_chunk<T>(stg[1], &bar[1], tab, base + lb + kCH);
   }
 
   for (int ch = 0; ch < nchunk; ++ch) {
     const int sidx = ch & 1;
-    const int lc = sd.l0 + ch * kCH;
+    const int lc = lb + ch * kCH;
     const int n = min(kCH, lmax - lc + 1);
     const int nq = (n + 3) >> 2;
     if (!mbar_wait(&bar[sidx], (ch >> 1) & 1)) {
@@ -1633,20 +1712,53 @@ void launch_adj_t(Plan& p, void* g, void* c, double msc, cudaStream_t st) {
   const int nch = (p.nring + RPT * NT - 1) / (RPT * NT);
   const int jm = p.nring - 1;
   const int2* mr0 = p.d_mrange;
+  // start states of launch (part, chunk), if the plan has them
+  const bool ss = p.s_badj.ls != nullptr && p.badj_nch == nch;
+  const auto sls = [&](int part, int chk) { return ss ? p.s_badj.ls + (int64_t)(part * nch + chk) * (p.M + 1) : nullptr; };
+  const auto soff = [&](int part, int chk) {
+    return ss ? p.s_badj_off + (int64_t)(part * nch + chk) * (p.M + 1) : nullptr;
+  };
+  const double2* sst = ss ? (const double2*)p.s_badj.st : nullptr;
+  const int* skk = ss ? p.s_badj.kk : nullptr;
   for (int part = 0; part < 2; ++part) {
     if (part == 1 && !p.has_refl) break;
     for (int chk = 0; chk < nch; ++chk)
       k_rec_adj<T, SPIN, RPT, NT, false><<<p.lmax + 1, NT, red_bytes, st>>>(
           p.d_ring, p.d_mseed, mr0 + part * (p.lmax + 1), (const TabEntry<T>*)p.d_rtab, (const V*)p.d_F,
           p.Lpad, p.lmax, p.spin, p.M, part, (part > 0 || chk > 0) ? 1 : 0, (T)msc, (V*)g, (V*)c, p.d_status, chk,
-          p.omx_tb, p.d_mmode, jm);
+          p.omx_tb, p.d_mmode, jm, sls(part, chk), soff(part, chk), sst, skk);
     if (part == 0 && p.d_mmode) {  // mirror-pair orders of full-sky plans: direct rings with their mirrors
       allow_dynamic_smem((const void*)k_rec_adj<T, SPIN, RPT, NT, true>, red_bytes);
       for (int chk = 0; chk < nch; ++chk)
         k_rec_adj<T, SPIN, RPT, NT, true><<<p.lmax + 1, NT, red_bytes, st>>>(
             p.d_ring, p.d_mseed, mr0, (const TabEntry<T>*)p.d_rtab, (const V*)p.d_F, p.Lpad, p.lmax, p.spin, p.M, 0,
-            1, (T)msc, (V*)g, (V*)c, p.d_status, chk, p.omx_tb, p.d_mmode, jm);
+            1, (T)msc, (V*)g, (V*)c, p.d_status, chk, p.omx_tb, p.d_mmode, jm, sls(0, chk), soff(0, chk), sst, skk);
     }
+  }
+}
+
+// FP64 block adjoint start states, one precompute launch per (ring part, ring chunk)
+template <bool SPIN, int RPT, int NT>
+void badj_starts_t(Plan& p, cudaStream_t st) {
+  const int nch = (p.nring + RPT * NT - 1) / (RPT * NT);
+  PSHT_REQUIRE(nch == p.badj_nch, PSHT_ECUDA, "internal: block adjoint chunks");
+  for (int part = 0; part < (p.has_refl ? 2 : 1); ++part)
+    for (int chk = 0; chk < nch; ++chk) {
+      const int64_t o = (int64_t)(part * nch + chk) * (p.M + 1);
+      k_rec_adj_start<SPIN, RPT, NT><<<p.M + 1, NT, 0, st>>>(
+          p.d_ring, p.d_mseed, p.d_mrange + part * (p.lmax + 1), (const TabEntry<double>*)p.d_rtab, p.lmax, p.M, chk,
+          p.omx_tb, p.s_badj_off + o, p.s_badj.ls + o, (double2*)p.s_badj.st, p.s_badj.kk);
+    }
+}
+template <bool SPIN>
+void badj_starts_s(Plan& p, cudaStream_t st) {
+  switch (p.adj_rpt * 10000 + p.adj_threads) {
+    case 20128: badj_starts_t<SPIN, 2, 128>(p, st); break;
+    case 40128: badj_starts_t<SPIN, 4, 128>(p, st); break;
+    case 40256: badj_starts_t<SPIN, 4, 256>(p, st); break;
+    case 80128: badj_starts_t<SPIN, 8, 128>(p, st); break;
+    case 80256: badj_starts_t<SPIN, 8, 256>(p, st); break;
+    default: badj_starts_t<SPIN, 8, 512>(p, st); break;
   }
 }
 
@@ -1725,6 +1837,10 @@ void build_rec_starts(Plan& p, cudaStream_t st) {
   if (p.prec == 64) {
     if (p.spin) run(0.0, std::true_type{});
     else run(0.0, std::false_type{});
+    if (p.s_badj.ls) {
+      if (p.spin) badj_starts_s<true>(p, st);
+      else badj_starts_s<false>(p, st);
+    }
   } else {
     if (p.spin) run(0.0f, std::true_type{});
     else run(0.0f, std::false_type{});
