@@ -258,21 +258,14 @@ __global__ void __launch_bounds__(kInterpThreads) k_gather(const TileItem* __res
     tile[e] = (gr < nrows && gc < gstride) ? G[(int64_t)gr * gstride + gc] : mk((T)0, (T)0);
   }
   __syncthreads();
-  // the records of the thread's next two points (FP32), or the next point's cell and output index
-  // (FP64), are loaded ahead of their use: where the outputs go to scattered addresses (points in
-  // random order) the record loads queue behind the partial-sector writes, and one iteration of
-  // lead did not cover their latency
+  // the next point's record (FP32) or cell and output index (FP64) are loaded one iteration ahead
   const int pend = it.p0 + it.np;
   int pt = it.p0 + threadIdx.x;
   if constexpr (sizeof(T) == 4) {
-    const int bd = blockDim.x;
-    const int4 z4 = make_int4(0, 0, 0, 0);
-    int4 rn = pt < pend ? prec[pt] : z4;
-    int4 rnn = pt + bd < pend ? prec[pt + bd] : z4;
-    for (; pt < pend; pt += bd) {
+    int4 rn = pt < pend ? prec[pt] : make_int4(0, 0, 0, 0);
+    for (; pt < pend; pt += blockDim.x) {
       const int4 rc = rn;
-      rn = rnn;
-      if (pt + 2 * bd < pend) rnn = prec[pt + 2 * bd];
+      if (pt + (int)blockDim.x < pend) rn = prec[pt + blockDim.x];
       T wr[W], wq[W];
       Weights<T, W>::from(__int_as_float(rc.z), __int_as_float(rc.w), beta, wr, wq);
       f[rc.x] = interp_point<T, W>(tile, pitch, rc.y, wr, wq);
