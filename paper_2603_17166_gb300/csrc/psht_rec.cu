@@ -709,6 +709,9 @@ __global__ void __launch_bounds__(32) k_rec_syn_w(const RecItem* __restrict__ it
     }
   }
   __syncwarp();
+  // once every column of the warp sums, it stays so (counts only fall, and only below the
+  // working range): the warp then takes the plain path without testing its columns again
+  bool fastw = false;
 
   for (int ch = 0; ch < nchunk; ++ch) {
     const int sidx = ch % NST;
@@ -727,8 +730,11 @@ __global__ void __launch_bounds__(32) k_rec_syn_w(const RecItem* __restrict__ it
       const TabEntry<T>* st = stg[sidx].v;
       const PQV* PQ = &sPQ[0][sidx][0];
       for (int q = 0; q < nq; ++q) {
-        bool fast, skip;
-        classify<T, SPIN, RPT>(S, nr_w, vm, fast, skip);
+        bool fast = fastw, skip = false;
+        if (!fastw) {
+          classify<T, SPIN, RPT>(S, nr_w, vm, fast, skip);
+          fastw = fast;
+        }
         if (fast) {
           if (nr_w >= RPT) syn_quad_d<SPIN, RPT, true, false, NI>(tb, S, A, st, 4 * q, PQ, pqs, RPT);
           else syn_quad_d<SPIN, RPT, true, false, NI>(tb, S, A, st, 4 * q, PQ, pqs, nr_w);
@@ -1448,6 +1454,7 @@ __global__ void __launch_bounds__(32, NS == 1 ? (MIR ? 16 : (RPT >= 8 ? 16 : 20)
 
   bool failed = false;
   bool blk_any = false;  // a quad of the current 8-l block had summing columns (warp-uniform)
+  bool fastw = false;    // every column sums (then for good): no more column tests
   for (int ch = 0; ch < nchunk; ++ch) {
     const int sidx = ch % NST;
     const bool ok = mbar_wait(&bar[sidx], (uint32_t)((ch / NST) & 1));
@@ -1464,8 +1471,11 @@ __global__ void __launch_bounds__(32, NS == 1 ? (MIR ? 16 : (RPT >= 8 ? 16 : 20)
     const int nq = (min(CH, nl - li0) + 3) >> 2;
     const TabEntry<float>* st = stg[sidx].v;
     for (int q = 0; q < nq; ++q) {
-      bool fast, skip;
-      classify<float, SPIN, RPT>(S, nr_w, vm, fast, skip);
+      bool fast = fastw, skip = false;
+      if (!fastw) {
+        classify<float, SPIN, RPT>(S, nr_w, vm, fast, skip);
+        fastw = fast;
+      }
       blk_any = blk_any || !skip;
       const int row0 = (q & 1) * 4;
       if (skip) {
