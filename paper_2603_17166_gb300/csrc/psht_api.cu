@@ -316,9 +316,8 @@ void layout(Plan& p, double theta_star) {
   p.nalm = (int64_t)(p.lmax + 1) * (p.lmax + 2) / 2;
   p.tstride = p.nalm + 64;  // one chunk of zero records after the last order
   // launch shapes of the recursion
-  // rings per lane of the one-warp synthesis: FP64 1, FP32 one packed pair (2 rings per lane measured
-  // faster than 4 at lmax 4096: the same issue rate, and items of 64 rings leave fewer idle slots)
-  p.syn_rpt = (p.prec == 64) ? 1 : 2;
+  // rings per lane of the one-warp synthesis: FP64 1, FP32 kSynRpt32 (one packed pair)
+  p.syn_rpt = (p.prec == 64) ? 1 : kSynRpt32;
   p.syn_threads = 32;  // one warp per synthesis item (k_rec_syn_w)
   // adjoint.  FP32: one warp per item of 32 adj_rpt rings (k_rec_adj_w), the items of an order
   // meeting in a float4-per-coefficient accumulator.  FP64: one CTA per m and chunk of

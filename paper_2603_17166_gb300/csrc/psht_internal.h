@@ -34,6 +34,11 @@ struct Error {
 // 4 steps of l, so values may pass 2^R_EXP by the growth of 4 steps (< 2^32) before rescaling.
 template <typename T>
 struct ScaleConst;
+// ring slots per lane of the FP32 synthesis recursion (packed pairs: a multiple of 2).  One pair
+// measured faster than two at lmax 4096, also with the plan-time start states (1.94 against
+// 2.04 ms): the same issue rate, and items of 64 rings leave fewer idle slots and shorter stretches
+// of partly dropped columns than items of 128.
+constexpr int kSynRpt32 = 2;
 template <>
 struct ScaleConst<double> {
   static constexpr int F = 500;      // exponent step of one rescale

@@ -1778,7 +1778,7 @@ void launch_syn_s(Plan& p, int nsets, const void* const* g, const void* const* c
   if constexpr (sizeof(T) == 8) {
     launch_syn_t<T, SPIN, 1>(p, nsets, g, c, F, msc, st);  // FP64: one ring per lane (syn_rpt 1)
   } else {
-    launch_syn_t<T, SPIN, 2>(p, nsets, g, c, F, msc, st);  // FP32 slots come in pairs (syn_rpt 2)
+    launch_syn_t<T, SPIN, kSynRpt32>(p, nsets, g, c, F, msc, st);  // FP32: packed slot pairs
   }
 }
 template <typename T, bool SPIN>
@@ -1822,12 +1822,13 @@ void build_rec_table(Plan& p, cudaStream_t st) {
 }
 
 void build_rec_starts(Plan& p, cudaStream_t st) {
-  PSHT_REQUIRE(p.syn_threads == 32 && p.syn_rpt == (p.prec == 64 ? 1 : 2), PSHT_ECUDA, "internal: synthesis shape");
+  PSHT_REQUIRE(p.syn_threads == 32 && p.syn_rpt == (p.prec == 64 ? 1 : kSynRpt32), PSHT_ECUDA,
+               "internal: synthesis shape");
   PSHT_REQUIRE(p.prec == 64 || (p.adj_rpt == 4 && p.adj_threads == 32), PSHT_ECUDA, "internal: FP32 adjoint shape");
   const auto run = [&](auto tag, auto spin) {
     using T = decltype(tag);
     constexpr bool S = decltype(spin)::value;
-    constexpr int SR = sizeof(T) == 8 ? 1 : 2;
+    constexpr int SR = sizeof(T) == 8 ? 1 : kSynRpt32;
     const auto* tab = (const TabEntry<T>*)p.d_rtab;
     if (p.nitems > 0)
       k_rec_start<T, S, SR, RecItem><<<p.nitems, 32, 0, st>>>(p.d_items, p.d_ring, p.d_mseed, tab, p.lmax, p.omx_tb,
