@@ -159,10 +159,10 @@ def hbm_peak():
 # kernel (profiles/k_rec_fp32_spin2_lmax4096.md, profiles/fp64_kernels_spin2_lmax4096.md; the
 # recursion's size does not depend on the point count); None where no capture of the current
 # kernel exists.
-KERNEL_TRAFFIC = {("fp32", "rec_adjoint"): 535.763712e6 + 229.814272e6,
-                  ("fp32", "rec_synthesis"): 472.998144e6 + 22.789120e6,
-                  ("fp64", "rec_adjoint"): 416.974592e6 + 221.827328e6,
-                  ("fp64", "rec_synthesis"): 614.166528e6 + 50.765568e6}
+KERNEL_TRAFFIC = {("fp32", "rec_adjoint"): 508.318976e6 + 219.949056e6,
+                  ("fp32", "rec_synthesis"): 393.273088e6 + 19.787264e6,
+                  ("fp64", "rec_adjoint"): 399.548672e6 + 209.762560e6,
+                  ("fp64", "rec_synthesis"): 548.968192e6 + 47.232512e6}
 
 # kernel names of each stage per form (the launch list in profiles/ has them all)
 STAGE_KERNELS = {
